@@ -1,0 +1,21 @@
+"""FP64 CPU oracle for the pSRM EM iteration.
+
+TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import, call,
+link or run anything in this package; only ``tests/``, the smoke check in
+``__graft_entry__`` and the CPU-baseline / reference arm of ``bench.py`` use
+it.  It shares no code with the CUDA path.
+"""
+from .psrm import (  # noqa: F401
+    center,
+    estep,
+    estep_dense,
+    loglik,
+    loglik_dense,
+    sigma_update,
+    polar_factor,
+    mstep,
+    fit,
+    transform,
+    ppca_fixed_point,
+    State,
+)
