@@ -1,0 +1,207 @@
+/*
+ * srm.h -- C ABI of libsrm, a GB300 (sm_103a) implementation of the EM
+ * iteration of the probabilistic Shared Response Model.
+ *
+ * Method: Anderson et al., "Enabling Factor Analysis on Thousand-Subject
+ * Neuroimaging Datasets" (arXiv 1608.04647), Sec. II and Algorithm 1 (D-SRM).
+ *
+ *   model (Sec. II-A, Eq. 1):  x_it = W_i s_t + mu_i + eps_it,
+ *       W_i (v_i x k) with W_i^T W_i = I,  s_t ~ N(0, Sigma_s),
+ *       eps_it ~ N(0, rho_i^2 I),  i = 1..N subjects,  t = 1..T samples.
+ *   E-step (eq:srm_inversion_opt, eq:srm_wt_psi_w, eq:srm_mean_distributed):
+ *       rho_0 = sum_i rho_i^-2,  Phi = (Sigma_s^-1 + rho_0 I)^-1,
+ *       E[S] = Phi * sum_i rho_i^-2 W_i^T X^_i         (k x T)
+ *   M-step (eq:srm_variance_update_optimized, eq:srm_mapping_update,
+ *           eq:srm_rho_update):
+ *       Sigma_s = Phi + E[S] E[S]^T / T,
+ *       A_i = X^_i E[S]^T,  W_i = A_i (A_i^T A_i)^-1/2,
+ *       rho_i^2 = (||X^_i||_F^2 - 2 tr(W_i^T A_i) + T tr Sigma_s) / (T v_i)
+ *   X^_i is subject i's data demeaned over time (Algorithm 1, initialisation).
+ *
+ * Conventions for every entry point:
+ *   - Matrices are row-major.  X_i is v_i x T (T contiguous), W_i is v_i x k
+ *     (k contiguous), E[S] is k x T (T contiguous), Sigma_s is k x k.
+ *   - "_dev" pointers are device (HBM) pointers on the context's device; all
+ *     other pointers are host pointers.  The caller owns every pointer it
+ *     passes; the library owns the context and everything it allocates.
+ *   - Compute calls are asynchronous on the context's stream.  Calls that
+ *     return host data synchronise that stream.  Numerical failures detected
+ *     on the device (non-finite values, a non-positive-definite matrix, an
+ *     eigen-solver that did not converge) are raised by the next
+ *     synchronising call as SRM_ERR_NUMERIC.
+ *   - No exception crosses the ABI.  On failure the call returns a non-zero
+ *     srm_status and srm_last_error() describes it; the context is left
+ *     usable unless the status is SRM_ERR_CUDA.
+ *   - One context must not be used from two host threads at once.
+ */
+#ifndef SRM_H
+#define SRM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SRM_API __attribute__((visibility("default")))
+#else
+#define SRM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SRM_OK = 0,
+    SRM_ERR_ARG = 1,      /* invalid argument (null pointer, bad size, bad flag) */
+    SRM_ERR_CUDA = 2,     /* a CUDA runtime/driver call failed */
+    SRM_ERR_NOMEM = 3,    /* device or host allocation failed */
+    SRM_ERR_NUMERIC = 4,  /* device-side numerical failure (see above) */
+    SRM_ERR_STATE = 5,    /* call out of order (e.g. srm_get_s before any E-step) */
+    SRM_ERR_UNSUPPORTED = 6 /* valid request this build does not support */
+} srm_status;
+
+typedef enum { SRM_F32 = 0, SRM_BF16 = 1 } srm_dtype;
+
+/* srm_config.flags */
+#define SRM_BATCHED    (1u << 0) /* grouped persistent tensor-core contractions over all
+                                    subjects (requires store_dtype == SRM_BF16); without it
+                                    the plain per-subject FP32 SIMT form runs (requires
+                                    store_dtype == SRM_F32) */
+#define SRM_GRAPH      (1u << 1) /* srm_fit replays one EM iteration as a CUDA graph */
+#define SRM_FINAL_LL   (1u << 3) /* srm_fit also evaluates the log-likelihood of the final
+                                    parameters (one extra E-step, E[S] not replaced) */
+#define SRM_HOST_INPUT (1u << 4) /* X pointers given to srm_init are host pointers; the
+                                    library streams them to the device subject by subject */
+#define SRM_PROFILE    (1u << 5) /* time every kernel with CUDA events on the context stream
+                                    (srm_get_kernel_times); disables SRM_GRAPH */
+
+typedef struct {
+    int32_t n_subjects;      /* N >= 1 */
+    const int64_t* voxels;   /* host array of N voxel counts v_i >= k (may differ) */
+    int32_t T;               /* samples per subject, T >= 2 */
+    int32_t k;               /* features, 1 <= k <= 128, k <= T */
+    srm_dtype in_dtype;      /* element type of the X_i given to srm_init */
+    srm_dtype store_dtype;   /* element type of the library's resident copy of X^_i */
+    uint32_t flags;          /* SRM_* flags above */
+    int32_t max_iter;        /* capacity of the log-likelihood trace (>= total iterations
+                                run over the context's life; 0 -> 1024) */
+} srm_config;
+
+typedef struct srm_ctx srm_ctx;  /* opaque; created by srm_init, freed by srm_destroy */
+
+/*
+ * srm_init -- create a context, copy and demean the data (Algorithm 1,
+ * initialisation: mu_i = (1/T) sum_t x_it, x^_it = x_it - mu_i), compute
+ * ||X^_i||_F^2, and set rho_i^2 = 1, Sigma_s = I_k, W_i = W0_i.
+ *
+ *   cfg       configuration (read during the call only).
+ *   X         N pointers; X[i] is v_i x T row-major, element type cfg->in_dtype,
+ *             device pointers unless SRM_HOST_INPUT.  Read during the call only:
+ *             the library keeps its own demeaned copy in cfg->store_dtype.
+ *   W0_dev    N device pointers; W0_dev[i] is v_i x k row-major FP32 with
+ *             orthonormal columns (Algorithm 1: "a random orthogonal matrix").
+ *             Read during the call only.
+ *   stream    cudaStream_t the context runs on, or NULL for a library-owned
+ *             non-blocking stream.  The device is the current CUDA device.
+ *   out       receives the context.
+ * Returns SRM_ERR_ARG for N < 1, k outside [1, 128], k > T, k > v_i, a null
+ * pointer, or an unsupported dtype/flag combination; SRM_ERR_NOMEM if the
+ * resident copy does not fit.  The call synchronises the stream.
+ */
+SRM_API srm_status srm_init(const srm_config* cfg, const void* const* X, const float* const* W0_dev,
+                    void* stream, srm_ctx** out);
+
+/*
+ * srm_estep -- one E-step at the current parameters (Algorithm 1, E-step):
+ * the reduction y = sum_i rho_i^-2 W_i^T X^_i, rho_0, Phi, E[S]
+ * (eq:srm_mean_distributed), the log-likelihood of the current parameters
+ * (appended to the trace) and the pending Sigma_s^new
+ * (eq:srm_variance_update_optimized).  Asynchronous.
+ */
+SRM_API srm_status srm_estep(srm_ctx* ctx);
+
+/*
+ * srm_mstep -- the M-step that follows an E-step (Algorithm 1, M-step):
+ * commit Sigma_s^new, form A_i = X^_i E[S]^T and its Gram matrix, set
+ * W_i = A_i (A_i^T A_i)^-1/2 (eq:srm_mapping_update) and rho_i^2
+ * (eq:srm_rho_update).  SRM_ERR_STATE if no E-step preceded it.  Asynchronous.
+ */
+SRM_API srm_status srm_mstep(srm_ctx* ctx);
+
+/*
+ * srm_fit -- n_iter EM iterations (E-step then M-step each).  If ll_host is
+ * not NULL it receives the n_iter log-likelihoods of the parameters each
+ * E-step used (n_iter + 1 values with SRM_FINAL_LL) and the call synchronises;
+ * otherwise the call is asynchronous.
+ */
+SRM_API srm_status srm_fit(srm_ctx* ctx, int32_t n_iter, double* ll_host);
+
+/*
+ * srm_transform -- map new data of one subject to the shared space
+ * (Sec. II-A: W_i^T x): S_out = W_i^T (X_new - mean_t X_new).
+ *   subject    0 <= subject < N
+ *   X_new_dev  v_i x T_new row-major, cfg->in_dtype, device pointer
+ *   T_new      >= 1 columns
+ *   S_out_dev  k x T_new row-major FP32, device pointer (written)
+ * Asynchronous.
+ */
+SRM_API srm_status srm_transform(srm_ctx* ctx, int32_t subject, const void* X_new_dev, int32_t T_new,
+                         float* S_out_dev);
+
+/* srm_get_w -- W_i = A_i (A_i^T A_i)^-1/2 (eq:srm_mapping_update) materialised as
+ * v_i x k row-major FP32 into W_dev (device, caller-owned).  Asynchronous. */
+SRM_API srm_status srm_get_w(srm_ctx* ctx, int32_t subject, float* W_dev);
+
+/* srm_get_s -- E[S] of the last E-step, k x T row-major FP32, into S_dev (device).
+ * SRM_ERR_STATE before the first E-step.  Asynchronous. */
+SRM_API srm_status srm_get_s(srm_ctx* ctx, float* S_dev);
+
+/* srm_get_params -- current rho_i^2 (N doubles) and Sigma_s (k x k doubles) to the
+ * host; either pointer may be NULL.  Synchronises. */
+SRM_API srm_status srm_get_params(srm_ctx* ctx, double* rho2_host, double* sigma_host);
+
+/* srm_get_ll -- the whole log-likelihood trace so far: writes min(*n, count) values
+ * to ll_host and sets *n = count.  Synchronises. */
+SRM_API srm_status srm_get_ll(srm_ctx* ctx, double* ll_host, int32_t* n);
+
+/* srm_synchronize -- wait for the context's stream and report device-side status. */
+SRM_API srm_status srm_synchronize(srm_ctx* ctx);
+
+/*
+ * srm_get_state / srm_set_state -- checkpoint of the EM state (rho^2, Sigma_s,
+ * the per-subject mapping factors, the log-likelihood trace and the iteration
+ * count) to a host buffer.  With buf == NULL, srm_get_state only sets *bytes to
+ * the size needed.  srm_set_state requires a context created with the same
+ * configuration; SRM_ERR_ARG on a size or header mismatch.  Both synchronise.
+ */
+SRM_API srm_status srm_get_state(srm_ctx* ctx, void* buf, size_t* bytes);
+SRM_API srm_status srm_set_state(srm_ctx* ctx, const void* buf, size_t bytes);
+
+/*
+ * srm_get_kernel_times -- with SRM_PROFILE: for each kernel kind, its name,
+ * launch count and total CUDA-event time (ms) since the last reset.  Writes up
+ * to *n entries; sets *n to the number of kinds.  names[j] points to static
+ * strings.  reset != 0 clears the counters after reading.  Synchronises.
+ */
+SRM_API srm_status srm_get_kernel_times(srm_ctx* ctx, const char** names, int64_t* launches, double* ms,
+                                int32_t* n, int32_t reset);
+
+/*
+ * srm_layout -- sizes the library chose for this context (for reporting):
+ * out[0] = padded row stride of the resident X^ (elements), out[1] = padded k
+ * of the tensor-core operands, out[2] = total resident rows (all subjects, padded),
+ * out[3] = bytes of the resident X^, out[4] = bytes of the per-subject
+ * mapping factors A_i.  n = number of entries the caller's array holds.
+ */
+SRM_API srm_status srm_layout(srm_ctx* ctx, int64_t* out, int32_t n);
+
+/* Thread-local description of the last failure in this thread ("" if none). */
+SRM_API const char* srm_last_error(void);
+
+/* Free the context and everything it owns.  NULL is a no-op.  Synchronises. */
+SRM_API void srm_destroy(srm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SRM_H */

@@ -1,0 +1,330 @@
+"""GB300 (sm_103a) probabilistic Shared Response Model EM (arXiv 1608.04647).
+
+Thin ctypes binding over ``libsrm.so``, the C-ABI library declared in
+``include/srm.h``.  Every step of the EM iteration runs in the library's CUDA
+kernels; this module only marshals arguments.  PyTorch is used for device
+memory (the caller's tensors) and streams.  There is no CPU fallback: if the
+library is missing or its CUDA calls fail, the calls raise.
+
+Low-level functions carry the C names (``srm_init``, ``srm_estep``,
+``srm_mstep``, ``srm_fit``, ``srm_transform``, ...); :class:`SRM` wraps a
+context for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "SRM", "SrmError", "load_library", "srm_config", "SRM_BATCHED", "SRM_GRAPH", "SRM_FINAL_LL",
+    "SRM_HOST_INPUT", "SRM_PROFILE", "SRM_F32", "SRM_BF16",
+    "srm_init", "srm_estep", "srm_mstep", "srm_fit", "srm_transform", "srm_get_w", "srm_get_s",
+    "srm_get_params", "srm_get_ll", "srm_synchronize", "srm_get_state", "srm_set_state",
+    "srm_get_kernel_times", "srm_layout", "srm_last_error", "srm_destroy",
+]
+
+SRM_OK, SRM_ERR_ARG, SRM_ERR_CUDA, SRM_ERR_NOMEM, SRM_ERR_NUMERIC, SRM_ERR_STATE, SRM_ERR_UNSUPPORTED = range(7)
+STATUS_NAMES = {0: "SRM_OK", 1: "SRM_ERR_ARG", 2: "SRM_ERR_CUDA", 3: "SRM_ERR_NOMEM", 4: "SRM_ERR_NUMERIC",
+                5: "SRM_ERR_STATE", 6: "SRM_ERR_UNSUPPORTED"}
+SRM_F32, SRM_BF16 = 0, 1
+SRM_BATCHED = 1 << 0
+SRM_GRAPH = 1 << 1
+SRM_FINAL_LL = 1 << 3
+SRM_HOST_INPUT = 1 << 4
+SRM_PROFILE = 1 << 5
+
+
+class SrmError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class srm_config(ctypes.Structure):
+    _fields_ = [
+        ("n_subjects", ctypes.c_int32),
+        ("voxels", ctypes.POINTER(ctypes.c_int64)),
+        ("T", ctypes.c_int32),
+        ("k", ctypes.c_int32),
+        ("in_dtype", ctypes.c_int),
+        ("store_dtype", ctypes.c_int),
+        ("flags", ctypes.c_uint32),
+        ("max_iter", ctypes.c_int32),
+    ]
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def load_library(path: Optional[str] = None):
+    """Load libsrm.so (built in-tree by ``_build.build()``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsrm.so not found at {path}; build it with paper_1608_04647_gb300._build.build()")
+    lib = ctypes.CDLL(path)
+    st = ctypes.c_int
+    sig = {
+        "srm_init": (st, [ctypes.POINTER(srm_config), ctypes.POINTER(_P), ctypes.POINTER(_P), _P,
+                          ctypes.POINTER(_P)]),
+        "srm_estep": (st, [_P]),
+        "srm_mstep": (st, [_P]),
+        "srm_fit": (st, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+        "srm_transform": (st, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
+        "srm_get_w": (st, [_P, ctypes.c_int32, _P]),
+        "srm_get_s": (st, [_P, _P]),
+        "srm_get_params": (st, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+        "srm_get_ll": (st, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
+        "srm_synchronize": (st, [_P]),
+        "srm_get_state": (st, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
+        "srm_set_state": (st, [_P, _P, ctypes.c_size_t]),
+        "srm_get_kernel_times": (st, [_P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.c_int32]),
+        "srm_layout": (st, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
+        "srm_last_error": (ctypes.c_char_p, []),
+        "srm_destroy": (None, [_P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def srm_last_error() -> str:
+    return load_library().srm_last_error().decode()
+
+
+def _check(status: int, where: str):
+    if status != SRM_OK:
+        raise SrmError(status, where, srm_last_error())
+
+
+# ---------------------------------------------------------------- C names
+def srm_init(cfg: srm_config, X_ptrs: Sequence[int], W0_ptrs: Sequence[int], stream: int = 0) -> int:
+    lib = load_library()
+    n = len(X_ptrs)
+    xa = (_P * n)(*X_ptrs)
+    wa = (_P * n)(*W0_ptrs)
+    out = _P()
+    _check(lib.srm_init(ctypes.byref(cfg), xa, wa, _P(stream or None), ctypes.byref(out)), "srm_init")
+    return out.value
+
+
+def srm_estep(ctx: int):
+    _check(load_library().srm_estep(_P(ctx)), "srm_estep")
+
+
+def srm_mstep(ctx: int):
+    _check(load_library().srm_mstep(_P(ctx)), "srm_mstep")
+
+
+def srm_fit(ctx: int, n_iter: int, n_out: int) -> np.ndarray:
+    ll = np.zeros(max(n_out, 1), dtype=np.float64)
+    _check(load_library().srm_fit(_P(ctx), n_iter, ll.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "srm_fit")
+    return ll[:n_out]
+
+
+def srm_fit_async(ctx: int, n_iter: int):
+    _check(load_library().srm_fit(_P(ctx), n_iter, None), "srm_fit")
+
+
+def srm_transform(ctx: int, subject: int, X_new_ptr: int, T_new: int, S_out_ptr: int):
+    _check(load_library().srm_transform(_P(ctx), subject, _P(X_new_ptr), T_new, _P(S_out_ptr)), "srm_transform")
+
+
+def srm_get_w(ctx: int, subject: int, W_ptr: int):
+    _check(load_library().srm_get_w(_P(ctx), subject, _P(W_ptr)), "srm_get_w")
+
+
+def srm_get_s(ctx: int, S_ptr: int):
+    _check(load_library().srm_get_s(_P(ctx), _P(S_ptr)), "srm_get_s")
+
+
+def srm_get_params(ctx: int, N: int, k: int):
+    rho2 = np.zeros(N)
+    sig = np.zeros((k, k))
+    _check(load_library().srm_get_params(_P(ctx), rho2.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "srm_get_params")
+    return rho2, sig
+
+
+def srm_get_ll(ctx: int) -> np.ndarray:
+    lib = load_library()
+    n = ctypes.c_int32(0)
+    _check(lib.srm_get_ll(_P(ctx), None, ctypes.byref(n)), "srm_get_ll")
+    out = np.zeros(max(n.value, 1))
+    m = ctypes.c_int32(n.value)
+    _check(lib.srm_get_ll(_P(ctx), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(m)),
+           "srm_get_ll")
+    return out[: n.value]
+
+
+def srm_synchronize(ctx: int):
+    _check(load_library().srm_synchronize(_P(ctx)), "srm_synchronize")
+
+
+def srm_get_state(ctx: int) -> bytes:
+    lib = load_library()
+    nb = ctypes.c_size_t(0)
+    _check(lib.srm_get_state(_P(ctx), None, ctypes.byref(nb)), "srm_get_state")
+    buf = ctypes.create_string_buffer(nb.value)
+    _check(lib.srm_get_state(_P(ctx), ctypes.cast(buf, _P), ctypes.byref(nb)), "srm_get_state")
+    return buf.raw[: nb.value]
+
+
+def srm_set_state(ctx: int, state: bytes):
+    buf = ctypes.create_string_buffer(state, len(state))
+    _check(load_library().srm_set_state(_P(ctx), ctypes.cast(buf, _P), len(state)), "srm_set_state")
+
+
+def srm_get_kernel_times(ctx: int, reset: bool = False) -> dict:
+    lib = load_library()
+    n = ctypes.c_int32(64)
+    names = (ctypes.c_char_p * 64)()
+    launches = (ctypes.c_int64 * 64)()
+    ms = (ctypes.c_double * 64)()
+    _check(lib.srm_get_kernel_times(_P(ctx), names, launches, ms, ctypes.byref(n), int(reset)),
+           "srm_get_kernel_times")
+    return {names[j].decode(): (int(launches[j]), float(ms[j])) for j in range(n.value)}
+
+
+def srm_layout(ctx: int) -> dict:
+    out = (ctypes.c_int64 * 5)()
+    _check(load_library().srm_layout(_P(ctx), out, 5), "srm_layout")
+    keys = ["ldT", "kld", "rows_padded", "xhat_bytes", "a_bytes"]
+    return dict(zip(keys, [int(x) for x in out]))
+
+
+def srm_destroy(ctx: int):
+    load_library().srm_destroy(_P(ctx))
+
+
+# ---------------------------------------------------------------- wrapper
+class SRM:
+    """One pSRM context on the current CUDA device.
+
+    X:   list of N subject matrices (v_i x T, row-major): torch CUDA tensors
+         (float32 or bfloat16), or with ``host_input=True`` contiguous CPU
+         tensors / NumPy arrays (pinned memory recommended).
+    W0:  list of N torch CUDA float32 tensors (v_i x k) with orthonormal columns.
+    store: "bf16" -> batched tensor-core form; "f32" -> plain per-subject form.
+    """
+
+    def __init__(self, X: Sequence, W0: Sequence, k: int, store: str = "bf16", graph: bool = False,
+                 final_ll: bool = False, profile: bool = False, host_input: bool = False,
+                 max_iter: int = 1024, stream=None):
+        import torch
+
+        self.N = len(X)
+        self.k = int(k)
+        self.T = int(X[0].shape[1])
+        self.voxels = [int(x.shape[0]) for x in X]
+        self._vox = (ctypes.c_int64 * self.N)(*self.voxels)
+        xdt = X[0].dtype
+        in_dtype = SRM_BF16 if xdt in (torch.bfloat16,) else SRM_F32
+        if host_input and isinstance(X[0], np.ndarray):
+            in_dtype = SRM_F32
+        flags = 0
+        if store == "bf16":
+            flags |= SRM_BATCHED
+        if graph:
+            flags |= SRM_GRAPH
+        if final_ll:
+            flags |= SRM_FINAL_LL
+        if profile:
+            flags |= SRM_PROFILE
+        if host_input:
+            flags |= SRM_HOST_INPUT
+        self.final_ll = final_ll
+        self.cfg = srm_config(self.N, ctypes.cast(self._vox, ctypes.POINTER(ctypes.c_int64)), self.T, self.k,
+                              in_dtype, SRM_BF16 if store == "bf16" else SRM_F32, flags, max_iter)
+        if host_input:
+            xp = [x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr() for x in X]
+        else:
+            xp = [x.data_ptr() for x in X]
+        wp = [w.data_ptr() for w in W0]
+        self._stream = stream
+        s = stream.cuda_stream if stream is not None else 0
+        self.ctx = srm_init(self.cfg, xp, wp, s)
+
+    def estep(self):
+        srm_estep(self.ctx)
+
+    def mstep(self):
+        srm_mstep(self.ctx)
+
+    def fit(self, n_iter: int) -> np.ndarray:
+        return srm_fit(self.ctx, n_iter, n_iter + (1 if self.final_ll else 0))
+
+    def fit_async(self, n_iter: int):
+        srm_fit_async(self.ctx, n_iter)
+
+    def synchronize(self):
+        srm_synchronize(self.ctx)
+
+    def get_w(self, i: int):
+        import torch
+        W = torch.empty((self.voxels[i], self.k), dtype=torch.float32, device="cuda")
+        srm_get_w(self.ctx, i, W.data_ptr())
+        self.synchronize()
+        return W
+
+    def get_s(self):
+        import torch
+        S = torch.empty((self.k, self.T), dtype=torch.float32, device="cuda")
+        srm_get_s(self.ctx, S.data_ptr())
+        self.synchronize()
+        return S
+
+    def params(self):
+        return srm_get_params(self.ctx, self.N, self.k)
+
+    def ll(self) -> np.ndarray:
+        return srm_get_ll(self.ctx)
+
+    def transform(self, i: int, X_new):
+        import torch
+        S = torch.empty((self.k, int(X_new.shape[1])), dtype=torch.float32, device="cuda")
+        srm_transform(self.ctx, i, X_new.data_ptr(), int(X_new.shape[1]), S.data_ptr())
+        self.synchronize()
+        return S
+
+    def state(self) -> bytes:
+        return srm_get_state(self.ctx)
+
+    def set_state(self, b: bytes):
+        srm_set_state(self.ctx, b)
+
+    def kernel_times(self, reset: bool = False) -> dict:
+        return srm_get_kernel_times(self.ctx, reset)
+
+    def layout(self) -> dict:
+        return srm_layout(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            srm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,726 @@
+// C ABI of libsrm: context life cycle, memory layout, and the order of the
+// launches of one EM iteration (Algorithm 1 of Anderson et al., arXiv
+// 1608.04647: E-step reduction -> E[S] on the "master" -> Sigma_s -> W_i and
+// rho_i^2 per subject).  On one GPU the paper's MPI Reduce/Bcast become
+// device-resident reductions; nothing leaves HBM inside an iteration.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "srm_internal.cuh"
+
+namespace srm {
+
+namespace {
+thread_local std::string g_err;
+}
+
+const char* const kKernelNames[KK_COUNT] = {
+    "center", "estep_simt", "estep_tc", "p_reduce", "y_sum", "chol", "phi", "es", "sigma",
+    "mstep_simt", "mstep_tc", "eig", "refine", "rho"};
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+srm_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return SRM_ERR_CUDA;
+}
+
+void prof_begin(Ctx* c, int kind, int* ev0) {
+  (void)kind;
+  if ((int)c->ev_pool.size() <= c->ev_next + 1) {
+    for (int q = 0; q < 256; ++q) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      c->ev_pool.push_back(e);
+    }
+  }
+  *ev0 = c->ev_next++;
+  cudaEventRecord(c->ev_pool[*ev0], c->stream);
+}
+
+void prof_end(Ctx* c, int kind, int ev0) {
+  const int ev1 = c->ev_next++;
+  cudaEventRecord(c->ev_pool[ev1], c->stream);
+  c->pending.push_back({kind, ev0, ev1});
+}
+
+namespace {
+
+template <typename T>
+srm_status dalloc(T** p, size_t count, const char* what) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string("cudaMalloc failed for ") + what + " (" + std::to_string(count * sizeof(T)) + " bytes): " +
+              cudaGetErrorString(e));
+    return SRM_ERR_NOMEM;
+  }
+  return SRM_OK;
+}
+
+__global__ void cast_kernel(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) b[e] = (float)a[e];
+}
+
+#define CK(expr)                                               \
+  do {                                                         \
+    cudaError_t _e = (expr);                                   \
+    if (_e != cudaSuccess) return cuda_fail(_e, #expr);        \
+  } while (0)
+
+#define TRY(expr)                         \
+  do {                                    \
+    srm_status _s = (expr);               \
+    if (_s != SRM_OK) return _s;          \
+  } while (0)
+
+#define LAUNCH(c, kind, expr)                              \
+  do {                                                     \
+    int _ev0 = -1;                                         \
+    if ((c)->profile) prof_begin((c), (kind), &_ev0);      \
+    cudaError_t _e = (expr);                               \
+    if (_e != cudaSuccess) return cuda_fail(_e, #expr);    \
+    if ((c)->profile) prof_end((c), (kind), _ev0);         \
+  } while (0)
+
+void free_all(Ctx* c) {
+  if (c->tc) tc_destroy(c);
+  void* ptrs[] = {c->Xh, c->A, c->sqnorm, c->rowsq, c->d_off, c->d_v, c->rho2, c->Sigma, c->SigmaNext, c->L,
+                  c->Phi, c->scal, c->M64, c->M32, c->Uwarm, c->G64, c->U64, c->H64, c->Xr64, c->eigv, c->Y,
+                  c->ES64, c->ESt, c->ESb, c->esPart, c->ll, c->iter, c->status, c->Ppart, c->chunk_src,
+                  c->chunk_src_off, c->Zbuf, c->Gpart, c->gslot_off, c->tr_buf, c->tr_part};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+// Plain path: per-subject launch geometry and the partial-slot tables.
+srm_status setup_plain(Ctx* c) {
+  const int N = c->N;
+  c->p_nsplit.resize(N);
+  c->p_slot_base.resize(N);
+  c->a_nblk.resize(N);
+  c->g_slot_base.resize(N);
+  int64_t pbase = 0;
+  int gbase = 0;
+  const int target = 2 * c->num_sms;
+  std::vector<int> gslot_off(N + 1);
+  std::vector<ChunkSrc> src;
+  std::vector<int> src_off(N * c->nchunk + 1);
+  for (int i = 0; i < N; ++i) {
+    int ns = std::max(1, target / c->nchunk);
+    ns = (int)std::min<int64_t>(ns, std::max<int64_t>(1, c->vpad[i] / 64));
+    c->p_nsplit[i] = ns;
+    c->p_slot_base[i] = pbase;
+    pbase += (int64_t)ns * c->nchunk * TCH * c->kld;
+    const int64_t ntile = c->vpad[i] / 64;
+    c->a_nblk[i] = (int)std::min<int64_t>(ntile, target);
+    c->g_slot_base[i] = gbase;
+    gslot_off[i] = gbase;
+    gbase += c->a_nblk[i];
+  }
+  gslot_off[N] = gbase;
+  for (int i = 0; i < N; ++i)
+    for (int ch = 0; ch < c->nchunk; ++ch) {
+      src_off[i * c->nchunk + ch] = (int)src.size();
+      for (int s = 0; s < c->p_nsplit[i]; ++s)
+        src.push_back({c->p_slot_base[i] + ((int64_t)s * c->nchunk + ch) * TCH * c->kld});
+    }
+  src_off[N * c->nchunk] = (int)src.size();
+  c->Ppart_elems = pbase;
+  c->n_gslots = gbase;
+  c->Gpart_elems = (int64_t)gbase * c->kld * c->kld;
+  TRY(dalloc(&c->Ppart, c->Ppart_elems, "E-pass partials"));
+  TRY(dalloc(&c->Gpart, c->Gpart_elems, "Gram partials"));
+  TRY(dalloc(&c->chunk_src, src.size(), "chunk table"));
+  TRY(dalloc(&c->chunk_src_off, src_off.size(), "chunk table offsets"));
+  TRY(dalloc(&c->gslot_off, gslot_off.size(), "Gram slot table"));
+  CK(cudaMemcpy(c->chunk_src, src.data(), src.size() * sizeof(ChunkSrc), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->chunk_src_off, src_off.data(), src_off.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->gslot_off, gslot_off.data(), gslot_off.size() * sizeof(int), cudaMemcpyHostToDevice));
+  return SRM_OK;
+}
+
+srm_status check_status(Ctx* c) {
+  int st = 0;
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) {
+    std::string m = "device reported a numerical failure:";
+    if (st & ST_NONFINITE) m += " non-finite value;";
+    if (st & ST_NOT_PD) m += " I + rho0 Sigma_s not positive definite;";
+    if (st & ST_EIG_NOCONV) m += " Jacobi eigen-solver did not converge;";
+    if (st & ST_RANK) m += " A_i^T A_i numerically singular (polar factor undefined);";
+    if (st & ST_TIMEOUT) m += " a bounded wait in a tensor-core kernel gave up;";
+    if (st & ST_BOUNDS) m += " a kernel index check refused an access;";
+    set_error(m);
+    CK(cudaMemset(c->status, 0, sizeof(int)));
+    return SRM_ERR_NUMERIC;
+  }
+  return SRM_OK;
+}
+
+srm_status do_estep(Ctx* c) {
+  if (c->batched) {
+    LAUNCH(c, KK_P_TC, launch_p_tc(c));
+  } else {
+    for (int i = 0; i < c->N; ++i) LAUNCH(c, KK_P_SIMT, launch_p_simt(c, i));
+  }
+  LAUNCH(c, KK_P_REDUCE, launch_p_reduce(c));
+  LAUNCH(c, KK_Y_SUM, launch_y_sum(c));
+  LAUNCH(c, KK_CHOL, launch_chol(c));
+  LAUNCH(c, KK_PHI, launch_phi(c));
+  LAUNCH(c, KK_ES, launch_es(c));
+  LAUNCH(c, KK_SIGMA, launch_sigma(c));
+  return SRM_OK;
+}
+
+srm_status do_mstep(Ctx* c) {
+  if (c->batched) {
+    LAUNCH(c, KK_A_TC, launch_a_tc(c));
+  } else {
+    for (int i = 0; i < c->N; ++i) LAUNCH(c, KK_A_SIMT, launch_a_simt(c, i));
+  }
+  LAUNCH(c, KK_EIG, launch_eig(c));
+  LAUNCH(c, KK_REFINE, launch_refine(c));
+  LAUNCH(c, KK_RHO, launch_rho(c));
+  return SRM_OK;
+}
+
+srm_status valid_ctx(srm_ctx* ctx) {
+  if (!ctx) {
+    set_error("null context");
+    return SRM_ERR_ARG;
+  }
+  return SRM_OK;
+}
+
+struct StateHeader {
+  uint64_t magic;
+  int32_t version, N, T, k, kld, batched, n_ll;
+  int64_t iters_done, Vpad_tot;
+};
+constexpr uint64_t kStateMagic = 0x314d5253'50534743ull;
+
+}  // namespace
+}  // namespace srm
+
+using namespace srm;
+
+struct srm_ctx : public srm::Ctx {};
+
+extern "C" {
+
+const char* srm_last_error(void) { return g_err.c_str(); }
+
+srm_status srm_init(const srm_config* cfg, const void* const* X, const float* const* W0_dev, void* stream,
+                    srm_ctx** out) {
+  g_err.clear();
+  if (!cfg || !X || !W0_dev || !out || !cfg->voxels) {
+    set_error("srm_init: null argument");
+    return SRM_ERR_ARG;
+  }
+  *out = nullptr;
+  if (cfg->n_subjects < 1 || cfg->k < 1 || cfg->k > KMAX || cfg->T < 2 || cfg->k > cfg->T) {
+    set_error("srm_init: need N >= 1, 1 <= k <= 128, T >= 2, k <= T");
+    return SRM_ERR_ARG;
+  }
+  if ((cfg->in_dtype != SRM_F32 && cfg->in_dtype != SRM_BF16) ||
+      (cfg->store_dtype != SRM_F32 && cfg->store_dtype != SRM_BF16)) {
+    set_error("srm_init: unknown dtype");
+    return SRM_ERR_ARG;
+  }
+  const bool batched = (cfg->flags & SRM_BATCHED) != 0;
+  if (batched != (cfg->store_dtype == SRM_BF16)) {
+    set_error("srm_init: SRM_BATCHED requires store_dtype SRM_BF16 and the plain form requires SRM_F32");
+    return SRM_ERR_ARG;
+  }
+  const uint32_t known = SRM_BATCHED | SRM_GRAPH | SRM_FINAL_LL | SRM_HOST_INPUT | SRM_PROFILE;
+  if (cfg->flags & ~known) {
+    set_error("srm_init: unknown flag bits");
+    return SRM_ERR_ARG;
+  }
+  for (int i = 0; i < cfg->n_subjects; ++i) {
+    if (cfg->voxels[i] < cfg->k || cfg->voxels[i] > (int64_t)1 << 31) {
+      set_error("srm_init: voxel count of subject " + std::to_string(i) + " must be in [k, 2^31]");
+      return SRM_ERR_ARG;
+    }
+    if (!X[i] || !W0_dev[i]) {
+      set_error("srm_init: null data or W0 pointer for subject " + std::to_string(i));
+      return SRM_ERR_ARG;
+    }
+  }
+  srm_ctx* c = new srm_ctx();
+  srm_status st = SRM_OK;
+  auto fail = [&](srm_status s) {
+    free_all(c);
+    delete c;
+    return s;
+  };
+  c->N = cfg->n_subjects;
+  c->T = cfg->T;
+  c->k = cfg->k;
+  c->in_dtype = cfg->in_dtype;
+  c->store = cfg->store_dtype;
+  c->flags = cfg->flags;
+  c->batched = batched;
+  c->profile = (cfg->flags & SRM_PROFILE) != 0;
+  c->max_iter = cfg->max_iter > 0 ? cfg->max_iter : 1024;
+  cudaError_t ce = cudaGetDevice(&c->device);
+  if (ce != cudaSuccess) return fail(cuda_fail(ce, "cudaGetDevice"));
+  cudaDeviceProp prop;
+  ce = cudaGetDeviceProperties(&prop, c->device);
+  if (ce != cudaSuccess) return fail(cuda_fail(ce, "cudaGetDeviceProperties"));
+  c->num_sms = prop.multiProcessorCount;
+  if (stream) {
+    c->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    ce = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) return fail(cuda_fail(ce, "cudaStreamCreate"));
+    c->own_stream = true;
+  }
+  c->kld = batched ? (c->k <= 64 ? 64 : 128) : ((c->k + 15) / 16) * 16;
+  c->ldT = ((c->T + 7) / 8) * 8;
+  c->nchunk = (c->T + TCH - 1) / TCH;
+  c->nes_blk = (c->T + 31) / 32;
+  c->v.resize(c->N);
+  c->vpad.resize(c->N);
+  c->off.resize(c->N + 1);
+  int64_t acc = 0;
+  for (int i = 0; i < c->N; ++i) {
+    c->v[i] = cfg->voxels[i];
+    c->vpad[i] = ((c->v[i] + ROW_PAD - 1) / ROW_PAD) * ROW_PAD;
+    c->off[i] = acc;
+    acc += c->vpad[i];
+    c->Vtot += c->v[i];
+  }
+  c->off[c->N] = acc;
+  c->Vpad_tot = acc;
+
+  const int N = c->N, k = c->k, T = c->T;
+  const size_t xel = c->store == SRM_BF16 ? 2 : 4;
+  const size_t ael = batched ? 2 : 4;
+  const int64_t ldTt = ((T + 63) / 64) * 64;  // rows of E[S]^T, padded for whole 32-wide chunks
+  if ((st = dalloc(reinterpret_cast<char**>(&c->Xh), (size_t)c->Vpad_tot * c->ldT * xel, "resident X^")) != SRM_OK)
+    return fail(st);
+  if ((st = dalloc(reinterpret_cast<char**>(&c->A), (size_t)c->Vpad_tot * c->kld * ael, "A_i")) != SRM_OK)
+    return fail(st);
+#define AL(ptr, n, what) \
+  if ((st = dalloc(&c->ptr, (size_t)(n), what)) != SRM_OK) return fail(st);
+  AL(sqnorm, N, "norms");
+  AL(rowsq, c->Vpad_tot, "row norms");
+  AL(d_off, N + 1, "offsets");
+  AL(d_v, N, "voxel counts");
+  AL(rho2, N, "rho2");
+  AL(Sigma, k * k, "Sigma");
+  AL(SigmaNext, k * k, "Sigma next");
+  AL(L, k * k, "L");
+  AL(Phi, k * k, "Phi");
+  AL(scal, 16, "scalars");
+  AL(M64, (int64_t)N * k * k, "M64");
+  AL(M32, (int64_t)N * c->kld * c->kld, "M32");
+  AL(Uwarm, (int64_t)N * k * k, "Uwarm");
+  AL(G64, (int64_t)N * k * k, "G64");
+  AL(U64, (int64_t)N * k * k, "U64");
+  AL(H64, (int64_t)N * k * k, "H64");
+  AL(Xr64, (int64_t)N * k * k, "Xr64");
+  AL(eigv, (int64_t)N * k, "eigenvalues");
+  AL(Y, (int64_t)k * T, "y");
+  AL(ES64, (int64_t)k * T, "E[S]");
+  AL(ll, c->max_iter, "ll trace");
+  AL(iter, 1, "iteration counter");
+  AL(status, 1, "status");
+  AL(esPart, (int64_t)c->nes_blk * (k * k + 1), "E[S] partials");
+  AL(Zbuf, (int64_t)N * k * T, "per-subject reductions");
+  if (batched) {
+    AL(ESb, (int64_t)c->kld * c->ldT, "E[S] bf16");
+    ce = cudaMemset(c->ESb, 0, (size_t)c->kld * c->ldT * 2);
+  } else {
+    AL(ESt, (int64_t)ldTt * c->kld, "E[S]^T fp32");
+    ce = cudaMemset(c->ESt, 0, (size_t)ldTt * c->kld * 4);
+  }
+#undef AL
+  if (ce != cudaSuccess) return fail(cuda_fail(ce, "cudaMemset"));
+  ce = cudaMemcpy(c->d_off, c->off.data(), (N + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMemcpy(c->d_v, c->v.data(), N * sizeof(int64_t), cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) return fail(cuda_fail(ce, "cudaMemcpy"));
+
+  prepare_small_kernels(prop.sharedMemPerBlockOptin);
+  prepare_simt_kernels(prop.sharedMemPerBlockOptin);
+  if (batched) {
+    if ((st = tc_setup(c)) != SRM_OK) return fail(st);
+  } else {
+    if ((st = setup_plain(c)) != SRM_OK) return fail(st);
+  }
+  ce = cudaMemsetAsync(c->A, 0, (size_t)c->Vpad_tot * c->kld * ael, c->stream);
+  if (ce != cudaSuccess) return fail(cuda_fail(ce, "cudaMemsetAsync"));
+
+  // centre the data (host input is streamed through a staging buffer)
+  const size_t iel = cfg->in_dtype == SRM_BF16 ? 2 : 4;
+  void* stage = nullptr;
+  if (cfg->flags & SRM_HOST_INPUT) {
+    int64_t vmax = 0;
+    for (int i = 0; i < N; ++i) vmax = std::max(vmax, c->v[i]);
+    ce = cudaMalloc(&stage, (size_t)vmax * T * iel);
+    if (ce != cudaSuccess) {
+      cudaGetLastError();
+      set_error("srm_init: cannot allocate the host-input staging buffer");
+      return fail(SRM_ERR_NOMEM);
+    }
+  }
+  for (int i = 0; i < N; ++i) {
+    const void* src = X[i];
+    if (stage) {
+      ce = cudaMemcpyAsync(stage, X[i], (size_t)c->v[i] * T * iel, cudaMemcpyHostToDevice, c->stream);
+      if (ce != cudaSuccess) break;
+      src = stage;
+    }
+    int ev0 = -1;
+    if (c->profile) prof_begin(c, KK_CENTER, &ev0);
+    ce = launch_center(c, i, src, cfg->in_dtype, T);
+    if (ce != cudaSuccess) break;
+    if (c->profile) prof_end(c, KK_CENTER, ev0);
+    ce = launch_load_w0(c, i, W0_dev[i]);
+    if (ce != cudaSuccess) break;
+  }
+  if (ce == cudaSuccess) ce = launch_sqnorm_reduce(c);
+  if (ce == cudaSuccess) ce = launch_init_params(c);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+  if (stage) cudaFree(stage);
+  if (ce != cudaSuccess) return fail(cuda_fail(ce, "srm_init: centring / initialisation"));
+  cudaFree(c->rowsq);
+  c->rowsq = nullptr;
+  if ((st = check_status(c)) != SRM_OK) return fail(st);
+  *out = c;
+  return SRM_OK;
+}
+
+srm_status srm_estep(srm_ctx* c) {
+  TRY(valid_ctx(c));
+  if (c->n_ll >= c->max_iter) {
+    set_error("srm_estep: log-likelihood trace is full (raise max_iter)");
+    return SRM_ERR_STATE;
+  }
+  TRY(do_estep(c));
+  c->n_ll++;
+  c->have_estep = true;
+  c->have_es = true;
+  return SRM_OK;
+}
+
+srm_status srm_mstep(srm_ctx* c) {
+  TRY(valid_ctx(c));
+  if (!c->have_estep) {
+    set_error("srm_mstep: no E-step precedes this M-step");
+    return SRM_ERR_STATE;
+  }
+  TRY(do_mstep(c));
+  c->have_estep = false;
+  c->iters_done++;
+  return SRM_OK;
+}
+
+srm_status srm_fit(srm_ctx* c, int32_t n_iter, double* ll_host) {
+  TRY(valid_ctx(c));
+  if (n_iter < 0) {
+    set_error("srm_fit: n_iter < 0");
+    return SRM_ERR_ARG;
+  }
+  const bool final_ll = (c->flags & SRM_FINAL_LL) != 0;
+  const int need = n_iter + (final_ll ? 1 : 0);
+  if (c->n_ll + need > c->max_iter) {
+    set_error("srm_fit: log-likelihood trace capacity exceeded (raise max_iter)");
+    return SRM_ERR_STATE;
+  }
+  const int ll0 = c->n_ll;
+  const bool use_graph = (c->flags & SRM_GRAPH) && !c->profile;
+  if (use_graph && n_iter > 0 && !c->graph_exec) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    srm_status s1 = do_estep(c);
+    srm_status s2 = s1 == SRM_OK ? do_mstep(c) : s1;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (s2 != SRM_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s2;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->graph_exec = nullptr;
+      return cuda_fail(e, "cudaGraphInstantiate");
+    }
+  }
+  for (int it = 0; it < n_iter; ++it) {
+    if (use_graph) {
+      CK(cudaGraphLaunch(c->graph_exec, c->stream));
+    } else {
+      TRY(do_estep(c));
+      TRY(do_mstep(c));
+    }
+    c->n_ll++;
+    c->iters_done++;
+  }
+  c->have_estep = false;
+  if (n_iter > 0) c->have_es = true;
+  if (final_ll) {
+    // one more E-step for the likelihood of the final parameters; E[S] of the
+    // last iteration is kept (saved and restored around it)
+    double* save = nullptr;
+    if (c->have_es) {
+      CK(cudaMallocAsync(&save, sizeof(double) * c->k * c->T, c->stream));
+      CK(cudaMemcpyAsync(save, c->ES64, sizeof(double) * c->k * c->T, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    TRY(do_estep(c));
+    c->n_ll++;
+    if (save) {
+      CK(cudaMemcpyAsync(c->ES64, save, sizeof(double) * c->k * c->T, cudaMemcpyDeviceToDevice, c->stream));
+      CK(cudaFreeAsync(save, c->stream));
+    }
+    c->have_es = true;
+  }
+  if (ll_host) {
+    CK(cudaMemcpyAsync(ll_host, c->ll + ll0, sizeof(double) * (c->n_ll - ll0), cudaMemcpyDeviceToHost, c->stream));
+    TRY(check_status(c));
+  }
+  return SRM_OK;
+}
+
+srm_status srm_transform(srm_ctx* c, int32_t subject, const void* X_new, int32_t T_new, float* S_out) {
+  TRY(valid_ctx(c));
+  if (subject < 0 || subject >= c->N || !X_new || !S_out || T_new < 1) {
+    set_error("srm_transform: bad subject, pointer or T_new");
+    return SRM_ERR_ARG;
+  }
+  const int64_t v = c->v[subject];
+  const int64_t ldn = ((T_new + 7) / 8) * 8;
+  const int nchunk = (T_new + TCH - 1) / TCH;
+  int ns = std::max(1, 2 * c->num_sms / nchunk);
+  ns = (int)std::min<int64_t>(ns, std::max<int64_t>(1, v / 64));
+  const int64_t need_buf = v * ldn, need_part = (int64_t)ns * nchunk * TCH * c->kld;
+  if (need_buf > c->tr_elems) {
+    if (c->tr_buf) cudaFree(c->tr_buf);
+    c->tr_buf = nullptr;
+    c->tr_elems = 0;
+    TRY(dalloc(&c->tr_buf, need_buf, "transform buffer"));
+    c->tr_elems = need_buf;
+  }
+  if (need_part > c->tr_part_elems) {
+    if (c->tr_part) cudaFree(c->tr_part);
+    c->tr_part = nullptr;
+    c->tr_part_elems = 0;
+    TRY(dalloc(&c->tr_part, need_part, "transform partials"));
+    c->tr_part_elems = need_part;
+  }
+  CK(launch_center_generic(X_new, c->in_dtype, v, T_new, T_new, c->tr_buf, ldn, nullptr, c->stream));
+  const char* A = static_cast<const char*>(c->A) + c->off[subject] * c->kld * (c->batched ? 2 : 4);
+  CK(launch_p_simt_generic(A, c->batched, c->kld, c->kld, c->tr_buf, ldn, v, T_new, ns, c->tr_part, c->stream));
+  CK(launch_transform_finish(c, subject, c->tr_part, ns, T_new, S_out));
+  return SRM_OK;
+}
+
+srm_status srm_get_w(srm_ctx* c, int32_t subject, float* W) {
+  TRY(valid_ctx(c));
+  if (subject < 0 || subject >= c->N || !W) {
+    set_error("srm_get_w: bad subject or null pointer");
+    return SRM_ERR_ARG;
+  }
+  CK(launch_get_w(c, subject, W));
+  return SRM_OK;
+}
+
+srm_status srm_get_s(srm_ctx* c, float* S) {
+  TRY(valid_ctx(c));
+  if (!S) {
+    set_error("srm_get_s: null pointer");
+    return SRM_ERR_ARG;
+  }
+  if (!c->have_es) {
+    set_error("srm_get_s: no E-step has run");
+    return SRM_ERR_STATE;
+  }
+  const int64_t n = (int64_t)c->k * c->T;
+  cast_kernel<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->ES64, S, n);
+  CK(cudaGetLastError());
+  return SRM_OK;
+}
+
+srm_status srm_get_params(srm_ctx* c, double* rho2, double* sigma) {
+  TRY(valid_ctx(c));
+  TRY(check_status(c));
+  if (rho2) CK(cudaMemcpy(rho2, c->rho2, sizeof(double) * c->N, cudaMemcpyDeviceToHost));
+  if (sigma) CK(cudaMemcpy(sigma, c->Sigma, sizeof(double) * c->k * c->k, cudaMemcpyDeviceToHost));
+  return SRM_OK;
+}
+
+srm_status srm_get_ll(srm_ctx* c, double* ll_host, int32_t* n) {
+  TRY(valid_ctx(c));
+  if (!n) {
+    set_error("srm_get_ll: null count");
+    return SRM_ERR_ARG;
+  }
+  TRY(check_status(c));
+  const int m = std::min(*n, c->n_ll);
+  if (ll_host && m > 0) CK(cudaMemcpy(ll_host, c->ll, sizeof(double) * m, cudaMemcpyDeviceToHost));
+  *n = c->n_ll;
+  return SRM_OK;
+}
+
+srm_status srm_synchronize(srm_ctx* c) {
+  TRY(valid_ctx(c));
+  return check_status(c);
+}
+
+srm_status srm_get_state(srm_ctx* c, void* buf, size_t* bytes) {
+  TRY(valid_ctx(c));
+  if (!bytes) {
+    set_error("srm_get_state: null size");
+    return SRM_ERR_ARG;
+  }
+  const int N = c->N, k = c->k;
+  const size_t ael = c->batched ? 2 : 4;
+  const size_t nA = (size_t)c->Vpad_tot * c->kld * ael;
+  const size_t need = sizeof(StateHeader) + sizeof(double) * (N + k * k + (size_t)N * k * k + c->n_ll) +
+                      sizeof(float) * ((size_t)N * k * k + (size_t)N * c->kld * c->kld) + nA;
+  if (!buf) {
+    *bytes = need;
+    return SRM_OK;
+  }
+  if (*bytes < need) {
+    set_error("srm_get_state: buffer too small");
+    *bytes = need;
+    return SRM_ERR_ARG;
+  }
+  if (c->have_estep) {
+    set_error("srm_get_state: an E-step is pending; checkpoint between iterations");
+    return SRM_ERR_STATE;
+  }
+  TRY(check_status(c));
+  StateHeader h{kStateMagic, 1, N, c->T, k, c->kld, c->batched ? 1 : 0, c->n_ll, c->iters_done, c->Vpad_tot};
+  char* p = static_cast<char*>(buf);
+  memcpy(p, &h, sizeof h);
+  p += sizeof h;
+  auto get = [&](const void* d, size_t nb) -> cudaError_t {
+    cudaError_t e = cudaMemcpy(p, d, nb, cudaMemcpyDeviceToHost);
+    p += nb;
+    return e;
+  };
+  CK(get(c->rho2, sizeof(double) * N));
+  CK(get(c->Sigma, sizeof(double) * k * k));
+  CK(get(c->M64, sizeof(double) * N * k * k));
+  CK(get(c->ll, sizeof(double) * c->n_ll));
+  CK(get(c->Uwarm, sizeof(float) * N * k * k));
+  CK(get(c->M32, sizeof(float) * N * c->kld * c->kld));
+  CK(get(c->A, nA));
+  *bytes = need;
+  return SRM_OK;
+}
+
+srm_status srm_set_state(srm_ctx* c, const void* buf, size_t bytes) {
+  TRY(valid_ctx(c));
+  if (!buf || bytes < sizeof(StateHeader)) {
+    set_error("srm_set_state: buffer too small");
+    return SRM_ERR_ARG;
+  }
+  StateHeader h;
+  memcpy(&h, buf, sizeof h);
+  if (h.magic != kStateMagic || h.version != 1 || h.N != c->N || h.T != c->T || h.k != c->k || h.kld != c->kld ||
+      h.batched != (c->batched ? 1 : 0) || h.Vpad_tot != c->Vpad_tot || h.n_ll < 0 || h.n_ll > c->max_iter) {
+    set_error("srm_set_state: checkpoint does not match this context's configuration");
+    return SRM_ERR_ARG;
+  }
+  const int N = c->N, k = c->k;
+  const size_t ael = c->batched ? 2 : 4;
+  const size_t nA = (size_t)c->Vpad_tot * c->kld * ael;
+  const size_t need = sizeof(StateHeader) + sizeof(double) * (N + k * k + (size_t)N * k * k + h.n_ll) +
+                      sizeof(float) * ((size_t)N * k * k + (size_t)N * c->kld * c->kld) + nA;
+  if (bytes != need) {
+    set_error("srm_set_state: size mismatch");
+    return SRM_ERR_ARG;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  const char* p = static_cast<const char*>(buf) + sizeof h;
+  auto put = [&](void* d, size_t nb) -> cudaError_t {
+    cudaError_t e = cudaMemcpy(d, p, nb, cudaMemcpyHostToDevice);
+    p += nb;
+    return e;
+  };
+  CK(put(c->rho2, sizeof(double) * N));
+  CK(put(c->Sigma, sizeof(double) * k * k));
+  CK(put(c->M64, sizeof(double) * N * k * k));
+  CK(put(c->ll, sizeof(double) * h.n_ll));
+  CK(put(c->Uwarm, sizeof(float) * N * k * k));
+  CK(put(c->M32, sizeof(float) * N * c->kld * c->kld));
+  CK(put(c->A, nA));
+  const int it = h.n_ll;
+  CK(cudaMemcpy(c->iter, &it, sizeof(int), cudaMemcpyHostToDevice));
+  c->n_ll = h.n_ll;
+  c->iters_done = h.iters_done;
+  c->have_estep = false;
+  c->have_es = false;
+  return SRM_OK;
+}
+
+srm_status srm_get_kernel_times(srm_ctx* c, const char** names, int64_t* launches, double* ms, int32_t* n,
+                                int32_t reset) {
+  TRY(valid_ctx(c));
+  if (!n) {
+    set_error("srm_get_kernel_times: null count");
+    return SRM_ERR_ARG;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  for (const auto& p : c->pending) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, c->ev_pool[p.ev0], c->ev_pool[p.ev1]));
+    c->prof_launches[p.kind]++;
+    c->prof_ms[p.kind] += t;
+  }
+  c->pending.clear();
+  c->ev_next = 0;
+  const int m = std::min<int>(*n, KK_COUNT);
+  for (int j = 0; j < m; ++j) {
+    if (names) names[j] = kKernelNames[j];
+    if (launches) launches[j] = c->prof_launches[j];
+    if (ms) ms[j] = c->prof_ms[j];
+  }
+  *n = KK_COUNT;
+  if (reset) {
+    for (int j = 0; j < KK_COUNT; ++j) {
+      c->prof_launches[j] = 0;
+      c->prof_ms[j] = 0;
+    }
+  }
+  return SRM_OK;
+}
+
+srm_status srm_layout(srm_ctx* c, int64_t* out, int32_t n) {
+  TRY(valid_ctx(c));
+  if (!out) {
+    set_error("srm_layout: null output");
+    return SRM_ERR_ARG;
+  }
+  const int64_t vals[5] = {c->ldT, c->kld, c->Vpad_tot,
+                           c->Vpad_tot * c->ldT * (c->store == SRM_BF16 ? 2 : 4),
+                           c->Vpad_tot * c->kld * (c->batched ? 2 : 4)};
+  for (int j = 0; j < n && j < 5; ++j) out[j] = vals[j];
+  return SRM_OK;
+}
+
+void srm_destroy(srm_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+}  // extern "C"

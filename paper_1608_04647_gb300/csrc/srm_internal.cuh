@@ -1,0 +1,197 @@
+// Internal declarations shared by the translation units of libsrm.
+// Method: probabilistic SRM EM iteration, Sec. II and Algorithm 1 of
+// Anderson et al. (arXiv 1608.04647).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/srm.h"
+
+namespace srm {
+
+constexpr int KMAX = 128;         // largest k supported
+constexpr int ROW_PAD = 128;      // each subject's rows are padded to a multiple of this
+constexpr int TCH = 64;           // t-chunk width of the partial-sum slots and reductions
+
+// Device-side status bits (ctx->status word).
+enum : int {
+  ST_NONFINITE = 1,     // a NaN / Inf reached a k x k step
+  ST_NOT_PD = 2,        // Cholesky met a non-positive pivot
+  ST_EIG_NOCONV = 4,    // Jacobi sweep cap reached
+  ST_RANK = 8,          // A_i^T A_i numerically singular (polar factor undefined)
+  ST_TIMEOUT = 16,      // a bounded wait inside a tensor-core kernel gave up
+  ST_BOUNDS = 32,       // a kernel's own index check refused an access
+};
+
+// Kernel kinds for SRM_PROFILE timing.
+enum KernelKind : int {
+  KK_CENTER = 0,
+  KK_P_SIMT,
+  KK_P_TC,
+  KK_P_REDUCE,
+  KK_Y_SUM,
+  KK_CHOL,
+  KK_PHI,
+  KK_ES,
+  KK_SIGMA,
+  KK_A_SIMT,
+  KK_A_TC,
+  KK_EIG,
+  KK_REFINE,
+  KK_RHO,
+  KK_COUNT
+};
+extern const char* const kKernelNames[KK_COUNT];
+
+// One source of a (subject, t-chunk) partial: float offset of the [TCH][kld]
+// block inside the partial buffer.
+struct ChunkSrc {
+  int64_t off;
+};
+
+struct Ctx {
+  // ---- configuration
+  int N = 0, T = 0, k = 0;
+  int kld = 0;        // leading dimension of A rows / partial rows (k padded)
+  int ldT = 0;        // row stride of resident X^ (T padded to 8)
+  int nchunk = 0;     // ceil(T / TCH)
+  srm_dtype in_dtype = SRM_F32, store = SRM_F32;
+  uint32_t flags = 0;
+  bool batched = false;
+  int max_iter = 1024;
+  int device = 0, num_sms = 0;
+  std::vector<int64_t> v, vpad, off;  // per subject: rows, padded rows, row offset
+  int64_t Vtot = 0, Vpad_tot = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+
+  // ---- resident data
+  void* Xh = nullptr;        // [Vpad_tot][ldT] store dtype, demeaned, zero padded
+  void* A = nullptr;         // [Vpad_tot][kld]: FP32 (plain) or BF16 (batched)
+  double* sqnorm = nullptr;  // [N] ||X^_i||_F^2
+  double* rowsq = nullptr;   // [Vpad_tot] per-row sum of squares (init scratch)
+  int64_t* d_off = nullptr;  // [N+1] row offsets
+  int64_t* d_v = nullptr;    // [N]
+
+  // ---- EM parameters (device)
+  double* rho2 = nullptr;       // [N]
+  double* Sigma = nullptr;      // [k][k]
+  double* SigmaNext = nullptr;  // [k][k]
+  double* L = nullptr;          // [k][k] Cholesky factor of I + rho0 Sigma
+  double* Phi = nullptr;        // [k][k]
+  double* scal = nullptr;       // [16] scalars of the current E-step (see k_small.cu)
+  double* M64 = nullptr;        // [N][k][k] (A_i^T A_i)^-1/2
+  float* M32 = nullptr;         // [N][kld][kld] FP32 copy used by the reduction
+  float* Uwarm = nullptr;       // [N][k][k] eigenvectors of the last Gram (warm start)
+  double* G64 = nullptr;        // [N][k][k] Gram matrices, then scratch
+  double* U64 = nullptr;        // [N][k][k] refined eigenvectors
+  double* H64 = nullptr;        // [N][k][k] scratch
+  double* Xr64 = nullptr;       // [N][k][k] re-orthonormalised eigenvectors
+  double* eigv = nullptr;       // [N][k] eigenvalues
+  double* Y = nullptr;          // [k][T] FP64 reduction sum_i rho_i^-2 W_i^T X^_i
+  double* ES64 = nullptr;       // [k][T] E[S]
+  float* ESt = nullptr;         // [ldT][kld] FP32 E[S]^T (plain-path operand)
+  __nv_bfloat16* ESb = nullptr; // [kld][ldT] BF16 E[S] (tensor-core operand)
+  double* esPart = nullptr;     // [nes_blk][k*k + 1] E[S]E[S]^T and <y, E[S]> partials
+  int nes_blk = 0;
+  double* ll = nullptr;         // [max_iter]
+  int* iter = nullptr;          // device E-step counter (index into ll)
+  int* status = nullptr;        // device status word
+
+  // ---- partial sums of the two contractions
+  float* Ppart = nullptr;       // E-pass partial blocks [..][TCH][kld]
+  int64_t Ppart_elems = 0;
+  ChunkSrc* chunk_src = nullptr;  // device table
+  int* chunk_src_off = nullptr;   // [N * nchunk + 1]
+  float* Zbuf = nullptr;        // [N][k][T] per-subject rho^-2 M_i P_i
+  float* Gpart = nullptr;       // M-pass Gram partials [..][kld][kld]
+  int64_t Gpart_elems = 0;
+  int* gslot_off = nullptr;     // [N+1] Gram slot ranges per subject
+  int n_gslots = 0;
+
+  // plain-path launch geometry (per subject)
+  std::vector<int> p_nsplit;        // E-pass v-splits per subject
+  std::vector<int64_t> p_slot_base; // float offset of subject's first partial block
+  std::vector<int> a_nblk;          // M-pass blocks per subject
+  std::vector<int> g_slot_base;     // first Gram slot per subject
+
+  // tensor-core path state (k_tc.cu)
+  void* tc = nullptr;
+
+  // ---- host bookkeeping
+  int n_ll = 0;            // E-steps launched
+  bool have_estep = false; // an E-step result is pending for an M-step
+  bool have_es = false;    // E[S] exists
+  int64_t iters_done = 0;
+
+  // graph
+  cudaGraphExec_t graph_exec = nullptr;
+
+  // profiling
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct PendingTiming { int kind; int ev0, ev1; };
+  std::vector<PendingTiming> pending;
+  int ev_next = 0;
+  int64_t prof_launches[KK_COUNT] = {0};
+  double prof_ms[KK_COUNT] = {0};
+
+  // transform scratch
+  float* tr_buf = nullptr;
+  int64_t tr_elems = 0;
+  float* tr_part = nullptr;
+  int64_t tr_part_elems = 0;
+};
+
+// error helpers (api.cu)
+void set_error(const std::string& msg);
+srm_status cuda_fail(cudaError_t e, const char* what);
+
+// profiling bracket (api.cu)
+void prof_begin(Ctx* c, int kind, int* ev0);
+void prof_end(Ctx* c, int kind, int ev0);
+
+// ---- launchers (return cudaError_t of the launch)
+// k_center.cu
+cudaError_t launch_center(Ctx* c, int subject, const void* X, srm_dtype in_dtype, int64_t ldx);
+cudaError_t launch_center_generic(const void* X, srm_dtype in_dtype, int64_t rows, int T, int64_t ldx,
+                                  float* out, int64_t ldo, double* rowsq, cudaStream_t s);
+cudaError_t launch_sqnorm_reduce(Ctx* c);
+cudaError_t launch_load_w0(Ctx* c, int subject, const float* W0);
+cudaError_t launch_get_w(Ctx* c, int subject, float* W);
+cudaError_t launch_init_params(Ctx* c);
+
+// k_simt.cu (plain per-subject FP32 form)
+cudaError_t launch_p_simt(Ctx* c, int subject);
+cudaError_t launch_p_simt_generic(const void* A, bool a_bf16, int kld, int kq, const float* X, int64_t ldx,
+                                  int64_t rows, int T, int nsplit, float* part, cudaStream_t s);
+cudaError_t launch_a_simt(Ctx* c, int subject);
+
+// k_small.cu
+cudaError_t launch_p_reduce(Ctx* c);
+cudaError_t launch_y_sum(Ctx* c);
+cudaError_t launch_chol(Ctx* c);
+cudaError_t launch_phi(Ctx* c);
+cudaError_t launch_es(Ctx* c);
+cudaError_t launch_sigma(Ctx* c);
+cudaError_t launch_eig(Ctx* c);
+cudaError_t launch_refine(Ctx* c);
+cudaError_t launch_rho(Ctx* c);
+cudaError_t launch_transform_finish(Ctx* c, int subject, const float* part, int nsplit, int T_new, float* S_out);
+
+// one-time kernel attributes (dynamic shared memory limits); called by srm_init
+void prepare_small_kernels(int max_smem);
+void prepare_simt_kernels(int max_smem);
+
+// k_tc.cu (grouped persistent tensor-core form)
+srm_status tc_setup(Ctx* c);
+void tc_destroy(Ctx* c);
+cudaError_t launch_p_tc(Ctx* c);
+cudaError_t launch_a_tc(Ctx* c);
+
+}  // namespace srm

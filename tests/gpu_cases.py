@@ -1,0 +1,59 @@
+"""Shared helpers of the GPU parity tests: run the library and the FP64
+oracle on the same seeded planted inputs and compare result by result."""
+import dataclasses
+
+import numpy as np
+
+import oracle
+import synth
+
+
+@dataclasses.dataclass
+class Case:
+    name: str
+    voxels: list
+    T: int
+    k: int
+    n_iter: int
+    seed: int = 0
+    rho2_range: tuple = (0.1, 1.0)
+
+
+def make_inputs(case: Case):
+    spec = synth.PlantedSpec(case.name, len(case.voxels), ("fixed", 0, 0), case.T, case.k, case.n_iter,
+                             case.rho2_range, case.seed)
+    d = synth.planted_dataset(spec, voxel_counts=case.voxels, dtype=np.float32)
+    d["W0"] = [w.astype(np.float32) for w in d["W0"]]
+    return d
+
+
+def run_oracle(d, n_iter, final_ll=True):
+    return oracle.fit([x.astype(np.float64) for x in d["X"]], [w.astype(np.float64) for w in d["W0"]], n_iter,
+                      final_ll=final_ll)
+
+
+def run_gpu(d, k, n_iter, store="f32", graph=False, final_ll=True, input_bf16=False):
+    import torch
+
+    import paper_1608_04647_gb300 as srm
+    X = [torch.from_numpy(x).cuda() for x in d["X"]]
+    if input_bf16:
+        X = [x.to(torch.bfloat16) for x in X]
+    W0 = [torch.from_numpy(w).cuda() for w in d["W0"]]
+    m = srm.SRM(X, W0, k, store=store, graph=graph, final_ll=final_ll)
+    ll = m.fit(n_iter)
+    out = {"ll": ll, "W": [m.get_w(i).cpu().numpy().astype(np.float64) for i in range(len(X))],
+           "ES": m.get_s().cpu().numpy().astype(np.float64)}
+    out["rho2"], out["Sigma_s"] = m.params()
+    out["model"] = m
+    return out
+
+
+def rel_errors(g, o):
+    """Per-result relative errors (max-norm), as stated for each result."""
+    ew = max(np.abs(a - b).max() / np.abs(b).max() for a, b in zip(g["W"], o["W"]))
+    es = np.abs(g["ES"] - o["ES"]).max() / np.abs(o["ES"]).max()
+    er = np.max(np.abs(g["rho2"] - o["rho2"]) / o["rho2"])
+    el = np.max(np.abs(g["ll"] - o["ll"]) / np.abs(o["ll"]))
+    esg = np.abs(g["Sigma_s"] - o["Sigma_s"]).max() / np.abs(o["Sigma_s"]).max()
+    return {"W": ew, "ES": es, "rho2": er, "ll": el, "Sigma_s": esg}
