@@ -1,0 +1,395 @@
+"""Benchmark of the pSRM EM iteration on GB300.
+
+One step = one EM iteration (E-pass, E-step k x k work, M-pass with the fused
+Gram, eigen / polar / rho update) over the whole resident workload.
+
+Default workload: the greeneyes-like case - 16 subjects with uneven voxel
+counts v_i ~ U[20000, 60000], T = 1000, k = 50 - on synthetic planted data
+(the paper's datasets are not available).  The headline ``value`` is EM
+iterations/s of the batched BF16-storage tensor-core form; the plain
+per-subject FP32 form is timed beside it on the same workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config 1]
+                    [--impl ours|reference] [--store bf16|f32] [--no-cpu-baseline]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload (its own seed) on its own GPU; the path's one exchange step (the
+k x T reduction of Algorithm 1) is not distributed here.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "pSRM EM iterations/s (BF16-batched tensor-core form; FP32 plain form reported beside)"
+UNIT = "EM iterations/s"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            if self.t is not None:
+                self.t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(config: int, rank: int):
+    import synth
+    spec = synth.config_spec(config)
+    vox = synth.draw_voxel_counts(spec)
+    return spec, vox
+
+
+def algorithmic_bytes(vox, T, k, xbytes, abytes):
+    """Bytes one EM iteration must move (per pass: read X^ once; A_i read in
+    the E-pass and written in the M-pass)."""
+    V = float(sum(vox))
+    e_pass = V * T * xbytes + V * k * abytes
+    m_pass = V * T * xbytes + V * k * abytes
+    return e_pass, m_pass
+
+
+def paper_flops(vox, T, k):
+    """Flop model of Sec. V-A per subject per iteration: two V_i x T x K
+    products, one V_i x K x K product and a V_i x K economy SVD counted as
+    Householder QR (2 m n^2 - 2/3 n^3)."""
+    return float(sum(2 * (2 * v * T * k) + 2 * v * k * k + (2 * v * k * k - 2.0 / 3.0 * k ** 3) for v in vox))
+
+
+def time_fit(model, stream, steps, warmup):
+    import torch
+    model.fit_async(warmup)
+    model.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    model.fit_async(steps)
+    e1.record(stream)
+    e1.synchronize()
+    model.synchronize()
+    return e0.elapsed_time(e1)  # ms
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_1608_04647_gb300 as srm
+    from paper_1608_04647_gb300 import _build
+    from synth.planted_torch import planted_dataset_torch
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    srm.load_library()
+    spec, vox = workload(args.config, rank)
+    T, k = spec.T, spec.k
+    peaks = load_peaks()
+    d = planted_dataset_torch(spec, vox, device="cuda", seed_offset=rank)
+    stream = torch.cuda.Stream()
+    max_iter = args.warmup + args.steps + 64
+
+    def make(store, graph=True, profile=False):
+        return srm.SRM(d["X"], d["W0"], k, store=store, graph=graph, profile=profile, max_iter=max_iter,
+                       stream=stream)
+
+    results = {}
+    stores = [args.store] if args.store != "both" else ["bf16", "f32"]
+    clocks = None
+    for store in stores:
+        m = make(store)
+        lay = m.layout()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(dev) as cs:
+            ms = time_fit(m, stream, args.steps, args.warmup)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        ll = m.ll()
+        results[store] = {"ms_total": ms, "ms_per_step": ms / args.steps, "layout": lay,
+                          "ll_last": float(ll[-1]), "ll_monotone": bool(np.all(np.diff(ll) >= -1e-6 * np.abs(ll[1:])))}
+        if store == stores[0]:
+            clocks = cs.summary()
+        m.close()
+        del m
+        # per-kernel CUDA-event times over a profiled run of the same K steps
+        mp = make(store, graph=False, profile=True)
+        mp.fit_async(args.warmup)
+        mp.kernel_times(reset=True)
+        mp.fit_async(args.steps)
+        kt = mp.kernel_times()
+        mp.close()
+        del mp
+        results[store]["kernels"] = {n: {"launches": l, "ms": t} for n, (l, t) in kt.items() if l > 0}
+        torch.cuda.empty_cache()
+    head = stores[0]
+    xb = 2 if head == "bf16" else 4
+    ab = 2 if head == "bf16" else 4
+    e_bytes, m_bytes = algorithmic_bytes(vox, T, k, xb, ab)
+    ks = results[head]["kernels"]
+    kname_e = "estep_tc" if head == "bf16" else "estep_simt"
+    kname_m = "mstep_tc" if head == "bf16" else "mstep_simt"
+    ms_step = results[head]["ms_per_step"]
+    value = world * 1000.0 / ms_step
+    roofline = None
+    if kname_e in ks and kname_m in ks:
+        # dominant kernel = the larger share of the two streaming passes
+        te = ks[kname_e]["ms"] / args.steps
+        tm = ks[kname_m]["ms"] / args.steps
+        name, t, b = (kname_e, te, e_bytes) if te >= tm else (kname_m, tm, m_bytes)
+        if head == "f32":
+            b = b / len(vox)  # per launch (one launch per subject)
+            t = t / len(vox)
+        achieved = b / (t * 1e-3) / 1e9
+        roofline = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+                    "peak_source": peaks["source"] + " (burst copy)",
+                    "bytes_per_launch": b, "ms_per_launch": t}
+    iter_bytes = e_bytes + m_bytes
+    kernels_per_step = sum(v["launches"] for v in ks.values()) / args.steps
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": head,
+        "data": "synthetic planted (Sec. II-A model; greeneyes-like shapes), generated on device",
+        "config": {"workload": spec.name, "N": len(vox), "T": T, "k": k, "voxels_total": int(sum(vox)),
+                   "store": head, "l2": "inputs larger than L2 (resident X^ %.2f GB > 129 MB)" %
+                   (results[head]["layout"]["xhat_bytes"] / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "graph": True},
+        "hbm_gbs_iteration": round(iter_bytes / (ms_step * 1e-3) / 1e9, 1),
+        "roofline": roofline,
+        "paper_gflops": round(paper_flops(vox, T, k) / (ms_step * 1e-3) / 1e9, 1),
+        "gpu_launches": int(round(kernels_per_step * args.steps)),
+        "clocks": clocks,
+        "kernels_ms_per_step": {n: round(v["ms"] / args.steps, 4) for n, v in ks.items()},
+        "ll_monotone": results[head]["ll_monotone"],
+    }
+    if "f32" in results and head != "f32":
+        r = results["f32"]
+        out["fp32_plain"] = {"value": round(world * 1000.0 / r["ms_per_step"], 3), "ms_per_step":
+                             round(r["ms_per_step"], 4),
+                             "kernels_ms_per_step": {n: round(v["ms"] / args.steps, 4) for n, v in
+                                                     r["kernels"].items()}}
+    if not args.no_e2e:
+        out["e2e"] = run_e2e(args, d, spec, vox, stream, world)
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(spec, vox, budget_s=args.cpu_budget)
+    return out
+
+
+def run_e2e(args, d, spec, vox, stream, world):
+    """One whole user job through the public API with host buffers: pinned
+    host X -> srm_init (host input: H2D copy + centring) -> srm_fit(n_iter)
+    -> parameters, E[S] and the log-likelihood back to the host.
+    Value = EM iterations / job time."""
+    import torch
+
+    import paper_1608_04647_gb300 as srm
+    Xh = [x.to("cpu").pin_memory() for x in d["X"]]
+    n_iter = spec.n_iter
+    h2d = sum(x.numel() * x.element_size() for x in Xh)
+    times = []
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = srm.SRM(Xh, d["W0"], spec.k, store=args.store if args.store != "both" else "bf16", graph=True,
+                    host_input=True, stream=stream, max_iter=n_iter + 4)
+        ll = m.fit(n_iter)
+        rho2, sig = m.params()
+        S = m.get_s().cpu()
+        t1 = time.perf_counter()
+        m.close()
+        times.append(t1 - t0)
+    d2h = S.numel() * 4 + rho2.nbytes + sig.nbytes + ll.nbytes
+    best = min(times)
+    return {"value": round(world * n_iter / best, 3), "unit": UNIT, "job_s": round(best, 4),
+            "iterations_per_job": n_iter, "h2d_bytes_per_step": int(h2d / n_iter),
+            "d2h_bytes_per_step": int(d2h / n_iter),
+            "note": "step = one EM iteration of a %d-iteration job; host->device copy of X from pinned memory, "
+                    "centring, fit and result read-back inside the timed region" % n_iter}
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        return max((i.get("num_threads", 0) for i in info), default=None)
+    except Exception:
+        return None
+
+
+def cpu_baseline(spec, vox, budget_s=20.0, n_sub=None):
+    """The FP64 oracle (as it stands) on the host cores: one EM iteration over a
+    sample of the workload's subjects, scaled to the whole workload."""
+    import oracle
+    import synth
+    n_sub = n_sub or min(len(vox), 4)
+    sub = vox[:n_sub]
+    dd = synth.planted_dataset(spec, voxel_counts=sub, dtype=np.float64)
+    Xh = [oracle.center(x)[0] for x in dd["X"]]
+    del dd["X"]
+    t0 = time.perf_counter()
+    iters = 0
+    while True:
+        oracle.fit(Xh, dd["W0"], 1, centered=True)
+        iters += 1
+        if time.perf_counter() - t0 > budget_s or iters >= 5:
+            break
+    dt = (time.perf_counter() - t0) / iters
+    scale = float(sum(vox)) / float(sum(sub))
+    per_iter_full = dt * scale
+    return {"value": round(1.0 / per_iter_full, 5), "unit": UNIT, "cores": os.cpu_count(),
+            "blas_threads": blas_threads(), "kind": "oracle",
+            "sample": "%d of %d subjects (%d voxels), %d EM iteration(s) of the FP64 NumPy oracle, time scaled by "
+                      "total voxels (x%.2f)" % (n_sub, len(vox), int(sum(sub)), iters, scale)}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle as it stands, on the host cores, on a
+    bounded sample of the same workload; each step one EM iteration of a
+    sample of subjects, scaled to the whole workload."""
+    import oracle
+    import synth
+    spec, vox = workload(args.config, rank)
+    n_sub = min(len(vox), 2)
+    sub = vox[:n_sub]
+    dd = synth.planted_dataset(spec, voxel_counts=sub, dtype=np.float64)
+    Xh = [oracle.center(x)[0] for x in dd["X"]]
+    st = None
+    for _ in range(args.warmup):
+        oracle.fit(Xh, dd["W0"], 1, centered=True)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.fit(Xh, dd["W0"], 1, centered=True)
+    dt = (time.perf_counter() - t0) / args.steps
+    scale = float(sum(vox)) / float(sum(sub))
+    per_iter = dt * scale
+    value = 1.0 / per_iter
+    sample = ("%d of %d subjects (%d voxels) per step, one FP64 oracle EM iteration, time scaled by total voxels "
+              "(x%.2f)" % (n_sub, len(vox), int(sum(sub)), scale))
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per_iter * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic planted (Sec. II-A model; greeneyes-like shapes)",
+            "config": {"workload": spec.name, "N": len(vox), "T": spec.T, "k": spec.k,
+                       "voxels_total": int(sum(vox))},
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": os.cpu_count(),
+                             "blas_threads": blas_threads(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--store", choices=["bf16", "f32", "both"], default="both")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, rank, world)))
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,27 @@
+/*
+ * srm_debug.h -- self-test entry point of libsrm's tensor-core building
+ * blocks (not part of the EM method; the paper has no counterpart).
+ *
+ * srm_debug_mma computes, on one CTA of the current device,
+ *   D (128 x N, FP32, row-major) = A * B^T
+ * with BF16 operands loaded by TMA into 128-byte-swizzled shared memory and
+ * multiplied by tcgen05.mma with the FP32 accumulator in tensor memory.
+ *   mn_major == 0: A is 128 x K and B is N x K (K contiguous, "K-major"),
+ *                  the layout of the M-pass operands X^_i and E[S].
+ *   mn_major != 0: A is K x 128 and B is K x N (M / N contiguous, "MN-major"),
+ *                  the layout of the E-pass operands X^_i and A_i.
+ *   N in {64, 128}; K in {64, 128, 192, 256}.  A, B, D are device pointers
+ *   owned by the caller (A and B 16-byte aligned).  Synchronous; returns
+ *   SRM_ERR_ARG on bad sizes or pointers, SRM_ERR_CUDA on a CUDA error.
+ */
+#ifndef SRM_DEBUG_H
+#define SRM_DEBUG_H
+#include "srm.h"
+#ifdef __cplusplus
+extern "C" {
+#endif
+SRM_API srm_status srm_debug_mma(int32_t mn_major, const void* A, const void* B, float* D, int32_t N, int32_t K);
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -42,6 +42,9 @@ void prof_begin(Ctx* c, int kind, int* ev0) {
   cudaEventRecord(c->ev_pool[*ev0], c->stream);
 }
 
+// CUDA kernels behind one launcher call of each kind
+static const int kKernelsPerKind[KK_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 4, 4};
+
 void prof_end(Ctx* c, int kind, int ev0) {
   const int ev1 = c->ev_next++;
   cudaEventRecord(c->ev_pool[ev1], c->stream);
@@ -355,6 +358,7 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
   if (ce != cudaSuccess) return fail(cuda_fail(ce, "cudaMemcpy"));
 
   prepare_small_kernels(prop.sharedMemPerBlockOptin);
+  prepare_center_kernels(prop.sharedMemPerBlockOptin);
   prepare_simt_kernels(prop.sharedMemPerBlockOptin);
   if (batched) {
     if ((st = tc_setup(c)) != SRM_OK) return fail(st);
@@ -682,7 +686,7 @@ srm_status srm_get_kernel_times(srm_ctx* c, const char** names, int64_t* launche
   for (const auto& p : c->pending) {
     float t = 0.f;
     CK(cudaEventElapsedTime(&t, c->ev_pool[p.ev0], c->ev_pool[p.ev1]));
-    c->prof_launches[p.kind]++;
+    c->prof_launches[p.kind] += kKernelsPerKind[p.kind];
     c->prof_ms[p.kind] += t;
   }
   c->pending.clear();

@@ -206,6 +206,13 @@ cudaError_t launch_load_w0(Ctx* c, int i, const float* W0) {
   return cudaGetLastError();
 }
 
+void prepare_center_kernels(int max_smem) {
+  (void)max_smem;
+  const int need = (int)(sizeof(float) * KMAX * KMAX);
+  cudaFuncSetAttribute(get_w_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+  cudaFuncSetAttribute(get_w_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+}
+
 cudaError_t launch_get_w(Ctx* c, int i, float* W) {
   const int64_t n = c->v[i] * c->k;
   const size_t sm = sizeof(float) * c->k * c->kld;

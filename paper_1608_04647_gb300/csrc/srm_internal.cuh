@@ -186,6 +186,7 @@ cudaError_t launch_transform_finish(Ctx* c, int subject, const float* part, int 
 
 // one-time kernel attributes (dynamic shared memory limits); called by srm_init
 void prepare_small_kernels(int max_smem);
+void prepare_center_kernels(int max_smem);
 void prepare_simt_kernels(int max_smem);
 
 // k_tc.cu (grouped persistent tensor-core form)

@@ -1,0 +1,50 @@
+"""Device-side planted-data generator (PyTorch), for workloads too large to
+draw on the host: same generative model and distributions as
+``synth.planted`` (Sec. II-A, Eq. 1), drawn with torch's CUDA generator.
+The values differ from the NumPy generator's (different random streams);
+tests that compare against the oracle use the NumPy generator.
+Nothing here computes an EM quantity."""
+from __future__ import annotations
+
+import math
+from typing import List, Optional, Sequence
+
+import torch
+
+from .planted import PlantedSpec, draw_voxel_counts, planted_rho2
+
+
+def _orthonormal(v: int, k: int, gen: torch.Generator, device) -> torch.Tensor:
+    g = torch.randn(v, k, generator=gen, device=device, dtype=torch.float32)
+    q, r = torch.linalg.qr(g)
+    s = torch.sign(torch.diagonal(r))
+    s[s == 0] = 1.0
+    return (q * s[None, :]).contiguous()
+
+
+def planted_dataset_torch(spec: PlantedSpec, voxel_counts: Optional[Sequence[int]] = None, device="cuda",
+                          dtype=torch.float32, seed_offset: int = 0, keep_truth: bool = False):
+    """X_i (v_i x T, `dtype`) and W0_i (v_i x k, float32) on `device`."""
+    vs = list(voxel_counts) if voxel_counts is not None else draw_voxel_counts(spec)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(1_000_003 * (spec.seed + 1) + seed_offset)
+    sd = torch.sqrt(torch.linspace(2.0, 0.5, spec.k, device=device))
+    S = sd[:, None] * torch.randn(spec.k, spec.T, generator=gen, device=device)
+    rho2 = torch.tensor(planted_rho2(spec)[: len(vs)], device=device, dtype=torch.float32)
+    X: List[torch.Tensor] = []
+    W0: List[torch.Tensor] = []
+    Wt: List[torch.Tensor] = []
+    for i, v in enumerate(vs):
+        W = _orthonormal(v, spec.k, gen, device)
+        x = W @ S
+        x += torch.randn(v, 1, generator=gen, device=device)
+        x += math.sqrt(float(rho2[i])) * torch.randn(v, spec.T, generator=gen, device=device)
+        X.append(x.to(dtype) if dtype != torch.float32 else x)
+        if keep_truth:
+            Wt.append(W)
+        del W
+        W0.append(_orthonormal(v, spec.k, gen, device))
+    out = {"X": X, "W0": W0, "voxel_counts": vs, "S_true": S, "rho2_true": rho2}
+    if keep_truth:
+        out["W_true"] = Wt
+    return out

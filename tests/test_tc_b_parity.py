@@ -1,0 +1,53 @@
+"""GPU parity of the batched BF16-storage tensor-core form against the FP64
+oracle (bar 2e-2 relative, per result), on shapes that span several tiles,
+ragged tails, several T-blocks, k = 100 (padded to 128) and many subjects."""
+import numpy as np
+import pytest
+
+from gpu_cases import Case, make_inputs, rel_errors, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+TOL_BF16 = 2e-2
+
+TC_CASES = [
+    Case("raider-like", [2000] * 4, 300, 10, 10, seed=0),
+    Case("uneven-k50", [2999, 4100, 3333], 333, 50, 8, seed=1),
+    Case("k100-two-tblocks", [5000, 4321], 700, 100, 5, seed=3, rho2_range=(0.5, 2.0)),
+    Case("three-tblocks", [3000, 2500], 1100, 20, 5, seed=4),
+    Case("tiny", [7], 9, 1, 6, seed=5),
+    Case("k-odd", [130, 129, 257], 64, 17, 6, seed=6),
+    Case("many-subjects", [int(x) for x in np.random.default_rng(9).integers(150, 900, size=40)], 200, 12, 5,
+         seed=9),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    from paper_1608_04647_gb300 import _build as b
+    b.build()
+
+
+@pytest.mark.parametrize("case", TC_CASES, ids=lambda c: c.name)
+def test_batched_bf16_matches_oracle(case):
+    d = make_inputs(case)
+    o = run_oracle(d, case.n_iter)
+    g = run_gpu(d, case.k, case.n_iter, store="bf16")
+    err = rel_errors(g, o)
+    print(case.name, {k: f"{v:.2e}" for k, v in err.items()})
+    for key, e in err.items():
+        assert e <= TOL_BF16, (key, e)
+    for w in g["W"]:
+        np.testing.assert_allclose(w.T @ w, np.eye(case.k), atol=2e-2)
+    assert np.all(np.diff(g["ll"]) >= -TOL_BF16 * np.abs(g["ll"][1:]))
+
+
+def test_batched_graph_deterministic():
+    case = TC_CASES[1]
+    d = make_inputs(case)
+    a = run_gpu(d, case.k, case.n_iter, store="bf16", graph=False)
+    b = run_gpu(d, case.k, case.n_iter, store="bf16", graph=True)
+    c = run_gpu(d, case.k, case.n_iter, store="bf16", graph=True)
+    np.testing.assert_array_equal(a["ll"], b["ll"])
+    np.testing.assert_array_equal(b["ES"], c["ES"])
+    for x, y in zip(b["W"], c["W"]):
+        np.testing.assert_array_equal(x, y)
