@@ -19,7 +19,7 @@ thread_local std::string g_err;
 }
 
 const char* const kKernelNames[KK_COUNT] = {
-    "center", "estep_simt", "estep_tc", "p_reduce", "y_sum", "chol", "phi", "es", "sigma",
+    "center", "estep_simt", "estep_tc", "p_reduce", "y_sum", "phi", "es", "sigma",
     "mstep_simt", "mstep_tc", "eig", "refine", "rho"};
 
 void set_error(const std::string& msg) { g_err = msg; }
@@ -43,7 +43,7 @@ void prof_begin(Ctx* c, int kind, int* ev0) {
 }
 
 // CUDA kernels behind one launcher call of each kind
-static const int kKernelsPerKind[KK_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 4, 4};
+static const int kKernelsPerKind[KK_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 4, 4};
 
 void prof_end(Ctx* c, int kind, int ev0) {
   const int ev1 = c->ev_next++;
@@ -104,6 +104,9 @@ void free_all(Ctx* c) {
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
 }
 
 // Plain path: per-subject launch geometry and the partial-slot tables.
@@ -172,16 +175,54 @@ srm_status check_status(Ctx* c) {
   return SRM_OK;
 }
 
+// Launches on `s` until destruction: the launchers use c->stream.
+struct OnStream {
+  Ctx* c;
+  cudaStream_t saved;
+  OnStream(Ctx* cc, cudaStream_t s) : c(cc), saved(cc->stream) { c->stream = s; }
+  ~OnStream() { c->stream = saved; }
+};
+
+// The per-subject tail of an M-step (eigen-decompositions, M_i, rho_i^2,
+// the Sigma_s eigen-basis) and the Phi of the next E-step.  None of it is
+// needed by the next E-pass (which reads only A_i), so it runs on a second
+// stream beside that pass when an iteration follows.
+srm_status do_side_chain(Ctx* c) {
+  LAUNCH(c, KK_EIG, launch_eig(c));
+  LAUNCH(c, KK_REFINE, launch_refine(c));
+  LAUNCH(c, KK_RHO, launch_rho(c));
+  LAUNCH(c, KK_PHI, launch_phi(c));
+  return SRM_OK;
+}
+
+// Runs a pending M-step tail on the main stream (before anything that reads
+// rho^2, M_i or Sigma_s).
+srm_status flush_pending(Ctx* c) {
+  if (!c->side_pending) return SRM_OK;
+  TRY(do_side_chain(c));
+  c->side_pending = false;
+  return SRM_OK;
+}
+
 srm_status do_estep(Ctx* c) {
+  const bool overlap = c->side_pending;
+  if (overlap) {
+    CK(cudaEventRecord(c->ev_fork, c->stream));
+    CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    {
+      OnStream on(c, c->side);
+      TRY(do_side_chain(c));
+    }
+    CK(cudaEventRecord(c->ev_join, c->side));
+    c->side_pending = false;
+  }
   if (c->batched) {
     LAUNCH(c, KK_P_TC, launch_p_tc(c));
   } else {
     for (int i = 0; i < c->N; ++i) LAUNCH(c, KK_P_SIMT, launch_p_simt(c, i));
   }
+  if (overlap) CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
   LAUNCH(c, KK_P_REDUCE, launch_p_reduce(c));
-  LAUNCH(c, KK_Y_SUM, launch_y_sum(c));
-  LAUNCH(c, KK_CHOL, launch_chol(c));
-  LAUNCH(c, KK_PHI, launch_phi(c));
   LAUNCH(c, KK_ES, launch_es(c));
   LAUNCH(c, KK_SIGMA, launch_sigma(c));
   return SRM_OK;
@@ -193,9 +234,7 @@ srm_status do_mstep(Ctx* c) {
   } else {
     for (int i = 0; i < c->N; ++i) LAUNCH(c, KK_A_SIMT, launch_a_simt(c, i));
   }
-  LAUNCH(c, KK_EIG, launch_eig(c));
-  LAUNCH(c, KK_REFINE, launch_refine(c));
-  LAUNCH(c, KK_RHO, launch_rho(c));
+  c->side_pending = true;
   return SRM_OK;
 }
 
@@ -291,10 +330,14 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
     if (ce != cudaSuccess) return fail(cuda_fail(ce, "cudaStreamCreate"));
     c->own_stream = true;
   }
+  ce = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+  if (ce != cudaSuccess) return fail(cuda_fail(ce, "side stream / events"));
   c->kld = batched ? (c->k <= 64 ? 64 : 128) : ((c->k + 15) / 16) * 16;
   c->ldT = ((c->T + 7) / 8) * 8;
   c->nchunk = (c->T + TCH - 1) / TCH;
-  c->nes_blk = (c->T + 31) / 32;
+  c->nes_blk = es_blocks(c->T);
   c->v.resize(c->N);
   c->vpad.resize(c->N);
   c->off.resize(c->N + 1);
@@ -331,12 +374,12 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
   AL(scal, 16, "scalars");
   AL(M64, (int64_t)N * k * k, "M64");
   AL(M32, (int64_t)N * c->kld * c->kld, "M32");
-  AL(Uwarm, (int64_t)N * k * k, "Uwarm");
-  AL(G64, (int64_t)N * k * k, "G64");
-  AL(U64, (int64_t)N * k * k, "U64");
-  AL(H64, (int64_t)N * k * k, "H64");
-  AL(Xr64, (int64_t)N * k * k, "Xr64");
-  AL(eigv, (int64_t)N * k, "eigenvalues");
+  AL(Uwarm, (int64_t)(N + 1) * k * k, "Uwarm");
+  AL(G64, (int64_t)(N + 1) * k * k, "G64");
+  AL(U64, (int64_t)(N + 1) * k * k, "U64");
+  AL(H64, (int64_t)(N + 1) * k * k, "H64");
+  AL(Xr64, (int64_t)(N + 1) * k * k, "Xr64");
+  AL(eigv, (int64_t)(N + 1) * k, "eigenvalues");
   AL(Y, (int64_t)k * T, "y");
   AL(ES64, (int64_t)k * T, "E[S]");
   AL(ll, c->max_iter, "ll trace");
@@ -398,6 +441,7 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
   }
   if (ce == cudaSuccess) ce = launch_sqnorm_reduce(c);
   if (ce == cudaSuccess) ce = launch_init_params(c);
+  if (ce == cudaSuccess) ce = launch_phi(c);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
   if (stage) cudaFree(stage);
   if (ce != cudaSuccess) return fail(cuda_fail(ce, "srm_init: centring / initialisation"));
@@ -447,26 +491,29 @@ srm_status srm_fit(srm_ctx* c, int32_t n_iter, double* ll_host) {
   }
   const int ll0 = c->n_ll;
   const bool use_graph = (c->flags & SRM_GRAPH) && !c->profile;
-  if (use_graph && n_iter > 0 && !c->graph_exec) {
-    cudaGraph_t g = nullptr;
-    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    srm_status s1 = do_estep(c);
-    srm_status s2 = s1 == SRM_OK ? do_mstep(c) : s1;
-    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-    if (s2 != SRM_OK) {
-      if (g) cudaGraphDestroy(g);
-      return s2;
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&c->graph_exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-      c->graph_exec = nullptr;
-      return cuda_fail(e, "cudaGraphInstantiate");
-    }
-  }
   for (int it = 0; it < n_iter; ++it) {
-    if (use_graph) {
+    if (use_graph && c->side_pending) {
+      if (!c->graph_exec) {
+        // one steady-state iteration: [pending M-step tail || E-pass] -> E-step
+        // k x k work -> M-pass (whose tail stays pending)
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        srm_status s1 = do_estep(c);
+        srm_status s2 = s1 == SRM_OK ? do_mstep(c) : s1;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        c->side_pending = true;
+        if (s2 != SRM_OK) {
+          if (g) cudaGraphDestroy(g);
+          return s2;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+          c->graph_exec = nullptr;
+          return cuda_fail(e, "cudaGraphInstantiate");
+        }
+      }
       CK(cudaGraphLaunch(c->graph_exec, c->stream));
     } else {
       TRY(do_estep(c));
@@ -475,6 +522,7 @@ srm_status srm_fit(srm_ctx* c, int32_t n_iter, double* ll_host) {
     c->n_ll++;
     c->iters_done++;
   }
+  TRY(flush_pending(c));
   c->have_estep = false;
   if (n_iter > 0) c->have_es = true;
   if (final_ll) {
@@ -506,6 +554,7 @@ srm_status srm_transform(srm_ctx* c, int32_t subject, const void* X_new, int32_t
     set_error("srm_transform: bad subject, pointer or T_new");
     return SRM_ERR_ARG;
   }
+  TRY(flush_pending(c));
   const int64_t v = c->v[subject];
   const int64_t ldn = ((T_new + 7) / 8) * 8;
   const int nchunk = (T_new + TCH - 1) / TCH;
@@ -539,6 +588,7 @@ srm_status srm_get_w(srm_ctx* c, int32_t subject, float* W) {
     set_error("srm_get_w: bad subject or null pointer");
     return SRM_ERR_ARG;
   }
+  TRY(flush_pending(c));
   CK(launch_get_w(c, subject, W));
   return SRM_OK;
 }
@@ -561,6 +611,7 @@ srm_status srm_get_s(srm_ctx* c, float* S) {
 
 srm_status srm_get_params(srm_ctx* c, double* rho2, double* sigma) {
   TRY(valid_ctx(c));
+  TRY(flush_pending(c));
   TRY(check_status(c));
   if (rho2) CK(cudaMemcpy(rho2, c->rho2, sizeof(double) * c->N, cudaMemcpyDeviceToHost));
   if (sigma) CK(cudaMemcpy(sigma, c->Sigma, sizeof(double) * c->k * c->k, cudaMemcpyDeviceToHost));
@@ -582,6 +633,7 @@ srm_status srm_get_ll(srm_ctx* c, double* ll_host, int32_t* n) {
 
 srm_status srm_synchronize(srm_ctx* c) {
   TRY(valid_ctx(c));
+  TRY(flush_pending(c));
   return check_status(c);
 }
 
@@ -594,8 +646,8 @@ srm_status srm_get_state(srm_ctx* c, void* buf, size_t* bytes) {
   const int N = c->N, k = c->k;
   const size_t ael = c->batched ? 2 : 4;
   const size_t nA = (size_t)c->Vpad_tot * c->kld * ael;
-  const size_t need = sizeof(StateHeader) + sizeof(double) * (N + k * k + (size_t)N * k * k + c->n_ll) +
-                      sizeof(float) * ((size_t)N * k * k + (size_t)N * c->kld * c->kld) + nA;
+  const size_t need = sizeof(StateHeader) + sizeof(double) * (N + 3 * k * k + (size_t)N * k * k + c->n_ll) +
+                      sizeof(float) * ((size_t)(N + 1) * k * k + (size_t)N * c->kld * c->kld) + nA;
   if (!buf) {
     *bytes = need;
     return SRM_OK;
@@ -609,8 +661,9 @@ srm_status srm_get_state(srm_ctx* c, void* buf, size_t* bytes) {
     set_error("srm_get_state: an E-step is pending; checkpoint between iterations");
     return SRM_ERR_STATE;
   }
+  TRY(flush_pending(c));
   TRY(check_status(c));
-  StateHeader h{kStateMagic, 1, N, c->T, k, c->kld, c->batched ? 1 : 0, c->n_ll, c->iters_done, c->Vpad_tot};
+  StateHeader h{kStateMagic, 2, N, c->T, k, c->kld, c->batched ? 1 : 0, c->n_ll, c->iters_done, c->Vpad_tot};
   char* p = static_cast<char*>(buf);
   memcpy(p, &h, sizeof h);
   p += sizeof h;
@@ -623,7 +676,9 @@ srm_status srm_get_state(srm_ctx* c, void* buf, size_t* bytes) {
   CK(get(c->Sigma, sizeof(double) * k * k));
   CK(get(c->M64, sizeof(double) * N * k * k));
   CK(get(c->ll, sizeof(double) * c->n_ll));
-  CK(get(c->Uwarm, sizeof(float) * N * k * k));
+  CK(get(c->G64 + (size_t)N * k * k, sizeof(double) * k * k));
+  CK(get(c->Xr64 + (size_t)N * k * k, sizeof(double) * k * k));
+  CK(get(c->Uwarm, sizeof(float) * (N + 1) * k * k));
   CK(get(c->M32, sizeof(float) * N * c->kld * c->kld));
   CK(get(c->A, nA));
   *bytes = need;
@@ -638,7 +693,7 @@ srm_status srm_set_state(srm_ctx* c, const void* buf, size_t bytes) {
   }
   StateHeader h;
   memcpy(&h, buf, sizeof h);
-  if (h.magic != kStateMagic || h.version != 1 || h.N != c->N || h.T != c->T || h.k != c->k || h.kld != c->kld ||
+  if (h.magic != kStateMagic || h.version != 2 || h.N != c->N || h.T != c->T || h.k != c->k || h.kld != c->kld ||
       h.batched != (c->batched ? 1 : 0) || h.Vpad_tot != c->Vpad_tot || h.n_ll < 0 || h.n_ll > c->max_iter) {
     set_error("srm_set_state: checkpoint does not match this context's configuration");
     return SRM_ERR_ARG;
@@ -646,8 +701,8 @@ srm_status srm_set_state(srm_ctx* c, const void* buf, size_t bytes) {
   const int N = c->N, k = c->k;
   const size_t ael = c->batched ? 2 : 4;
   const size_t nA = (size_t)c->Vpad_tot * c->kld * ael;
-  const size_t need = sizeof(StateHeader) + sizeof(double) * (N + k * k + (size_t)N * k * k + h.n_ll) +
-                      sizeof(float) * ((size_t)N * k * k + (size_t)N * c->kld * c->kld) + nA;
+  const size_t need = sizeof(StateHeader) + sizeof(double) * (N + 3 * k * k + (size_t)N * k * k + h.n_ll) +
+                      sizeof(float) * ((size_t)(N + 1) * k * k + (size_t)N * c->kld * c->kld) + nA;
   if (bytes != need) {
     set_error("srm_set_state: size mismatch");
     return SRM_ERR_ARG;
@@ -663,7 +718,9 @@ srm_status srm_set_state(srm_ctx* c, const void* buf, size_t bytes) {
   CK(put(c->Sigma, sizeof(double) * k * k));
   CK(put(c->M64, sizeof(double) * N * k * k));
   CK(put(c->ll, sizeof(double) * h.n_ll));
-  CK(put(c->Uwarm, sizeof(float) * N * k * k));
+  CK(put(c->G64 + (size_t)N * k * k, sizeof(double) * k * k));
+  CK(put(c->Xr64 + (size_t)N * k * k, sizeof(double) * k * k));
+  CK(put(c->Uwarm, sizeof(float) * (N + 1) * k * k));
   CK(put(c->M32, sizeof(float) * N * c->kld * c->kld));
   CK(put(c->A, nA));
   const int it = h.n_ll;
@@ -672,7 +729,9 @@ srm_status srm_set_state(srm_ctx* c, const void* buf, size_t bytes) {
   c->iters_done = h.iters_done;
   c->have_estep = false;
   c->have_es = false;
-  return SRM_OK;
+  c->side_pending = false;
+  CK(launch_phi(c));
+  return check_status(c);
 }
 
 srm_status srm_get_kernel_times(srm_ctx* c, const char** names, int64_t* launches, double* ms, int32_t* n,
@@ -723,6 +782,7 @@ srm_status srm_layout(srm_ctx* c, int64_t* out, int32_t n) {
 void srm_destroy(srm_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->side) cudaStreamSynchronize(c->side);
   free_all(c);
   delete c;
 }

@@ -127,16 +127,25 @@ __global__ void __launch_bounds__(256) get_w_kernel(const TA* __restrict__ A, in
   W[idx] = acc;
 }
 
+// rho_i^2 = 1, Sigma_s = I (Algorithm 1 initialisation), M_i = I (the
+// starting W_i are orthonormal), identity eigen-bases, and the
+// eigen-decomposition of Sigma_s = I kept for the first Phi.
 __global__ void init_params_kernel(int N, int k, int kld, double* rho2, double* Sigma, double* M64,
-                                   float* M32, float* Uwarm, int* iter, int* status) {
+                                   float* M32, float* Uwarm, double* G64, double* Xr64, int* iter, int* status) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t kk = (int64_t)k * k;
   for (int64_t e = tid; e < N; e += stride) rho2[e] = 1.0;
-  for (int64_t e = tid; e < (int64_t)k * k; e += stride) Sigma[e] = (e / k == e % k) ? 1.0 : 0.0;
-  for (int64_t e = tid; e < (int64_t)N * k * k; e += stride) {
-    const int64_t w = e % ((int64_t)k * k);
+  for (int64_t e = tid; e < kk; e += stride) {
+    const double d = (e / k == e % k) ? 1.0 : 0.0;
+    Sigma[e] = d;
+    G64[N * kk + e] = d;
+    Xr64[N * kk + e] = d;
+  }
+  for (int64_t e = tid; e < (int64_t)(N + 1) * kk; e += stride) {
+    const int64_t w = e % kk;
     const double d = (w / k == w % k) ? 1.0 : 0.0;
-    M64[e] = d;
+    if (e < (int64_t)N * kk) M64[e] = d;
     Uwarm[e] = (float)d;
   }
   for (int64_t e = tid; e < (int64_t)N * kld * kld; e += stride) {
@@ -229,7 +238,7 @@ cudaError_t launch_get_w(Ctx* c, int i, float* W) {
 
 cudaError_t launch_init_params(Ctx* c) {
   init_params_kernel<<<64, 256, 0, c->stream>>>(c->N, c->k, c->kld, c->rho2, c->Sigma, c->M64, c->M32, c->Uwarm,
-                                                c->iter, c->status);
+                                                c->G64, c->Xr64, c->iter, c->status);
   return cudaGetLastError();
 }
 

@@ -1,31 +1,34 @@
 // The k x k and k x T steps of one EM iteration (everything but the two
-// streaming passes over X^).  FP64 is used where the paper's reduced
-// E-step and M-step need it; k x k eigen-work runs in FP32 and is refined to
-// FP64 accuracy with FP64 matrix products.
+// streaming passes over X^).
 //
-//  E-step (Algorithm 1, master process):
-//    p_reduce : Z_i = rho_i^-2 M_i P_i  from the E-pass partials, with
-//               W_i^T X^_i = M_i (A_i^T X^_i)  (eq:srm_mean_distributed)
-//    y_sum    : y = sum_i Z_i                               (FP64)
-//    chol     : rho_0 = sum_i rho_i^-2 (eq:srm_wt_psi_w), Cholesky of
-//               I + rho_0 Sigma_s, ln det, likelihood scalars
-//    phi      : Phi = (Sigma_s^-1 + rho_0 I)^-1 = (I + rho_0 Sigma_s)^-1 Sigma_s
-//               (eq:srm_inversion_opt), one right-hand side per block
-//    es       : E[S] = Phi y (eq:srm_mean_distributed; Phi equals
-//               Sigma_s^T [I - rho_0 (Sigma_s^-1 + rho_0 I)^-1]), the operand
-//               copies for the M-pass, and per-block partials of
-//               E[S] E[S]^T and <y, Phi y>
-//    sigma    : Sigma_s^new = Phi + E[S] E[S]^T / T
-//               (eq:srm_variance_update_optimized) and the log-likelihood
-//  M-step (per subject, after the M-pass):
-//    eig      : G_i = A_i^T A_i from the Gram partials; FP32 cyclic Jacobi
-//               (warm-started from the previous eigenvectors)
-//    refine   : FP64 refinement of the eigenvectors, then
-//               M_i = (A_i^T A_i)^-1/2 through the Daleckii-Krein first-order
-//               correction, ||A_i||_* = tr (A_i^T A_i)^1/2, and
-//               rho_i^2 = (||X^_i||^2 - 2 ||A_i||_* + T tr Sigma_s^new)/(T v_i)
-//               (eq:srm_rho_update with tr(W_i^T A_i) = ||A_i||_* for the
-//               polar factor W_i of eq:srm_mapping_update)
+// E-step (Algorithm 1, master process):
+//   p_reduce : Z_i = rho_i^-2 M_i P_i from the E-pass partials, using
+//              W_i^T X^_i = M_i (A_i^T X^_i)        (eq:srm_mean_distributed)
+//   y_sum    : y = sum_i Z_i                        (FP64, subjects in order)
+//   phi      : rho_0 = sum_i rho_i^-2 (eq:srm_wt_psi_w) and
+//              Phi = (Sigma_s^-1 + rho_0 I)^-1 (eq:srm_inversion_opt), written
+//              as the matrix function Phi = g(Sigma_s), g(x) = x / (1 + rho_0 x),
+//              of the FP64 eigen-decomposition of Sigma_s kept from the M-step;
+//              ln det(I + rho_0 Sigma_s) = sum ln(1 + rho_0 lambda) for the
+//              log-likelihood.  Phi equals the paper's
+//              Sigma_s^T [I - rho_0 (Sigma_s^-1 + rho_0 I)^-1].
+//   es       : E[S] = Phi y, the operand copies for the M-pass, and per-block
+//              partials of E[S] E[S]^T and <y, Phi y>   (FP64)
+//   sigma    : Sigma_s^new = Phi + E[S] E[S]^T / T
+//              (eq:srm_variance_update_optimized) and the log-likelihood
+// M-step (per subject, plus Sigma_s^new as one more symmetric matrix):
+//   eig      : G_i = A_i^T A_i from the Gram partials; cyclic Jacobi in FP32,
+//              warm-started from the previous eigenvectors
+//   refine   : FP64 re-orthonormalisation U = U_0 (3I - U_0^T U_0)/2 and
+//              G' = U^T G U (off-diagonal part E of order 1e-6 |G|)
+//   rho      : first-order (Daleckii-Krein) correction of a matrix function
+//              f(G) = U (f(Lambda) + F o E) U^T with the divided differences
+//              F_ab = f[lambda_a, lambda_b]; for f(x) = x^-1/2 this gives
+//              M_i = (A_i^T A_i)^-1/2 to FP64 accuracy (error O(|E|^2)),
+//              ||A_i||_* = tr (A_i^T A_i)^1/2 = sum sqrt(lambda) + O(|E|^2), and
+//              rho_i^2 = (||X^_i||^2 - 2 ||A_i||_* + T tr Sigma_s^new)/(T v_i)
+//              (eq:srm_rho_update, with tr(W_i^T A_i) = ||A_i||_* for the
+//              polar factor W_i of eq:srm_mapping_update).
 #include <math.h>
 
 #include "srm_internal.cuh"
@@ -35,13 +38,6 @@ namespace srm {
 namespace {
 
 inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
-
-template <typename K>
-void set_smem_once(K kernel, size_t bytes) {
-  // cudaFuncSetAttribute is not a stream operation; calling it once per
-  // kernel and size is enough.
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
 
 __device__ __forceinline__ void flag(int* status, int bits) { atomicOr(status, bits); }
 
@@ -61,23 +57,35 @@ __global__ void __launch_bounds__(256) p_reduce_kernel(int N, int T, int k, int 
   const int t0 = c * TCH;
   const float* Mi = M32 + (int64_t)i * kld * kld;
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) Ms[(e / k) * (k + 1) + e % k] = Mi[(e / k) * kld + e % k];
-  for (int e = threadIdx.x; e < TCH * kld; e += blockDim.x) Ps[(e / kld) * (kld + 1) + e % kld] = 0.f;
-  __syncthreads();
   const int b = src_off[i * nchunk + c], en = src_off[i * nchunk + c + 1];
-  for (int s = b; s < en; ++s) {
-    const float* p = part + src[s].off;
-    for (int e = threadIdx.x; e < TCH * kld; e += blockDim.x) Ps[(e / kld) * (kld + 1) + e % kld] += p[e];
+  const int n4 = TCH * kld / 4;
+  for (int e4 = threadIdx.x; e4 < n4; e4 += blockDim.x) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int s = b; s < en; ++s) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(part + src[s].off) + e4);
+      acc.x += v.x;
+      acc.y += v.y;
+      acc.z += v.z;
+      acc.w += v.w;
+    }
+    const int e = 4 * e4, t = e / kld, f = e % kld;
+    float* d = Ps + t * (kld + 1) + f;
+    d[0] = acc.x;
+    d[1] = acc.y;
+    d[2] = acc.z;
+    d[3] = acc.w;
   }
   __syncthreads();
   const float rinv = (float)(1.0 / rho2[i]);
-  for (int e = threadIdx.x; e < k * TCH; e += blockDim.x) {
-    const int f = e / TCH, t = e % TCH;
-    if (t0 + t >= T) continue;
-    float z = 0.f;
-    const float* mr = Ms + f * (k + 1);
-    const float* pr = Ps + t * (kld + 1);
-    for (int m = 0; m < k; ++m) z = fmaf(mr[m], pr[m], z);
-    Z[((int64_t)i * k + f) * T + t0 + t] = rinv * z;
+  const int tl = threadIdx.x & (TCH - 1);
+  if (t0 + tl < T) {
+    const float* pr = Ps + tl * (kld + 1);
+    for (int f = threadIdx.x / TCH; f < k; f += blockDim.x / TCH) {
+      const float* mr = Ms + f * (k + 1);
+      float z = 0.f;
+      for (int m = 0; m < k; ++m) z = fmaf(mr[m], pr[m], z);
+      Z[((int64_t)i * k + f) * T + t0 + tl] = rinv * z;
+    }
   }
 }
 
@@ -94,121 +102,133 @@ __global__ void __launch_bounds__(256) y_sum_kernel(int N, int64_t kT, const flo
 // scal[] layout
 enum { SC_RHO0 = 0, SC_LOGDET = 1, SC_VLOGRHO = 2, SC_SQRHO = 3, SC_YPHIY = 4, SC_TRSIG = 5 };
 
-// One block: rho_0 and likelihood sums over subjects, Cholesky of
-// C = I + rho_0 Sigma_s (lower, in place), ln det C.
-__global__ void __launch_bounds__(256) chol_kernel(int N, int k, const double* __restrict__ rho2,
-                                                   const double* __restrict__ sqnorm,
-                                                   const int64_t* __restrict__ vox,
-                                                   const double* __restrict__ Sigma, double* __restrict__ Lout,
-                                                   double* __restrict__ scal, int* status) {
-  extern __shared__ double C[];  // [k][k+1] (chol_kernel only)
+// Block reduction of three doubles over blockDim.x (a power of two <= 256) threads.
+__device__ void block_sum3(double& a, double& b, double& c) {
   __shared__ double red[3][256];
   const int tid = threadIdx.x;
-  double a = 0, b = 0, d = 0;
-  for (int i = tid; i < N; i += blockDim.x) {
-    const double r = rho2[i];
-    if (!(r > 0.0) || !isfinite(r)) flag(status, ST_NONFINITE);
-    a += 1.0 / r;
-    b += (double)vox[i] * log(r);
-    d += sqnorm[i] / r;
-  }
   red[0][tid] = a;
   red[1][tid] = b;
-  red[2][tid] = d;
+  red[2][tid] = c;
   __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
-    if (tid < s)
-      for (int q = 0; q < 3; ++q) red[q][tid] += red[q][tid + s];
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (tid < s) {
+      red[0][tid] += red[0][tid + s];
+      red[1][tid] += red[1][tid + s];
+      red[2][tid] += red[2][tid + s];
+    }
     __syncthreads();
   }
-  const double rho0 = red[0][0];
-  const int ld = k + 1;
+  a = red[0][0];
+  b = red[1][0];
+  c = red[2][0];
+  __syncthreads();
+}
+
+// grid k blocks (row a of Phi), 256 threads.
+//   Sigma_s = U (Lambda + E) U^T with U = Us, G' = Lambda + E = Gp (k x k).
+//   Phi = U (g(Lambda) + F o E) U^T,  g(x) = x/(1 + rho0 x),
+//   F_bd = g[lambda_b, lambda_d] = 1 / ((1 + rho0 lambda_b)(1 + rho0 lambda_d)).
+__global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __restrict__ rho2,
+                                                  const double* __restrict__ sqnorm,
+                                                  const int64_t* __restrict__ vox, const double* __restrict__ Us,
+                                                  const double* __restrict__ Gp, double* __restrict__ Phi,
+                                                  double* __restrict__ scal, int* status) {
+  extern __shared__ double ph_smem[];
+  double* w = ph_smem;          // [k]  1 / (1 + rho0 lambda)
+  double* ua = w + k;           // [k]  row a of U
+  double* tv = ua + k;          // [k]  (U[a,:] B)
+  double* Uss = tv + k;         // [k][k] U
+  double* Gps = Uss + k * k;    // [k][k] G', symmetrised
+  const int a = blockIdx.x, tid = threadIdx.x;
   for (int e = tid; e < k * k; e += blockDim.x) {
-    const int r = e / k, cc = e % k;
-    C[r * ld + cc] = (r == cc ? 1.0 : 0.0) + rho0 * Sigma[e];
+    const int b = e / k, d = e % k;
+    Uss[e] = Us[e];
+    Gps[e] = 0.5 * (Gp[b * k + d] + Gp[d * k + b]);
+  }
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int i = tid; i < N; i += blockDim.x) {
+    const double r = rho2[i];
+    s0 += 1.0 / r;
+    if (a == 0) {
+      if (!(r > 0.0) || !isfinite(r)) flag(status, ST_NONFINITE);
+      s1 += (double)vox[i] * log(r);
+      s2 += sqnorm[i] / r;
+    }
+  }
+  block_sum3(s0, s1, s2);
+  const double rho0 = s0;
+  for (int b = tid; b < k; b += blockDim.x) {
+    w[b] = 1.0 / (1.0 + rho0 * Gp[b * k + b]);
+    ua[b] = Us[a * k + b];
   }
   __syncthreads();
-  const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-  for (int j = 0; j < k; ++j) {
+  // tv[d] = sum_b U[a][b] B[b][d],  B_bd = (b == d) ? lambda_b w_b : w_b w_d G'_bd
+  for (int d = tid; d < k; d += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < k; ++b) s = fma(ua[b] * w[b], Gps[b * k + d], s);
+    // the diagonal term: lambda_d w_d (not w_d^2 lambda_d)
+    s = (s - ua[d] * w[d] * Gps[d * k + d]) * w[d] + ua[d] * Gps[d * k + d] * w[d];
+    tv[d] = s;
+  }
+  __syncthreads();
+  for (int cc = tid; cc < k; cc += blockDim.x) {
+    double s = 0.0;
+    for (int d = 0; d < k; ++d) s = fma(tv[d], Uss[cc * k + d], s);
+    if (!isfinite(s)) flag(status, ST_NONFINITE);
+    Phi[a * k + cc] = s;
+  }
+  if (a == 0) {
+    double ld = 0.0;
+    for (int b = tid; b < k; b += blockDim.x) {
+      const double lam = Gp[b * k + b];
+      if (!(lam > 0.0)) flag(status, ST_NOT_PD);
+      ld += log1p(rho0 * lam);
+    }
+    double z0 = 0.0, z1 = 0.0;
+    block_sum3(ld, z0, z1);
     if (tid == 0) {
-      const double p = C[j * ld + j];
-      if (!(p > 0.0) || !isfinite(p)) flag(status, ST_NOT_PD);
-      C[j * ld + j] = sqrt(p > 1e-300 ? p : 1e-300);
+      scal[SC_RHO0] = rho0;
+      scal[SC_LOGDET] = ld;
+      scal[SC_VLOGRHO] = s1;
+      scal[SC_SQRHO] = s2;
     }
-    __syncthreads();
-    const double piv = C[j * ld + j];
-    for (int r = j + 1 + tid; r < k; r += blockDim.x) C[r * ld + j] /= piv;
-    __syncthreads();
-    for (int r = j + 1 + warp; r < k; r += nw) {
-      const double lr = C[r * ld + j];
-      for (int cc = j + 1 + lane; cc <= r; cc += 32) C[r * ld + cc] -= lr * C[cc * ld + j];
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < k * k; e += blockDim.x) {
-    const int r = e / k, cc = e % k;
-    Lout[e] = (cc <= r) ? C[r * ld + cc] : 0.0;
-  }
-  if (tid == 0) {
-    double ld2 = 0.0;
-    for (int j = 0; j < k; ++j) ld2 += log(C[j * ld + j]);
-    scal[SC_RHO0] = rho0;
-    scal[SC_LOGDET] = 2.0 * ld2;
-    scal[SC_VLOGRHO] = red[1][0];
-    scal[SC_SQRHO] = red[2][0];
   }
 }
 
-// Phi[:, j] = L^-T L^-1 Sigma_s[:, j]; one warp per right-hand side.
-__global__ void __launch_bounds__(32) phi_kernel(int k, const double* __restrict__ L,
-                                                 const double* __restrict__ Sigma, double* __restrict__ Phi) {
-  __shared__ double z[KMAX];
-  const int j = blockIdx.x, lane = threadIdx.x;
-  for (int r = 0; r < k; ++r) {
-    double s = 0.0;
-    for (int m = lane; m < r; m += 32) s += L[r * k + m] * z[m];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) z[r] = (Sigma[r * k + j] - s) / L[r * k + r];
-    __syncwarp();
-  }
-  for (int r = k - 1; r >= 0; --r) {
-    double s = 0.0;
-    for (int m = r + 1 + lane; m < k; m += 32) s += L[m * k + r] * z[m];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) z[r] = (z[r] - s) / L[r * k + r];
-    __syncwarp();
-  }
-  for (int r = lane; r < k; r += 32) Phi[r * k + j] = z[r];
-}
+constexpr int ES_T = 8;  // t per es block
 
-constexpr int ES_T = 32;  // t per es block
-
-// E[S][:, t0:t0+32] = Phi_sym y[:, t0:t0+32]; partial E E^T and <y, E>.
-__global__ void __launch_bounds__(256) es_kernel(int k, int T, int kld, int ldT, const double* __restrict__ Phi,
-                                                 const double* __restrict__ Y, double* __restrict__ ES64,
-                                                 float* __restrict__ ESt, __nv_bfloat16* __restrict__ ESb,
-                                                 double* __restrict__ part) {
+// y[:, t0:t0+8] = sum_i Z_i[:, t0:t0+8] (FP64, subjects in order), then
+// E[S][:, t0:t0+8] = Phi_sym y; partial E E^T and <y, E>.
+__global__ void __launch_bounds__(256) es_kernel(int N, int k, int T, int kld, int ldT, const double* __restrict__ Phi,
+                                                 const float* __restrict__ Z, double* __restrict__ Y,
+                                                 double* __restrict__ ES64, float* __restrict__ ESt,
+                                                 __nv_bfloat16* __restrict__ ESb, double* __restrict__ part) {
   extern __shared__ double es_smem[];
-  double* Ps = es_smem;              // [k][k]
-  double* Ys = Ps + k * k;           // [k][ES_T]
+  double* Ys = es_smem;              // [k][ES_T]
   double* Es = Ys + k * ES_T;        // [k][ES_T]
+  double* Ps = Es + k * ES_T;        // [k][k] Phi (symmetrised)
   const int t0 = blockIdx.x * ES_T;
   const int tid = threadIdx.x;
+  const int64_t kT = (int64_t)k * T;
   for (int e = tid; e < k * k; e += blockDim.x) {
-    const int a = e / k, b = e % k;
-    Ps[e] = 0.5 * (Phi[a * k + b] + Phi[b * k + a]);
+    const int f = e / k, m = e % k;
+    Ps[e] = 0.5 * (Phi[f * k + m] + Phi[m * k + f]);
   }
   for (int e = tid; e < k * ES_T; e += blockDim.x) {
     const int f = e / ES_T, tt = e % ES_T;
-    Ys[e] = (t0 + tt < T) ? Y[(int64_t)f * T + t0 + tt] : 0.0;
+    double y = 0.0;
+    if (t0 + tt < T) {
+      const float* zp = Z + (int64_t)f * T + t0 + tt;
+      for (int i = 0; i < N; ++i) y += (double)zp[(int64_t)i * kT];
+      Y[(int64_t)f * T + t0 + tt] = y;
+    }
+    Ys[e] = y;
   }
   __syncthreads();
   for (int e = tid; e < k * ES_T; e += blockDim.x) {
     const int f = e / ES_T, tt = e % ES_T;
     double s = 0.0;
-    for (int m = 0; m < k; ++m) s += Ps[f * k + m] * Ys[m * ES_T + tt];
+    for (int m = 0; m < k; ++m) s = fma(Ps[f * k + m], Ys[m * ES_T + tt], s);
     Es[e] = s;
     const int t = t0 + tt;
     if (t < T) {
@@ -219,22 +239,18 @@ __global__ void __launch_bounds__(256) es_kernel(int k, int T, int kld, int ldT,
   }
   __syncthreads();
   double* out = part + (int64_t)blockIdx.x * (k * k + 1);
-  for (int e = tid; e < k * (k + 1) / 2; e += blockDim.x) {
-    // e -> (a, b) with a <= b, row-major upper triangle
-    int a = 0, rem = e;
-    while (rem >= k - a) {
-      rem -= k - a;
-      ++a;
-    }
-    const int b = a + rem;
+  for (int e = tid; e < k * k; e += blockDim.x) {
+    const int a = e / k, b = e % k;
+    if (b < a) continue;
     double s = 0.0;
-    for (int tt = 0; tt < ES_T; ++tt) s += Es[a * ES_T + tt] * Es[b * ES_T + tt];
+#pragma unroll
+    for (int tt = 0; tt < ES_T; ++tt) s = fma(Es[a * ES_T + tt], Es[b * ES_T + tt], s);
     out[a * k + b] = s;
     out[b * k + a] = s;
   }
   if (tid < 32) {
     double s = 0.0;
-    for (int e = tid; e < k * ES_T; e += 32) s += Ys[e] * Es[e];
+    for (int e = tid; e < k * ES_T; e += 32) s = fma(Ys[e], Es[e], s);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (tid == 0) out[k * k] = s;
@@ -246,6 +262,7 @@ __global__ void __launch_bounds__(128) sigma_kernel(int k, int T, int nblk, doub
                                                     const double* __restrict__ part, double* __restrict__ SigmaNext,
                                                     double* __restrict__ scal, double* __restrict__ ll, int* iter,
                                                     int max_iter, int* status) {
+  __shared__ double red[128];
   const int a = blockIdx.x;
   for (int b = threadIdx.x; b < k; b += blockDim.x) {
     double s = 0.0;
@@ -254,62 +271,89 @@ __global__ void __launch_bounds__(128) sigma_kernel(int k, int T, int nblk, doub
     if (!isfinite(v)) flag(status, ST_NONFINITE);
     SigmaNext[a * k + b] = v;
   }
-  if (a == 0 && threadIdx.x == 0) {
+  if (a == 0) {
     double ye = 0.0;
-    for (int q = 0; q < nblk; ++q) ye += part[(int64_t)q * (k * k + 1) + k * k];
-    scal[SC_YPHIY] = ye;
-    const double L = -0.5 * ((double)T * Vtot * 1.8378770664093454835606594728112 + (double)T * scal[SC_VLOGRHO] +
-                             (double)T * scal[SC_LOGDET] + scal[SC_SQRHO] - ye);
-    if (!isfinite(L)) flag(status, ST_NONFINITE);
-    const int it = *iter;
-    if (it >= 0 && it < max_iter) ll[it] = L;
-    *iter = it + 1;
+    for (int q = threadIdx.x; q < nblk; q += blockDim.x) ye += part[(int64_t)q * (k * k + 1) + k * k];
+    red[threadIdx.x] = ye;
+    __syncthreads();
+    for (int s = 64; s > 0; s >>= 1) {
+      if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      ye = red[0];
+      scal[SC_YPHIY] = ye;
+      const double L = -0.5 * ((double)T * Vtot * 1.8378770664093454835606594728112 + (double)T * scal[SC_VLOGRHO] +
+                               (double)T * scal[SC_LOGDET] + scal[SC_SQRHO] - ye);
+      if (!isfinite(L)) flag(status, ST_NONFINITE);
+      const int it = *iter;
+      if (it >= 0 && it < max_iter) ll[it] = L;
+      *iter = it + 1;
+    }
   }
 }
 
 // ------------------------------------------------------------------ M-step
-// One block per subject.  G_i (FP64) = sum of Gram partials; FP32 Jacobi on
-// U_w^T G U_w (U_w = previous eigenvectors); U_0 = U_w V written to U64.
-__global__ void __launch_bounds__(256) eig_kernel(int k, int kld, const float* __restrict__ gpart,
-                                                  const int* __restrict__ gslot_off, double* __restrict__ G64,
-                                                  float* __restrict__ Uwarm, double* __restrict__ U64,
+// Jacobi tolerances (FP32): a pair is rotated while |g_pq| > JAC_TOL g_max
+// (g_max = largest diagonal entry, i.e. about |G|_2).  FP32 rounding keeps
+// refreshing off-diagonal noise of a few 1e-7 g_max, so the sweep loop ends
+// after a sweep in which no off-diagonal entry exceeded JAC_STOP g_max; that
+// sweep still rotates the smaller ones.  What remains (~1e-6 g_max) is
+// removed to second order by the FP64 refinement.
+constexpr float JAC_TOL = 1e-6f;
+constexpr float JAC_STOP = 4e-6f;
+constexpr int JAC_MAX_SWEEPS = 24;
+
+// One block per symmetric matrix: blocks 0..N-1 take G_i from the Gram
+// partials, block N takes Sigma_s^new.  FP32 cyclic Jacobi on U_w^T G U_w
+// (U_w = previous eigenvectors), round-robin ordering: kk/2 disjoint
+// rotations per round, each 2x2 block of G transformed by one thread
+// (J_p^T G_pq J_q), so a round needs two barriers.  Output U_0 = U_w V (FP64).
+__global__ void __launch_bounds__(256) eig_kernel(int N, int k, int kld, const float* __restrict__ gpart,
+                                                  const int* __restrict__ gslot_off,
+                                                  const double* __restrict__ SigmaNext, double* __restrict__ G64,
+                                                  const float* __restrict__ Uwarm, double* __restrict__ U64,
                                                   int* status) {
   extern __shared__ float eig_smem[];
-  const int kk = k + (k & 1);   // even size for the round-robin schedule
+  const int kk = k + (k & 1);
   const int ld = kk + 1;
   float* Gs = eig_smem;         // [kk][ld]
   float* Vs = Gs + kk * ld;     // [kk][ld]
   float* Us = Vs + kk * ld;     // [kk][ld]
   __shared__ float cs[KMAX / 2][2];
   __shared__ int pq[KMAX / 2][2];
-  __shared__ float redf[2][256];
+  __shared__ int nrot;
+  __shared__ float gmax;
   const int i = blockIdx.x, tid = threadIdx.x;
-  const int s0 = gslot_off[i], s1 = gslot_off[i + 1];
   double* Gi = G64 + (int64_t)i * k * k;
-  for (int e = tid; e < k * k; e += blockDim.x) {
-    const int a = e / k, b = e % k;
-    double s = 0.0;
-    for (int q = s0; q < s1; ++q) s += (double)gpart[(int64_t)q * kld * kld + a * kld + b];
-    Gi[e] = s;
+  if (i < N) {
+    const int s0 = gslot_off[i], s1 = gslot_off[i + 1];
+    for (int e = tid; e < k * k; e += blockDim.x) {
+      const int a = e / k, b = e % k;
+      double s = 0.0;
+      for (int q = s0; q < s1; ++q) s += (double)gpart[(int64_t)q * kld * kld + a * kld + b];
+      Gi[e] = s;
+    }
+  } else {
+    for (int e = tid; e < k * k; e += blockDim.x) Gi[e] = SigmaNext[e];
   }
   __syncthreads();
-  // symmetrise in FP64 (both triangles were accumulated separately)
-  for (int e = tid; e < k * k; e += blockDim.x) {
-    const int a = e / k, b = e % k;
-    const float g = (float)(0.5 * (Gi[a * k + b] + Gi[b * k + a]));
-    if (!isfinite(g)) flag(status, ST_NONFINITE);
-    Gs[a * ld + b] = g;
-    Us[a * ld + b] = Uwarm[(int64_t)i * k * k + e];
-  }
   for (int e = tid; e < kk * kk; e += blockDim.x) {
     const int a = e / kk, b = e % kk;
-    if (a >= k || b >= k) {
-      Gs[a * ld + b] = (a == b) ? 1.f : 0.f;
-      Us[a * ld + b] = (a == b) ? 1.f : 0.f;
+    float g, u;
+    if (a < k && b < k) {
+      g = (float)(0.5 * (Gi[a * k + b] + Gi[b * k + a]));
+      u = Uwarm[(int64_t)i * k * k + a * k + b];
+    } else {
+      g = (a == b) ? 1.f : 0.f;
+      u = g;
     }
+    if (!isfinite(g)) flag(status, ST_NONFINITE);
+    Gs[a * ld + b] = g;
+    Us[a * ld + b] = u;
   }
   __syncthreads();
-  // Vs = G U ; Gs = U^T Vs   (rotate into the warm basis)
+  // rotate into the warm basis: Vs = G U, Gs = U^T Vs
   for (int e = tid; e < kk * kk; e += blockDim.x) {
     const int a = e / kk, b = e % kk;
     float s = 0.f;
@@ -328,47 +372,35 @@ __global__ void __launch_bounds__(256) eig_kernel(int k, int kld, const float* _
     const int a = e / kk, b = e % kk;
     Vs[a * ld + b] = (a == b) ? 1.f : 0.f;
   }
-  __syncthreads();
-  // cyclic Jacobi, round-robin ordering: kk/2 disjoint rotations per round
   const int npair = kk / 2;
   bool converged = false;
-  for (int sweep = 0; sweep < 30 && !converged; ++sweep) {
-    float off = 0.f, dg = 0.f;
-    for (int e = tid; e < k * k; e += blockDim.x) {
-      const int a = e / k, b = e % k;
-      const float g = Gs[a * ld + b];
-      if (a == b) dg += g * g;
-      else off += g * g;
-    }
-    redf[0][tid] = off;
-    redf[1][tid] = dg;
+  __syncthreads();
+  if (tid == 0) {
+    float gm = 0.f;
+    for (int a = 0; a < k; ++a) gm = fmaxf(gm, fabsf(Gs[a * ld + a]));
+    gmax = gm;
+  }
+  for (int sweep = 0; sweep < JAC_MAX_SWEEPS; ++sweep) {
+    if (tid == 0) nrot = 0;
     __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-      if (tid < s) {
-        redf[0][tid] += redf[0][tid + s];
-        redf[1][tid] += redf[1][tid + s];
-      }
-      __syncthreads();
-    }
-    converged = !(redf[0][0] > 1e-11f * redf[1][0]);
-    __syncthreads();
-    if (converged) break;
+    const float thr = 1e-30f + JAC_TOL * gmax;
+    const float big = JAC_STOP * gmax;
     for (int round = 0; round < kk - 1; ++round) {
       if (tid < npair) {
         const int j = tid;
         const int pa = (j == 0) ? 0 : 1 + ((j - 1 + round) % (kk - 1));
-        const int pb_pos = kk - 1 - j;
-        const int pb = 1 + ((pb_pos - 1 + round) % (kk - 1));
+        const int pb = 1 + ((kk - 2 - j + round) % (kk - 1));
         const int p = min(pa, pb), q = max(pa, pb);
         float c = 1.f, s = 0.f;
         if (q < k) {
           const float gpq = Gs[p * ld + q];
           const float gpp = Gs[p * ld + p], gqq = Gs[q * ld + q];
-          if (fabsf(gpq) > 1e-30f + 1e-9f * sqrtf(fabsf(gpp * gqq))) {
+          if (fabsf(gpq) > thr) {
             const float tau = (gqq - gpp) / (2.f * gpq);
             const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
             c = rsqrtf(1.f + t * t);
             s = t * c;
+            if (fabsf(gpq) > big) atomicAdd(&nrot, 1);
           }
         }
         cs[j][0] = c;
@@ -377,36 +409,38 @@ __global__ void __launch_bounds__(256) eig_kernel(int k, int kld, const float* _
         pq[j][1] = q;
       }
       __syncthreads();
-      for (int e = tid; e < npair * kk; e += blockDim.x) {
-        const int j = e / kk, col = e % kk;
-        const float c = cs[j][0], s = cs[j][1];
-        if (s == 0.f) continue;
-        const int p = pq[j][0], q = pq[j][1];
-        const float gp = Gs[p * ld + col], gq = Gs[q * ld + col];
-        Gs[p * ld + col] = c * gp - s * gq;
-        Gs[q * ld + col] = s * gp + c * gq;
+      // G <- J^T G J, one 2x2 block (rows of pair j, columns of pair l) per item
+      for (int e = tid; e < npair * npair; e += blockDim.x) {
+        const int j = e / npair, l = e % npair;
+        const float cj = cs[j][0], sj = cs[j][1], cl = cs[l][0], sl = cs[l][1];
+        if (sj == 0.f && sl == 0.f) continue;
+        const int pj = pq[j][0], qj = pq[j][1], pl = pq[l][0], ql = pq[l][1];
+        const float g00 = Gs[pj * ld + pl], g01 = Gs[pj * ld + ql];
+        const float g10 = Gs[qj * ld + pl], g11 = Gs[qj * ld + ql];
+        const float r00 = cj * g00 - sj * g10, r01 = cj * g01 - sj * g11;
+        const float r10 = sj * g00 + cj * g10, r11 = sj * g01 + cj * g11;
+        Gs[pj * ld + pl] = cl * r00 - sl * r01;
+        Gs[pj * ld + ql] = sl * r00 + cl * r01;
+        Gs[qj * ld + pl] = cl * r10 - sl * r11;
+        Gs[qj * ld + ql] = sl * r10 + cl * r11;
       }
-      __syncthreads();
+      // V <- V J
       for (int e = tid; e < npair * kk; e += blockDim.x) {
-        const int j = e / kk, row = e % kk;
-        const float c = cs[j][0], s = cs[j][1];
-        if (s == 0.f) continue;
-        const int p = pq[j][0], q = pq[j][1];
-        const float gp = Gs[row * ld + p], gq = Gs[row * ld + q];
-        Gs[row * ld + p] = c * gp - s * gq;
-        Gs[row * ld + q] = s * gp + c * gq;
-        const float vp = Vs[row * ld + p], vq = Vs[row * ld + q];
-        Vs[row * ld + p] = c * vp - s * vq;
-        Vs[row * ld + q] = s * vp + c * vq;
+        const int l = e / kk, row = e % kk;
+        const float cl = cs[l][0], sl = cs[l][1];
+        if (sl == 0.f) continue;
+        const int pl = pq[l][0], ql = pq[l][1];
+        const float vp = Vs[row * ld + pl], vq = Vs[row * ld + ql];
+        Vs[row * ld + pl] = cl * vp - sl * vq;
+        Vs[row * ld + ql] = sl * vp + cl * vq;
       }
       __syncthreads();
     }
+    converged = (nrot == 0);
+    __syncthreads();
+    if (converged) break;
   }
-  if (!converged && tid == 0) {
-    // FP32 Jacobi reaching its sweep cap is only a precision loss (the FP64
-    // refinement follows); a large remaining off-diagonal is a failure.
-    if (redf[0][0] > 1e-6f * redf[1][0]) flag(status, ST_EIG_NOCONV);
-  }
+  if (!converged && tid == 0) flag(status, ST_EIG_NOCONV);
   // U_0 = U_w V
   double* Uo = U64 + (int64_t)i * k * k;
   for (int e = tid; e < k * k; e += blockDim.x) {
@@ -418,34 +452,50 @@ __global__ void __launch_bounds__(256) eig_kernel(int k, int kld, const float* _
 }
 
 // D_b = alpha op(A_b) op(B_b) + beta C_b for a batch of k x k FP64 matrices.
-// grid (nband, nbatch); block 256; rows of the band split across threads.
+// grid (nband, nbatch), 256 threads.  op(B) is staged in shared memory as
+// [m][c] and the band of op(A) as [r][m]; with sym != 0 only c >= r is
+// computed and mirrored (the product is known to be symmetric).
 __global__ void __launch_bounds__(256) bgemm64_kernel(int k, int nband, const double* __restrict__ A, int tA,
                                                       const double* __restrict__ B, int tB, double alpha,
                                                       const double* __restrict__ C, double beta,
-                                                      double* __restrict__ D) {
+                                                      double* __restrict__ D, int sym) {
+  extern __shared__ double bg_smem[];
+  const int ldb = k + 1;
+  double* Bs = bg_smem;              // [k][k+1]
+  double* As = Bs + k * ldb;         // [band][k+1]
   const int b = blockIdx.y;
   const int r0 = (k * blockIdx.x) / nband, r1 = (k * (blockIdx.x + 1)) / nband;
+  const int nr = r1 - r0;
   const int64_t base = (int64_t)b * k * k;
   const double* Ab = A + base;
   const double* Bb = B + base;
-  for (int e = threadIdx.x; e < (r1 - r0) * k; e += blockDim.x) {
-    const int r = r0 + e / k, c = e % k;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int m = e / k, c = e % k;
+    Bs[m * ldb + c] = tB ? Bb[c * k + m] : Bb[e];
+  }
+  for (int e = threadIdx.x; e < nr * k; e += blockDim.x) {
+    const int r = e / k, m = e % k;
+    As[r * ldb + m] = tA ? Ab[m * k + r0 + r] : Ab[(r0 + r) * k + m];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nr * k; e += blockDim.x) {
+    const int r = e / k, c = e % k;
+    if (sym && c < r0 + r) continue;
     double s = 0.0;
-    for (int m = 0; m < k; ++m) {
-      const double a = tA ? Ab[m * k + r] : Ab[r * k + m];
-      const double bb = tB ? Bb[c * k + m] : Bb[m * k + c];
-      s = fma(a, bb, s);
-    }
+    const double* ar = As + r * ldb;
+    for (int m = 0; m < k; ++m) s = fma(ar[m], Bs[m * ldb + c], s);
     double out = alpha * s;
-    if (C) out += beta * C[base + r * k + c];
-    D[base + r * k + c] = out;
+    if (C) out += beta * C[base + (r0 + r) * k + c];
+    D[base + (r0 + r) * k + c] = out;
+    if (sym) D[base + c * k + r0 + r] = out;
   }
 }
 
-// Per subject: eigenvalues lambda = diag(G'), G' = U^T G U; the Daleckii-Krein
-// matrix B = diag(lambda^-1/2) + F o E with F_ab = -1/(s_a s_b (s_a + s_b)),
-// s = sqrt(lambda), E = off-diagonal part of G'; nuclear norm and rho update.
-// Block 0 also commits Sigma_s <- Sigma_s^new.
+// Per matrix: eigenvalues lambda = diag(G'), G' = U^T G U (FP64); for the
+// subjects (i < N) the Daleckii-Krein matrix for f(x) = x^-1/2,
+//   B = diag(lambda^-1/2) + F o E,  F_ab = -1 / (s_a s_b (s_a + s_b)), s = sqrt(lambda),
+// the nuclear norm sum s_a and the rho update.  Block 0 commits
+// Sigma_s <- Sigma_s^new.  Block N (Sigma_s^new) only checks its eigenvalues.
 __global__ void __launch_bounds__(128) dk_rho_kernel(int N, int k, int T, const double* __restrict__ Gp,
                                                      double* __restrict__ Bout, double* __restrict__ eigv,
                                                      const double* __restrict__ sqnorm,
@@ -455,19 +505,28 @@ __global__ void __launch_bounds__(128) dk_rho_kernel(int N, int k, int T, const 
                                                      int* status) {
   __shared__ double sq[KMAX];
   __shared__ double red[128];
+  __shared__ double lmax_s;
   const int i = blockIdx.x, tid = threadIdx.x;
   const double* G = Gp + (int64_t)i * k * k;
-  double* Bm = Bout + (int64_t)i * k * k;
-  double lmax = 0.0;
-  for (int a = 0; a < k; ++a) lmax = fmax(lmax, G[a * k + a]);
+  if (tid == 0) {
+    double lm = 0.0;
+    for (int a = 0; a < k; ++a) lm = fmax(lm, G[a * k + a]);
+    lmax_s = lm;
+  }
+  __syncthreads();
+  const double lmax = lmax_s;
   for (int a = tid; a < k; a += blockDim.x) {
     const double l = G[a * k + a];
-    if (!(l > 1e-12 * lmax) || !isfinite(l)) flag(status, ST_RANK);
+    if (!(l > 1e-12 * lmax) || !isfinite(l)) flag(status, i < N ? ST_RANK : ST_NOT_PD);
     const double lc = l > 1e-300 ? l : 1e-300;
     sq[a] = sqrt(lc);
     eigv[(int64_t)i * k + a] = l;
   }
+  if (i == 0)
+    for (int e = tid; e < k * k; e += blockDim.x) Sigma[e] = SigmaNext[e];
+  if (i >= N) return;
   __syncthreads();
+  double* Bm = Bout + (int64_t)i * k * k;
   for (int e = tid; e < k * k; e += blockDim.x) {
     const int a = e / k, b = e % k;
     double v;
@@ -491,19 +550,17 @@ __global__ void __launch_bounds__(128) dk_rho_kernel(int N, int k, int T, const 
     rho2[i] = r;
     if (i == 0) scal[SC_TRSIG] = tr;
   }
-  if (i == 0)
-    for (int e = tid; e < k * k; e += blockDim.x) Sigma[e] = SigmaNext[e];
 }
 
-// M32 (padded, FP32), M64 stays; Uwarm <- FP32 copy of the refined U.
+// M32 (padded, FP32) from M64; Uwarm <- FP32 copy of the refined U (N + 1 matrices).
 __global__ void finish_m_kernel(int N, int k, int kld, const double* __restrict__ M64, const double* __restrict__ U,
                                 float* __restrict__ M32, float* __restrict__ Uwarm) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)N * k * k) return;
+  if (e >= (int64_t)(N + 1) * k * k) return;
   const int64_t i = e / ((int64_t)k * k);
   const int w = (int)(e % ((int64_t)k * k));
   const int a = w / k, b = w % k;
-  M32[i * kld * kld + a * kld + b] = (float)M64[e];
+  if (i < N) M32[i * kld * kld + a * kld + b] = (float)M64[e];
   Uwarm[e] = (float)U[e];
 }
 
@@ -524,20 +581,33 @@ __global__ void __launch_bounds__(256) transform_finish_kernel(int k, int kld, i
   S[e] = acc;
 }
 
-int refine_bands(const Ctx* c) {
-  int nb = (2 * c->num_sms + c->N - 1) / c->N;
+int refine_bands(const Ctx* c, int nbatch) {
+  int nb = (2 * c->num_sms + nbatch - 1) / nbatch;
   nb = nb < 1 ? 1 : nb;
   const int mx = c->k / 4 > 0 ? c->k / 4 : 1;
   return nb > mx ? mx : nb;
 }
 
+cudaError_t bgemm(Ctx* c, int nbatch, const double* A, int tA, const double* B, int tB, double alpha,
+                  const double* C, double beta, double* D, int sym) {
+  const int k = c->k;
+  const int nb = refine_bands(c, nbatch);
+  const int band = (k + nb - 1) / nb;
+  const size_t sm = sizeof(double) * (size_t)(k + band) * (k + 1);
+  bgemm64_kernel<<<dim3(nb, nbatch), 256, sm, c->stream>>>(k, nb, A, tA, B, tB, alpha, C, beta, D, sym);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
+int es_blocks(int T) { return (T + ES_T - 1) / ES_T; }
+
 void prepare_small_kernels(int max_smem) {
-  set_smem_once(p_reduce_kernel, max_smem);
-  set_smem_once(chol_kernel, max_smem - 8 * 1024);
-  set_smem_once(es_kernel, max_smem);
-  set_smem_once(eig_kernel, max_smem - 4 * 1024);
+  cudaFuncSetAttribute(p_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 4 * 1024);
+  cudaFuncSetAttribute(bgemm64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  cudaFuncSetAttribute(es_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  cudaFuncSetAttribute(phi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
 }
 
 cudaError_t launch_p_reduce(Ctx* c) {
@@ -554,22 +624,19 @@ cudaError_t launch_y_sum(Ctx* c) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_chol(Ctx* c) {
-  const size_t sm = sizeof(double) * c->k * (c->k + 1);
-  chol_kernel<<<1, 256, sm, c->stream>>>(c->N, c->k, c->rho2, c->sqnorm, c->d_v, c->Sigma, c->L, c->scal, c->status);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_phi(Ctx* c) {
-  phi_kernel<<<c->k, 32, 0, c->stream>>>(c->k, c->L, c->Sigma, c->Phi);
+  const int64_t kk = (int64_t)c->k * c->k;
+  const size_t sm = sizeof(double) * (3 * c->k + 2 * c->k * c->k);
+  phi_kernel<<<c->k, 256, sm, c->stream>>>(c->N, c->k, c->rho2, c->sqnorm, c->d_v, c->Xr64 + c->N * kk,
+                                           c->G64 + c->N * kk, c->Phi, c->scal, c->status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_es(Ctx* c) {
-  const size_t sm = sizeof(double) * (c->k * c->k + 2 * c->k * ES_T);
-  es_kernel<<<c->nes_blk, 256, sm, c->stream>>>(c->k, c->T, c->kld, c->ldT, c->Phi, c->Y, c->ES64,
-                                                c->batched ? nullptr : c->ESt,
-                                                c->batched ? c->ESb : nullptr, c->esPart);
+  const size_t sm = sizeof(double) * (2 * c->k * ES_T + c->k * c->k);
+  es_kernel<<<c->nes_blk, 256, sm, c->stream>>>(c->N, c->k, c->T, c->kld, c->ldT, c->Phi, c->Zbuf, c->Y, c->ES64,
+                                                c->batched ? nullptr : c->ESt, c->batched ? c->ESb : nullptr,
+                                                c->esPart);
   return cudaGetLastError();
 }
 
@@ -582,38 +649,35 @@ cudaError_t launch_sigma(Ctx* c) {
 cudaError_t launch_eig(Ctx* c) {
   const int kk = c->k + (c->k & 1);
   const size_t sm = sizeof(float) * 3 * kk * (kk + 1);
-  eig_kernel<<<c->N, 256, sm, c->stream>>>(c->k, c->kld, c->Gpart, c->gslot_off, c->G64, c->Uwarm, c->U64,
-                                           c->status);
+  eig_kernel<<<c->N + 1, 256, sm, c->stream>>>(c->N, c->k, c->kld, c->Gpart, c->gslot_off, c->SigmaNext, c->G64,
+                                               c->Uwarm, c->U64, c->status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_refine(Ctx* c) {
-  const int k = c->k, N = c->N;
-  const int nb = refine_bands(c);
-  dim3 g(nb, N);
-  // H = U0^T U0 - I
-  // (the identity is subtracted by the next step: U1 = U0 - 1/2 U0 (U0^T U0 - I)
-  //  = 1.5 U0 - 0.5 U0 (U0^T U0))
-  bgemm64_kernel<<<g, 256, 0, c->stream>>>(k, nb, c->U64, 1, c->U64, 0, 1.0, nullptr, 0.0, c->H64);
-  // X = 1.5 U0 - 0.5 U0 H   (first-order re-orthonormalisation)
-  bgemm64_kernel<<<g, 256, 0, c->stream>>>(k, nb, c->U64, 0, c->H64, 0, -0.5, c->U64, 1.5, c->Xr64);
+  const int n1 = c->N + 1;
+  cudaError_t e;
+  // H = U0^T U0 (symmetric)
+  if ((e = bgemm(c, n1, c->U64, 1, c->U64, 0, 1.0, nullptr, 0.0, c->H64, 1)) != cudaSuccess) return e;
+  // X = U0 (3I - U0^T U0) / 2 = 1.5 U0 - 0.5 U0 H
+  if ((e = bgemm(c, n1, c->U64, 0, c->H64, 0, -0.5, c->U64, 1.5, c->Xr64, 0)) != cudaSuccess) return e;
   // H = G X
-  bgemm64_kernel<<<g, 256, 0, c->stream>>>(k, nb, c->G64, 0, c->Xr64, 0, 1.0, nullptr, 0.0, c->H64);
-  // G' = X^T H
-  bgemm64_kernel<<<g, 256, 0, c->stream>>>(k, nb, c->Xr64, 1, c->H64, 0, 1.0, nullptr, 0.0, c->G64);
-  return cudaGetLastError();
+  if ((e = bgemm(c, n1, c->G64, 0, c->Xr64, 0, 1.0, nullptr, 0.0, c->H64, 0)) != cudaSuccess) return e;
+  // G' = X^T H (symmetric)
+  return bgemm(c, n1, c->Xr64, 1, c->H64, 0, 1.0, nullptr, 0.0, c->G64, 1);
 }
 
 cudaError_t launch_rho(Ctx* c) {
   const int k = c->k, N = c->N;
-  const int nb = refine_bands(c);
-  dim3 g(nb, N);
-  dk_rho_kernel<<<N, 128, 0, c->stream>>>(N, k, c->T, c->G64, c->H64, c->eigv, c->sqnorm, c->d_v, c->SigmaNext,
-                                          c->Sigma, c->rho2, c->scal, c->status);
-  // T1 = X B ; M = T1 X^T
-  bgemm64_kernel<<<g, 256, 0, c->stream>>>(k, nb, c->Xr64, 0, c->H64, 0, 1.0, nullptr, 0.0, c->G64);
-  bgemm64_kernel<<<g, 256, 0, c->stream>>>(k, nb, c->G64, 0, c->Xr64, 1, 1.0, nullptr, 0.0, c->M64);
-  const int64_t n = (int64_t)N * k * k;
+  dk_rho_kernel<<<N + 1, 128, 0, c->stream>>>(N, k, c->T, c->G64, c->H64, c->eigv, c->sqnorm, c->d_v, c->SigmaNext,
+                                              c->Sigma, c->rho2, c->scal, c->status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // subjects only; entry N of G64 / Xr64 (Sigma_s) is kept for the next E-step.
+  // T1 = X B (into G64) ; M = T1 X^T (symmetric)
+  if ((e = bgemm(c, N, c->Xr64, 0, c->H64, 0, 1.0, nullptr, 0.0, c->G64, 0)) != cudaSuccess) return e;
+  if ((e = bgemm(c, N, c->G64, 0, c->Xr64, 1, 1.0, nullptr, 0.0, c->M64, 1)) != cudaSuccess) return e;
+  const int64_t n = (int64_t)(N + 1) * k * k;
   finish_m_kernel<<<nblocks(n, 256), 256, 0, c->stream>>>(N, k, c->kld, c->M64, c->Xr64, c->M32, c->Uwarm);
   return cudaGetLastError();
 }

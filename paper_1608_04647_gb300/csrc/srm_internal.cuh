@@ -35,7 +35,6 @@ enum KernelKind : int {
   KK_P_TC,
   KK_P_REDUCE,
   KK_Y_SUM,
-  KK_CHOL,
   KK_PHI,
   KK_ES,
   KK_SIGMA,
@@ -69,6 +68,9 @@ struct Ctx {
   int64_t Vtot = 0, Vpad_tot = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t side = nullptr;          // second stream for the M-step tail
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool side_pending = false;            // an M-step's tail has not run yet
 
   // ---- resident data
   void* Xh = nullptr;        // [Vpad_tot][ldT] store dtype, demeaned, zero padded
@@ -87,12 +89,13 @@ struct Ctx {
   double* scal = nullptr;       // [16] scalars of the current E-step (see k_small.cu)
   double* M64 = nullptr;        // [N][k][k] (A_i^T A_i)^-1/2
   float* M32 = nullptr;         // [N][kld][kld] FP32 copy used by the reduction
-  float* Uwarm = nullptr;       // [N][k][k] eigenvectors of the last Gram (warm start)
-  double* G64 = nullptr;        // [N][k][k] Gram matrices, then scratch
-  double* U64 = nullptr;        // [N][k][k] refined eigenvectors
-  double* H64 = nullptr;        // [N][k][k] scratch
-  double* Xr64 = nullptr;       // [N][k][k] re-orthonormalised eigenvectors
-  double* eigv = nullptr;       // [N][k] eigenvalues
+  // entries 0..N-1: subjects' Gram matrices; entry N: Sigma_s
+  float* Uwarm = nullptr;       // [N+1][k][k] last eigenvectors (Jacobi warm start)
+  double* G64 = nullptr;        // [N+1][k][k] Gram / Sigma_s^new, then U^T G U; entry N kept for Phi
+  double* U64 = nullptr;        // [N+1][k][k] FP32 Jacobi eigenvectors (promoted)
+  double* H64 = nullptr;        // [N+1][k][k] scratch
+  double* Xr64 = nullptr;       // [N+1][k][k] re-orthonormalised eigenvectors; entry N kept for Phi
+  double* eigv = nullptr;       // [N+1][k] eigenvalues
   double* Y = nullptr;          // [k][T] FP64 reduction sum_i rho_i^-2 W_i^T X^_i
   double* ES64 = nullptr;       // [k][T] E[S]
   float* ESt = nullptr;         // [ldT][kld] FP32 E[S]^T (plain-path operand)
@@ -173,9 +176,9 @@ cudaError_t launch_p_simt_generic(const void* A, bool a_bf16, int kld, int kq, c
 cudaError_t launch_a_simt(Ctx* c, int subject);
 
 // k_small.cu
+int es_blocks(int T);
 cudaError_t launch_p_reduce(Ctx* c);
 cudaError_t launch_y_sum(Ctx* c);
-cudaError_t launch_chol(Ctx* c);
 cudaError_t launch_phi(Ctx* c);
 cudaError_t launch_es(Ctx* c);
 cudaError_t launch_sigma(Ctx* c);
