@@ -21,6 +21,14 @@
 extern "C" {
 #endif
 SRM_API srm_status srm_debug_mma(int32_t mn_major, const void* A, const void* B, float* D, int32_t N, int32_t K);
+
+/*
+ * srm_debug_eig_sweeps -- diagnostics of the last M-step: the number of
+ * cyclic Jacobi sweeps each eigen-decomposition took (entries 0..N-1: the
+ * subjects' A_i^T A_i; entry N: Sigma_s).  Writes min(n, N + 1) ints to the
+ * host array out.  Synchronises.
+ */
+SRM_API srm_status srm_debug_eig_sweeps(srm_ctx* ctx, int32_t* out, int32_t n);
 #ifdef __cplusplus
 }
 #endif

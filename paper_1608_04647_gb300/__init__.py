@@ -26,6 +26,7 @@ __all__ = [
     "srm_init", "srm_estep", "srm_mstep", "srm_fit", "srm_transform", "srm_get_w", "srm_get_s",
     "srm_get_params", "srm_get_ll", "srm_synchronize", "srm_get_state", "srm_set_state",
     "srm_get_kernel_times", "srm_layout", "srm_last_error", "srm_destroy", "srm_debug_mma",
+    "srm_debug_eig_sweeps",
 ]
 
 SRM_OK, SRM_ERR_ARG, SRM_ERR_CUDA, SRM_ERR_NOMEM, SRM_ERR_NUMERIC, SRM_ERR_STATE, SRM_ERR_UNSUPPORTED = range(7)
@@ -92,6 +93,7 @@ def load_library(path: Optional[str] = None):
         "srm_layout": (st, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
         "srm_last_error": (ctypes.c_char_p, []),
         "srm_debug_mma": (st, [ctypes.c_int32, _P, _P, _P, ctypes.c_int32, ctypes.c_int32]),
+        "srm_debug_eig_sweeps": (st, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
         "srm_destroy": (None, [_P]),
     }
     for name, (res, args) in sig.items():
@@ -210,6 +212,14 @@ def srm_layout(ctx: int) -> dict:
 def srm_debug_mma(mn_major: int, A_ptr: int, B_ptr: int, D_ptr: int, N: int, K: int):
     """Self-test of the tensor-core building blocks (include/srm_debug.h)."""
     _check(load_library().srm_debug_mma(int(mn_major), _P(A_ptr), _P(B_ptr), _P(D_ptr), N, K), "srm_debug_mma")
+
+
+def srm_debug_eig_sweeps(ctx: int, n: int) -> np.ndarray:
+    """Jacobi sweeps of the last M-step per matrix (subjects, then Sigma_s)."""
+    out = np.zeros(n, dtype=np.int32)
+    _check(load_library().srm_debug_eig_sweeps(_P(ctx), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), n),
+           "srm_debug_eig_sweeps")
+    return out
 
 
 def srm_destroy(ctx: int):

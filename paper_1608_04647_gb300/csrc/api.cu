@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "srm_internal.cuh"
+#include "../../include/srm_debug.h"
 
 namespace srm {
 
@@ -97,7 +98,7 @@ void free_all(Ctx* c) {
   if (c->tc) tc_destroy(c);
   void* ptrs[] = {c->Xh, c->A, c->sqnorm, c->rowsq, c->d_off, c->d_v, c->rho2, c->Sigma, c->SigmaNext, c->L,
                   c->Phi, c->scal, c->M64, c->M32, c->Uwarm, c->G64, c->U64, c->H64, c->Xr64, c->eigv, c->Y,
-                  c->ES64, c->ESt, c->ESb, c->esPart, c->ll, c->iter, c->status, c->Ppart, c->chunk_src,
+                  c->ES64, c->ESt, c->ESb, c->esPart, c->ll, c->iter, c->status, c->Ppart, c->chunk_src, c->jac_sweeps,
                   c->chunk_src_off, c->Zbuf, c->Gpart, c->gslot_off, c->tr_buf, c->tr_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -195,6 +196,8 @@ srm_status do_side_chain(Ctx* c) {
   return SRM_OK;
 }
 
+}  // namespace
+
 // Runs a pending M-step tail on the main stream (before anything that reads
 // rho^2, M_i or Sigma_s).
 srm_status flush_pending(Ctx* c) {
@@ -203,6 +206,8 @@ srm_status flush_pending(Ctx* c) {
   c->side_pending = false;
   return SRM_OK;
 }
+
+namespace {
 
 srm_status do_estep(Ctx* c) {
   const bool overlap = c->side_pending;
@@ -258,7 +263,6 @@ constexpr uint64_t kStateMagic = 0x314d5253'50534743ull;
 
 using namespace srm;
 
-struct srm_ctx : public srm::Ctx {};
 
 extern "C" {
 
@@ -380,6 +384,7 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
   AL(H64, (int64_t)(N + 1) * k * k, "H64");
   AL(Xr64, (int64_t)(N + 1) * k * k, "Xr64");
   AL(eigv, (int64_t)(N + 1) * k, "eigenvalues");
+  AL(jac_sweeps, N + 1, "Jacobi sweep counts");
   AL(Y, (int64_t)k * T, "y");
   AL(ES64, (int64_t)k * T, "E[S]");
   AL(ll, c->max_iter, "ll trace");
@@ -776,6 +781,19 @@ srm_status srm_layout(srm_ctx* c, int64_t* out, int32_t n) {
                            c->Vpad_tot * c->ldT * (c->store == SRM_BF16 ? 2 : 4),
                            c->Vpad_tot * c->kld * (c->batched ? 2 : 4)};
   for (int j = 0; j < n && j < 5; ++j) out[j] = vals[j];
+  return SRM_OK;
+}
+
+srm_status srm_debug_eig_sweeps(srm_ctx* c, int32_t* out, int32_t n) {
+  TRY(valid_ctx(c));
+  if (!out || n < 0) {
+    set_error("srm_debug_eig_sweeps: null output");
+    return SRM_ERR_ARG;
+  }
+  TRY(flush_pending(c));
+  TRY(check_status(c));
+  const int m = std::min(n, c->N + 1);
+  if (m > 0) CK(cudaMemcpy(out, c->jac_sweeps, sizeof(int) * m, cudaMemcpyDeviceToHost));
   return SRM_OK;
 }
 

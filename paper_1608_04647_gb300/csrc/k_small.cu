@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(256) eig_kernel(int N, int k, int kld, const f
                                                   const int* __restrict__ gslot_off,
                                                   const double* __restrict__ SigmaNext, double* __restrict__ G64,
                                                   const float* __restrict__ Uwarm, double* __restrict__ U64,
-                                                  int* status) {
+                                                  int* __restrict__ sweeps_out, int* status) {
   extern __shared__ float eig_smem[];
   const int kk = k + (k & 1);
   const int ld = kk + 1;
@@ -380,7 +380,8 @@ __global__ void __launch_bounds__(256) eig_kernel(int N, int k, int kld, const f
     for (int a = 0; a < k; ++a) gm = fmaxf(gm, fabsf(Gs[a * ld + a]));
     gmax = gm;
   }
-  for (int sweep = 0; sweep < JAC_MAX_SWEEPS; ++sweep) {
+  int sweep = 0;
+  for (; sweep < JAC_MAX_SWEEPS; ++sweep) {
     if (tid == 0) nrot = 0;
     __syncthreads();
     const float thr = 1e-30f + JAC_TOL * gmax;
@@ -441,6 +442,7 @@ __global__ void __launch_bounds__(256) eig_kernel(int N, int k, int kld, const f
     if (converged) break;
   }
   if (!converged && tid == 0) flag(status, ST_EIG_NOCONV);
+  if (tid == 0 && sweeps_out) sweeps_out[i] = sweep + 1;
   // U_0 = U_w V
   double* Uo = U64 + (int64_t)i * k * k;
   for (int e = tid; e < k * k; e += blockDim.x) {
@@ -650,7 +652,7 @@ cudaError_t launch_eig(Ctx* c) {
   const int kk = c->k + (c->k & 1);
   const size_t sm = sizeof(float) * 3 * kk * (kk + 1);
   eig_kernel<<<c->N + 1, 256, sm, c->stream>>>(c->N, c->k, c->kld, c->Gpart, c->gslot_off, c->SigmaNext, c->G64,
-                                               c->Uwarm, c->U64, c->status);
+                                               c->Uwarm, c->U64, c->jac_sweeps, c->status);
   return cudaGetLastError();
 }
 

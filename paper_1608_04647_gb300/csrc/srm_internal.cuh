@@ -96,6 +96,7 @@ struct Ctx {
   double* H64 = nullptr;        // [N+1][k][k] scratch
   double* Xr64 = nullptr;       // [N+1][k][k] re-orthonormalised eigenvectors; entry N kept for Phi
   double* eigv = nullptr;       // [N+1][k] eigenvalues
+  int* jac_sweeps = nullptr;    // [N+1] Jacobi sweeps of the last M-step (diagnostics)
   double* Y = nullptr;          // [k][T] FP64 reduction sum_i rho_i^-2 W_i^T X^_i
   double* ES64 = nullptr;       // [k][T] E[S]
   float* ESt = nullptr;         // [ldT][kld] FP32 E[S]^T (plain-path operand)
@@ -151,6 +152,9 @@ struct Ctx {
   int64_t tr_part_elems = 0;
 };
 
+// runs a deferred M-step tail (api.cu)
+srm_status flush_pending(Ctx* c);
+
 // error helpers (api.cu)
 void set_error(const std::string& msg);
 srm_status cuda_fail(cudaError_t e, const char* what);
@@ -199,3 +203,6 @@ cudaError_t launch_p_tc(Ctx* c);
 cudaError_t launch_a_tc(Ctx* c);
 
 }  // namespace srm
+
+// The opaque handle of the C ABI is the context itself.
+struct srm_ctx : public srm::Ctx {};

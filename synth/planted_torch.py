@@ -9,17 +9,24 @@ from __future__ import annotations
 import math
 from typing import List, Optional, Sequence
 
+import numpy as np
 import torch
 
 from .planted import PlantedSpec, draw_voxel_counts, planted_rho2
 
 
 def _orthonormal(v: int, k: int, gen: torch.Generator, device) -> torch.Tensor:
-    g = torch.randn(v, k, generator=gen, device=device, dtype=torch.float32)
-    q, r = torch.linalg.qr(g)
-    s = torch.sign(torch.diagonal(r))
-    s[s == 0] = 1.0
-    return (q * s[None, :]).contiguous()
+    """Q of the QR factorisation of a Gaussian v x k matrix with diag(R) > 0,
+    computed as Cholesky-QR applied twice (the large products on the device,
+    the k x k Cholesky factor on the host), so that no device linear-algebra
+    library is needed."""
+    q = torch.randn(v, k, generator=gen, device=device, dtype=torch.float32)
+    for _ in range(2):
+        g = (q.T.double() @ q.double()).cpu().numpy()
+        r = np.linalg.cholesky(g).T  # upper, positive diagonal
+        rinv = torch.from_numpy(np.linalg.inv(r)).to(device)
+        q = (q.double() @ rinv).float()
+    return q.contiguous()
 
 
 def planted_dataset_torch(spec: PlantedSpec, voxel_counts: Optional[Sequence[int]] = None, device="cuda",
