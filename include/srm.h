@@ -148,6 +148,34 @@ SRM_API srm_status srm_fit(srm_ctx* ctx, int32_t n_iter, double* ll_host);
 SRM_API srm_status srm_transform(srm_ctx* ctx, int32_t subject, const void* X_new_dev, int32_t T_new,
                          float* S_out_dev);
 
+/*
+ * srm_transform_noalloc -- the same result as srm_transform, for callers that
+ * must not allocate device memory: code that runs while a CUDA stream is
+ * being captured into a graph (an allocation there breaks the capture),
+ * real-time or latency-bound loops where a cudaMalloc would synchronise the
+ * device, and hosts whose memory is pre-assigned by a pool or another
+ * framework.  srm_transform allocates (and grows) its scratch on first use;
+ * this entry point allocates nothing: no cudaMalloc, no cudaFree and no
+ * allocating library routine.  The paper has no counterpart.
+ *
+ * Scratch lives in one fixed device array of 16 MiB compiled into the
+ * library (every GPU that loads the library holds it until the process
+ * exits).  A call needs 4 * v_i bytes (rounded up to 256) for the row means
+ * plus 64 * kld * 4 bytes per 64 columns of X_new for one v-split (kld = k
+ * padded: to 64 or 128 in the batched form, to a multiple of 16 in the plain
+ * form); larger requests return SRM_ERR_ARG with the sizes in
+ * srm_last_error().  Arguments, layout and result are those of srm_transform.
+ *
+ * The first call on a device (with that device current) looks up the
+ * device address of the array once; make that first call before any stream
+ * capture.  Every call uses the same array and overwrites what it reads, so
+ * nothing needs clearing, but calls whose work overlaps on the GPU (on
+ * different streams, or from different contexts of one process on one
+ * device) race on the array: order them on one stream.  Asynchronous.
+ */
+SRM_API srm_status srm_transform_noalloc(srm_ctx* ctx, int32_t subject, const void* X_new_dev, int32_t T_new,
+                                         float* S_out_dev);
+
 /* srm_get_w -- W_i = A_i (A_i^T A_i)^-1/2 (eq:srm_mapping_update) materialised as
  * v_i x k row-major FP32 into W_dev (device, caller-owned).  Asynchronous. */
 SRM_API srm_status srm_get_w(srm_ctx* ctx, int32_t subject, float* W_dev);

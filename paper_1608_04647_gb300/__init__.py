@@ -26,7 +26,7 @@ __all__ = [
     "srm_init", "srm_estep", "srm_mstep", "srm_fit", "srm_transform", "srm_get_w", "srm_get_s",
     "srm_get_params", "srm_get_ll", "srm_synchronize", "srm_get_state", "srm_set_state",
     "srm_get_kernel_times", "srm_layout", "srm_last_error", "srm_destroy", "srm_debug_mma",
-    "srm_debug_eig_sweeps",
+    "srm_transform_noalloc", "srm_debug_eig_sweeps",
 ]
 
 SRM_OK, SRM_ERR_ARG, SRM_ERR_CUDA, SRM_ERR_NOMEM, SRM_ERR_NUMERIC, SRM_ERR_STATE, SRM_ERR_UNSUPPORTED = range(7)
@@ -93,6 +93,7 @@ def load_library(path: Optional[str] = None):
         "srm_layout": (st, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
         "srm_last_error": (ctypes.c_char_p, []),
         "srm_debug_mma": (st, [ctypes.c_int32, _P, _P, _P, ctypes.c_int32, ctypes.c_int32]),
+        "srm_transform_noalloc": (st, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
         "srm_debug_eig_sweeps": (st, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
         "srm_destroy": (None, [_P]),
     }
@@ -144,6 +145,13 @@ def srm_fit_async(ctx: int, n_iter: int):
 
 def srm_transform(ctx: int, subject: int, X_new_ptr: int, T_new: int, S_out_ptr: int):
     _check(load_library().srm_transform(_P(ctx), subject, _P(X_new_ptr), T_new, _P(S_out_ptr)), "srm_transform")
+
+
+def srm_transform_noalloc(ctx: int, subject: int, X_new_ptr: int, T_new: int, S_out_ptr: int):
+    """srm_transform for callers that must not allocate device memory: scratch
+    comes from a fixed 16 MiB device array inside the library (see srm.h)."""
+    _check(load_library().srm_transform_noalloc(_P(ctx), subject, _P(X_new_ptr), T_new, _P(S_out_ptr)),
+           "srm_transform_noalloc")
 
 
 def srm_get_w(ctx: int, subject: int, W_ptr: int):
