@@ -61,7 +61,20 @@ __global__ void __launch_bounds__(256) p_reduce_kernel(int N, int T, int k, int 
   const int n4 = TCH * kld / 4;
   for (int e4 = threadIdx.x; e4 < n4; e4 += blockDim.x) {
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int s = b; s < en; ++s) {
+    int s = b;
+    for (; s + 4 <= en; s += 4) {  // four independent loads in flight, summed in order
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = __ldg(reinterpret_cast<const float4*>(part + src[s + u].off) + e4);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        acc.x += v[u].x;
+        acc.y += v[u].y;
+        acc.z += v[u].z;
+        acc.w += v[u].w;
+      }
+    }
+    for (; s < en; ++s) {
       const float4 v = __ldg(reinterpret_cast<const float4*>(part + src[s].off) + e4);
       acc.x += v.x;
       acc.y += v.y;
@@ -257,30 +270,53 @@ __global__ void __launch_bounds__(256) es_kernel(int N, int k, int T, int kld, i
   }
 }
 
-// grid k blocks (row a of Sigma_s^new); block 0 also finishes the likelihood.
-__global__ void __launch_bounds__(128) sigma_kernel(int k, int T, int nblk, double Vtot, const double* __restrict__ Phi,
+// grid k blocks (row a of Sigma_s^new), 256 threads: element b of the row is
+// summed over the nblk partials by SIG_SPLIT threads (contiguous q ranges),
+// combined in a fixed order; block 0 also finishes the likelihood.
+constexpr int SIG_SPLIT = 4;
+
+__global__ void __launch_bounds__(256) sigma_kernel(int k, int T, int nblk, double Vtot, const double* __restrict__ Phi,
                                                     const double* __restrict__ part, double* __restrict__ SigmaNext,
                                                     double* __restrict__ scal, double* __restrict__ ll, int* iter,
                                                     int max_iter, int* status) {
-  __shared__ double red[128];
-  const int a = blockIdx.x;
-  for (int b = threadIdx.x; b < k; b += blockDim.x) {
+  __shared__ double red[256];
+  __shared__ double ps[SIG_SPLIT][KMAX];
+  const int a = blockIdx.x, tid = threadIdx.x;
+  const int64_t stride = (int64_t)k * k + 1;
+  for (int e = tid; e < SIG_SPLIT * k; e += blockDim.x) {
+    const int g = e / k, b = e - g * k;
+    const int q0 = (nblk * g) / SIG_SPLIT, q1 = (nblk * (g + 1)) / SIG_SPLIT;
     double s = 0.0;
-    for (int q = 0; q < nblk; ++q) s += part[(int64_t)q * (k * k + 1) + a * k + b];
+    int q = q0;
+    for (; q + 4 <= q1; q += 4) {
+      const double x0 = part[(int64_t)q * stride + a * k + b], x1 = part[(int64_t)(q + 1) * stride + a * k + b];
+      const double x2 = part[(int64_t)(q + 2) * stride + a * k + b], x3 = part[(int64_t)(q + 3) * stride + a * k + b];
+      s += x0;
+      s += x1;
+      s += x2;
+      s += x3;
+    }
+    for (; q < q1; ++q) s += part[(int64_t)q * stride + a * k + b];
+    ps[g][b] = s;
+  }
+  __syncthreads();
+  for (int b = tid; b < k; b += blockDim.x) {
+    double s = 0.0;
+    for (int g = 0; g < SIG_SPLIT; ++g) s += ps[g][b];
     const double v = 0.5 * (Phi[a * k + b] + Phi[b * k + a]) + s / (double)T;
     if (!isfinite(v)) flag(status, ST_NONFINITE);
     SigmaNext[a * k + b] = v;
   }
   if (a == 0) {
     double ye = 0.0;
-    for (int q = threadIdx.x; q < nblk; q += blockDim.x) ye += part[(int64_t)q * (k * k + 1) + k * k];
-    red[threadIdx.x] = ye;
+    for (int q = tid; q < nblk; q += blockDim.x) ye += part[(int64_t)q * stride + k * k];
+    red[tid] = ye;
     __syncthreads();
-    for (int s = 64; s > 0; s >>= 1) {
-      if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    for (int st = 128; st > 0; st >>= 1) {
+      if (tid < st) red[tid] += red[tid + st];
       __syncthreads();
     }
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       ye = red[0];
       scal[SC_YPHIY] = ye;
       const double L = -0.5 * ((double)T * Vtot * 1.8378770664093454835606594728112 + (double)T * scal[SC_VLOGRHO] +
@@ -294,146 +330,131 @@ __global__ void __launch_bounds__(128) sigma_kernel(int k, int T, int nblk, doub
 }
 
 // ------------------------------------------------------------------ M-step
-// Jacobi tolerances (FP32): a pair is rotated while |g_pq| > JAC_TOL g_max
-// (g_max = largest diagonal entry, i.e. about |G|_2).  FP32 rounding keeps
-// refreshing off-diagonal noise of a few 1e-7 g_max, so the sweep loop ends
-// after a sweep in which no off-diagonal entry exceeded JAC_STOP g_max; that
-// sweep still rotates the smaller ones.  What remains (~1e-6 g_max) is
-// removed to second order by the FP64 refinement.
-constexpr float JAC_TOL = 1e-6f;
-constexpr float JAC_STOP = 4e-6f;
 constexpr int JAC_MAX_SWEEPS = 24;
 
 // One block per symmetric matrix: blocks 0..N-1 take G_i from the Gram
-// partials, block N takes Sigma_s^new.  FP32 cyclic Jacobi on U_w^T G U_w
-// (U_w = previous eigenvectors), round-robin ordering: kk/2 disjoint
-// rotations per round, each 2x2 block of G transformed by one thread
-// (J_p^T G_pq J_q), so a round needs two barriers.  Output U_0 = U_w V (FP64).
-__global__ void __launch_bounds__(256) eig_kernel(int N, int k, int kld, const float* __restrict__ gpart,
-                                                  const int* __restrict__ gslot_off,
-                                                  const double* __restrict__ SigmaNext, double* __restrict__ G64,
-                                                  const float* __restrict__ Uwarm, double* __restrict__ U64,
-                                                  int* __restrict__ sweeps_out, int* status) {
+// partials, block N takes Sigma_s^new.  FP32 one-sided (Hestenes) Jacobi:
+// the columns of Y = G V are made mutually orthogonal by plane rotations
+// applied to the columns of Y and V alike, starting from V = U_w (the
+// previous eigenvectors).  When they are orthogonal, V diagonalises G^2 and
+// hence G (G is symmetric positive semi-definite).  Round-robin ordering of
+// the column pairs; one warp owns one pair in a round: it holds the two
+// columns of Y and of V in registers, forms their Gram entries with warp
+// reductions, rotates, and writes them back; one barrier per round.
+// A pair is rotated while |y_p.y_q| > OSJ_TOL |y_p| |y_q| (FP32 dot products
+// of nearly orthogonal columns carry noise of a few 1e-7 relative); the sweep
+// loop ends after a sweep with no pair above OSJ_STOP, at most
+// JAC_MAX_SWEEPS sweeps.  The remaining off-diagonal part of V^T G V
+// (about OSJ_TOL min(lambda_p, lambda_q)) is removed to second order by the
+// FP64 refinement.  Output U_0 = V (FP64).
+constexpr float OSJ_TOL = 2e-6f;
+constexpr float OSJ_STOP = 8e-6f;
+
+template <int RPL>  // rows per lane: kk <= 32 * RPL
+__global__ void __launch_bounds__(1024) eig_kernel(int N, int k, int kld, const float* __restrict__ gpart,
+                                                   const int* __restrict__ gslot_off,
+                                                   const double* __restrict__ SigmaNext, double* __restrict__ G64,
+                                                   const float* __restrict__ Uwarm, double* __restrict__ U64,
+                                                   int* __restrict__ sweeps_out, int* status) {
   extern __shared__ float eig_smem[];
   const int kk = k + (k & 1);
-  const int ld = kk + 1;
-  float* Gs = eig_smem;         // [kk][ld]
-  float* Vs = Gs + kk * ld;     // [kk][ld]
-  float* Us = Vs + kk * ld;     // [kk][ld]
-  __shared__ float cs[KMAX / 2][2];
-  __shared__ int pq[KMAX / 2][2];
+  float* Gs = eig_smem;           // [kk][kk] G (symmetric)
+  float* Yc = Gs + kk * kk;       // columns of Y: column j at Yc + j * kk
+  float* Vc = Yc + kk * kk;       // columns of V
+  uint16_t* tab = reinterpret_cast<uint16_t*>(Vc + kk * kk);  // [kk-1][kk/2]: p | q << 8
   __shared__ int nrot;
-  __shared__ float gmax;
-  const int i = blockIdx.x, tid = threadIdx.x;
+  const int i = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
   double* Gi = G64 + (int64_t)i * k * k;
+  const float* Uw = Uwarm + (int64_t)i * k * k;
+  const int npair = kk / 2;
+  for (int e = tid; e < (kk - 1) * npair; e += nt) {
+    const int round = e / npair, j = e - round * npair;
+    const int pa = (j == 0) ? 0 : 1 + ((j - 1 + round) % (kk - 1));
+    const int pb = 1 + ((kk - 2 - j + round) % (kk - 1));
+    tab[e] = (uint16_t)(min(pa, pb) | (max(pa, pb) << 8));
+  }
   if (i < N) {
     const int s0 = gslot_off[i], s1 = gslot_off[i + 1];
-    for (int e = tid; e < k * k; e += blockDim.x) {
+    for (int e = tid; e < k * k; e += nt) {
       const int a = e / k, b = e % k;
-      double s = 0.0;
-      for (int q = s0; q < s1; ++q) s += (double)gpart[(int64_t)q * kld * kld + a * kld + b];
-      Gi[e] = s;
+      double sum = 0.0;
+      for (int q = s0; q < s1; ++q) sum += (double)gpart[(int64_t)q * kld * kld + a * kld + b];
+      Gi[e] = sum;
     }
   } else {
-    for (int e = tid; e < k * k; e += blockDim.x) Gi[e] = SigmaNext[e];
+    for (int e = tid; e < k * k; e += nt) Gi[e] = SigmaNext[e];
   }
   __syncthreads();
-  for (int e = tid; e < kk * kk; e += blockDim.x) {
+  // Gs = G (symmetrised, FP32; the padding row/column is zero), Vc = U_w (padded with e_k)
+  for (int e = tid; e < kk * kk; e += nt) {
     const int a = e / kk, b = e % kk;
-    float g, u;
+    float g = 0.f, u;
     if (a < k && b < k) {
       g = (float)(0.5 * (Gi[a * k + b] + Gi[b * k + a]));
-      u = Uwarm[(int64_t)i * k * k + a * k + b];
+      u = Uw[a * k + b];
     } else {
-      g = (a == b) ? 1.f : 0.f;
-      u = g;
+      u = (a == b) ? 1.f : 0.f;
     }
     if (!isfinite(g)) flag(status, ST_NONFINITE);
-    Gs[a * ld + b] = g;
-    Us[a * ld + b] = u;
+    Gs[a * kk + b] = g;
+    Vc[b * kk + a] = u;  // column b, row a
   }
   __syncthreads();
-  // rotate into the warm basis: Vs = G U, Gs = U^T Vs
-  for (int e = tid; e < kk * kk; e += blockDim.x) {
-    const int a = e / kk, b = e % kk;
-    float s = 0.f;
-    for (int m = 0; m < kk; ++m) s = fmaf(Gs[a * ld + m], Us[m * ld + b], s);
-    Vs[a * ld + b] = s;
+  // Y = G V (column-major)
+  for (int e = tid; e < kk * kk; e += nt) {
+    const int j = e / kk, r = e % kk;
+    float sum = 0.f;
+    for (int m = 0; m < kk; ++m) sum = fmaf(Gs[r * kk + m], Vc[j * kk + m], sum);
+    Yc[j * kk + r] = sum;
   }
-  __syncthreads();
-  for (int e = tid; e < kk * kk; e += blockDim.x) {
-    const int a = e / kk, b = e % kk;
-    float s = 0.f;
-    for (int m = 0; m < kk; ++m) s = fmaf(Us[m * ld + a], Vs[m * ld + b], s);
-    Gs[a * ld + b] = s;
-  }
-  __syncthreads();
-  for (int e = tid; e < kk * kk; e += blockDim.x) {
-    const int a = e / kk, b = e % kk;
-    Vs[a * ld + b] = (a == b) ? 1.f : 0.f;
-  }
-  const int npair = kk / 2;
   bool converged = false;
-  __syncthreads();
-  if (tid == 0) {
-    float gm = 0.f;
-    for (int a = 0; a < k; ++a) gm = fmaxf(gm, fabsf(Gs[a * ld + a]));
-    gmax = gm;
-  }
   int sweep = 0;
   for (; sweep < JAC_MAX_SWEEPS; ++sweep) {
     if (tid == 0) nrot = 0;
     __syncthreads();
-    const float thr = 1e-30f + JAC_TOL * gmax;
-    const float big = JAC_STOP * gmax;
     for (int round = 0; round < kk - 1; ++round) {
-      if (tid < npair) {
-        const int j = tid;
-        const int pa = (j == 0) ? 0 : 1 + ((j - 1 + round) % (kk - 1));
-        const int pb = 1 + ((kk - 2 - j + round) % (kk - 1));
-        const int p = min(pa, pb), q = max(pa, pb);
-        float c = 1.f, s = 0.f;
-        if (q < k) {
-          const float gpq = Gs[p * ld + q];
-          const float gpp = Gs[p * ld + p], gqq = Gs[q * ld + q];
-          if (fabsf(gpq) > thr) {
-            const float tau = (gqq - gpp) / (2.f * gpq);
-            const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-            c = rsqrtf(1.f + t * t);
-            s = t * c;
-            if (fabsf(gpq) > big) atomicAdd(&nrot, 1);
-          }
+      for (int j = warp; j < npair; j += nw) {
+        const uint16_t tq = tab[round * npair + j];
+        const int p = tq & 255, q = tq >> 8;
+        float yp[RPL], yq[RPL], vp[RPL], vq[RPL];
+        float a = 0.f, b = 0.f, g = 0.f;
+#pragma unroll
+        for (int u = 0; u < RPL; ++u) {
+          const int r = lane + 32 * u;
+          const bool in = r < kk;
+          yp[u] = in ? Yc[p * kk + r] : 0.f;
+          yq[u] = in ? Yc[q * kk + r] : 0.f;
+          vp[u] = in ? Vc[p * kk + r] : 0.f;
+          vq[u] = in ? Vc[q * kk + r] : 0.f;
+          a = fmaf(yp[u], yp[u], a);
+          b = fmaf(yq[u], yq[u], b);
+          g = fmaf(yp[u], yq[u], g);
         }
-        cs[j][0] = c;
-        cs[j][1] = s;
-        pq[j][0] = p;
-        pq[j][1] = q;
-      }
-      __syncthreads();
-      // G <- J^T G J, one 2x2 block (rows of pair j, columns of pair l) per item
-      for (int e = tid; e < npair * npair; e += blockDim.x) {
-        const int j = e / npair, l = e % npair;
-        const float cj = cs[j][0], sj = cs[j][1], cl = cs[l][0], sl = cs[l][1];
-        if (sj == 0.f && sl == 0.f) continue;
-        const int pj = pq[j][0], qj = pq[j][1], pl = pq[l][0], ql = pq[l][1];
-        const float g00 = Gs[pj * ld + pl], g01 = Gs[pj * ld + ql];
-        const float g10 = Gs[qj * ld + pl], g11 = Gs[qj * ld + ql];
-        const float r00 = cj * g00 - sj * g10, r01 = cj * g01 - sj * g11;
-        const float r10 = sj * g00 + cj * g10, r11 = sj * g01 + cj * g11;
-        Gs[pj * ld + pl] = cl * r00 - sl * r01;
-        Gs[pj * ld + ql] = sl * r00 + cl * r01;
-        Gs[qj * ld + pl] = cl * r10 - sl * r11;
-        Gs[qj * ld + ql] = sl * r10 + cl * r11;
-      }
-      // V <- V J
-      for (int e = tid; e < npair * kk; e += blockDim.x) {
-        const int l = e / kk, row = e % kk;
-        const float cl = cs[l][0], sl = cs[l][1];
-        if (sl == 0.f) continue;
-        const int pl = pq[l][0], ql = pq[l][1];
-        const float vp = Vs[row * ld + pl], vq = Vs[row * ld + ql];
-        Vs[row * ld + pl] = cl * vp - sl * vq;
-        Vs[row * ld + ql] = sl * vp + cl * vq;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          g += __shfl_xor_sync(0xffffffffu, g, o);
+        }
+        const float ag = fabsf(g), sab = sqrtf(a * b);
+        if (q < k && ag > OSJ_TOL * sab && ag > 1e-30f) {
+          const float tau = (b - a) * __fdividef(1.f, 2.f * g);
+          const float w = 1.f + tau * tau;
+          const float t = copysignf(__fdividef(1.f, fabsf(tau) + w * rsqrtf(w)), tau);
+          const float c = rsqrtf(1.f + t * t), sn = t * c;
+#pragma unroll
+          for (int u = 0; u < RPL; ++u) {
+            const int r = lane + 32 * u;
+            if (r < kk) {
+              Yc[p * kk + r] = c * yp[u] - sn * yq[u];
+              Yc[q * kk + r] = sn * yp[u] + c * yq[u];
+              Vc[p * kk + r] = c * vp[u] - sn * vq[u];
+              Vc[q * kk + r] = sn * vp[u] + c * vq[u];
+            }
+          }
+          if (lane == 0 && ag > OSJ_STOP * sab) atomicAdd(&nrot, 1);
+        }
       }
       __syncthreads();
     }
@@ -443,14 +464,22 @@ __global__ void __launch_bounds__(256) eig_kernel(int N, int k, int kld, const f
   }
   if (!converged && tid == 0) flag(status, ST_EIG_NOCONV);
   if (tid == 0 && sweeps_out) sweeps_out[i] = sweep + 1;
-  // U_0 = U_w V
+  // U_0 = V
   double* Uo = U64 + (int64_t)i * k * k;
-  for (int e = tid; e < k * k; e += blockDim.x) {
+  for (int e = tid; e < k * k; e += nt) {
     const int a = e / k, b = e % k;
-    float s = 0.f;
-    for (int m = 0; m < kk; ++m) s = fmaf(Us[a * ld + m], Vs[m * ld + b], s);
-    Uo[e] = (double)s;
+    Uo[e] = (double)Vc[b * kk + a];
   }
+}
+
+size_t eig_smem_bytes(int k) {
+  const int kk = k + (k & 1);
+  return sizeof(float) * 3 * kk * kk + sizeof(uint16_t) * (kk - 1) * (kk / 2) + 16;
+}
+
+int eig_threads(int k) {
+  const int npair = (k + (k & 1)) / 2;
+  return 32 * (npair < 32 ? (npair < 1 ? 1 : npair) : 32);
 }
 
 // D_b = alpha op(A_b) op(B_b) + beta C_b for a batch of k x k FP64 matrices.
@@ -506,51 +535,62 @@ __global__ void __launch_bounds__(128) dk_rho_kernel(int N, int k, int T, const 
                                                      double* __restrict__ rho2, double* __restrict__ scal,
                                                      int* status) {
   __shared__ double sq[KMAX];
-  __shared__ double red[128];
-  __shared__ double lmax_s;
+  __shared__ double red[3][128];
   const int i = blockIdx.x, tid = threadIdx.x;
   const double* G = Gp + (int64_t)i * k * k;
-  if (tid == 0) {
-    double lm = 0.0;
-    for (int a = 0; a < k; ++a) lm = fmax(lm, G[a * k + a]);
-    lmax_s = lm;
+  // lambda = diag(G'), its maximum, tr Sigma_s^new (parallel, fixed-order tree)
+  double lam = 0.0, lm = 0.0, tr = 0.0;
+  if (tid < k) {
+    lam = G[tid * k + tid];
+    lm = lam;
+    tr = SigmaNext[tid * k + tid];
   }
+  red[0][tid] = lm;
+  red[1][tid] = tr;
   __syncthreads();
-  const double lmax = lmax_s;
-  for (int a = tid; a < k; a += blockDim.x) {
-    const double l = G[a * k + a];
-    if (!(l > 1e-12 * lmax) || !isfinite(l)) flag(status, i < N ? ST_RANK : ST_NOT_PD);
-    const double lc = l > 1e-300 ? l : 1e-300;
-    sq[a] = sqrt(lc);
-    eigv[(int64_t)i * k + a] = l;
+  for (int st = 64; st > 0; st >>= 1) {
+    if (tid < st) {
+      red[0][tid] = fmax(red[0][tid], red[0][tid + st]);
+      red[1][tid] += red[1][tid + st];
+    }
+    __syncthreads();
+  }
+  const double lmax = red[0][0], trS = red[1][0];
+  if (tid < k) {
+    if (!(lam > 1e-12 * lmax) || !isfinite(lam)) flag(status, i < N ? ST_RANK : ST_NOT_PD);
+    sq[tid] = sqrt(lam > 1e-300 ? lam : 1e-300);
+    eigv[(int64_t)i * k + tid] = lam;
   }
   if (i == 0)
     for (int e = tid; e < k * k; e += blockDim.x) Sigma[e] = SigmaNext[e];
   if (i >= N) return;
   __syncthreads();
+  // off-diagonal divided differences are multiplied by E = O(1e-6 |G|), so
+  // FP32 factors keep B to FP64 accuracy
   double* Bm = Bout + (int64_t)i * k * k;
   for (int e = tid; e < k * k; e += blockDim.x) {
-    const int a = e / k, b = e % k;
+    const int a = e / k, b = e - a * k;
     double v;
-    if (a == b) v = 1.0 / sq[a];
-    else v = -0.5 * (G[a * k + b] + G[b * k + a]) / (sq[a] * sq[b] * (sq[a] + sq[b]));
+    if (a == b) {
+      v = 1.0 / sq[a];
+    } else {
+      const float sa = (float)sq[a], sb = (float)sq[b];
+      const float f = -1.f / (sa * sb * (sa + sb));
+      v = (double)f * (0.5 * (G[a * k + b] + G[b * k + a]));
+    }
     Bm[e] = v;
   }
-  double nuc = 0.0;
-  for (int a = tid; a < k; a += blockDim.x) nuc += sq[a];
-  red[tid] = nuc;
+  red[2][tid] = (tid < k) ? sq[tid] : 0.0;
   __syncthreads();
-  for (int s = 64; s > 0; s >>= 1) {
-    if (tid < s) red[tid] += red[tid + s];
+  for (int st = 64; st > 0; st >>= 1) {
+    if (tid < st) red[2][tid] += red[2][tid + st];
     __syncthreads();
   }
   if (tid == 0) {
-    double tr = 0.0;
-    for (int a = 0; a < k; ++a) tr += SigmaNext[a * k + a];
-    const double r = (sqnorm[i] - 2.0 * red[0] + (double)T * tr) / ((double)T * (double)vox[i]);
+    const double r = (sqnorm[i] - 2.0 * red[2][0] + (double)T * trS) / ((double)T * (double)vox[i]);
     if (!(r > 0.0) || !isfinite(r)) flag(status, ST_NONFINITE);
     rho2[i] = r;
-    if (i == 0) scal[SC_TRSIG] = tr;
+    if (i == 0) scal[SC_TRSIG] = trS;
   }
 }
 
@@ -606,7 +646,9 @@ int es_blocks(int T) { return (T + ES_T - 1) / ES_T; }
 
 void prepare_small_kernels(int max_smem) {
   cudaFuncSetAttribute(p_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-  cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 4 * 1024);
+  cudaFuncSetAttribute(eig_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 4 * 1024);
+  cudaFuncSetAttribute(eig_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 4 * 1024);
+  cudaFuncSetAttribute(eig_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 4 * 1024);
   cudaFuncSetAttribute(bgemm64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   cudaFuncSetAttribute(es_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   cudaFuncSetAttribute(phi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
@@ -643,16 +685,24 @@ cudaError_t launch_es(Ctx* c) {
 }
 
 cudaError_t launch_sigma(Ctx* c) {
-  sigma_kernel<<<c->k, 128, 0, c->stream>>>(c->k, c->T, c->nes_blk, (double)c->Vtot, c->Phi, c->esPart, c->SigmaNext,
+  sigma_kernel<<<c->k, 256, 0, c->stream>>>(c->k, c->T, c->nes_blk, (double)c->Vtot, c->Phi, c->esPart, c->SigmaNext,
                                             c->scal, c->ll, c->iter, c->max_iter, c->status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_eig(Ctx* c) {
+  const size_t sm = eig_smem_bytes(c->k);
+  const int nt = eig_threads(c->k);
   const int kk = c->k + (c->k & 1);
-  const size_t sm = sizeof(float) * 3 * kk * (kk + 1);
-  eig_kernel<<<c->N + 1, 256, sm, c->stream>>>(c->N, c->k, c->kld, c->Gpart, c->gslot_off, c->SigmaNext, c->G64,
-                                               c->Uwarm, c->U64, c->jac_sweeps, c->status);
+  if (kk <= 32)
+    eig_kernel<1><<<c->N + 1, nt, sm, c->stream>>>(c->N, c->k, c->kld, c->Gpart, c->gslot_off, c->SigmaNext, c->G64,
+                                                   c->Uwarm, c->U64, c->jac_sweeps, c->status);
+  else if (kk <= 64)
+    eig_kernel<2><<<c->N + 1, nt, sm, c->stream>>>(c->N, c->k, c->kld, c->Gpart, c->gslot_off, c->SigmaNext, c->G64,
+                                                   c->Uwarm, c->U64, c->jac_sweeps, c->status);
+  else
+    eig_kernel<4><<<c->N + 1, nt, sm, c->stream>>>(c->N, c->k, c->kld, c->Gpart, c->gslot_off, c->SigmaNext, c->G64,
+                                                   c->Uwarm, c->U64, c->jac_sweeps, c->status);
   return cudaGetLastError();
 }
 
