@@ -650,6 +650,11 @@ void prepare_small_kernels(int max_smem) {
   cudaFuncSetAttribute(eig_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 4 * 1024);
   cudaFuncSetAttribute(eig_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 4 * 1024);
   cudaFuncSetAttribute(bgemm64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  // these run beside the E-pass: take the SM's full shared-memory carve-out too
+  cudaFuncSetAttribute(eig_kernel<1>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(eig_kernel<2>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(eig_kernel<4>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(bgemm64_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   cudaFuncSetAttribute(es_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   cudaFuncSetAttribute(phi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
 }

@@ -56,6 +56,8 @@ struct TcState {
   SegM* d_seg = nullptr;
   int* d_seg_off = nullptr;
   int grid = 0;
+  bool m_res = false;   // M-pass keeps E[S] resident in shared memory
+  size_t m_smem = 0;
 };
 
 // Warp-uniform bounded wait (all lanes agree on the outcome).
@@ -63,12 +65,29 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
   bool ok = mbar_wait(bar, parity, abort, status, ST_TIMEOUT);
   return __all_sync(0xffffffffu, ok);
 }
+// The same for waits that span a whole work item (lane 0 polls with back-off).
+__device__ __forceinline__ bool warp_wait_patient(uint64_t* bar, uint32_t parity, volatile int* abort, int* status) {
+  bool ok = true;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait_patient(bar, parity, abort, status, ST_TIMEOUT, 2048);
+  ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+  return ok && mbar_try_wait(bar, parity);
+}
 
 __host__ __device__ constexpr uint32_t e_stage_bytes(int kld) { return 8u * E_KR * 128u + (uint32_t)(kld / 64) * E_KR * 128u; }
 __host__ __device__ constexpr uint32_t m_stage_bytes(int kld) { return 128u * 128u + (uint32_t)kld * 128u; }
 constexpr uint32_t kBarBytes = 256;
 constexpr size_t e_smem_bytes(int kld) { return 1024 + (size_t)E_STAGES * e_stage_bytes(kld) + kBarBytes; }
-constexpr size_t m_smem_bytes(int kld) { return 1024 + (size_t)M_STAGES * m_stage_bytes(kld) + 65536 + kBarBytes; }
+// Gram operand buffers: kld = 64 uses one feature atom per buffer plus one
+// shared zero atom (48 KB); kld = 128 uses two atoms per buffer (64 KB).
+__host__ __device__ constexpr uint32_t gop_bytes(int kld) { return kld == 64 ? 49152u : 65536u; }
+constexpr int M_STAGES_RES = 3;  // stages when E[S] is resident (X tiles only)
+constexpr size_t m_smem_bytes(int kld) {
+  return 1024 + (size_t)M_STAGES * m_stage_bytes(kld) + gop_bytes(kld) + kBarBytes;
+}
+constexpr size_t m_smem_bytes_res(int kld, int nk) {
+  return 1024 + (size_t)M_STAGES_RES * 16384u + (size_t)nk * kld * 128u + gop_bytes(kld) + kBarBytes;
+}
+constexpr size_t kMaxSmem = 232448;  // opt-in limit per block
 
 // ------------------------------------------------------------------ E-pass
 template <int KLD>
@@ -206,7 +225,7 @@ __global__ void __launch_bounds__(NT, 1)
     for (int w = w0; w < w1; ++w) {
       const WorkE it = work[w];
       const int n_mt = min(4, (T - it.tb * E_TB + 127) / 128);
-      if (!warp_wait(acc_full, acc_ph, abort_s, status)) break;
+      if (!warp_wait_patient(acc_full, acc_ph, abort_s, status)) break;
       acc_ph ^= 1u;
       tc_fence_after();
       float* slot = part + (int64_t)it.slot * E_TB * KLD;
@@ -235,14 +254,18 @@ __global__ void __launch_bounds__(NT, 1)
 }
 
 // ------------------------------------------------------------------ M-pass
-template <int KLD>
+// RES: E[S] (all 64-column chunks, kld rows each) is loaded once per CTA and
+// stays in shared memory; the stages then carry X^ tiles only.  Otherwise
+// every stage carries an X^ tile and the matching E[S] chunk.
+template <int KLD, bool RES>
 __global__ void __launch_bounds__(NT, 1)
     mstep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE,
                     const SegM* __restrict__ segs, const int* __restrict__ seg_off, int T,
                     __nv_bfloat16* __restrict__ Aout, float* __restrict__ gpart, int* status) {
+  constexpr int S_N = RES ? M_STAGES_RES : M_STAGES;
   constexpr uint32_t X_BYTES = 128u * 128u;
-  constexpr uint32_t STAGE = m_stage_bytes(KLD);
-  constexpr uint32_t GOP = 32768u;  // one Gram operand buffer: 2 feature atoms x 128 rows x 128 B
+  constexpr uint32_t E_CHUNK = (uint32_t)KLD * 128u;
+  constexpr uint32_t STAGE = RES ? X_BYTES : m_stage_bytes(KLD);
   constexpr uint32_t TMEM_COLS = (3 * KLD <= 256) ? 256 : 512;
   constexpr uint32_t IDESC_MAIN = idesc_bf16(128, KLD, false, false);
   constexpr uint32_t IDESC_GRAM = idesc_bf16(128, KLD, true, true);
@@ -250,27 +273,37 @@ __global__ void __launch_bounds__(NT, 1)
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* gop = smem + M_STAGES * STAGE;  // 2 x GOP
-  uint64_t* full = reinterpret_cast<uint64_t*>(gop + 2 * GOP);
-  uint64_t* empty = full + M_STAGES;
-  uint64_t* acc_full = empty + M_STAGES;   // [2]
+  uint8_t* eres = smem + S_N * STAGE;                      // resident E[S] chunks (RES only)
+  uint8_t* gop = eres + (RES ? (uint32_t)nk * E_CHUNK : 0u);  // Gram operand buffers
+  uint64_t* full = reinterpret_cast<uint64_t*>(gop + gop_bytes(KLD));
+  uint64_t* empty = full + S_N;
+  uint64_t* acc_full = empty + S_N;        // [2]
   uint64_t* acc_empty = acc_full + 2;      // [2]
   uint64_t* gram_ready = acc_empty + 2;    // [2]
   uint64_t* gram_free = gram_ready + 2;    // [2]
   uint64_t* gram_full = gram_free + 2;
   uint64_t* gram_empty = gram_full + 1;
   uint64_t* done = gram_empty + 1;
-  uint32_t* tmem_s = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* e_full = done + 1;
+  uint32_t* tmem_s = reinterpret_cast<uint32_t*>(e_full + 1);
   volatile int* abort_s = reinterpret_cast<volatile int*>(tmem_s + 1);
+  // Gram operand buffer b, feature atom a (a = 1 only for kld = 128) and the
+  // distance from atom 0 to atom 1 (the descriptor's leading-byte offset)
+  auto gop_atom = [&](int b, int a) -> uint8_t* {
+    return KLD == 64 ? gop + b * 16384 : gop + b * 32768 + a * 16384;
+  };
+  auto gop_lbo = [&](int b) -> uint32_t { return KLD == 64 ? 32768u - 16384u * b : 16384u; };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g0 = seg_off[blockIdx.x], g1 = seg_off[blockIdx.x + 1];
 
-  // zero both Gram operand buffers (the feature atom 64..127 stays zero when kld = 64)
-  for (uint32_t e = threadIdx.x; e < 2 * GOP / 16; e += NT) reinterpret_cast<uint4*>(gop)[e] = make_uint4(0, 0, 0, 0);
+  // zero the Gram operand buffers (with kld = 64 the shared atom 64..127 stays zero)
+  for (uint32_t e = threadIdx.x; e < gop_bytes(KLD) / 16; e += NT)
+    reinterpret_cast<uint4*>(gop)[e] = make_uint4(0, 0, 0, 0);
   fence_proxy_async_smem();
   if (threadIdx.x == 0) {
-    for (int s = 0; s < M_STAGES; ++s) {
+    mbar_init(e_full, 1);
+    for (int s = 0; s < S_N; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -304,9 +337,13 @@ __global__ void __launch_bounds__(NT, 1)
     if (lane == 0) {
       int s = 0;
       uint32_t ph = 0;
-      int issued[M_STAGES] = {0};
-      uint32_t iss_ph[M_STAGES] = {0};
+      int issued[S_N] = {0};
+      uint32_t iss_ph[S_N] = {0};
       bool ok = true;
+      if (RES && g0 < g1) {
+        mbar_arrive_expect_tx(e_full, (uint32_t)nk * E_CHUNK);
+        for (int kc = 0; kc < nk; ++kc) tma_load_2d(eres + kc * E_CHUNK, &mapE, 64 * kc, 0, e_full);
+      }
       for (int g = g0; g < g1 && ok; ++g) {
         const SegM sg = segs[g];
         for (int64_t tile = sg.tile_begin; tile < sg.tile_end && ok; ++tile) {
@@ -318,10 +355,10 @@ __global__ void __launch_bounds__(NT, 1)
             uint8_t* st = smem + s * STAGE;
             mbar_arrive_expect_tx(&full[s], STAGE);
             tma_load_2d(st, &mapX, 64 * kc, (int)(tile * 128), &full[s]);
-            tma_load_2d(st + X_BYTES, &mapE, 64 * kc, 0, &full[s]);
+            if (!RES) tma_load_2d(st + X_BYTES, &mapE, 64 * kc, 0, &full[s]);
             issued[s] = 1;
             iss_ph[s] = ph;
-            if (++s == M_STAGES) {
+            if (++s == S_N) {
               s = 0;
               ph ^= 1u;
             }
@@ -329,10 +366,12 @@ __global__ void __launch_bounds__(NT, 1)
         }
       }
       if (!ok) {
-        for (int q = 0; q < M_STAGES; ++q)
+        for (int q = 0; q < S_N; ++q)
           if (issued[q]) {
             for (uint32_t it2 = 0; it2 < (1u << 22) && !mbar_try_wait(&full[q], iss_ph[q]); ++it2) __nanosleep(128);
           }
+        if (RES && g0 < g1)
+          for (uint32_t it2 = 0; it2 < (1u << 22) && !mbar_try_wait(e_full, 0); ++it2) __nanosleep(128);
       }
     }
   } else if (warp == 1) {
@@ -353,16 +392,18 @@ __global__ void __launch_bounds__(NT, 1)
           ge_ph ^= 1u;
         }
         tc_fence_after();
-        const uint32_t g = smem_u32(gop + b * GOP);
+        const uint32_t g = smem_u32(gop_atom(b, 0));
+        const uint32_t lbo = gop_lbo(b);
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const uint64_t d = sdesc_sw128(g + j * 2048, 16384, 1024);
+          const uint64_t d = sdesc_sw128(g + j * 2048, lbo, 1024);
           mma_bf16(tgram, d, d, IDESC_GRAM, (firstseg && j == 0) ? 0u : 1u);
         }
         mma_commit(&gram_free[b]);
         if (lastseg) mma_commit(gram_full);
         return true;
       };
+      if (RES && g0 < g1 && !mbar_wait(e_full, 0, abort_s, status, ST_TIMEOUT)) ok = false;
       for (int g = g0; g < g1 && ok; ++g) {
         const SegM sg = segs[g];
         for (int64_t tile = sg.tile_begin; tile < sg.tile_end && ok; ++tile, ++n) {
@@ -381,13 +422,13 @@ __global__ void __launch_bounds__(NT, 1)
             }
             tc_fence_after();
             const uint32_t xs = smem_u32(smem + s * STAGE);
-            const uint32_t es = xs + X_BYTES;
+            const uint32_t es = RES ? smem_u32(eres + kc * E_CHUNK) : xs + X_BYTES;
 #pragma unroll
             for (int j = 0; j < 4; ++j)
               mma_bf16(dacc, sdesc_sw128(xs + 32 * j, 16, 1024), sdesc_sw128(es + 32 * j, 16, 1024), IDESC_MAIN,
                        (kc | j) ? 1u : 0u);
             mma_commit(&empty[s]);
-            if (++s == M_STAGES) {
+            if (++s == S_N) {
               s = 0;
               ph ^= 1u;
             }
@@ -431,7 +472,7 @@ __global__ void __launch_bounds__(NT, 1)
         gf_ph[b] ^= 1u;
         tc_fence_after();
         __nv_bfloat16* arow = Aout + (tile * 128 + row) * (int64_t)KLD;
-        uint8_t* gb = gop + b * GOP;
+
 #pragma unroll
         for (int cc = 0; cc < KLD / 32; ++cc) {
           float r[32];
@@ -450,7 +491,7 @@ __global__ void __launch_bounds__(NT, 1)
             const uint4 v = make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
             ga[u] = v;
             const int phys = (cbase + u) ^ (row & 7);
-            *reinterpret_cast<uint4*>(gb + atom * 16384 + row * 128 + phys * 16) = v;
+            *reinterpret_cast<uint4*>(gop_atom(b, atom) + row * 128 + phys * 16) = v;
           }
         }
         fence_proxy_async_smem();
@@ -730,13 +771,26 @@ srm_status tc_setup(Ctx* c) {
     return SRM_ERR_NOMEM;
   }
   // kernel attributes
+  const int nk = (c->T + 63) / 64;
+  s->m_res = m_smem_bytes_res(c->kld, nk) <= kMaxSmem;
+  s->m_smem = s->m_res ? m_smem_bytes_res(c->kld, nk) : m_smem_bytes(c->kld);
+  // The E-pass leaves room on each SM for the M-step tail that runs beside it
+  // on the second stream; ask for the largest shared-memory carve-out so that
+  // the tail's blocks fit next to the persistent CTA.
+  cudaFuncSetAttribute(estep_tc_kernel<64>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(estep_tc_kernel<128>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
   if (c->kld == 64) {
     cudaFuncSetAttribute(estep_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e_smem_bytes(64));
-    cudaFuncSetAttribute(mstep_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m_smem_bytes(64));
+    cudaFuncSetAttribute(mstep_tc_kernel<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)m_smem_bytes(64));
+    cudaFuncSetAttribute(mstep_tc_kernel<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
   } else {
     cudaFuncSetAttribute(estep_tc_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e_smem_bytes(128));
-    cudaFuncSetAttribute(mstep_tc_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(mstep_tc_kernel<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)m_smem_bytes(128));
+    cudaFuncSetAttribute(mstep_tc_kernel<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core kernel attributes");
@@ -767,12 +821,17 @@ cudaError_t launch_p_tc(Ctx* c) {
 cudaError_t launch_a_tc(Ctx* c) {
   auto* s = static_cast<TcState*>(c->tc);
   auto* A = static_cast<__nv_bfloat16*>(c->A);
-  if (c->kld == 64)
-    mstep_tc_kernel<64><<<s->grid, NT, m_smem_bytes(64), c->stream>>>(s->mapXm, s->mapE, s->d_seg, s->d_seg_off,
-                                                                       c->T, A, c->Gpart, c->status);
-  else
-    mstep_tc_kernel<128><<<s->grid, NT, m_smem_bytes(128), c->stream>>>(s->mapXm, s->mapE, s->d_seg,
-                                                                         s->d_seg_off, c->T, A, c->Gpart, c->status);
+#define M_LAUNCH(KLD, RES)                                                                                  \
+  mstep_tc_kernel<KLD, RES><<<s->grid, NT, s->m_smem, c->stream>>>(s->mapXm, s->mapE, s->d_seg, s->d_seg_off, \
+                                                                   c->T, A, c->Gpart, c->status)
+  if (c->kld == 64) {
+    if (s->m_res) M_LAUNCH(64, true);
+    else M_LAUNCH(64, false);
+  } else {
+    if (s->m_res) M_LAUNCH(128, true);
+    else M_LAUNCH(128, false);
+  }
+#undef M_LAUNCH
   return cudaGetLastError();
 }
 

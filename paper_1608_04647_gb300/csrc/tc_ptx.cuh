@@ -57,6 +57,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   return false;
 }
 
+// Bounded wait for long waits (a whole work item): exponential back-off
+// from 64 ns to max_ns between polls, so that a waiting warp leaves the
+// issue slots to other work on the SM.  Same give-up rule as mbar_wait.
+__device__ __forceinline__ bool mbar_wait_patient(uint64_t* bar, uint32_t parity, volatile int* abort, int* status,
+                                                  int timeout_bit, uint32_t max_ns) {
+  uint32_t ns = 64;
+  for (uint32_t it = 0; it < (1u << 22); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    __nanosleep(ns);
+    ns = ns < max_ns ? 2 * ns : max_ns;
+  }
+  *abort = 1;
+  atomicOr(status, timeout_bit);
+  return false;
+}
+
 // ------------------------------------------------------------------ TMA
 __device__ __forceinline__ void tma_prefetch(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
