@@ -20,7 +20,7 @@ thread_local std::string g_err;
 }
 
 const char* const kKernelNames[KK_COUNT] = {
-    "center", "estep_simt", "estep_tc", "p_reduce", "y_sum", "phi", "es", "sigma",
+    "center", "estep_simt", "estep_tc", "p_reduce", "phi", "es", "sigma",
     "mstep_simt", "mstep_tc", "eig", "refine", "rho"};
 
 void set_error(const std::string& msg) { g_err = msg; }
@@ -44,7 +44,7 @@ void prof_begin(Ctx* c, int kind, int* ev0) {
 }
 
 // CUDA kernels behind one launcher call of each kind
-static const int kKernelsPerKind[KK_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 4, 4};
+static const int kKernelsPerKind[KK_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 4, 4};
 
 void prof_end(Ctx* c, int kind, int ev0) {
   const int ev1 = c->ev_next++;
@@ -99,7 +99,7 @@ void free_all(Ctx* c) {
   void* ptrs[] = {c->Xh, c->A, c->sqnorm, c->rowsq, c->d_off, c->d_v, c->rho2, c->Sigma, c->SigmaNext, c->L,
                   c->Phi, c->scal, c->M64, c->M32, c->Uwarm, c->G64, c->U64, c->H64, c->Xr64, c->eigv, c->Y,
                   c->ES64, c->ESt, c->ESb, c->esPart, c->ll, c->iter, c->status, c->Ppart, c->chunk_src, c->jac_sweeps,
-                  c->chunk_src_off, c->Zbuf, c->Gpart, c->gslot_off, c->tr_buf, c->tr_part};
+                  c->chunk_src_off, c->Ypart, c->Gpart, c->gslot_off, c->tr_buf, c->tr_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -342,6 +342,7 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
   c->ldT = ((c->T + 7) / 8) * 8;
   c->nchunk = (c->T + TCH - 1) / TCH;
   c->nes_blk = es_blocks(c->T);
+  c->zgroups = zsum_groups(c->N, c->nchunk, c->num_sms);
   c->v.resize(c->N);
   c->vpad.resize(c->N);
   c->off.resize(c->N + 1);
@@ -391,7 +392,7 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
   AL(iter, 1, "iteration counter");
   AL(status, 1, "status");
   AL(esPart, (int64_t)c->nes_blk * (k * k + 1), "E[S] partials");
-  AL(Zbuf, (int64_t)N * k * T, "per-subject reductions");
+  AL(Ypart, (int64_t)c->zgroups * k * T, "subject-group reductions");
   if (batched) {
     AL(ESb, (int64_t)c->kld * c->ldT, "E[S] bf16");
     ce = cudaMemset(c->ESb, 0, (size_t)c->kld * c->ldT * 2);

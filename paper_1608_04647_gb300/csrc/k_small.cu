@@ -3,8 +3,8 @@
 //
 // E-step (Algorithm 1, master process):
 //   p_reduce : Z_i = rho_i^-2 M_i P_i from the E-pass partials, using
-//              W_i^T X^_i = M_i (A_i^T X^_i)        (eq:srm_mean_distributed)
-//   y_sum    : y = sum_i Z_i                        (FP64, subjects in order)
+//              W_i^T X^_i = M_i (A_i^T X^_i)        (eq:srm_mean_distributed),
+//              summed over groups of subjects (FP64, subjects in order)
 //   phi      : rho_0 = sum_i rho_i^-2 (eq:srm_wt_psi_w) and
 //              Phi = (Sigma_s^-1 + rho_0 I)^-1 (eq:srm_inversion_opt), written
 //              as the matrix function Phi = g(Sigma_s), g(x) = x / (1 + rho_0 x),
@@ -31,6 +31,8 @@
 //              polar factor W_i of eq:srm_mapping_update).
 #include <math.h>
 
+#include <algorithm>
+
 #include "srm_internal.cuh"
 
 namespace srm {
@@ -42,74 +44,108 @@ inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); 
 __device__ __forceinline__ void flag(int* status, int bits) { atomicOr(status, bits); }
 
 // ------------------------------------------------------------------ E-step
-// grid (nchunk, N), 256 threads.  Sums the subject's partial blocks for one
-// 64-wide t-chunk in a fixed order, then Z = rho^-2 M P.
-__global__ void __launch_bounds__(256) p_reduce_kernel(int N, int T, int k, int kld, int nchunk,
+// grid (nchunk, G), 256 threads.  Block (c, g) takes the subjects
+// [N g / G, N (g + 1) / G) in order.  For each it sums the subject's partial
+// blocks of t-chunk c in slot order into P (TCH x kld), forms
+// Z_i = rho_i^-2 M_i P in FP32 (sum over m in order) and adds it to an FP64
+// accumulator; the block then writes ypart[g][f][t].  y = sum_g ypart[g]
+// (es, groups in order).  Thread (tx, ty) of the 16 x 16 grid holds the
+// 4 x FW tile t = tx + 16 u, f = ty + 16 w, which reads P and M from shared
+// memory at one load per two FMAs without bank conflicts (P rows padded to
+// an odd stride, M stored m-major).
+template <int FW>  // kld = 16 FW
+__global__ void __launch_bounds__(256) p_reduce_kernel(int N, int G, int T, int k, int nchunk,
                                                        const float* __restrict__ part,
                                                        const ChunkSrc* __restrict__ src,
                                                        const int* __restrict__ src_off,
                                                        const float* __restrict__ M32,
-                                                       const double* __restrict__ rho2, float* __restrict__ Z) {
+                                                       const double* __restrict__ rho2, double* __restrict__ ypart) {
+  constexpr int KLD = 16 * FW;
   extern __shared__ float pr_smem[];
-  float* Ms = pr_smem;                  // [k][k+1]
-  float* Ps = pr_smem + k * (k + 1);    // [TCH][kld+1]
-  const int c = blockIdx.x, i = blockIdx.y;
+  float* Ms = pr_smem;               // [KLD][KLD]: Ms[m * KLD + f] = M_i[m][f] = M_i[f][m]
+  float* Ps = pr_smem + KLD * KLD;   // [TCH][KLD + 1]
+  const int c = blockIdx.x, g = blockIdx.y;
   const int t0 = c * TCH;
-  const float* Mi = M32 + (int64_t)i * kld * kld;
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) Ms[(e / k) * (k + 1) + e % k] = Mi[(e / k) * kld + e % k];
-  const int b = src_off[i * nchunk + c], en = src_off[i * nchunk + c + 1];
-  const int n4 = TCH * kld / 4;
-  for (int e4 = threadIdx.x; e4 < n4; e4 += blockDim.x) {
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    int s = b;
-    for (; s + 4 <= en; s += 4) {  // four independent loads in flight, summed in order
-      float4 v[4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int i0 = (int)(((int64_t)N * g) / G), i1 = (int)(((int64_t)N * (g + 1)) / G);
+  double acc[4][FW];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = __ldg(reinterpret_cast<const float4*>(part + src[s + u].off) + e4);
+  for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        acc.x += v[u].x;
-        acc.y += v[u].y;
-        acc.z += v[u].z;
-        acc.w += v[u].w;
+    for (int w = 0; w < FW; ++w) acc[u][w] = 0.0;
+  constexpr int n4 = TCH * KLD / 4;
+  for (int i = i0; i < i1; ++i) {
+    __syncthreads();  // the previous subject's tiles have been read
+    const float* Mi = M32 + (int64_t)i * KLD * KLD;
+    for (int e = tid; e < KLD * KLD; e += 256) {  // M_i is symmetric: row m read as column m
+      const int m = e / KLD, f = e - m * KLD;
+      Ms[e] = (f < k && m < k) ? Mi[e] : 0.f;
+    }
+    const int b = src_off[i * nchunk + c], en = src_off[i * nchunk + c + 1];
+    for (int e4 = tid; e4 < n4; e4 += 256) {
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+      int s = b;
+      for (; s + 4 <= en; s += 4) {  // four independent loads in flight, summed in order
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = __ldg(reinterpret_cast<const float4*>(part + src[s + u].off) + e4);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          a.x += v[u].x;
+          a.y += v[u].y;
+          a.z += v[u].z;
+          a.w += v[u].w;
+        }
       }
+      for (; s < en; ++s) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(part + src[s].off) + e4);
+        a.x += v.x;
+        a.y += v.y;
+        a.z += v.z;
+        a.w += v.w;
+      }
+      const int e = 4 * e4, t = e / KLD, f = e - t * KLD;
+      float* d = Ps + t * (KLD + 1) + f;
+      d[0] = a.x;
+      d[1] = a.y;
+      d[2] = a.z;
+      d[3] = a.w;
     }
-    for (; s < en; ++s) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(part + src[s].off) + e4);
-      acc.x += v.x;
-      acc.y += v.y;
-      acc.z += v.z;
-      acc.w += v.w;
+    __syncthreads();
+    float z[4][FW];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int w = 0; w < FW; ++w) z[u][w] = 0.f;
+    for (int m = 0; m < k; ++m) {
+      float pv[4], mv[FW];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pv[u] = Ps[(tx + 16 * u) * (KLD + 1) + m];
+#pragma unroll
+      for (int w = 0; w < FW; ++w) mv[w] = Ms[m * KLD + ty + 16 * w];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < FW; ++w) z[u][w] = fmaf(mv[w], pv[u], z[u][w]);
     }
-    const int e = 4 * e4, t = e / kld, f = e % kld;
-    float* d = Ps + t * (kld + 1) + f;
-    d[0] = acc.x;
-    d[1] = acc.y;
-    d[2] = acc.z;
-    d[3] = acc.w;
+    const float rinv = (float)(1.0 / rho2[i]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int w = 0; w < FW; ++w) acc[u][w] += (double)(rinv * z[u][w]);
   }
-  __syncthreads();
-  const float rinv = (float)(1.0 / rho2[i]);
-  const int tl = threadIdx.x & (TCH - 1);
-  if (t0 + tl < T) {
-    const float* pr = Ps + tl * (kld + 1);
-    for (int f = threadIdx.x / TCH; f < k; f += blockDim.x / TCH) {
-      const float* mr = Ms + f * (k + 1);
-      float z = 0.f;
-      for (int m = 0; m < k; ++m) z = fmaf(mr[m], pr[m], z);
-      Z[((int64_t)i * k + f) * T + t0 + tl] = rinv * z;
+  const int64_t kT = (int64_t)k * T;
+  double* out = ypart + (int64_t)g * kT;
+#pragma unroll
+  for (int w = 0; w < FW; ++w) {
+    const int f = ty + 16 * w;
+    if (f >= k) continue;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = t0 + tx + 16 * u;
+      if (t < T) out[(int64_t)f * T + t] = acc[u][w];
     }
   }
-}
-
-// y[f][t] = sum_i Z_i[f][t] in FP64, subjects in order.
-__global__ void __launch_bounds__(256) y_sum_kernel(int N, int64_t kT, const float* __restrict__ Z,
-                                                    double* __restrict__ Y) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= kT) return;
-  double acc = 0.0;
-  for (int i = 0; i < N; ++i) acc += (double)Z[(int64_t)i * kT + e];
-  Y[e] = acc;
 }
 
 // scal[] layout
@@ -210,10 +246,10 @@ __global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __
 
 constexpr int ES_T = 8;  // t per es block
 
-// y[:, t0:t0+8] = sum_i Z_i[:, t0:t0+8] (FP64, subjects in order), then
+// y[:, t0:t0+8] = sum_g ypart[g][:, t0:t0+8] (FP64, groups in order), then
 // E[S][:, t0:t0+8] = Phi_sym y; partial E E^T and <y, E>.
-__global__ void __launch_bounds__(256) es_kernel(int N, int k, int T, int kld, int ldT, const double* __restrict__ Phi,
-                                                 const float* __restrict__ Z, double* __restrict__ Y,
+__global__ void __launch_bounds__(256) es_kernel(int G, int k, int T, int kld, int ldT, const double* __restrict__ Phi,
+                                                 const double* __restrict__ ypart, double* __restrict__ Y,
                                                  double* __restrict__ ES64, float* __restrict__ ESt,
                                                  __nv_bfloat16* __restrict__ ESb, double* __restrict__ part) {
   extern __shared__ double es_smem[];
@@ -231,8 +267,17 @@ __global__ void __launch_bounds__(256) es_kernel(int N, int k, int T, int kld, i
     const int f = e / ES_T, tt = e % ES_T;
     double y = 0.0;
     if (t0 + tt < T) {
-      const float* zp = Z + (int64_t)f * T + t0 + tt;
-      for (int i = 0; i < N; ++i) y += (double)zp[(int64_t)i * kT];
+      const double* zp = ypart + (int64_t)f * T + t0 + tt;
+      int g = 0;
+      for (; g + 4 <= G; g += 4) {  // four loads in flight, added in group order
+        const double y0 = zp[(int64_t)g * kT], y1 = zp[(int64_t)(g + 1) * kT];
+        const double y2 = zp[(int64_t)(g + 2) * kT], y3 = zp[(int64_t)(g + 3) * kT];
+        y += y0;
+        y += y1;
+        y += y2;
+        y += y3;
+      }
+      for (; g < G; ++g) y += zp[(int64_t)g * kT];
       Y[(int64_t)f * T + t0 + tt] = y;
     }
     Ys[e] = y;
@@ -341,14 +386,17 @@ constexpr int JAC_MAX_SWEEPS = 24;
 // the column pairs; one warp owns one pair in a round: it holds the two
 // columns of Y and of V in registers, forms their Gram entries with warp
 // reductions, rotates, and writes them back; one barrier per round.
-// A pair is rotated while |y_p.y_q| > OSJ_TOL |y_p| |y_q| (FP32 dot products
-// of nearly orthogonal columns carry noise of a few 1e-7 relative); the sweep
-// loop ends after a sweep with no pair above OSJ_STOP, at most
-// JAC_MAX_SWEEPS sweeps.  The remaining off-diagonal part of V^T G V
-// (about OSJ_TOL min(lambda_p, lambda_q)) is removed to second order by the
-// FP64 refinement.  Output U_0 = V (FP64).
-constexpr float OSJ_TOL = 2e-6f;
-constexpr float OSJ_STOP = 8e-6f;
+// Convergence is tested between sweeps by one parallel pass over all pairs
+// (no rotations, so every thread takes its own pairs without barriers): the
+// loop ends as soon as no pair has |y_p.y_q| > OSJ_STOP |y_p| |y_q|, which
+// with a good warm start is often before the first sweep; a sweep rotates
+// every pair above OSJ_TOL.  At most JAC_MAX_SWEEPS sweeps.  The residual
+// off-diagonal part E of V^T G V is then bounded by OSJ_STOP min(lambda_p,
+// lambda_q) pair by pair; the FP64 refinement removes it to first order, so
+// what is left of it in G^{-1/2}, tr G^{1/2} and log det is of relative size
+// k OSJ_STOP^2 (about 5e-7 for k = 50).  Output U_0 = V (FP64).
+constexpr float OSJ_TOL = 1e-5f;
+constexpr float OSJ_STOP = 1e-4f;
 
 template <int RPL>  // rows per lane: kk <= 32 * RPL
 __global__ void __launch_bounds__(1024) eig_kernel(int N, int k, int kld, const float* __restrict__ gpart,
@@ -362,7 +410,7 @@ __global__ void __launch_bounds__(1024) eig_kernel(int N, int k, int kld, const 
   float* Yc = Gs + kk * kk;       // columns of Y: column j at Yc + j * kk
   float* Vc = Yc + kk * kk;       // columns of V
   uint16_t* tab = reinterpret_cast<uint16_t*>(Vc + kk * kk);  // [kk-1][kk/2]: p | q << 8
-  __shared__ int nrot;
+  float* nrm = Vc + kk * kk + ((kk - 1) * (kk / 2) + 1) / 2;    // [kk] |y_p|^2
   const int i = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
   double* Gi = G64 + (int64_t)i * k * k;
@@ -410,9 +458,37 @@ __global__ void __launch_bounds__(1024) eig_kernel(int N, int k, int kld, const 
   }
   bool converged = false;
   int sweep = 0;
-  for (; sweep < JAC_MAX_SWEEPS; ++sweep) {
-    if (tid == 0) nrot = 0;
+  for (;;) {
+    // convergence test: count the pairs with |y_p.y_q| > OSJ_STOP |y_p| |y_q|
     __syncthreads();
+    for (int p = tid; p < kk; p += nt) {
+      float a = 0.f;
+      for (int r = 0; r < kk; ++r) a = fmaf(Yc[p * kk + r], Yc[p * kk + r], a);
+      nrm[p] = a;
+    }
+    __syncthreads();
+    bool above = false;
+    for (int e = tid; e < kk * kk; e += nt) {
+      const int p = e / kk, q = e - p * kk;
+      if (q <= p || q >= k) continue;
+      const float* yp = Yc + p * kk;
+      const float* yq = Yc + q * kk;
+      float g0 = 0.f, g1 = 0.f;
+      int r = 0;
+      for (; r + 1 < kk; r += 2) {
+        g0 = fmaf(yp[r], yq[r], g0);
+        g1 = fmaf(yp[r + 1], yq[r + 1], g1);
+      }
+      if (r < kk) g0 = fmaf(yp[r], yq[r], g0);
+      const float g = g0 + g1;
+      if (g * g > OSJ_STOP * OSJ_STOP * nrm[p] * nrm[q] && fabsf(g) > 1e-30f) above = true;
+    }
+    if (__syncthreads_or(above) == 0) {
+      converged = true;
+      break;
+    }
+    if (sweep == JAC_MAX_SWEEPS) break;
+    ++sweep;
     for (int round = 0; round < kk - 1; ++round) {
       for (int j = warp; j < npair; j += nw) {
         const uint16_t tq = tab[round * npair + j];
@@ -453,17 +529,13 @@ __global__ void __launch_bounds__(1024) eig_kernel(int N, int k, int kld, const 
               Vc[q * kk + r] = sn * vp[u] + c * vq[u];
             }
           }
-          if (lane == 0 && ag > OSJ_STOP * sab) atomicAdd(&nrot, 1);
         }
       }
       __syncthreads();
     }
-    converged = (nrot == 0);
-    __syncthreads();
-    if (converged) break;
   }
   if (!converged && tid == 0) flag(status, ST_EIG_NOCONV);
-  if (tid == 0 && sweeps_out) sweeps_out[i] = sweep + 1;
+  if (tid == 0 && sweeps_out) sweeps_out[i] = sweep;
   // U_0 = V
   double* Uo = U64 + (int64_t)i * k * k;
   for (int e = tid; e < k * k; e += nt) {
@@ -474,7 +546,7 @@ __global__ void __launch_bounds__(1024) eig_kernel(int N, int k, int kld, const 
 
 size_t eig_smem_bytes(int k) {
   const int kk = k + (k & 1);
-  return sizeof(float) * 3 * kk * kk + sizeof(uint16_t) * (kk - 1) * (kk / 2) + 16;
+  return sizeof(float) * (3 * kk * kk + ((kk - 1) * (kk / 2) + 1) / 2 + kk) + 16;
 }
 
 int eig_threads(int k) {
@@ -645,7 +717,10 @@ cudaError_t bgemm(Ctx* c, int nbatch, const double* A, int tA, const double* B, 
 int es_blocks(int T) { return (T + ES_T - 1) / ES_T; }
 
 void prepare_small_kernels(int max_smem) {
-  cudaFuncSetAttribute(p_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  cudaFuncSetAttribute(p_reduce_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  cudaFuncSetAttribute(p_reduce_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  cudaFuncSetAttribute(p_reduce_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  cudaFuncSetAttribute(p_reduce_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   cudaFuncSetAttribute(eig_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 4 * 1024);
   cudaFuncSetAttribute(eig_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 4 * 1024);
   cudaFuncSetAttribute(eig_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 4 * 1024);
@@ -659,17 +734,24 @@ void prepare_small_kernels(int max_smem) {
   cudaFuncSetAttribute(phi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
 }
 
-cudaError_t launch_p_reduce(Ctx* c) {
-  const size_t sm = sizeof(float) * (c->k * (c->k + 1) + TCH * (c->kld + 1));
-  p_reduce_kernel<<<dim3(c->nchunk, c->N), 256, sm, c->stream>>>(c->N, c->T, c->k, c->kld, c->nchunk, c->Ppart,
-                                                                  c->chunk_src, c->chunk_src_off, c->M32, c->rho2,
-                                                                  c->Zbuf);
-  return cudaGetLastError();
+int zsum_groups(int N, int nchunk, int num_sms) {
+  const int want = (4 * num_sms + nchunk - 1) / nchunk;
+  return std::max(1, std::min(N, std::min(128, want)));
 }
 
-cudaError_t launch_y_sum(Ctx* c) {
-  const int64_t kT = (int64_t)c->k * c->T;
-  y_sum_kernel<<<nblocks(kT, 256), 256, 0, c->stream>>>(c->N, kT, c->Zbuf, c->Y);
+cudaError_t launch_p_reduce(Ctx* c) {
+  const size_t sm = sizeof(float) * ((size_t)c->kld * c->kld + TCH * (c->kld + 1));
+  const dim3 grid(c->nchunk, c->zgroups);
+  switch (c->kld) {
+#define PR_CASE(FW)                                                                                                  \
+  case 16 * FW:                                                                                                      \
+    p_reduce_kernel<FW><<<grid, 256, sm, c->stream>>>(c->N, c->zgroups, c->T, c->k, c->nchunk, c->Ppart,            \
+                                                      c->chunk_src, c->chunk_src_off, c->M32, c->rho2, c->Ypart); \
+    break;
+    PR_CASE(1) PR_CASE(2) PR_CASE(3) PR_CASE(4) PR_CASE(5) PR_CASE(6) PR_CASE(7) PR_CASE(8)
+#undef PR_CASE
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
@@ -683,7 +765,7 @@ cudaError_t launch_phi(Ctx* c) {
 
 cudaError_t launch_es(Ctx* c) {
   const size_t sm = sizeof(double) * (2 * c->k * ES_T + c->k * c->k);
-  es_kernel<<<c->nes_blk, 256, sm, c->stream>>>(c->N, c->k, c->T, c->kld, c->ldT, c->Phi, c->Zbuf, c->Y, c->ES64,
+  es_kernel<<<c->nes_blk, 256, sm, c->stream>>>(c->zgroups, c->k, c->T, c->kld, c->ldT, c->Phi, c->Ypart, c->Y, c->ES64,
                                                 c->batched ? nullptr : c->ESt, c->batched ? c->ESb : nullptr,
                                                 c->esPart);
   return cudaGetLastError();

@@ -38,7 +38,6 @@ constexpr int NT = 192;       // threads per CTA
 constexpr int E_KR = 32;      // voxel rows per E-pass stage
 constexpr int E_STAGES = 4;
 constexpr int E_TB = 512;     // t per E-pass item (4 accumulators of 128)
-constexpr int M_STAGES = 4;
 
 struct WorkE {
   int subject, tb, slot, pad;
@@ -57,6 +56,7 @@ struct TcState {
   int* d_seg_off = nullptr;
   int grid = 0;
   bool m_res = false;   // M-pass keeps E[S] resident in shared memory
+  int m_stages = 4;     // M-pass pipeline depth
   size_t m_smem = 0;
 };
 
@@ -80,13 +80,8 @@ constexpr size_t e_smem_bytes(int kld) { return 1024 + (size_t)E_STAGES * e_stag
 // Gram operand buffers: kld = 64 uses one feature atom per buffer plus one
 // shared zero atom (48 KB); kld = 128 uses two atoms per buffer (64 KB).
 __host__ __device__ constexpr uint32_t gop_bytes(int kld) { return kld == 64 ? 49152u : 65536u; }
-constexpr int M_STAGES_RES = 3;  // stages when E[S] is resident (X tiles only)
-constexpr size_t m_smem_bytes(int kld) {
-  return 1024 + (size_t)M_STAGES * m_stage_bytes(kld) + gop_bytes(kld) + kBarBytes;
-}
-constexpr size_t m_smem_bytes_res(int kld, int nk) {
-  return 1024 + (size_t)M_STAGES_RES * 16384u + (size_t)nk * kld * 128u + gop_bytes(kld) + kBarBytes;
-}
+constexpr int M_MAX_STAGES = 8;  // runtime stage count of the M-pass is at most this
+constexpr size_t m_fixed_bytes(int kld) { return 1024 + gop_bytes(kld) + kBarBytes; }
 constexpr size_t kMaxSmem = 232448;  // opt-in limit per block
 
 // ------------------------------------------------------------------ E-pass
@@ -260,9 +255,8 @@ __global__ void __launch_bounds__(NT, 1)
 template <int KLD, bool RES>
 __global__ void __launch_bounds__(NT, 1)
     mstep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE,
-                    const SegM* __restrict__ segs, const int* __restrict__ seg_off, int T,
+                    const SegM* __restrict__ segs, const int* __restrict__ seg_off, int T, int S_N,
                     __nv_bfloat16* __restrict__ Aout, float* __restrict__ gpart, int* status) {
-  constexpr int S_N = RES ? M_STAGES_RES : M_STAGES;
   constexpr uint32_t X_BYTES = 128u * 128u;
   constexpr uint32_t E_CHUNK = (uint32_t)KLD * 128u;
   constexpr uint32_t STAGE = RES ? X_BYTES : m_stage_bytes(KLD);
@@ -337,8 +331,8 @@ __global__ void __launch_bounds__(NT, 1)
     if (lane == 0) {
       int s = 0;
       uint32_t ph = 0;
-      int issued[S_N] = {0};
-      uint32_t iss_ph[S_N] = {0};
+      int issued[M_MAX_STAGES] = {0};
+      uint32_t iss_ph[M_MAX_STAGES] = {0};
       bool ok = true;
       if (RES && g0 < g1) {
         mbar_arrive_expect_tx(e_full, (uint32_t)nk * E_CHUNK);
@@ -772,8 +766,18 @@ srm_status tc_setup(Ctx* c) {
   }
   // kernel attributes
   const int nk = (c->T + 63) / 64;
-  s->m_res = m_smem_bytes_res(c->kld, nk) <= kMaxSmem;
-  s->m_smem = s->m_res ? m_smem_bytes_res(c->kld, nk) : m_smem_bytes(c->kld);
+  {
+    // stage count from the shared-memory budget: resident E[S] if that still
+    // leaves at least M_RES_MIN stages of X^ tiles, else streamed E[S] chunks
+    const size_t fixed = m_fixed_bytes(c->kld);
+    const size_t eres = (size_t)nk * c->kld * 128;
+    const long res_st = fixed + eres < kMaxSmem ? (long)((kMaxSmem - fixed - eres) / 16384) : 0;
+    const long str_st = (long)((kMaxSmem - fixed) / m_stage_bytes(c->kld));
+    constexpr long M_RES_MIN = 3;
+    s->m_res = res_st >= M_RES_MIN;
+    s->m_stages = (int)std::min<long>(M_MAX_STAGES, s->m_res ? res_st : str_st);
+    s->m_smem = fixed + (s->m_res ? eres + (size_t)s->m_stages * 16384 : (size_t)s->m_stages * m_stage_bytes(c->kld));
+  }
   // The E-pass leaves room on each SM for the M-step tail that runs beside it
   // on the second stream; ask for the largest shared-memory carve-out so that
   // the tail's blocks fit next to the persistent CTA.
@@ -783,13 +787,12 @@ srm_status tc_setup(Ctx* c) {
                        cudaSharedmemCarveoutMaxShared);
   if (c->kld == 64) {
     cudaFuncSetAttribute(estep_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e_smem_bytes(64));
-    cudaFuncSetAttribute(mstep_tc_kernel<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)m_smem_bytes(64));
+    cudaFuncSetAttribute(mstep_tc_kernel<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
     cudaFuncSetAttribute(mstep_tc_kernel<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
   } else {
     cudaFuncSetAttribute(estep_tc_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e_smem_bytes(128));
     cudaFuncSetAttribute(mstep_tc_kernel<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)m_smem_bytes(128));
+                         (int)kMaxSmem);
     cudaFuncSetAttribute(mstep_tc_kernel<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
   }
   cudaError_t e = cudaGetLastError();
@@ -823,7 +826,7 @@ cudaError_t launch_a_tc(Ctx* c) {
   auto* A = static_cast<__nv_bfloat16*>(c->A);
 #define M_LAUNCH(KLD, RES)                                                                                  \
   mstep_tc_kernel<KLD, RES><<<s->grid, NT, s->m_smem, c->stream>>>(s->mapXm, s->mapE, s->d_seg, s->d_seg_off, \
-                                                                   c->T, A, c->Gpart, c->status)
+                                                                   c->T, s->m_stages, A, c->Gpart, c->status)
   if (c->kld == 64) {
     if (s->m_res) M_LAUNCH(64, true);
     else M_LAUNCH(64, false);

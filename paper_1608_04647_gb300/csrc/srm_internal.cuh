@@ -34,7 +34,6 @@ enum KernelKind : int {
   KK_P_SIMT,
   KK_P_TC,
   KK_P_REDUCE,
-  KK_Y_SUM,
   KK_PHI,
   KK_ES,
   KK_SIGMA,
@@ -59,6 +58,7 @@ struct Ctx {
   int kld = 0;        // leading dimension of A rows / partial rows (k padded)
   int ldT = 0;        // row stride of resident X^ (T padded to 8)
   int nchunk = 0;     // ceil(T / TCH)
+  int zgroups = 0;    // subject groups of the E-step reduction
   srm_dtype in_dtype = SRM_F32, store = SRM_F32;
   uint32_t flags = 0;
   bool batched = false;
@@ -112,7 +112,7 @@ struct Ctx {
   int64_t Ppart_elems = 0;
   ChunkSrc* chunk_src = nullptr;  // device table
   int* chunk_src_off = nullptr;   // [N * nchunk + 1]
-  float* Zbuf = nullptr;        // [N][k][T] per-subject rho^-2 M_i P_i
+  double* Ypart = nullptr;      // [zgroups][k][T] sum of rho_i^-2 M_i P_i over a group of subjects
   float* Gpart = nullptr;       // M-pass Gram partials [..][kld][kld]
   int64_t Gpart_elems = 0;
   int* gslot_off = nullptr;     // [N+1] Gram slot ranges per subject
@@ -181,8 +181,8 @@ cudaError_t launch_a_simt(Ctx* c, int subject);
 
 // k_small.cu
 int es_blocks(int T);
+int zsum_groups(int N, int nchunk, int num_sms);
 cudaError_t launch_p_reduce(Ctx* c);
-cudaError_t launch_y_sum(Ctx* c);
 cudaError_t launch_phi(Ctx* c);
 cudaError_t launch_es(Ctx* c);
 cudaError_t launch_sigma(Ctx* c);

@@ -18,6 +18,8 @@ TC_CASES = [
     Case("k-odd", [130, 129, 257], 64, 17, 6, seed=6),
     Case("many-subjects", [int(x) for x in np.random.default_rng(9).integers(150, 900, size=40)], 200, 12, 5,
          seed=9),
+    Case("grouped-subjects", [int(x) for x in np.random.default_rng(11).integers(40, 250, size=150)], 1500, 8, 4,
+         seed=11),
 ]
 
 
