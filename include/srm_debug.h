@@ -23,10 +23,13 @@ extern "C" {
 SRM_API srm_status srm_debug_mma(int32_t mn_major, const void* A, const void* B, float* D, int32_t N, int32_t K);
 
 /*
- * srm_debug_eig_sweeps -- diagnostics of the last M-step: the number of
- * cyclic Jacobi sweeps each eigen-decomposition took (entries 0..N-1: the
- * subjects' A_i^T A_i; entry N: Sigma_s).  Writes min(n, N + 1) ints to the
- * host array out.  Synchronises.
+ * srm_debug_eig_sweeps -- diagnostics of the last M-step, one int per
+ * symmetric matrix.  Entries 0..N-1 (the subjects' A_i^T A_i): for k <= 64
+ * the number of Newton-Schulz steps of the polar factor, or 256 + the number
+ * of Jacobi sweeps when that result failed its accuracy certificate and the
+ * eigen-decomposition path took over; for k > 64 the number of Jacobi
+ * sweeps.  Entry N (Sigma_s): Jacobi sweeps.  Writes min(n, N + 1) ints to
+ * the host array out.  Synchronises.
  */
 SRM_API srm_status srm_debug_eig_sweeps(srm_ctx* ctx, int32_t* out, int32_t n);
 #ifdef __cplusplus

@@ -21,7 +21,7 @@ thread_local std::string g_err;
 
 const char* const kKernelNames[KK_COUNT] = {
     "center", "estep_simt", "estep_tc", "p_reduce", "phi", "es", "sigma",
-    "mstep_simt", "mstep_tc", "eig", "refine", "rho"};
+    "mstep_simt", "mstep_tc", "eig", "refine", "rho", "mtail", "polar"};
 
 void set_error(const std::string& msg) { g_err = msg; }
 
@@ -44,7 +44,7 @@ void prof_begin(Ctx* c, int kind, int* ev0) {
 }
 
 // CUDA kernels behind one launcher call of each kind
-static const int kKernelsPerKind[KK_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 4, 4};
+static const int kKernelsPerKind[KK_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 4, 4, 1, 1};
 
 void prof_end(Ctx* c, int kind, int ev0) {
   const int ev1 = c->ev_next++;
@@ -98,7 +98,7 @@ void free_all(Ctx* c) {
   if (c->tc) tc_destroy(c);
   void* ptrs[] = {c->Xh, c->A, c->sqnorm, c->rowsq, c->d_off, c->d_v, c->rho2, c->Sigma, c->SigmaNext, c->L,
                   c->Phi, c->scal, c->M64, c->M32, c->Uwarm, c->G64, c->U64, c->H64, c->Xr64, c->eigv, c->Y,
-                  c->ES64, c->ESt, c->ESb, c->esPart, c->ll, c->iter, c->status, c->Ppart, c->chunk_src, c->jac_sweeps,
+                  c->ES64, c->ESt, c->ESb, c->esPart, c->ll, c->iter, c->status, c->Ppart, c->chunk_src, c->jac_sweeps, c->ns_fb,
                   c->chunk_src_off, c->Ypart, c->Gpart, c->gslot_off, c->tr_buf, c->tr_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -106,6 +106,8 @@ void free_all(Ctx* c) {
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->side2) cudaStreamDestroy(c->side2);
+  if (c->ev_join2) cudaEventDestroy(c->ev_join2);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
 }
@@ -188,10 +190,34 @@ struct OnStream {
 // the Sigma_s eigen-basis) and the Phi of the next E-step.  None of it is
 // needed by the next E-pass (which reads only A_i), so it runs on a second
 // stream beside that pass when an iteration follows.
+srm_status do_sigma_eig(Ctx* c) {
+  LAUNCH(c, KK_EIG, launch_eig_sigma(c));
+  LAUNCH(c, KK_MTAIL, launch_mtail_sigma(c));
+  return SRM_OK;
+}
+
+// Newton-Schulz polar factors; subjects whose result fails its certificate
+// go through the eigen-decomposition path (the launches skip the others).
+srm_status do_polar(Ctx* c) {
+  LAUNCH(c, KK_POLAR, launch_polar(c));
+  LAUNCH(c, KK_EIG, launch_eig_fallback(c));
+  LAUNCH(c, KK_MTAIL, launch_mtail_fallback(c));
+  return SRM_OK;
+}
+
 srm_status do_side_chain(Ctx* c) {
-  LAUNCH(c, KK_EIG, launch_eig(c));
-  LAUNCH(c, KK_REFINE, launch_refine(c));
-  LAUNCH(c, KK_RHO, launch_rho(c));
+  if (ns_supported(c)) {
+    TRY(do_sigma_eig(c));
+    TRY(do_polar(c));
+  } else {
+    LAUNCH(c, KK_EIG, launch_eig(c));
+    if (mtail_supported(c)) {
+      LAUNCH(c, KK_MTAIL, launch_mtail(c));
+    } else {
+      LAUNCH(c, KK_REFINE, launch_refine(c));
+      LAUNCH(c, KK_RHO, launch_rho(c));
+    }
+  }
   LAUNCH(c, KK_PHI, launch_phi(c));
   return SRM_OK;
 }
@@ -214,7 +240,20 @@ srm_status do_estep(Ctx* c) {
   if (overlap) {
     CK(cudaEventRecord(c->ev_fork, c->stream));
     CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-    {
+    if (ns_supported(c)) {
+      // Sigma_s's eigen-decomposition on a third stream, the subjects' polar
+      // factors on the second; Phi waits for both
+      CK(cudaStreamWaitEvent(c->side2, c->ev_fork, 0));
+      {
+        OnStream on(c, c->side2);
+        TRY(do_sigma_eig(c));
+      }
+      CK(cudaEventRecord(c->ev_join2, c->side2));
+      OnStream on(c, c->side);
+      TRY(do_polar(c));
+      CK(cudaStreamWaitEvent(c->side, c->ev_join2, 0));
+      LAUNCH(c, KK_PHI, launch_phi(c));
+    } else {
       OnStream on(c, c->side);
       TRY(do_side_chain(c));
     }
@@ -335,6 +374,8 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
     c->own_stream = true;
   }
   ce = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   if (ce != cudaSuccess) return fail(cuda_fail(ce, "side stream / events"));
@@ -386,6 +427,7 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
   AL(Xr64, (int64_t)(N + 1) * k * k, "Xr64");
   AL(eigv, (int64_t)(N + 1) * k, "eigenvalues");
   AL(jac_sweeps, N + 1, "Jacobi sweep counts");
+  AL(ns_fb, N, "polar-factor fallback flags");
   AL(Y, (int64_t)k * T, "y");
   AL(ES64, (int64_t)k * T, "E[S]");
   AL(ll, c->max_iter, "ll trace");

@@ -403,7 +403,8 @@ __global__ void __launch_bounds__(1024) eig_kernel(int N, int k, int kld, const 
                                                    const int* __restrict__ gslot_off,
                                                    const double* __restrict__ SigmaNext, double* __restrict__ G64,
                                                    const float* __restrict__ Uwarm, double* __restrict__ U64,
-                                                   int* __restrict__ sweeps_out, int* status) {
+                                                   int* __restrict__ sweeps_out, int* status, int first,
+                                                   const int* __restrict__ only) {
   extern __shared__ float eig_smem[];
   const int kk = k + (k & 1);
   float* Gs = eig_smem;           // [kk][kk] G (symmetric)
@@ -411,7 +412,8 @@ __global__ void __launch_bounds__(1024) eig_kernel(int N, int k, int kld, const 
   float* Vc = Yc + kk * kk;       // columns of V
   uint16_t* tab = reinterpret_cast<uint16_t*>(Vc + kk * kk);  // [kk-1][kk/2]: p | q << 8
   float* nrm = Vc + kk * kk + ((kk - 1) * (kk / 2) + 1) / 2;    // [kk] |y_p|^2
-  const int i = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  const int i = blockIdx.x + first, tid = threadIdx.x, nt = blockDim.x;
+  if (only && i < N && only[i] == 0) return;  // this subject's polar factor is already certified
   const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
   double* Gi = G64 + (int64_t)i * k * k;
   const float* Uw = Uwarm + (int64_t)i * k * k;
@@ -535,7 +537,7 @@ __global__ void __launch_bounds__(1024) eig_kernel(int N, int k, int kld, const 
     }
   }
   if (!converged && tid == 0) flag(status, ST_EIG_NOCONV);
-  if (tid == 0 && sweeps_out) sweeps_out[i] = sweep;
+  if (tid == 0 && sweeps_out) sweeps_out[i] = sweep + (only ? 256 : 0);
   // U_0 = V
   double* Uo = U64 + (int64_t)i * k * k;
   for (int e = tid; e < k * k; e += nt) {
@@ -666,6 +668,513 @@ __global__ void __launch_bounds__(128) dk_rho_kernel(int N, int k, int T, const 
   }
 }
 
+// ---------------------------------------------------------------- polar factor by Newton-Schulz
+// For k <= NS_KMAX: M_i = (A_i^T A_i)^-1/2 and ||A_i||_* without an
+// eigen-decomposition when A_i^T A_i is well conditioned.  One CTA per
+// subject.  With G = A_i^T A_i (FP64 sum of the Gram partials) and
+// c = min(||G||_F, ||G||_inf) >= lambda_max, the coupled Newton-Schulz
+// iteration on A = G / c,
+//     P = Z Y,  T = (3 I - P) / 2,  Y <- Y T,  Z <- T Z,   Y_0 = A, Z_0 = I,
+// converges quadratically to Y = A^1/2, Z = A^-1/2 for a symmetric positive
+// definite A (eigenvalues in (0, 1]); it is the stable, coupled form.  It
+// stops two steps after max |P - I| < NS_TOL; M_0 = sym(Z) / sqrt(c).
+//
+// FP32 arithmetic leaves M_0 with an error of about eps cond(G) in the
+// directions of the small eigenvalues, so each result is certified: with
+// E = M_0 G M_0 - I and delta = M_0 - G^-1/2, first order gives
+// E_ab = (sqrt(lambda_a) + sqrt(lambda_b)) delta_ab in the eigenbasis of G,
+// while the polar factor's error A_i delta has entries sqrt(lambda_a)
+// delta_ab; so ||A_i delta||_F <= ||E||_F.  E is formed in compensated FP32
+// (error-free products and sums, G split into two FP32 parts), and a subject
+// with ||E||_F > cert sqrt(k) (or no convergence) is marked for the
+// eigen-decomposition path (Jacobi + FP64 refinement), which then
+// overwrites its M_i and rho_i^2.
+//
+// ||A_i||_* = tr(W^T A_i) for the polar factor W.  With W~ = A_i M_0 and
+// W = W~ (I + E)^-1/2 (orthonormal), tr(W^T A_i) = tr(M_0 G) - tr(E M_0 G)/2
+// + O(|E|^2), stationary at the exact M (the trace is maximal there).
+//
+// Matrices are KP x KP (KP = k rounded up to 4) FP32 in shared memory with
+// zero padding; the products use 4 x 4 register tiles whose operands are
+// read as float4 (the left operand as its transpose, which for these
+// symmetric matrices is itself).
+constexpr int NS_KMAX = 64;
+constexpr int NS_MAXIT = 40;
+constexpr float NS_TOL = 1e-4f;
+// accepted ||E||_F / sqrt(k): FP32 store (results compared at 1e-5) and BF16 store (2e-2)
+constexpr double NS_CERT_F32 = 2e-6;
+constexpr double NS_CERT_BF16 = 1e-4;
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float z = s - a;
+  e = (a - (s - z)) + (b - z);
+}
+
+// C = A^T B for KP x KP row-major operands (KP <= 64, multiple of 4), 256 threads.
+__device__ __forceinline__ void ns_mm(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ C,
+                                      int KP) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tr = (warp >> 1) * 4 + (lane >> 3), tc = (warp & 1) * 8 + (lane & 7);
+  const int nt4 = KP / 4;
+  if (tr >= nt4 || tc >= nt4) return;
+  float acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+#pragma unroll 4
+  for (int m = 0; m < KP; ++m) {
+    const float4 a = *reinterpret_cast<const float4*>(A + m * KP + 4 * tr);
+    const float4 b = *reinterpret_cast<const float4*>(B + m * KP + 4 * tc);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    *reinterpret_cast<float4*>(C + (4 * tr + u) * KP + 4 * tc) = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+}
+
+// The same product with error-free accumulation of A^T B_hi plus A^T B_lo:
+// returns the 4 x 4 tile as hi + lo parts in registers.
+__device__ __forceinline__ bool ns_mm2(const float* __restrict__ A, const float* __restrict__ Bh,
+                                       const float* __restrict__ Bl, int KP, float (&hi)[4][4], float (&lo)[4][4],
+                                       int& r0, int& c0) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tr = (warp >> 1) * 4 + (lane >> 3), tc = (warp & 1) * 8 + (lane & 7);
+  r0 = 4 * tr;
+  c0 = 4 * tc;
+  if (tr >= KP / 4 || tc >= KP / 4) return false;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) hi[u][v] = lo[u][v] = 0.f;
+  for (int m = 0; m < KP; ++m) {
+    const float4 a = *reinterpret_cast<const float4*>(A + m * KP + 4 * tr);
+    const float4 bh = *reinterpret_cast<const float4*>(Bh + m * KP + 4 * tc);
+    const float4 bl = *reinterpret_cast<const float4*>(Bl + m * KP + 4 * tc);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bhv[4] = {bh.x, bh.y, bh.z, bh.w}, blv[4] = {bl.x, bl.y, bl.z, bl.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const float p = av[u] * bhv[v];
+        const float pe = fmaf(av[u], bhv[v], -p);  // exact product error
+        float s, se;
+        two_sum(hi[u][v], p, s, se);
+        hi[u][v] = s;
+        lo[u][v] += se + pe;
+        lo[u][v] = fmaf(av[u], blv[v], lo[u][v]);
+      }
+  }
+  return true;
+}
+
+__device__ __forceinline__ float block_max_256(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float r = red[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) r = fmaxf(r, red[w]);
+  __syncthreads();
+  return r;
+}
+
+// Sum of three doubles over the 256 threads (fixed-order tree); every thread
+// gets the totals.
+__device__ void block_sum3_256(double& a, double& b, double& c, double (*red)[256]) {
+  const int tid = threadIdx.x;
+  red[0][tid] = a;
+  red[1][tid] = b;
+  red[2][tid] = c;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (tid < st) {
+      red[0][tid] += red[0][tid + st];
+      red[1][tid] += red[1][tid + st];
+      red[2][tid] += red[2][tid + st];
+    }
+    __syncthreads();
+  }
+  a = red[0][0];
+  b = red[1][0];
+  c = red[2][0];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) polar_ns_kernel(int N, int k, int kld, int T, const float* __restrict__ gpart,
+                                                       const int* __restrict__ gslot_off, double* __restrict__ G64,
+                                                       double* __restrict__ M64, float* __restrict__ M32,
+                                                       const double* __restrict__ sqnorm,
+                                                       const int64_t* __restrict__ vox,
+                                                       const double* __restrict__ SigmaNext,
+                                                       double* __restrict__ Sigma, double* __restrict__ rho2,
+                                                       double* __restrict__ scal, int* __restrict__ iters_out,
+                                                       int* __restrict__ fallback, double cert, int* status) {
+  extern __shared__ __align__(16) float ns_smem[];
+  __shared__ float redf[8];
+  __shared__ double redd[3][256];
+  const int KP = (k + 3) & ~3;
+  const int KK = KP * KP;
+  float* B0 = ns_smem;
+  float* B1 = B0 + KK;
+  float* B2 = B1 + KK;
+  float* B3 = B2 + KK;
+  const int i = blockIdx.x, tid = threadIdx.x;
+  double* Gi = G64 + (int64_t)i * k * k;
+  // G (FP64) from the Gram partials; ||G||_F^2, tr Sigma_s^new
+  const int s0 = gslot_off[i], s1 = gslot_off[i + 1];
+  double fro = 0.0, tr = 0.0, z0 = 0.0;
+  for (int e = tid; e < k * k; e += 256) {
+    const int a = e / k, b = e - a * k;
+    double sum = 0.0;
+    for (int q = s0; q < s1; ++q) sum += (double)gpart[(int64_t)q * kld * kld + a * kld + b];
+    Gi[e] = sum;
+    fro += sum * sum;
+  }
+  if (tid < k) tr = SigmaNext[tid * k + tid];
+  block_sum3_256(fro, tr, z0, redd);
+  // ||G||_inf (rows of the symmetrised G)
+  float rowmax = 0.f;
+  for (int a = tid; a < k; a += 256) {
+    double rs = 0.0;
+    for (int b = 0; b < k; ++b) rs += fabs(0.5 * (Gi[a * k + b] + Gi[b * k + a]));
+    rowmax = fmaxf(rowmax, (float)rs);
+  }
+  const float ginf = block_max_256(rowmax, redf);
+  const double trS = tr;
+  double c = sqrt(fro);
+  if ((double)ginf * (1.0 + 1e-6) < c) c = (double)ginf * (1.0 + 1e-6);  // both bound lambda_max from above
+  const bool good_c = isfinite(c) && c > 0.0;
+  const double cinv = good_c ? 1.0 / c : 0.0;
+  float* Y = B0;
+  float* Z = B1;
+  float* Tm = B2;
+  float* W = B3;
+  for (int e = tid; e < KK; e += 256) {
+    const int a = e / KP, b = e - a * KP;
+    float y = 0.f, z = 0.f;
+    if (a < k && b < k) {
+      y = (float)(0.5 * (Gi[a * k + b] + Gi[b * k + a]) * cinv);
+      z = (a == b) ? 1.f : 0.f;
+    }
+    Y[e] = y;
+    Z[e] = z;
+  }
+  __syncthreads();
+  int it = 0, extra = -1;
+  bool conv = false;
+  for (; good_c && it < NS_MAXIT; ++it) {
+    ns_mm(Z, Y, Tm, KP);  // P = Z^T Y
+    __syncthreads();
+    // T = (3I - (P + P^T)/2) / 2 on the k block (zero elsewhere); e = max |P - I|
+    float emax = 0.f;
+    for (int e = tid; e < KK; e += 256) {
+      const int a = e / KP, b = e - a * KP;
+      if (b < a) continue;
+      float t = 0.f;
+      if (a < k && b < k) {
+        const float pab = Tm[a * KP + b], pba = Tm[b * KP + a];
+        const float d = (a == b) ? 1.f : 0.f;
+        emax = fmaxf(emax, fmaxf(fabsf(pab - d), fabsf(pba - d)));
+        t = 1.5f * d - 0.25f * (pab + pba);
+      }
+      Tm[a * KP + b] = t;
+      Tm[b * KP + a] = t;
+    }
+    const float err = block_max_256(emax, redf);
+    if (!(err == err)) break;  // non-finite
+    if (extra < 0 && err < NS_TOL) extra = 2;
+    if (extra == 0) {
+      conv = true;
+      break;
+    }
+    if (extra > 0) --extra;
+    ns_mm(Y, Tm, W, KP);  // Y T
+    __syncthreads();
+    ns_mm(Tm, Z, Y, KP);  // T Z (into the old Y)
+    __syncthreads();
+    float* t = Z;
+    Z = Y;
+    Y = W;
+    W = t;
+  }
+  // M_0 = sym(Z) / sqrt(c) into W; G = G_hi + G_lo into the buffers of Y and T
+  float* Mb = W;
+  float* Gh = Y;
+  float* Gl = Tm;
+  float* Zb = Z;  // free once M_0 is formed
+  {
+    const float sc = (float)sqrt(cinv);
+    for (int e = tid; e < KK; e += 256) {
+      const int a = e / KP, b = e - a * KP;
+      float m = 0.f, gh = 0.f, gl = 0.f;
+      if (a < k && b < k) {
+        m = 0.5f * (Z[a * KP + b] + Z[b * KP + a]) * sc;
+        const double g = 0.5 * (Gi[a * k + b] + Gi[b * k + a]);
+        gh = (float)g;
+        gl = (float)(g - (double)gh);
+      }
+      Mb[e] = m;
+      Gh[e] = gh;
+      Gl[e] = gl;
+    }
+  }
+  __syncthreads();
+  // R = M_0 G (hi + lo tiles), stored transposed: P = R^T = G M_0 (hi in Zb, lo in Gh)
+  float th[4][4], tl[4][4];
+  int r0, c0;
+  bool act = ns_mm2(Mb, Gh, Gl, KP, th, tl, r0, c0);
+  __syncthreads();
+  float* Ph = Zb;
+  float* Pl = Gh;
+  if (act) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        Ph[(c0 + v) * KP + r0 + u] = th[u][v];
+        Pl[(c0 + v) * KP + r0 + u] = tl[u][v];
+      }
+  }
+  __syncthreads();
+  // E = M_0 P - I (hi + lo), ||E||_F^2; tr(M_0 G) = tr P; tr(E M_0 G) = sum_ab E_ab P_ab^T... = sum_ab E_ab R_ba
+  double e2 = 0.0, tmg = 0.0, corr = 0.0;
+  act = ns_mm2(Mb, Ph, Pl, KP, th, tl, r0, c0);
+  if (act) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int a = r0 + u, b = c0 + v;
+        if (a >= k || b >= k) continue;
+        const double ev = ((double)th[u][v] - (a == b ? 1.0 : 0.0)) + (double)tl[u][v];
+        e2 += ev * ev;
+        corr += ev * (double)Ph[a * KP + b];  // R_ba = P_ab
+      }
+  }
+  for (int a = tid; a < k; a += 256) tmg += (double)Ph[a * KP + a] + (double)Pl[a * KP + a];
+  block_sum3_256(e2, tmg, corr, redd);
+  const double enorm = sqrt(e2);
+  const bool ok = conv && good_c && enorm <= cert * sqrt((double)k) && isfinite(enorm);
+  if (tid == 0) {
+    if (iters_out) iters_out[i] = it;
+    fallback[i] = ok ? 0 : 1;
+    if (ok) {
+      const double nuc = tmg - 0.5 * corr;
+      const double r = (sqnorm[i] - 2.0 * nuc + (double)T * trS) / ((double)T * (double)vox[i]);
+      if (!(r > 0.0) || !isfinite(r)) flag(status, ST_NONFINITE);
+      rho2[i] = r;
+    }
+    if (i == 0) scal[SC_TRSIG] = trS;
+  }
+  if (ok) {
+    double* Mi = M64 + (int64_t)i * k * k;
+    float* M32i = M32 + (int64_t)i * kld * kld;
+    for (int e = tid; e < k * k; e += 256) {
+      const int a = e / k, b = e - a * k;
+      const float m = Mb[a * KP + b];
+      Mi[e] = (double)m;
+      M32i[a * kld + b] = m;
+    }
+  }
+  if (i == 0)
+    for (int e = tid; e < k * k; e += 256) Sigma[e] = SigmaNext[e];
+}
+
+size_t ns_smem_bytes(int k) {
+  const int KP = (k + 3) & ~3;
+  return sizeof(float) * 4 * (size_t)KP * KP;
+}
+
+// ---------------------------------------------------------------- fused M-step tail
+// refine + rho for k <= MT_KMAX in one launch: a cluster of MT_C CTAs per
+// symmetric matrix (subjects 0..N-1, Sigma_s^new as matrix N).  CTA r of a
+// cluster owns the rows a = r (mod MT_C) of every intermediate; each product
+// reads its right operand in full from global memory (L2), written there by
+// the whole cluster before a cluster barrier (release/acquire at cluster
+// scope; the loads bypass L1).  FP64 throughout, as in the unfused path:
+//   H  = U0^T U0                     (symmetric: upper triangle, mirrored)
+//   X  = 1.5 U0 - 0.5 U0 H           (re-orthonormalised eigenvectors)
+//   H' = G X,  G' = X^T H'           (symmetric)
+//   lambda = diag G', B = f(lambda) + F o E (Daleckii-Krein, f(x) = x^-1/2),
+//   rho_i^2 from sum sqrt(lambda)    (subjects)
+//   M  = X B X^T                     (symmetric; subjects only)
+// and the FP32 copies M32 and Uwarm.  The products' left operands and
+// outputs are this CTA's rows; the column loop runs over the lanes, so the
+// right operand (row-major, odd row stride in shared memory) is read without
+// bank conflicts and the left one is broadcast.
+constexpr int MT_C = 8;
+constexpr int MT_KMAX = 64;
+constexpr int MT_RMAX = (MT_KMAX + MT_C - 1) / MT_C;
+
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__global__ void __cluster_dims__(MT_C, 1, 1) __launch_bounds__(256)
+    mtail_kernel(int N, int k, int kld, int T, const double* __restrict__ U64, double* __restrict__ G64,
+                 double* __restrict__ H64, double* __restrict__ Xr64, double* __restrict__ M64,
+                 float* __restrict__ M32, float* __restrict__ Uwarm, double* __restrict__ eigv,
+                 const double* __restrict__ sqnorm, const int64_t* __restrict__ vox,
+                 const double* __restrict__ SigmaNext, double* __restrict__ Sigma, double* __restrict__ rho2,
+                 double* __restrict__ scal, int* status, int first, const int* __restrict__ only) {
+  extern __shared__ double mt_smem[];
+  const int kp = k | 1;                  // odd row stride
+  double* Xs = mt_smem;                  // [k][kp] X
+  double* Bs = Xs + k * kp;              // [k][kp] right operand
+  double* Rs = Bs + k * kp;              // [MT_RMAX][kp] own rows
+  double* sq = Rs + MT_RMAX * kp;        // [k] sqrt(lambda)
+  __shared__ double red[3][256];
+  const int r = blockIdx.x, i = blockIdx.y + first, tid = threadIdx.x;
+  if (only && i < N && only[i] == 0) return;  // whole cluster: same i
+  const int nr = (k - r + MT_C - 1) / MT_C;  // own rows: a = r + MT_C * al
+  const int64_t kk2 = (int64_t)k * k;
+  const double* Ui = U64 + i * kk2;
+  double* Gi = G64 + i * kk2;
+  double* Hi = H64 + i * kk2;
+  double* Xi = Xr64 + i * kk2;
+  // U0 -> Bs; own rows of U0 -> Rs
+  for (int e = tid; e < k * k; e += 256) Bs[(e / k) * kp + e % k] = Ui[e];
+  __syncthreads();
+  for (int e = tid; e < nr * k; e += 256) {
+    const int al = e / k, m = e - al * k;
+    Rs[al * kp + m] = Bs[(r + MT_C * al) * kp + m];
+  }
+  // H = U0^T U0 (rows a, columns c >= a, mirrored)
+  for (int e = tid; e < nr * k; e += 256) {
+    const int al = e / k, c = e - al * k, a = r + MT_C * al;
+    if (c < a) continue;
+    double s = 0.0;
+    for (int m = 0; m < k; ++m) s = fma(Bs[m * kp + a], Bs[m * kp + c], s);
+    Hi[a * k + c] = s;
+    Hi[c * k + a] = s;
+  }
+  cluster_barrier();
+  // X = 1.5 U0 - 0.5 U0 H
+  for (int e = tid; e < k * k; e += 256) Bs[(e / k) * kp + e % k] = __ldcg(Hi + e);
+  __syncthreads();
+  for (int e = tid; e < nr * k; e += 256) {
+    const int al = e / k, c = e - al * k, a = r + MT_C * al;
+    double s = 0.0;
+    for (int m = 0; m < k; ++m) s = fma(Rs[al * kp + m], Bs[m * kp + c], s);
+    const double x = 1.5 * Rs[al * kp + c] - 0.5 * s;
+    Xi[a * k + c] = x;
+    Uwarm[i * kk2 + a * k + c] = (float)x;
+  }
+  cluster_barrier();
+  // H' = G X (own rows of G; all of X)
+  for (int e = tid; e < k * k; e += 256) Xs[(e / k) * kp + e % k] = __ldcg(Xi + e);
+  for (int e = tid; e < nr * k; e += 256) {
+    const int al = e / k, m = e - al * k;
+    Rs[al * kp + m] = Gi[(r + MT_C * al) * k + m];
+  }
+  __syncthreads();
+  for (int e = tid; e < nr * k; e += 256) {
+    const int al = e / k, c = e - al * k, a = r + MT_C * al;
+    double s = 0.0;
+    for (int m = 0; m < k; ++m) s = fma(Rs[al * kp + m], Xs[m * kp + c], s);
+    Hi[a * k + c] = s;
+  }
+  cluster_barrier();
+  // G' = X^T H' (symmetric), into G64
+  for (int e = tid; e < k * k; e += 256) Bs[(e / k) * kp + e % k] = __ldcg(Hi + e);
+  __syncthreads();
+  for (int e = tid; e < nr * k; e += 256) {
+    const int al = e / k, c = e - al * k, a = r + MT_C * al;
+    if (c < a) continue;
+    double s = 0.0;
+    for (int m = 0; m < k; ++m) s = fma(Xs[m * kp + a], Bs[m * kp + c], s);
+    Gi[a * k + c] = s;
+    Gi[c * k + a] = s;
+  }
+  cluster_barrier();
+  // lambda = diag G'; its maximum, sum sqrt(lambda), tr Sigma_s^new (fixed-order tree)
+  double lam = 0.0, lm = 0.0, tr = 0.0, sl = 0.0;
+  if (tid < k) {
+    lam = __ldcg(Gi + tid * k + tid);
+    lm = lam;
+    tr = SigmaNext[tid * k + tid];
+    sl = sqrt(lam > 1e-300 ? lam : 1e-300);
+    sq[tid] = sl;
+  }
+  red[0][tid] = lm;
+  red[1][tid] = tr;
+  red[2][tid] = (tid < k) ? sl : 0.0;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (tid < st) {
+      red[0][tid] = fmax(red[0][tid], red[0][tid + st]);
+      red[1][tid] += red[1][tid + st];
+      red[2][tid] += red[2][tid + st];
+    }
+    __syncthreads();
+  }
+  const double lmax = red[0][0], trS = red[1][0], ssum = red[2][0];
+  if (r == 0) {
+    if (tid < k) {
+      if (!(lam > 1e-12 * lmax) || !isfinite(lam)) flag(status, i < N ? ST_RANK : ST_NOT_PD);
+      eigv[(int64_t)i * k + tid] = lam;
+    }
+    if (i == 0)
+      for (int e = tid; e < k * k; e += 256) Sigma[e] = SigmaNext[e];
+    if (i < N && tid == 0) {
+      const double rr = (sqnorm[i] - 2.0 * ssum + (double)T * trS) / ((double)T * (double)vox[i]);
+      if (!(rr > 0.0) || !isfinite(rr)) flag(status, ST_NONFINITE);
+      rho2[i] = rr;
+      if (i == 0) scal[SC_TRSIG] = trS;
+    }
+  }
+  if (i >= N) return;  // Sigma_s: X and G' are kept for the next E-step
+  // B = f(lambda) + F o E into H64: the off-diagonal divided differences
+  // multiply E = O(1e-4 |G|) and are taken in FP32
+  for (int e = tid; e < nr * k; e += 256) {
+    const int al = e / k, c = e - al * k, a = r + MT_C * al;
+    double v;
+    if (a == c) {
+      v = 1.0 / sq[a];
+    } else {
+      const float sa = (float)sq[a], sb = (float)sq[c];
+      const float f = -1.f / (sa * sb * (sa + sb));
+      v = (double)f * __ldcg(Gi + a * k + c);
+    }
+    Hi[a * k + c] = v;
+  }
+  cluster_barrier();
+  // T1 = X B (own rows, kept in Rs), then M = T1 X^T (symmetric)
+  for (int e = tid; e < k * k; e += 256) Bs[(e / k) * kp + e % k] = __ldcg(Hi + e);
+  __syncthreads();
+  for (int e = tid; e < nr * k; e += 256) {
+    const int al = e / k, c = e - al * k, a = r + MT_C * al;
+    double s = 0.0;
+    for (int m = 0; m < k; ++m) s = fma(Xs[a * kp + m], Bs[m * kp + c], s);
+    Rs[al * kp + c] = s;
+  }
+  __syncthreads();
+  double* Mi = M64 + i * kk2;
+  float* M32i = M32 + (int64_t)i * kld * kld;
+  for (int e = tid; e < nr * k; e += 256) {
+    const int al = e / k, c = e - al * k, a = r + MT_C * al;
+    if (c < a) continue;
+    double s = 0.0;
+    for (int m = 0; m < k; ++m) s = fma(Rs[al * kp + m], Xs[c * kp + m], s);
+    Mi[a * k + c] = s;
+    Mi[c * k + a] = s;
+    M32i[a * kld + c] = (float)s;
+    M32i[c * kld + a] = (float)s;
+  }
+}
+
+size_t mtail_smem_bytes(int k) {
+  const int kp = k | 1;
+  return sizeof(double) * ((size_t)2 * k * kp + (size_t)MT_RMAX * kp + k);
+}
+
 // M32 (padded, FP32) from M64; Uwarm <- FP32 copy of the refined U (N + 1 matrices).
 __global__ void finish_m_kernel(int N, int k, int kld, const double* __restrict__ M64, const double* __restrict__ U,
                                 float* __restrict__ M32, float* __restrict__ Uwarm) {
@@ -730,6 +1239,11 @@ void prepare_small_kernels(int max_smem) {
   cudaFuncSetAttribute(eig_kernel<2>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   cudaFuncSetAttribute(eig_kernel<4>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   cudaFuncSetAttribute(bgemm64_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(mtail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mtail_smem_bytes(MT_KMAX));
+  cudaFuncSetAttribute(polar_ns_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ns_smem_bytes(NS_KMAX));
+  cudaFuncSetAttribute(polar_ns_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(mtail_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   cudaFuncSetAttribute(es_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   cudaFuncSetAttribute(phi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
 }
@@ -777,21 +1291,28 @@ cudaError_t launch_sigma(Ctx* c) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_eig(Ctx* c) {
+// Eigen-decompositions of matrices first .. first + count - 1 (subjects
+// 0..N-1, Sigma_s = N); with only != nullptr, subjects whose flag is 0 skip.
+cudaError_t launch_eig_from(Ctx* c, int first, int count, const int* only) {
   const size_t sm = eig_smem_bytes(c->k);
   const int nt = eig_threads(c->k);
   const int kk = c->k + (c->k & 1);
+  const unsigned nb = (unsigned)count;
   if (kk <= 32)
-    eig_kernel<1><<<c->N + 1, nt, sm, c->stream>>>(c->N, c->k, c->kld, c->Gpart, c->gslot_off, c->SigmaNext, c->G64,
-                                                   c->Uwarm, c->U64, c->jac_sweeps, c->status);
+    eig_kernel<1><<<nb, nt, sm, c->stream>>>(c->N, c->k, c->kld, c->Gpart, c->gslot_off, c->SigmaNext, c->G64,
+                                             c->Uwarm, c->U64, c->jac_sweeps, c->status, first, only);
   else if (kk <= 64)
-    eig_kernel<2><<<c->N + 1, nt, sm, c->stream>>>(c->N, c->k, c->kld, c->Gpart, c->gslot_off, c->SigmaNext, c->G64,
-                                                   c->Uwarm, c->U64, c->jac_sweeps, c->status);
+    eig_kernel<2><<<nb, nt, sm, c->stream>>>(c->N, c->k, c->kld, c->Gpart, c->gslot_off, c->SigmaNext, c->G64,
+                                             c->Uwarm, c->U64, c->jac_sweeps, c->status, first, only);
   else
-    eig_kernel<4><<<c->N + 1, nt, sm, c->stream>>>(c->N, c->k, c->kld, c->Gpart, c->gslot_off, c->SigmaNext, c->G64,
-                                                   c->Uwarm, c->U64, c->jac_sweeps, c->status);
+    eig_kernel<4><<<nb, nt, sm, c->stream>>>(c->N, c->k, c->kld, c->Gpart, c->gslot_off, c->SigmaNext, c->G64,
+                                             c->Uwarm, c->U64, c->jac_sweeps, c->status, first, only);
   return cudaGetLastError();
 }
+
+cudaError_t launch_eig(Ctx* c) { return launch_eig_from(c, 0, c->N + 1, nullptr); }
+cudaError_t launch_eig_sigma(Ctx* c) { return launch_eig_from(c, c->N, 1, nullptr); }
+cudaError_t launch_eig_fallback(Ctx* c) { return launch_eig_from(c, 0, c->N, c->ns_fb); }
 
 cudaError_t launch_refine(Ctx* c) {
   const int n1 = c->N + 1;
@@ -805,6 +1326,29 @@ cudaError_t launch_refine(Ctx* c) {
   // G' = X^T H (symmetric)
   return bgemm(c, n1, c->Xr64, 1, c->H64, 0, 1.0, nullptr, 0.0, c->G64, 1);
 }
+
+bool ns_supported(const Ctx* c) { return c->k <= NS_KMAX && c->k <= MT_KMAX; }
+
+cudaError_t launch_polar(Ctx* c) {
+  polar_ns_kernel<<<c->N, 256, ns_smem_bytes(c->k), c->stream>>>(
+      c->N, c->k, c->kld, c->T, c->Gpart, c->gslot_off, c->G64, c->M64, c->M32, c->sqnorm, c->d_v, c->SigmaNext,
+      c->Sigma, c->rho2, c->scal, c->jac_sweeps, c->ns_fb, c->store == SRM_BF16 ? NS_CERT_BF16 : NS_CERT_F32,
+      c->status);
+  return cudaGetLastError();
+}
+
+bool mtail_supported(const Ctx* c) { return c->k <= MT_KMAX; }
+
+cudaError_t launch_mtail_from(Ctx* c, int first, int count, const int* only) {
+  mtail_kernel<<<dim3(MT_C, count), 256, mtail_smem_bytes(c->k), c->stream>>>(
+      c->N, c->k, c->kld, c->T, c->U64, c->G64, c->H64, c->Xr64, c->M64, c->M32, c->Uwarm, c->eigv, c->sqnorm, c->d_v,
+      c->SigmaNext, c->Sigma, c->rho2, c->scal, c->status, first, only);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mtail(Ctx* c) { return launch_mtail_from(c, 0, c->N + 1, nullptr); }
+cudaError_t launch_mtail_sigma(Ctx* c) { return launch_mtail_from(c, c->N, 1, nullptr); }
+cudaError_t launch_mtail_fallback(Ctx* c) { return launch_mtail_from(c, 0, c->N, c->ns_fb); }
 
 cudaError_t launch_rho(Ctx* c) {
   const int k = c->k, N = c->N;

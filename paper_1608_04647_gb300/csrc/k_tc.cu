@@ -81,6 +81,7 @@ constexpr size_t e_smem_bytes(int kld) { return 1024 + (size_t)E_STAGES * e_stag
 // shared zero atom (48 KB); kld = 128 uses two atoms per buffer (64 KB).
 __host__ __device__ constexpr uint32_t gop_bytes(int kld) { return kld == 64 ? 49152u : 65536u; }
 constexpr int M_MAX_STAGES = 8;  // runtime stage count of the M-pass is at most this
+constexpr int M_PF = 8;          // M-pass L2 prefetch distance (X^ chunks of 16 KB)
 constexpr size_t m_fixed_bytes(int kld) { return 1024 + gop_bytes(kld) + kBarBytes; }
 constexpr size_t kMaxSmem = 232448;  // opt-in limit per block
 
@@ -338,10 +339,26 @@ __global__ void __launch_bounds__(NT, 1)
         mbar_arrive_expect_tx(e_full, (uint32_t)nk * E_CHUNK);
         for (int kc = 0; kc < nk; ++kc) tma_load_2d(eres + kc * E_CHUNK, &mapE, 64 * kc, 0, e_full);
       }
+      // L2 prefetch cursor, M_PF chunks of X^ ahead of the loads: more bytes
+      // in flight than the shared-memory stages hold
+      int pg = g0, pkc = 0;
+      int64_t ptile = g0 < g1 ? segs[g0].tile_begin : 0;
+      auto pf_next = [&]() {
+        while (pg < g1 && ptile >= segs[pg].tile_end)
+          if (++pg < g1) ptile = segs[pg].tile_begin;
+        if (pg >= g1) return;
+        tma_prefetch_l2_2d(&mapX, 64 * pkc, (int)(ptile * 128));
+        if (++pkc == nk) {
+          pkc = 0;
+          ++ptile;
+        }
+      };
+      for (int q = 0; q < M_PF; ++q) pf_next();
       for (int g = g0; g < g1 && ok; ++g) {
         const SegM sg = segs[g];
         for (int64_t tile = sg.tile_begin; tile < sg.tile_end && ok; ++tile) {
           for (int kc = 0; kc < nk; ++kc) {
+            pf_next();
             if (!mbar_wait(&empty[s], ph ^ 1u, abort_s, status, ST_TIMEOUT)) {
               ok = false;
               break;

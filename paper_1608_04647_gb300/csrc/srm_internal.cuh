@@ -42,6 +42,8 @@ enum KernelKind : int {
   KK_EIG,
   KK_REFINE,
   KK_RHO,
+  KK_MTAIL,
+  KK_POLAR,
   KK_COUNT
 };
 extern const char* const kKernelNames[KK_COUNT];
@@ -69,6 +71,8 @@ struct Ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaStream_t side = nullptr;          // second stream for the M-step tail
+  cudaStream_t side2 = nullptr;         // third stream (Sigma_s eigen-decomposition)
+  cudaEvent_t ev_join2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool side_pending = false;            // an M-step's tail has not run yet
 
@@ -97,6 +101,7 @@ struct Ctx {
   double* Xr64 = nullptr;       // [N+1][k][k] re-orthonormalised eigenvectors; entry N kept for Phi
   double* eigv = nullptr;       // [N+1][k] eigenvalues
   int* jac_sweeps = nullptr;    // [N+1] Jacobi sweeps of the last M-step (diagnostics)
+  int* ns_fb = nullptr;         // [N] 1 = the subject's Newton-Schulz polar factor failed its certificate
   double* Y = nullptr;          // [k][T] FP64 reduction sum_i rho_i^-2 W_i^T X^_i
   double* ES64 = nullptr;       // [k][T] E[S]
   float* ESt = nullptr;         // [ldT][kld] FP32 E[S]^T (plain-path operand)
@@ -189,6 +194,14 @@ cudaError_t launch_sigma(Ctx* c);
 cudaError_t launch_eig(Ctx* c);
 cudaError_t launch_refine(Ctx* c);
 cudaError_t launch_rho(Ctx* c);
+bool mtail_supported(const Ctx* c);
+cudaError_t launch_mtail(Ctx* c);
+cudaError_t launch_mtail_sigma(Ctx* c);
+cudaError_t launch_eig_sigma(Ctx* c);
+cudaError_t launch_eig_fallback(Ctx* c);
+cudaError_t launch_mtail_fallback(Ctx* c);
+bool ns_supported(const Ctx* c);
+cudaError_t launch_polar(Ctx* c);
 cudaError_t launch_transform_finish(Ctx* c, int subject, const float* part, int nsplit, int T_new, float* S_out);
 
 // one-time kernel attributes (dynamic shared memory limits); called by srm_init
