@@ -43,23 +43,70 @@ inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); 
 
 __device__ __forceinline__ void flag(int* status, int bits) { atomicOr(status, bits); }
 
+// Error-free sum: s + e == a + b exactly (Knuth).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float z = s - a;
+  e = (a - (s - z)) + (b - z);
+}
+
+// scal[] layout
+enum { SC_RHO0 = 0, SC_LOGDET = 1, SC_VLOGRHO = 2, SC_SQRHO = 3, SC_YPHIY = 4, SC_TRSIG = 5 };
+
 // ------------------------------------------------------------------ E-step
-// grid (nchunk, G), 256 threads.  Block (c, g) takes the subjects
-// [N g / G, N (g + 1) / G) in order.  For each it sums the subject's partial
-// blocks of t-chunk c in slot order into P (TCH x kld), forms
-// Z_i = rho_i^-2 M_i P in FP32 (sum over m in order) and adds it to an FP64
-// accumulator; the block then writes ypart[g][f][t].  y = sum_g ypart[g]
-// (es, groups in order).  Thread (tx, ty) of the 16 x 16 grid holds the
-// 4 x FW tile t = tx + 16 u, f = ty + 16 w, which reads P and M from shared
-// memory at one load per two FMAs without bank conflicts (P rows padded to
-// an odd stride, M stored m-major).
+// The whole E-step after the E-pass, in one launch.  grid (nchunk, G), 256
+// threads.
+// (A) Block (c, g) takes the subjects [N g / G, N (g + 1) / G) in order.  For
+//     each it sums the subject's partial blocks of t-chunk c in slot order
+//     into P (TCH x kld), forms Z_i = rho_i^-2 M_i P in FP32 (sum over m in
+//     order) and adds it to an FP64 accumulator; the block then writes
+//     ypart[g][f][t].  Thread (tx, ty) of the 16 x 16 grid holds the 4 x FW
+//     tile t = tx + 16 u, f = ty + 16 w, which reads P and M from shared
+//     memory at one load per two FMAs without bank conflicts (P rows padded
+//     to an odd stride, M stored m-major).
+// (B) The last of the G blocks of chunk c (an atomic arrival count; the sums
+//     themselves run in a fixed order, so results do not depend on which
+//     block is last) forms y = sum_g ypart[g] (FP64, groups in order),
+//     E[S] = Phi y for the chunk (FP32, the same tiling), the chunk's
+//     E[S] E[S]^T and <y, E[S]> partials, and the operand copies of E[S].
+// (C) The last chunk to finish forms Sigma_s^new = Phi + E[S] E[S]^T / T
+//     (eq:srm_variance_update_optimized; chunk partials summed in order in
+//     FP64) and the log-likelihood.
+// The arrival counters are reset by the blocks that consume them, so the
+// launch can be replayed (CUDA graphs).
+struct EReduceArgs {
+  int N, G, T, k, nchunk, ldT, kld;
+  double Vtot;
+  const float* part;
+  const ChunkSrc* src;
+  const int* src_off;
+  const float* M32;
+  const double* rho2;
+  float2* ypart;           // [G][k][T] (hi, lo)
+  const double* Phi;
+  double* ES64;
+  float* ESt;              // plain form operand (or null)
+  __nv_bfloat16* ESb;      // batched form operand (or null)
+  float* sPart;            // [nchunk][k*k] E[S] E[S]^T of each chunk
+  double* yePart;          // [nchunk] <y, E[S]> of each chunk
+  double* SigmaNext;
+  double* scal;
+  double* ll;
+  int* iter;
+  int max_iter;
+  int* cnt;                // [nchunk + 1] arrival counters (zero between launches)
+  int* status;
+};
+
 template <int FW>  // kld = 16 FW
-__global__ void __launch_bounds__(256) p_reduce_kernel(int N, int G, int T, int k, int nchunk,
-                                                       const float* __restrict__ part,
-                                                       const ChunkSrc* __restrict__ src,
-                                                       const int* __restrict__ src_off,
-                                                       const float* __restrict__ M32,
-                                                       const double* __restrict__ rho2, double* __restrict__ ypart) {
+__global__ void __launch_bounds__(256) p_reduce_kernel(EReduceArgs ar) {
+  const int N = ar.N, G = ar.G, T = ar.T, k = ar.k, nchunk = ar.nchunk;
+  const float* __restrict__ part = ar.part;
+  const ChunkSrc* __restrict__ src = ar.src;
+  const int* __restrict__ src_off = ar.src_off;
+  const float* __restrict__ M32 = ar.M32;
+  const double* __restrict__ rho2 = ar.rho2;
+  float2* __restrict__ ypart = ar.ypart;
   constexpr int KLD = 16 * FW;
   extern __shared__ float pr_smem[];
   float* Ms = pr_smem;               // [KLD][KLD]: Ms[m * KLD + f] = M_i[m][f] = M_i[f][m]
@@ -68,11 +115,11 @@ __global__ void __launch_bounds__(256) p_reduce_kernel(int N, int G, int T, int 
   const int t0 = c * TCH;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int i0 = (int)(((int64_t)N * g) / G), i1 = (int)(((int64_t)N * (g + 1)) / G);
-  double acc[4][FW];
+  float acc[4][FW], accl[4][FW];  // hi + lo (error-free FP32 accumulation)
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int w = 0; w < FW; ++w) acc[u][w] = 0.0;
+    for (int w = 0; w < FW; ++w) acc[u][w] = accl[u][w] = 0.f;
   constexpr int n4 = TCH * KLD / 4;
   for (int i = i0; i < i1; ++i) {
     __syncthreads();  // the previous subject's tiles have been read
@@ -132,10 +179,15 @@ __global__ void __launch_bounds__(256) p_reduce_kernel(int N, int G, int T, int 
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int w = 0; w < FW; ++w) acc[u][w] += (double)(rinv * z[u][w]);
+      for (int w = 0; w < FW; ++w) {
+        float hs, he;
+        two_sum(acc[u][w], rinv * z[u][w], hs, he);
+        acc[u][w] = hs;
+        accl[u][w] += he;
+      }
   }
   const int64_t kT = (int64_t)k * T;
-  double* out = ypart + (int64_t)g * kT;
+  float2* out = ypart + (int64_t)g * kT;
 #pragma unroll
   for (int w = 0; w < FW; ++w) {
     const int f = ty + 16 * w;
@@ -143,13 +195,158 @@ __global__ void __launch_bounds__(256) p_reduce_kernel(int N, int G, int T, int 
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int t = t0 + tx + 16 * u;
-      if (t < T) out[(int64_t)f * T + t] = acc[u][w];
+      if (t < T) out[(int64_t)f * T + t] = make_float2(acc[u][w], accl[u][w]);
     }
+  }
+  // ---- (B) the last group block of this chunk
+  __shared__ int s_last;
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    s_last = (atomicAdd(&ar.cnt[c], 1) == G - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  if (tid == 0) ar.cnt[c] = 0;
+  __threadfence();
+  // y = sum_g ypart[g] (hi + lo, groups in order) -> Ps[t][f] (FP32); Phi (symmetrised, FP32) -> Ms[m][f]
+  for (int e = tid; e < TCH * KLD; e += 256) {
+    const int f = e / TCH, tt = e - f * TCH;
+    const int t = t0 + tt;
+    float yv = 0.f;
+    if (f < k && t < T) {
+      const float2* zp = ypart + (int64_t)f * T + t;
+      float yh = 0.f, yl = 0.f;
+      int q = 0;
+      for (; q + 8 <= G; q += 8) {  // eight loads in flight, added in group order
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldcg(zp + (int64_t)(q + u) * kT);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          float hs, he;
+          two_sum(yh, v[u].x, hs, he);
+          yh = hs;
+          yl += he + v[u].y;
+        }
+      }
+      for (; q < G; ++q) {
+        const float2 v = __ldcg(zp + (int64_t)q * kT);
+        float hs, he;
+        two_sum(yh, v.x, hs, he);
+        yh = hs;
+        yl += he + v.y;
+      }
+      yv = yh + yl;
+    }
+    Ps[tt * (KLD + 1) + f] = yv;
+  }
+  for (int e = tid; e < KLD * KLD; e += 256) {
+    const int m = e / KLD, f = e - m * KLD;
+    Ms[e] = (f < k && m < k) ? (float)(0.5 * (ar.Phi[m * k + f] + ar.Phi[f * k + m])) : 0.f;
+  }
+  __syncthreads();
+  float z[4][FW];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int w = 0; w < FW; ++w) z[u][w] = 0.f;
+  for (int m = 0; m < k; ++m) {
+    float pv[4], mv[FW];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) pv[u] = Ps[(tx + 16 * u) * (KLD + 1) + m];
+#pragma unroll
+    for (int w = 0; w < FW; ++w) mv[w] = Ms[m * KLD + ty + 16 * w];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int w = 0; w < FW; ++w) z[u][w] = fmaf(mv[w], pv[u], z[u][w]);
+  }
+  // E[S] outputs and <y, E[S]> for the chunk
+  double ye = 0.0;
+#pragma unroll
+  for (int w = 0; w < FW; ++w) {
+    const int f = ty + 16 * w;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int tt = tx + 16 * u, t = t0 + tt;
+      if (f < k && t < T) {
+        const float ev = z[u][w];
+        ye += (double)Ps[tt * (KLD + 1) + f] * (double)ev;
+        ar.ES64[(int64_t)f * T + t] = (double)ev;
+        if (ar.ESt) ar.ESt[(int64_t)t * ar.kld + f] = ev;
+        if (ar.ESb) ar.ESb[(int64_t)f * ar.ldT + t] = __float2bfloat16_rn(ev);
+      }
+    }
+  }
+  __syncthreads();  // y no longer needed: E[S] tile into Ps[t][f] (zero outside the data)
+#pragma unroll
+  for (int w = 0; w < FW; ++w) {
+    const int f = ty + 16 * w;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int tt = tx + 16 * u;
+      Ps[tt * (KLD + 1) + f] = (f < k && t0 + tt < T) ? z[u][w] : 0.f;
+    }
+  }
+  __syncthreads();
+  float* pc = ar.sPart + (int64_t)c * k * k;
+  for (int e = tid; e < k * k; e += 256) {
+    const int a = e / k, b = e - a * k;
+    if (b < a) continue;
+    float sab = 0.f;
+    for (int tt = 0; tt < TCH; ++tt) sab = fmaf(Ps[tt * (KLD + 1) + a], Ps[tt * (KLD + 1) + b], sab);
+    pc[a * k + b] = sab;
+    pc[b * k + a] = sab;
+  }
+  {
+    __shared__ double red_ye[256];
+    red_ye[tid] = ye;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+      if (tid < st) red_ye[tid] += red_ye[tid + st];
+      __syncthreads();
+    }
+    if (tid == 0) ar.yePart[c] = red_ye[0];
+  }
+  // ---- (C) the last chunk
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    s_last = (atomicAdd(&ar.cnt[nchunk], 1) == nchunk - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  if (tid == 0) ar.cnt[nchunk] = 0;
+  __threadfence();
+  const int64_t kk2 = (int64_t)k * k;
+  for (int e = tid; e < k * k; e += 256) {
+    const int a = e / k, b = e - a * k;
+    float sh = 0.f, sl = 0.f;  // chunks in order, error-free FP32 accumulation
+    for (int q = 0; q < nchunk; ++q) {
+      float hs, he;
+      two_sum(sh, __ldcg(ar.sPart + (int64_t)q * kk2 + e), hs, he);
+      sh = hs;
+      sl += he;
+    }
+    const double v = 0.5 * (ar.Phi[a * k + b] + ar.Phi[b * k + a]) + ((double)sh + (double)sl) / (double)T;
+    if (!isfinite(v)) flag(ar.status, ST_NONFINITE);
+    ar.SigmaNext[e] = v;
+  }
+  if (tid == 0) {
+    double yes = 0.0;
+    for (int q = 0; q < nchunk; ++q) yes += __ldcg(ar.yePart + q);
+    double* scal = ar.scal;
+    scal[SC_YPHIY] = yes;
+    const double L = -0.5 * ((double)T * ar.Vtot * 1.8378770664093454835606594728112 + (double)T * scal[SC_VLOGRHO] +
+                             (double)T * scal[SC_LOGDET] + scal[SC_SQRHO] - yes);
+    if (!isfinite(L)) flag(ar.status, ST_NONFINITE);
+    const int it = *ar.iter;
+    if (it >= 0 && it < ar.max_iter) ar.ll[it] = L;
+    *ar.iter = it + 1;
   }
 }
 
-// scal[] layout
-enum { SC_RHO0 = 0, SC_LOGDET = 1, SC_VLOGRHO = 2, SC_SQRHO = 3, SC_YPHIY = 4, SC_TRSIG = 5 };
 
 // Block reduction of three doubles over blockDim.x (a power of two <= 256) threads.
 __device__ void block_sum3(double& a, double& b, double& c) {
@@ -244,136 +441,6 @@ __global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __
   }
 }
 
-constexpr int ES_T = 8;  // t per es block
-
-// y[:, t0:t0+8] = sum_g ypart[g][:, t0:t0+8] (FP64, groups in order), then
-// E[S][:, t0:t0+8] = Phi_sym y; partial E E^T and <y, E>.
-__global__ void __launch_bounds__(256) es_kernel(int G, int k, int T, int kld, int ldT, const double* __restrict__ Phi,
-                                                 const double* __restrict__ ypart, double* __restrict__ Y,
-                                                 double* __restrict__ ES64, float* __restrict__ ESt,
-                                                 __nv_bfloat16* __restrict__ ESb, double* __restrict__ part) {
-  extern __shared__ double es_smem[];
-  double* Ys = es_smem;              // [k][ES_T]
-  double* Es = Ys + k * ES_T;        // [k][ES_T]
-  double* Ps = Es + k * ES_T;        // [k][k] Phi (symmetrised)
-  const int t0 = blockIdx.x * ES_T;
-  const int tid = threadIdx.x;
-  const int64_t kT = (int64_t)k * T;
-  for (int e = tid; e < k * k; e += blockDim.x) {
-    const int f = e / k, m = e % k;
-    Ps[e] = 0.5 * (Phi[f * k + m] + Phi[m * k + f]);
-  }
-  for (int e = tid; e < k * ES_T; e += blockDim.x) {
-    const int f = e / ES_T, tt = e % ES_T;
-    double y = 0.0;
-    if (t0 + tt < T) {
-      const double* zp = ypart + (int64_t)f * T + t0 + tt;
-      int g = 0;
-      for (; g + 4 <= G; g += 4) {  // four loads in flight, added in group order
-        const double y0 = zp[(int64_t)g * kT], y1 = zp[(int64_t)(g + 1) * kT];
-        const double y2 = zp[(int64_t)(g + 2) * kT], y3 = zp[(int64_t)(g + 3) * kT];
-        y += y0;
-        y += y1;
-        y += y2;
-        y += y3;
-      }
-      for (; g < G; ++g) y += zp[(int64_t)g * kT];
-      Y[(int64_t)f * T + t0 + tt] = y;
-    }
-    Ys[e] = y;
-  }
-  __syncthreads();
-  for (int e = tid; e < k * ES_T; e += blockDim.x) {
-    const int f = e / ES_T, tt = e % ES_T;
-    double s = 0.0;
-    for (int m = 0; m < k; ++m) s = fma(Ps[f * k + m], Ys[m * ES_T + tt], s);
-    Es[e] = s;
-    const int t = t0 + tt;
-    if (t < T) {
-      ES64[(int64_t)f * T + t] = s;
-      if (ESt) ESt[(int64_t)t * kld + f] = (float)s;
-      if (ESb) ESb[(int64_t)f * ldT + t] = __float2bfloat16_rn((float)s);
-    }
-  }
-  __syncthreads();
-  double* out = part + (int64_t)blockIdx.x * (k * k + 1);
-  for (int e = tid; e < k * k; e += blockDim.x) {
-    const int a = e / k, b = e % k;
-    if (b < a) continue;
-    double s = 0.0;
-#pragma unroll
-    for (int tt = 0; tt < ES_T; ++tt) s = fma(Es[a * ES_T + tt], Es[b * ES_T + tt], s);
-    out[a * k + b] = s;
-    out[b * k + a] = s;
-  }
-  if (tid < 32) {
-    double s = 0.0;
-    for (int e = tid; e < k * ES_T; e += 32) s = fma(Ys[e], Es[e], s);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (tid == 0) out[k * k] = s;
-  }
-}
-
-// grid k blocks (row a of Sigma_s^new), 256 threads: element b of the row is
-// summed over the nblk partials by SIG_SPLIT threads (contiguous q ranges),
-// combined in a fixed order; block 0 also finishes the likelihood.
-constexpr int SIG_SPLIT = 4;
-
-__global__ void __launch_bounds__(256) sigma_kernel(int k, int T, int nblk, double Vtot, const double* __restrict__ Phi,
-                                                    const double* __restrict__ part, double* __restrict__ SigmaNext,
-                                                    double* __restrict__ scal, double* __restrict__ ll, int* iter,
-                                                    int max_iter, int* status) {
-  __shared__ double red[256];
-  __shared__ double ps[SIG_SPLIT][KMAX];
-  const int a = blockIdx.x, tid = threadIdx.x;
-  const int64_t stride = (int64_t)k * k + 1;
-  for (int e = tid; e < SIG_SPLIT * k; e += blockDim.x) {
-    const int g = e / k, b = e - g * k;
-    const int q0 = (nblk * g) / SIG_SPLIT, q1 = (nblk * (g + 1)) / SIG_SPLIT;
-    double s = 0.0;
-    int q = q0;
-    for (; q + 4 <= q1; q += 4) {
-      const double x0 = part[(int64_t)q * stride + a * k + b], x1 = part[(int64_t)(q + 1) * stride + a * k + b];
-      const double x2 = part[(int64_t)(q + 2) * stride + a * k + b], x3 = part[(int64_t)(q + 3) * stride + a * k + b];
-      s += x0;
-      s += x1;
-      s += x2;
-      s += x3;
-    }
-    for (; q < q1; ++q) s += part[(int64_t)q * stride + a * k + b];
-    ps[g][b] = s;
-  }
-  __syncthreads();
-  for (int b = tid; b < k; b += blockDim.x) {
-    double s = 0.0;
-    for (int g = 0; g < SIG_SPLIT; ++g) s += ps[g][b];
-    const double v = 0.5 * (Phi[a * k + b] + Phi[b * k + a]) + s / (double)T;
-    if (!isfinite(v)) flag(status, ST_NONFINITE);
-    SigmaNext[a * k + b] = v;
-  }
-  if (a == 0) {
-    double ye = 0.0;
-    for (int q = tid; q < nblk; q += blockDim.x) ye += part[(int64_t)q * stride + k * k];
-    red[tid] = ye;
-    __syncthreads();
-    for (int st = 128; st > 0; st >>= 1) {
-      if (tid < st) red[tid] += red[tid + st];
-      __syncthreads();
-    }
-    if (tid == 0) {
-      ye = red[0];
-      scal[SC_YPHIY] = ye;
-      const double L = -0.5 * ((double)T * Vtot * 1.8378770664093454835606594728112 + (double)T * scal[SC_VLOGRHO] +
-                               (double)T * scal[SC_LOGDET] + scal[SC_SQRHO] - ye);
-      if (!isfinite(L)) flag(status, ST_NONFINITE);
-      const int it = *iter;
-      if (it >= 0 && it < max_iter) ll[it] = L;
-      *iter = it + 1;
-    }
-  }
-}
-
 // ------------------------------------------------------------------ M-step
 constexpr int JAC_MAX_SWEEPS = 24;
 
@@ -435,13 +502,26 @@ __global__ void __launch_bounds__(1024) eig_kernel(int N, int k, int kld, const 
   } else {
     for (int e = tid; e < k * k; e += nt) Gi[e] = SigmaNext[e];
   }
+  // scale: max |G_ab|, so that the FP32 Jacobi works on entries of order 1
+  // (Gram entries of large subjects exceed 1e12, and |y|^2 products would
+  // overflow FP32); the eigenvectors do not change
+  __shared__ unsigned gmax_bits;
+  if (tid == 0) gmax_bits = 0u;
   __syncthreads();
-  // Gs = G (symmetrised, FP32; the padding row/column is zero), Vc = U_w (padded with e_k)
+  {
+    float mx = 0.f;
+    for (int e = tid; e < k * k; e += nt) mx = fmaxf(mx, (float)fabs(Gi[e]));
+    atomicMax(&gmax_bits, __float_as_uint(mx));  // non-negative floats order as their bit patterns
+  }
+  __syncthreads();
+  const float gm = __uint_as_float(gmax_bits);
+  const double gsc = (gm > 0.f && isfinite(gm)) ? 1.0 / (double)gm : 1.0;
+  // Gs = G / max |G| (symmetrised, FP32; the padding row/column is zero), Vc = U_w (padded with e_k)
   for (int e = tid; e < kk * kk; e += nt) {
     const int a = e / kk, b = e % kk;
     float g = 0.f, u;
     if (a < k && b < k) {
-      g = (float)(0.5 * (Gi[a * k + b] + Gi[b * k + a]));
+      g = (float)(0.5 * (Gi[a * k + b] + Gi[b * k + a]) * gsc);
       u = Uw[a * k + b];
     } else {
       u = (a == b) ? 1.f : 0.f;
@@ -705,11 +785,6 @@ constexpr float NS_TOL = 1e-4f;
 constexpr double NS_CERT_F32 = 2e-6;
 constexpr double NS_CERT_BF16 = 1e-4;
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float z = s - a;
-  e = (a - (s - z)) + (b - z);
-}
 
 // C = A^T B for KP x KP row-major operands (KP <= 64, multiple of 4), 256 threads.
 __device__ __forceinline__ void ns_mm(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ C,
@@ -1223,13 +1298,13 @@ cudaError_t bgemm(Ctx* c, int nbatch, const double* A, int tA, const double* B, 
 
 }  // namespace
 
-int es_blocks(int T) { return (T + ES_T - 1) / ES_T; }
 
 void prepare_small_kernels(int max_smem) {
-  cudaFuncSetAttribute(p_reduce_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-  cudaFuncSetAttribute(p_reduce_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-  cudaFuncSetAttribute(p_reduce_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-  cudaFuncSetAttribute(p_reduce_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  // (these kernels also hold a few KB of static shared memory)
+  cudaFuncSetAttribute(p_reduce_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
+  cudaFuncSetAttribute(p_reduce_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
+  cudaFuncSetAttribute(p_reduce_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
+  cudaFuncSetAttribute(p_reduce_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
   cudaFuncSetAttribute(eig_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 4 * 1024);
   cudaFuncSetAttribute(eig_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 4 * 1024);
   cudaFuncSetAttribute(eig_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 4 * 1024);
@@ -1244,7 +1319,6 @@ void prepare_small_kernels(int max_smem) {
   cudaFuncSetAttribute(polar_ns_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                        cudaSharedmemCarveoutMaxShared);
   cudaFuncSetAttribute(mtail_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-  cudaFuncSetAttribute(es_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   cudaFuncSetAttribute(phi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
 }
 
@@ -1256,12 +1330,37 @@ int zsum_groups(int N, int nchunk, int num_sms) {
 cudaError_t launch_p_reduce(Ctx* c) {
   const size_t sm = sizeof(float) * ((size_t)c->kld * c->kld + TCH * (c->kld + 1));
   const dim3 grid(c->nchunk, c->zgroups);
+  EReduceArgs ar;
+  ar.N = c->N;
+  ar.G = c->zgroups;
+  ar.T = c->T;
+  ar.k = c->k;
+  ar.nchunk = c->nchunk;
+  ar.ldT = c->ldT;
+  ar.kld = c->kld;
+  ar.Vtot = (double)c->Vtot;
+  ar.part = c->Ppart;
+  ar.src = c->chunk_src;
+  ar.src_off = c->chunk_src_off;
+  ar.M32 = c->M32;
+  ar.rho2 = c->rho2;
+  ar.ypart = c->Ypart;
+  ar.Phi = c->Phi;
+  ar.ES64 = c->ES64;
+  ar.ESt = c->batched ? nullptr : c->ESt;
+  ar.ESb = c->batched ? c->ESb : nullptr;
+  ar.sPart = c->sPart;
+  ar.yePart = c->esPart;
+  ar.SigmaNext = c->SigmaNext;
+  ar.scal = c->scal;
+  ar.ll = c->ll;
+  ar.iter = c->iter;
+  ar.max_iter = c->max_iter;
+  ar.cnt = c->ered_cnt;
+  ar.status = c->status;
   switch (c->kld) {
-#define PR_CASE(FW)                                                                                                  \
-  case 16 * FW:                                                                                                      \
-    p_reduce_kernel<FW><<<grid, 256, sm, c->stream>>>(c->N, c->zgroups, c->T, c->k, c->nchunk, c->Ppart,            \
-                                                      c->chunk_src, c->chunk_src_off, c->M32, c->rho2, c->Ypart); \
-    break;
+#define PR_CASE(FW) \
+  case 16 * FW: p_reduce_kernel<FW><<<grid, 256, sm, c->stream>>>(ar); break;
     PR_CASE(1) PR_CASE(2) PR_CASE(3) PR_CASE(4) PR_CASE(5) PR_CASE(6) PR_CASE(7) PR_CASE(8)
 #undef PR_CASE
     default: return cudaErrorInvalidValue;
@@ -1274,20 +1373,6 @@ cudaError_t launch_phi(Ctx* c) {
   const size_t sm = sizeof(double) * (3 * c->k + 2 * c->k * c->k);
   phi_kernel<<<c->k, 256, sm, c->stream>>>(c->N, c->k, c->rho2, c->sqnorm, c->d_v, c->Xr64 + c->N * kk,
                                            c->G64 + c->N * kk, c->Phi, c->scal, c->status);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_es(Ctx* c) {
-  const size_t sm = sizeof(double) * (2 * c->k * ES_T + c->k * c->k);
-  es_kernel<<<c->nes_blk, 256, sm, c->stream>>>(c->zgroups, c->k, c->T, c->kld, c->ldT, c->Phi, c->Ypart, c->Y, c->ES64,
-                                                c->batched ? nullptr : c->ESt, c->batched ? c->ESb : nullptr,
-                                                c->esPart);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_sigma(Ctx* c) {
-  sigma_kernel<<<c->k, 256, 0, c->stream>>>(c->k, c->T, c->nes_blk, (double)c->Vtot, c->Phi, c->esPart, c->SigmaNext,
-                                            c->scal, c->ll, c->iter, c->max_iter, c->status);
   return cudaGetLastError();
 }
 

@@ -81,7 +81,8 @@ constexpr size_t e_smem_bytes(int kld) { return 1024 + (size_t)E_STAGES * e_stag
 // shared zero atom (48 KB); kld = 128 uses two atoms per buffer (64 KB).
 __host__ __device__ constexpr uint32_t gop_bytes(int kld) { return kld == 64 ? 49152u : 65536u; }
 constexpr int M_MAX_STAGES = 8;  // runtime stage count of the M-pass is at most this
-constexpr int M_PF = 8;          // M-pass L2 prefetch distance (X^ chunks of 16 KB)
+constexpr int M_PF = 8;          // M-pass L2 prefetch distance (X^ chunks of 16 KB) ...
+constexpr int M_PF_STAGES = 5;   // ... used when fewer shared-memory stages than this fit
 constexpr size_t m_fixed_bytes(int kld) { return 1024 + gop_bytes(kld) + kBarBytes; }
 constexpr size_t kMaxSmem = 232448;  // opt-in limit per block
 
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(NT, 1)
 template <int KLD, bool RES>
 __global__ void __launch_bounds__(NT, 1)
     mstep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE,
-                    const SegM* __restrict__ segs, const int* __restrict__ seg_off, int T, int S_N,
+                    const SegM* __restrict__ segs, const int* __restrict__ seg_off, int T, int S_N, int pf_dist,
                     __nv_bfloat16* __restrict__ Aout, float* __restrict__ gpart, int* status) {
   constexpr uint32_t X_BYTES = 128u * 128u;
   constexpr uint32_t E_CHUNK = (uint32_t)KLD * 128u;
@@ -339,21 +340,22 @@ __global__ void __launch_bounds__(NT, 1)
         mbar_arrive_expect_tx(e_full, (uint32_t)nk * E_CHUNK);
         for (int kc = 0; kc < nk; ++kc) tma_load_2d(eres + kc * E_CHUNK, &mapE, 64 * kc, 0, e_full);
       }
-      // L2 prefetch cursor, M_PF chunks of X^ ahead of the loads: more bytes
-      // in flight than the shared-memory stages hold
+      // L2 prefetch cursor, pf_dist chunks of X^ ahead of the loads: more
+      // bytes in flight than the shared-memory stages hold (used when the
+      // stages are few)
       int pg = g0, pkc = 0;
       int64_t ptile = g0 < g1 ? segs[g0].tile_begin : 0;
       auto pf_next = [&]() {
         while (pg < g1 && ptile >= segs[pg].tile_end)
           if (++pg < g1) ptile = segs[pg].tile_begin;
-        if (pg >= g1) return;
+        if (pg >= g1 || pf_dist == 0) return;
         tma_prefetch_l2_2d(&mapX, 64 * pkc, (int)(ptile * 128));
         if (++pkc == nk) {
           pkc = 0;
           ++ptile;
         }
       };
-      for (int q = 0; q < M_PF; ++q) pf_next();
+      for (int q = 0; q < pf_dist; ++q) pf_next();
       for (int g = g0; g < g1 && ok; ++g) {
         const SegM sg = segs[g];
         for (int64_t tile = sg.tile_begin; tile < sg.tile_end && ok; ++tile) {
@@ -843,7 +845,8 @@ cudaError_t launch_a_tc(Ctx* c) {
   auto* A = static_cast<__nv_bfloat16*>(c->A);
 #define M_LAUNCH(KLD, RES)                                                                                  \
   mstep_tc_kernel<KLD, RES><<<s->grid, NT, s->m_smem, c->stream>>>(s->mapXm, s->mapE, s->d_seg, s->d_seg_off, \
-                                                                   c->T, s->m_stages, A, c->Gpart, c->status)
+                                                                   c->T, s->m_stages, s->m_stages < M_PF_STAGES ? M_PF : 0, A, \
+                                                                   c->Gpart, c->status)
   if (c->kld == 64) {
     if (s->m_res) M_LAUNCH(64, true);
     else M_LAUNCH(64, false);

@@ -35,8 +35,6 @@ enum KernelKind : int {
   KK_P_TC,
   KK_P_REDUCE,
   KK_PHI,
-  KK_ES,
-  KK_SIGMA,
   KK_A_SIMT,
   KK_A_TC,
   KK_EIG,
@@ -106,8 +104,9 @@ struct Ctx {
   double* ES64 = nullptr;       // [k][T] E[S]
   float* ESt = nullptr;         // [ldT][kld] FP32 E[S]^T (plain-path operand)
   __nv_bfloat16* ESb = nullptr; // [kld][ldT] BF16 E[S] (tensor-core operand)
-  double* esPart = nullptr;     // [nes_blk][k*k + 1] E[S]E[S]^T and <y, E[S]> partials
+  double* esPart = nullptr;     // [nes_blk] <y, E[S]> of each 64-column chunk
   int nes_blk = 0;
+  int* ered_cnt = nullptr;      // [nchunk + 1] arrival counters of the fused E-step reduction
   double* ll = nullptr;         // [max_iter]
   int* iter = nullptr;          // device E-step counter (index into ll)
   int* status = nullptr;        // device status word
@@ -117,7 +116,8 @@ struct Ctx {
   int64_t Ppart_elems = 0;
   ChunkSrc* chunk_src = nullptr;  // device table
   int* chunk_src_off = nullptr;   // [N * nchunk + 1]
-  double* Ypart = nullptr;      // [zgroups][k][T] sum of rho_i^-2 M_i P_i over a group of subjects
+  float2* Ypart = nullptr;      // [zgroups][k][T] sum of rho_i^-2 M_i P_i over a group of subjects (hi, lo)
+  float* sPart = nullptr;       // [nchunk][k*k] E[S] E[S]^T of each 64-column chunk
   float* Gpart = nullptr;       // M-pass Gram partials [..][kld][kld]
   int64_t Gpart_elems = 0;
   int* gslot_off = nullptr;     // [N+1] Gram slot ranges per subject
@@ -185,12 +185,9 @@ cudaError_t launch_p_simt_generic(const void* A, bool a_bf16, int kld, int kq, c
 cudaError_t launch_a_simt(Ctx* c, int subject);
 
 // k_small.cu
-int es_blocks(int T);
 int zsum_groups(int N, int nchunk, int num_sms);
 cudaError_t launch_p_reduce(Ctx* c);
 cudaError_t launch_phi(Ctx* c);
-cudaError_t launch_es(Ctx* c);
-cudaError_t launch_sigma(Ctx* c);
 cudaError_t launch_eig(Ctx* c);
 cudaError_t launch_refine(Ctx* c);
 cudaError_t launch_rho(Ctx* c);

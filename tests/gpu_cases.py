@@ -17,12 +17,15 @@ class Case:
     n_iter: int
     seed: int = 0
     rho2_range: tuple = (0.1, 1.0)
+    scale: float = 1.0  # multiplies the planted data (large-magnitude Gram matrices)
 
 
 def make_inputs(case: Case):
     spec = synth.PlantedSpec(case.name, len(case.voxels), ("fixed", 0, 0), case.T, case.k, case.n_iter,
                              case.rho2_range, case.seed)
     d = synth.planted_dataset(spec, voxel_counts=case.voxels, dtype=np.float32)
+    if case.scale != 1.0:
+        d["X"] = [(x * np.float32(case.scale)).astype(np.float32) for x in d["X"]]
     d["W0"] = [w.astype(np.float32) for w in d["W0"]]
     return d
 

@@ -22,6 +22,9 @@ PLAIN_CASES = [
     # smallest shapes: one subject, k = 1, v barely above k
     Case("tiny", [7], 9, 1, 6, seed=5),
     Case("k-odd", [130, 129, 257], 64, 17, 6, seed=6),
+    # data of magnitude 1e4 (Gram entries near 1e20), k > 64: the eigen-solver path
+    Case("k80-scaled-1e4", [3000, 2600], 400, 80, 4, seed=12, scale=1e4),
+    Case("k50-scaled-1e4", [2500, 3100, 2000], 500, 50, 4, seed=13, scale=1e4),
     # more subjects than E-step reduction groups: several subjects per group
     Case("grouped-subjects", [int(x) for x in np.random.default_rng(11).integers(40, 250, size=150)], 1500, 8, 4,
          seed=11),

@@ -20,6 +20,8 @@ TC_CASES = [
          seed=9),
     Case("grouped-subjects", [int(x) for x in np.random.default_rng(11).integers(40, 250, size=150)], 1500, 8, 4,
          seed=11),
+    Case("k80-scaled-1e4", [3000, 2600], 400, 80, 4, seed=12, scale=1e4),
+    Case("k50-scaled-1e4", [2500, 3100, 2000], 500, 50, 4, seed=13, scale=1e4),
 ]
 
 
