@@ -112,6 +112,32 @@ def workload(config: int, rank: int):
     return spec, vox
 
 
+# ncu captures committed under profiles/, by workload: DRAM bytes per launch of
+# a kernel, valid while the kernel's source file is unchanged (its SHA-1 is
+# recorded beside the number)
+PROFILE_TAGS = {1: "greeneyes_like_N16_T1000_k50"}
+
+
+def profiled_traffic(kernel: str, config: int):
+    import hashlib
+    import re
+    tag = PROFILE_TAGS.get(config)
+    if tag is None:
+        return None, None
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{tag}.md")
+    if not os.path.exists(path):
+        return None, None
+    text = open(path).read()
+    mt = re.search(r"traffic_bytes_per_launch: (\d+)", text)
+    ms = re.search(r"source_sha1: ([0-9a-f]{40}) \(([\w.]+) when captured\)", text)
+    if not mt or not ms:
+        return None, None
+    src = os.path.join(ROOT, "paper_1608_04647_gb300", "csrc", ms.group(2))
+    if not os.path.exists(src) or hashlib.sha1(open(src, "rb").read()).hexdigest() != ms.group(1):
+        return None, os.path.relpath(path, ROOT) + " (stale: kernel source changed since the capture)"
+    return int(mt.group(1)), os.path.relpath(path, ROOT)
+
+
 def algorithmic_bytes(vox, T, k, xbytes, abytes):
     """Bytes one EM iteration must move (per pass: read X^ once; A_i read in
     the E-pass and written in the M-pass)."""
@@ -226,9 +252,10 @@ def run_ours(args, rank, world):
             b = b / len(vox)  # per launch (one launch per subject)
             t = t / len(vox)
         achieved = b / (t * 1e-3) / 1e9
+        traffic, tsrc = profiled_traffic(name, args.config) if head == "bf16" else (None, None)
         roofline = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
-                    "peak_source": peaks["source"] + " (burst copy)",
+                    "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                    "traffic_source": tsrc, "peak_source": peaks["source"] + " (burst copy)",
                     "bytes_per_launch": b, "ms_per_launch": t}
     iter_bytes = e_bytes + m_bytes
     kernels_per_step = sum(v["launches"] for v in ks.values()) / args.steps

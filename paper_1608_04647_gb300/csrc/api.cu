@@ -20,7 +20,7 @@ thread_local std::string g_err;
 }
 
 const char* const kKernelNames[KK_COUNT] = {
-    "center", "estep_simt", "estep_tc", "ereduce", "phi",
+    "center", "estep_simt", "estep_tc", "ereduce", "sigma", "phi",
     "mstep_simt", "mstep_tc", "eig", "refine", "rho", "mtail", "polar"};
 
 void set_error(const std::string& msg) { g_err = msg; }
@@ -44,7 +44,7 @@ void prof_begin(Ctx* c, int kind, int* ev0) {
 }
 
 // CUDA kernels behind one launcher call of each kind
-static const int kKernelsPerKind[KK_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 4, 4, 1, 1};
+static const int kKernelsPerKind[KK_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 4, 4, 1, 1};
 
 void prof_end(Ctx* c, int kind, int ev0) {
   const int ev1 = c->ev_next++;
@@ -108,6 +108,7 @@ void free_all(Ctx* c) {
   if (c->side) cudaStreamDestroy(c->side);
   if (c->side2) cudaStreamDestroy(c->side2);
   if (c->ev_join2) cudaEventDestroy(c->ev_join2);
+  if (c->ev_sig) cudaEventDestroy(c->ev_sig);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
 }
@@ -227,6 +228,10 @@ srm_status do_side_chain(Ctx* c) {
 // Runs a pending M-step tail on the main stream (before anything that reads
 // rho^2, M_i or Sigma_s).
 srm_status flush_pending(Ctx* c) {
+  if (c->sigma_pending) {
+    LAUNCH(c, KK_SIGMA, launch_sigma(c));
+    c->sigma_pending = false;
+  }
   if (!c->side_pending) return SRM_OK;
   TRY(do_side_chain(c));
   c->side_pending = false;
@@ -237,13 +242,24 @@ namespace {
 
 srm_status do_estep(Ctx* c) {
   const bool overlap = c->side_pending;
+  if (!overlap && c->sigma_pending) {
+    // an E-step followed by another without an M-step in between
+    LAUNCH(c, KK_SIGMA, launch_sigma(c));
+    c->sigma_pending = false;
+  }
   if (overlap) {
     CK(cudaEventRecord(c->ev_fork, c->stream));
     CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    if (c->sigma_pending) {
+      OnStream on(c, c->side);
+      LAUNCH(c, KK_SIGMA, launch_sigma(c));
+      c->sigma_pending = false;
+    }
     if (ns_supported(c)) {
       // Sigma_s's eigen-decomposition on a third stream, the subjects' polar
       // factors on the second; Phi waits for both
-      CK(cudaStreamWaitEvent(c->side2, c->ev_fork, 0));
+      CK(cudaEventRecord(c->ev_sig, c->side));
+      CK(cudaStreamWaitEvent(c->side2, c->ev_sig, 0));
       {
         OnStream on(c, c->side2);
         TRY(do_sigma_eig(c));
@@ -267,6 +283,7 @@ srm_status do_estep(Ctx* c) {
   }
   if (overlap) CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
   LAUNCH(c, KK_P_REDUCE, launch_p_reduce(c));
+  c->sigma_pending = true;
   return SRM_OK;
 }
 
@@ -374,6 +391,7 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
   ce = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
   if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&c->ev_join2, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&c->ev_sig, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   if (ce != cudaSuccess) return fail(cuda_fail(ce, "side stream / events"));
@@ -434,8 +452,8 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
   AL(esPart, c->nes_blk, "<y, E[S]> partials");
   AL(sPart, (int64_t)c->nes_blk * k * k, "E[S] E[S]^T partials");
   AL(Ypart, (int64_t)c->zgroups * k * T, "subject-group reductions");
-  AL(ered_cnt, c->nchunk + 1, "E-step arrival counters");
-  ce = cudaMemset(c->ered_cnt, 0, sizeof(int) * (c->nchunk + 1));
+  AL(ered_cnt, c->nchunk, "E-step arrival counters");
+  ce = cudaMemset(c->ered_cnt, 0, sizeof(int) * c->nchunk);
   if (ce != cudaSuccess) return fail(cuda_fail(ce, "cudaMemset"));
   if (batched) {
     AL(ESb, (int64_t)c->kld * c->ldT, "E[S] bf16");
@@ -584,6 +602,8 @@ srm_status srm_fit(srm_ctx* c, int32_t n_iter, double* ll_host) {
       CK(cudaMemcpyAsync(save, c->ES64, sizeof(double) * c->k * c->T, cudaMemcpyDeviceToDevice, c->stream));
     }
     TRY(do_estep(c));
+    LAUNCH(c, KK_SIGMA, launch_sigma(c));  // its log-likelihood
+    c->sigma_pending = false;
     c->n_ll++;
     if (save) {
       CK(cudaMemcpyAsync(c->ES64, save, sizeof(double) * c->k * c->T, cudaMemcpyDeviceToDevice, c->stream));
@@ -674,6 +694,7 @@ srm_status srm_get_ll(srm_ctx* c, double* ll_host, int32_t* n) {
     set_error("srm_get_ll: null count");
     return SRM_ERR_ARG;
   }
+  TRY(flush_pending(c));
   TRY(check_status(c));
   const int m = std::min(*n, c->n_ll);
   if (ll_host && m > 0) CK(cudaMemcpy(ll_host, c->ll, sizeof(double) * m, cudaMemcpyDeviceToHost));
@@ -780,6 +801,7 @@ srm_status srm_set_state(srm_ctx* c, const void* buf, size_t bytes) {
   c->have_estep = false;
   c->have_es = false;
   c->side_pending = false;
+  c->sigma_pending = false;
   CK(launch_phi(c));
   return check_status(c);
 }

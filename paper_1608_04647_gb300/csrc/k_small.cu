@@ -69,14 +69,12 @@ enum { SC_RHO0 = 0, SC_LOGDET = 1, SC_VLOGRHO = 2, SC_SQRHO = 3, SC_YPHIY = 4, S
 //     block is last) forms y = sum_g ypart[g] (FP64, groups in order),
 //     E[S] = Phi y for the chunk (FP32, the same tiling), the chunk's
 //     E[S] E[S]^T and <y, E[S]> partials, and the operand copies of E[S].
-// (C) The last chunk to finish forms Sigma_s^new = Phi + E[S] E[S]^T / T
-//     (eq:srm_variance_update_optimized; chunk partials summed in order in
-//     FP64) and the log-likelihood.
 // The arrival counters are reset by the blocks that consume them, so the
-// launch can be replayed (CUDA graphs).
+// launch can be replayed (CUDA graphs).  Sigma_s^new and the log-likelihood
+// (sigma_kernel) are left to the M-step tail, which runs beside the next
+// E-pass: the M-pass needs only E[S].
 struct EReduceArgs {
   int N, G, T, k, nchunk, ldT, kld;
-  double Vtot;
   const float* part;
   const ChunkSrc* src;
   const int* src_off;
@@ -89,12 +87,7 @@ struct EReduceArgs {
   __nv_bfloat16* ESb;      // batched form operand (or null)
   float* sPart;            // [nchunk][k*k] E[S] E[S]^T of each chunk
   double* yePart;          // [nchunk] <y, E[S]> of each chunk
-  double* SigmaNext;
-  double* scal;
-  double* ll;
-  int* iter;
-  int max_iter;
-  int* cnt;                // [nchunk + 1] arrival counters (zero between launches)
+  int* cnt;                // [nchunk] arrival counters (zero between launches)
   int* status;
 };
 
@@ -209,37 +202,53 @@ __global__ void __launch_bounds__(256) p_reduce_kernel(EReduceArgs ar) {
   if (!s_last) return;
   if (tid == 0) ar.cnt[c] = 0;
   __threadfence();
-  // y = sum_g ypart[g] (hi + lo, groups in order) -> Ps[t][f] (FP32); Phi (symmetrised, FP32) -> Ms[m][f]
-  for (int e = tid; e < TCH * KLD; e += 256) {
-    const int f = e / TCH, tt = e - f * TCH;
-    const int t = t0 + tt;
-    float yv = 0.f;
-    if (f < k && t < T) {
-      const float2* zp = ypart + (int64_t)f * T + t;
-      float yh = 0.f, yl = 0.f;
-      int q = 0;
-      for (; q + 8 <= G; q += 8) {  // eight loads in flight, added in group order
-        float2 v[8];
+  // y = sum_g ypart[g] (hi + lo, groups in order) -> Ps[t][f] (FP32); Phi (symmetrised, FP32) -> Ms[m][f].
+  // A thread's KLD/4 elements are taken four at a time, eight groups per
+  // step: 32 independent loads in flight.
+  for (int jb = 0; jb < KLD / 4; jb += 4) {
+    int off[4];
+    float yh[4], yl[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = __ldcg(zp + (int64_t)(q + u) * kT);
+    for (int j = 0; j < 4; ++j) {
+      const int e = tid + 256 * (jb + j);
+      const int f = e / TCH, tt = e - f * TCH;
+      off[j] = (f < k && t0 + tt < T) ? f * T + t0 + tt : -1;
+      yh[j] = yl[j] = 0.f;
+    }
+    int q = 0;
+    for (; q + 8 <= G; q += 8) {
+      float2 v[4][8];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          v[j][u] = off[j] >= 0 ? __ldcg(ypart + (int64_t)(q + u) * kT + off[j]) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           float hs, he;
-          two_sum(yh, v[u].x, hs, he);
-          yh = hs;
-          yl += he + v[u].y;
+          two_sum(yh[j], v[j][u].x, hs, he);
+          yh[j] = hs;
+          yl[j] += he + v[j][u].y;
         }
-      }
-      for (; q < G; ++q) {
-        const float2 v = __ldcg(zp + (int64_t)q * kT);
-        float hs, he;
-        two_sum(yh, v.x, hs, he);
-        yh = hs;
-        yl += he + v.y;
-      }
-      yv = yh + yl;
     }
-    Ps[tt * (KLD + 1) + f] = yv;
+    for (; q < G; ++q) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 v = off[j] >= 0 ? __ldcg(ypart + (int64_t)q * kT + off[j]) : make_float2(0.f, 0.f);
+        float hs, he;
+        two_sum(yh[j], v.x, hs, he);
+        yh[j] = hs;
+        yl[j] += he + v.y;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int e = tid + 256 * (jb + j);
+      const int f = e / TCH, tt = e - f * TCH;
+      Ps[tt * (KLD + 1) + f] = off[j] >= 0 ? yh[j] + yl[j] : 0.f;
+    }
   }
   for (int e = tid; e < KLD * KLD; e += 256) {
     const int m = e / KLD, f = e - m * KLD;
@@ -308,42 +317,6 @@ __global__ void __launch_bounds__(256) p_reduce_kernel(EReduceArgs ar) {
       __syncthreads();
     }
     if (tid == 0) ar.yePart[c] = red_ye[0];
-  }
-  // ---- (C) the last chunk
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    s_last = (atomicAdd(&ar.cnt[nchunk], 1) == nchunk - 1);
-  }
-  __syncthreads();
-  if (!s_last) return;
-  if (tid == 0) ar.cnt[nchunk] = 0;
-  __threadfence();
-  const int64_t kk2 = (int64_t)k * k;
-  for (int e = tid; e < k * k; e += 256) {
-    const int a = e / k, b = e - a * k;
-    float sh = 0.f, sl = 0.f;  // chunks in order, error-free FP32 accumulation
-    for (int q = 0; q < nchunk; ++q) {
-      float hs, he;
-      two_sum(sh, __ldcg(ar.sPart + (int64_t)q * kk2 + e), hs, he);
-      sh = hs;
-      sl += he;
-    }
-    const double v = 0.5 * (ar.Phi[a * k + b] + ar.Phi[b * k + a]) + ((double)sh + (double)sl) / (double)T;
-    if (!isfinite(v)) flag(ar.status, ST_NONFINITE);
-    ar.SigmaNext[e] = v;
-  }
-  if (tid == 0) {
-    double yes = 0.0;
-    for (int q = 0; q < nchunk; ++q) yes += __ldcg(ar.yePart + q);
-    double* scal = ar.scal;
-    scal[SC_YPHIY] = yes;
-    const double L = -0.5 * ((double)T * ar.Vtot * 1.8378770664093454835606594728112 + (double)T * scal[SC_VLOGRHO] +
-                             (double)T * scal[SC_LOGDET] + scal[SC_SQRHO] - yes);
-    if (!isfinite(L)) flag(ar.status, ST_NONFINITE);
-    const int it = *ar.iter;
-    if (it >= 0 && it < ar.max_iter) ar.ll[it] = L;
-    *ar.iter = it + 1;
   }
 }
 
@@ -438,6 +411,56 @@ __global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __
       scal[SC_VLOGRHO] = s1;
       scal[SC_SQRHO] = s2;
     }
+  }
+}
+
+// Sigma_s^new = Phi + E[S] E[S]^T / T (eq:srm_variance_update_optimized) from
+// the chunk partials (summed in chunk order, error-free FP32 accumulation),
+// and the log-likelihood of the E-step that produced them.  grid k blocks
+// (row a), 256 threads; block 0 also finishes the likelihood.
+__global__ void __launch_bounds__(256) sigma_kernel(int k, int T, int nchunk, double Vtot, const double* __restrict__ Phi,
+                                                    const float* __restrict__ sPart,
+                                                    const double* __restrict__ yePart, double* __restrict__ SigmaNext,
+                                                    double* __restrict__ scal, double* __restrict__ ll, int* iter,
+                                                    int max_iter, int* status) {
+  const int a = blockIdx.x, tid = threadIdx.x;
+  const int64_t kk2 = (int64_t)k * k;
+  for (int b = tid; b < k; b += 256) {
+    const int e = a * k + b;
+    float sh = 0.f, sl = 0.f;
+    int q = 0;
+    for (; q + 8 <= nchunk; q += 8) {  // eight loads in flight, added in chunk order
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = sPart[(int64_t)(q + u) * kk2 + e];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        float hs, he;
+        two_sum(sh, v[u], hs, he);
+        sh = hs;
+        sl += he;
+      }
+    }
+    for (; q < nchunk; ++q) {
+      float hs, he;
+      two_sum(sh, sPart[(int64_t)q * kk2 + e], hs, he);
+      sh = hs;
+      sl += he;
+    }
+    const double v = 0.5 * (Phi[a * k + b] + Phi[b * k + a]) + ((double)sh + (double)sl) / (double)T;
+    if (!isfinite(v)) flag(status, ST_NONFINITE);
+    SigmaNext[e] = v;
+  }
+  if (a == 0 && tid == 0) {
+    double yes = 0.0;
+    for (int q = 0; q < nchunk; ++q) yes += yePart[q];
+    scal[SC_YPHIY] = yes;
+    const double L = -0.5 * ((double)T * Vtot * 1.8378770664093454835606594728112 + (double)T * scal[SC_VLOGRHO] +
+                             (double)T * scal[SC_LOGDET] + scal[SC_SQRHO] - yes);
+    if (!isfinite(L)) flag(status, ST_NONFINITE);
+    const int it = *iter;
+    if (it >= 0 && it < max_iter) ll[it] = L;
+    *iter = it + 1;
   }
 }
 
@@ -902,40 +925,58 @@ __global__ void __launch_bounds__(256) polar_ns_kernel(int N, int k, int kld, in
   float* B3 = B2 + KK;
   const int i = blockIdx.x, tid = threadIdx.x;
   double* Gi = G64 + (int64_t)i * k * k;
-  // G (FP64) from the Gram partials; ||G||_F^2, tr Sigma_s^new
-  const int s0 = gslot_off[i], s1 = gslot_off[i + 1];
-  double fro = 0.0, tr = 0.0, z0 = 0.0;
-  for (int e = tid; e < k * k; e += 256) {
-    const int a = e / k, b = e - a * k;
-    double sum = 0.0;
-    for (int q = s0; q < s1; ++q) sum += (double)gpart[(int64_t)q * kld * kld + a * kld + b];
-    Gi[e] = sum;
-    fro += sum * sum;
-  }
-  if (tid < k) tr = SigmaNext[tid * k + tid];
-  block_sum3_256(fro, tr, z0, redd);
-  // ||G||_inf (rows of the symmetrised G)
-  float rowmax = 0.f;
-  for (int a = tid; a < k; a += 256) {
-    double rs = 0.0;
-    for (int b = 0; b < k; ++b) rs += fabs(0.5 * (Gi[a * k + b] + Gi[b * k + a]));
-    rowmax = fmaxf(rowmax, (float)rs);
-  }
-  const float ginf = block_max_256(rowmax, redf);
-  const double trS = tr;
-  double c = sqrt(fro);
-  if ((double)ginf * (1.0 + 1e-6) < c) c = (double)ginf * (1.0 + 1e-6);  // both bound lambda_max from above
-  const bool good_c = isfinite(c) && c > 0.0;
-  const double cinv = good_c ? 1.0 / c : 0.0;
   float* Y = B0;
   float* Z = B1;
   float* Tm = B2;
   float* W = B3;
+  // G (FP64) from the Gram partials (four slot loads in flight), kept as
+  // FP32 hi + lo in W / Tm for the iteration's start; ||G||_F^2, tr Sigma_s^new
+  const int s0 = gslot_off[i], s1 = gslot_off[i + 1];
+  double fro = 0.0, tr = 0.0, z0 = 0.0;
+  for (int e = tid; e < KK; e += 256) {
+    const int a = e / KP, b = e - a * KP;
+    double sum = 0.0;
+    if (a < k && b < k) {
+      const float* gp = gpart + a * kld + b;
+      int q = s0;
+      for (; q + 4 <= s1; q += 4) {
+        const float g0 = __ldg(gp + (int64_t)q * kld * kld), g1 = __ldg(gp + (int64_t)(q + 1) * kld * kld);
+        const float g2 = __ldg(gp + (int64_t)(q + 2) * kld * kld), g3 = __ldg(gp + (int64_t)(q + 3) * kld * kld);
+        sum += (double)g0;
+        sum += (double)g1;
+        sum += (double)g2;
+        sum += (double)g3;
+      }
+      for (; q < s1; ++q) sum += (double)__ldg(gp + (int64_t)q * kld * kld);
+      Gi[a * k + b] = sum;
+      fro += sum * sum;
+    }
+    const float hi = (float)sum;
+    W[e] = hi;
+    Tm[e] = (float)(sum - (double)hi);
+  }
+  if (tid < k) tr = SigmaNext[tid * k + tid];
+  block_sum3_256(fro, tr, z0, redd);  // (its barriers also publish W, Tm)
+  // ||sym(G)||_inf <= max_a sum_b (|G_ab| + |G_ba|) / 2, from the FP32 copy
+  float rowmax = 0.f;
+  for (int a = tid; a < k; a += 256) {
+    float rs = 0.f;
+    for (int b = 0; b < k; ++b) rs += 0.5f * (fabsf(W[a * KP + b]) + fabsf(W[b * KP + a]));
+    rowmax = fmaxf(rowmax, rs);
+  }
+  const float ginf = block_max_256(rowmax, redf);
+  const double trS = tr;
+  double c = sqrt(fro);
+  if ((double)ginf * (1.0 + 1e-5) < c) c = (double)ginf * (1.0 + 1e-5);  // both bound lambda_max from above
+  const bool good_c = isfinite(c) && c > 0.0;
+  const double cinv = good_c ? 1.0 / c : 0.0;
+  // Y = sym(G) / c, Z = I (k block), zero padding
   for (int e = tid; e < KK; e += 256) {
     const int a = e / KP, b = e - a * KP;
     float y = 0.f, z = 0.f;
     if (a < k && b < k) {
-      y = (float)(0.5 * (Gi[a * k + b] + Gi[b * k + a]) * cinv);
+      const double gab = (double)W[e] + (double)Tm[e], gba = (double)W[b * KP + a] + (double)Tm[b * KP + a];
+      y = (float)(0.5 * (gab + gba) * cinv);
       z = (a == b) ? 1.f : 0.f;
     }
     Y[e] = y;
@@ -1338,7 +1379,6 @@ cudaError_t launch_p_reduce(Ctx* c) {
   ar.nchunk = c->nchunk;
   ar.ldT = c->ldT;
   ar.kld = c->kld;
-  ar.Vtot = (double)c->Vtot;
   ar.part = c->Ppart;
   ar.src = c->chunk_src;
   ar.src_off = c->chunk_src_off;
@@ -1351,11 +1391,6 @@ cudaError_t launch_p_reduce(Ctx* c) {
   ar.ESb = c->batched ? c->ESb : nullptr;
   ar.sPart = c->sPart;
   ar.yePart = c->esPart;
-  ar.SigmaNext = c->SigmaNext;
-  ar.scal = c->scal;
-  ar.ll = c->ll;
-  ar.iter = c->iter;
-  ar.max_iter = c->max_iter;
   ar.cnt = c->ered_cnt;
   ar.status = c->status;
   switch (c->kld) {
@@ -1365,6 +1400,12 @@ cudaError_t launch_p_reduce(Ctx* c) {
 #undef PR_CASE
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sigma(Ctx* c) {
+  sigma_kernel<<<c->k, 256, 0, c->stream>>>(c->k, c->T, c->nchunk, (double)c->Vtot, c->Phi, c->sPart, c->esPart,
+                                            c->SigmaNext, c->scal, c->ll, c->iter, c->max_iter, c->status);
   return cudaGetLastError();
 }
 

@@ -34,6 +34,7 @@ enum KernelKind : int {
   KK_P_SIMT,
   KK_P_TC,
   KK_P_REDUCE,
+  KK_SIGMA,
   KK_PHI,
   KK_A_SIMT,
   KK_A_TC,
@@ -70,9 +71,10 @@ struct Ctx {
   bool own_stream = false;
   cudaStream_t side = nullptr;          // second stream for the M-step tail
   cudaStream_t side2 = nullptr;         // third stream (Sigma_s eigen-decomposition)
-  cudaEvent_t ev_join2 = nullptr;
+  cudaEvent_t ev_join2 = nullptr, ev_sig = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool side_pending = false;            // an M-step's tail has not run yet
+  bool sigma_pending = false;           // an E-step's Sigma_s^new / log-likelihood have not been formed yet
 
   // ---- resident data
   void* Xh = nullptr;        // [Vpad_tot][ldT] store dtype, demeaned, zero padded
@@ -106,7 +108,7 @@ struct Ctx {
   __nv_bfloat16* ESb = nullptr; // [kld][ldT] BF16 E[S] (tensor-core operand)
   double* esPart = nullptr;     // [nes_blk] <y, E[S]> of each 64-column chunk
   int nes_blk = 0;
-  int* ered_cnt = nullptr;      // [nchunk + 1] arrival counters of the fused E-step reduction
+  int* ered_cnt = nullptr;      // [nchunk] arrival counters of the fused E-step reduction
   double* ll = nullptr;         // [max_iter]
   int* iter = nullptr;          // device E-step counter (index into ll)
   int* status = nullptr;        // device status word
@@ -187,6 +189,7 @@ cudaError_t launch_a_simt(Ctx* c, int subject);
 // k_small.cu
 int zsum_groups(int N, int nchunk, int num_sms);
 cudaError_t launch_p_reduce(Ctx* c);
+cudaError_t launch_sigma(Ctx* c);
 cudaError_t launch_phi(Ctx* c);
 cudaError_t launch_eig(Ctx* c);
 cudaError_t launch_refine(Ctx* c);
