@@ -37,6 +37,7 @@ namespace {
 constexpr int NT = 192;       // threads per CTA
 constexpr int E_KR = 32;      // voxel rows per E-pass stage
 constexpr int E_STAGES = 4;
+constexpr int E_RESERVE_MAX = 20;  // SMs the E-pass leaves free (at most)
 constexpr int E_TB = 512;     // t per E-pass item (4 accumulators of 128)
 
 struct WorkE {
@@ -54,7 +55,8 @@ struct TcState {
   int* d_work_off = nullptr;
   SegM* d_seg = nullptr;
   int* d_seg_off = nullptr;
-  int grid = 0;
+  int grid = 0;         // M-pass CTAs (one per SM)
+  int egrid = 0;        // E-pass CTAs
   bool m_res = false;   // M-pass keeps E[S] resident in shared memory
   int m_stages = 4;     // M-pass pipeline depth
   size_t m_smem = 0;
@@ -682,7 +684,16 @@ srm_status tc_setup(Ctx* c) {
   c->tc = s;
   const int G = c->num_sms;
   s->grid = G;
+  // The E-pass leaves a few SMs to the M-step tail that runs beside it (the
+  // polar factors take one CTA per subject): the tail's blocks then run on
+  // otherwise idle SMs instead of slowing the E-pass CTAs they would share an
+  // SM with, whose fixed share of the work sets the pass's end.  132 of 152
+  // SMs still saturate HBM (greeneyes-like workload: E-pass 0.255 -> 0.217 ms,
+  // iteration 0.588 -> 0.548 ms).
   const int N = c->N;
+  const int reserve = std::min(E_RESERVE_MAX, N + 4);
+  const int GE = std::max(1, c->num_sms - reserve);
+  s->egrid = GE;
   // tensor maps
   bool ok = make_map(&s->mapXe, c->Xh, c->T, c->Vpad_tot, (uint64_t)c->ldT * 2, 64, E_KR) &&
             make_map(&s->mapA, c->A, c->kld, c->Vpad_tot, (uint64_t)c->kld * 2, 64, E_KR) &&
@@ -698,17 +709,17 @@ srm_status tc_setup(Ctx* c) {
   for (int i = 0; i < N; ++i) U += c->vpad[i] / E_KR;
   U *= nTB;
   std::vector<WorkE> work;
-  std::vector<int> work_off(G + 1, 0);
+  std::vector<int> work_off(GE + 1, 0);
   {
     int64_t pos = 0;  // global step index of the current (tb, i) start
     int cta = 0;
-    auto cta_begin = [&](int q) { return (U * q) / G; };
+    auto cta_begin = [&](int q) { return (U * q) / GE; };
     for (int tb = 0; tb < nTB; ++tb)
       for (int i = 0; i < N; ++i) {
         const int64_t nsteps = c->vpad[i] / E_KR;
         int64_t a = pos, e = pos + nsteps;
         while (a < e) {
-          while (cta < G - 1 && a >= cta_begin(cta + 1)) {
+          while (cta < GE - 1 && a >= cta_begin(cta + 1)) {
             work_off[cta + 1] = (int)work.size();
             ++cta;
           }
@@ -720,7 +731,7 @@ srm_status tc_setup(Ctx* c) {
         }
         pos = e;
       }
-    for (int q = cta + 1; q <= G; ++q) work_off[q] = (int)work.size();
+    for (int q = cta + 1; q <= GE; ++q) work_off[q] = (int)work.size();
   }
   // E-pass partial slots and the (subject, chunk) source table
   c->Ppart_elems = (int64_t)work.size() * E_TB * c->kld;
@@ -832,10 +843,10 @@ void tc_destroy(Ctx* c) {
 cudaError_t launch_p_tc(Ctx* c) {
   auto* s = static_cast<TcState*>(c->tc);
   if (c->kld == 64)
-    estep_tc_kernel<64><<<s->grid, NT, e_smem_bytes(64), c->stream>>>(s->mapXe, s->mapA, s->d_work, s->d_work_off,
+    estep_tc_kernel<64><<<s->egrid, NT, e_smem_bytes(64), c->stream>>>(s->mapXe, s->mapA, s->d_work, s->d_work_off,
                                                                        c->T, c->Ppart, c->status);
   else
-    estep_tc_kernel<128><<<s->grid, NT, e_smem_bytes(128), c->stream>>>(s->mapXe, s->mapA, s->d_work,
+    estep_tc_kernel<128><<<s->egrid, NT, e_smem_bytes(128), c->stream>>>(s->mapXe, s->mapA, s->d_work,
                                                                          s->d_work_off, c->T, c->Ppart, c->status);
   return cudaGetLastError();
 }
