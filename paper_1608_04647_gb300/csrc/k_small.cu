@@ -73,6 +73,8 @@ enum { SC_RHO0 = 0, SC_LOGDET = 1, SC_VLOGRHO = 2, SC_SQRHO = 3, SC_YPHIY = 4, S
 // launch can be replayed (CUDA graphs).  Sigma_s^new and the log-likelihood
 // (sigma_kernel) are left to the M-step tail, which runs beside the next
 // E-pass: the M-pass needs only E[S].
+constexpr int PR_MAX_SLOTS = 64;  // slot offsets staged in shared memory per (subject, chunk)
+
 struct EReduceArgs {
   int N, G, T, k, nchunk, ldT, kld;
   const float* part;
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(256) p_reduce_kernel(EReduceArgs ar) {
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int w = 0; w < FW; ++w) acc[u][w] = accl[u][w] = 0.f;
-  constexpr int n4 = TCH * KLD / 4;
+  static_assert(TCH * KLD / 4 == 256 * FW, "a thread owns FW float4 positions of a slot block");
   for (int i = i0; i < i1; ++i) {
     __syncthreads();  // the previous subject's tiles have been read
     const float* Mi = M32 + (int64_t)i * KLD * KLD;
@@ -122,34 +124,47 @@ __global__ void __launch_bounds__(256) p_reduce_kernel(EReduceArgs ar) {
       Ms[e] = (f < k && m < k) ? Mi[e] : 0.f;
     }
     const int b = src_off[i * nchunk + c], en = src_off[i * nchunk + c + 1];
-    for (int e4 = tid; e4 < n4; e4 += 256) {
-      float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-      int s = b;
-      for (; s + 4 <= en; s += 4) {  // four independent loads in flight, summed in order
-        float4 v[4];
+    // slot offsets of this (subject, chunk) staged in shared memory
+    __shared__ int64_t s_off[PR_MAX_SLOTS];
+    const int ns = en - b;
+    for (int q = tid; q < ns && q < PR_MAX_SLOTS; q += 256) s_off[q] = src[b + q].off;
+    __syncthreads();
+    // a thread's FW float4 positions, two slots at a time: 2 FW loads in flight, summed in slot order
+    float4 a4[FW];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = __ldg(reinterpret_cast<const float4*>(part + src[s + u].off) + e4);
+    for (int j = 0; j < FW; ++j) a4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < ns; q += 2) {
+      const int64_t o0 = q < PR_MAX_SLOTS ? s_off[q] : src[b + q].off;
+      const bool two = q + 1 < ns;
+      const int64_t o1 = two ? (q + 1 < PR_MAX_SLOTS ? s_off[q + 1] : src[b + q + 1].off) : o0;
+      float4 v0[FW], v1[FW];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          a.x += v[u].x;
-          a.y += v[u].y;
-          a.z += v[u].z;
-          a.w += v[u].w;
+      for (int j = 0; j < FW; ++j) {
+        v0[j] = __ldg(reinterpret_cast<const float4*>(part + o0) + tid + 256 * j);
+        v1[j] = two ? __ldg(reinterpret_cast<const float4*>(part + o1) + tid + 256 * j) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int j = 0; j < FW; ++j) {
+        a4[j].x += v0[j].x;
+        a4[j].y += v0[j].y;
+        a4[j].z += v0[j].z;
+        a4[j].w += v0[j].w;
+        if (two) {
+          a4[j].x += v1[j].x;
+          a4[j].y += v1[j].y;
+          a4[j].z += v1[j].z;
+          a4[j].w += v1[j].w;
         }
       }
-      for (; s < en; ++s) {
-        const float4 v = __ldg(reinterpret_cast<const float4*>(part + src[s].off) + e4);
-        a.x += v.x;
-        a.y += v.y;
-        a.z += v.z;
-        a.w += v.w;
-      }
-      const int e = 4 * e4, t = e / KLD, f = e - t * KLD;
+    }
+#pragma unroll
+    for (int j = 0; j < FW; ++j) {
+      const int e = 4 * (tid + 256 * j), t = e / KLD, f = e - t * KLD;
       float* d = Ps + t * (KLD + 1) + f;
-      d[0] = a.x;
-      d[1] = a.y;
-      d[2] = a.z;
-      d[3] = a.w;
+      d[0] = a4[j].x;
+      d[1] = a4[j].y;
+      d[2] = a4[j].z;
+      d[3] = a4[j].w;
     }
     __syncthreads();
     float z[4][FW];
