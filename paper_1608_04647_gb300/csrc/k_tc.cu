@@ -59,6 +59,7 @@ struct TcState {
   int egrid = 0;        // E-pass CTAs
   bool m_res = false;   // M-pass keeps E[S] resident in shared memory
   int m_stages = 4;     // M-pass pipeline depth
+  int m_gop = 2;        // M-pass Gram operand buffers
   size_t m_smem = 0;
 };
 
@@ -80,12 +81,18 @@ __host__ __device__ constexpr uint32_t m_stage_bytes(int kld) { return 128u * 12
 constexpr uint32_t kBarBytes = 256;
 constexpr size_t e_smem_bytes(int kld) { return 1024 + (size_t)E_STAGES * e_stage_bytes(kld) + kBarBytes; }
 // Gram operand buffers: kld = 64 uses one feature atom per buffer plus one
-// shared zero atom (48 KB); kld = 128 uses two atoms per buffer (64 KB).
-__host__ __device__ constexpr uint32_t gop_bytes(int kld) { return kld == 64 ? 49152u : 65536u; }
+// shared zero atom; kld = 128 uses two atoms per buffer.
+// One or two Gram operand buffers (chosen at run time): with one, the
+// epilogue of tile n + 1 waits for the Gram MMA of tile n, and the bytes saved
+// buy one more X^ stage.
+__host__ __device__ constexpr uint32_t gop_bytes(int kld, int nb) {
+  return kld == 64 ? 16384u * (uint32_t)(nb + 1) : 32768u * (uint32_t)nb;
+}
 constexpr int M_MAX_STAGES = 8;  // runtime stage count of the M-pass is at most this
 constexpr int M_PF = 8;          // M-pass L2 prefetch distance (X^ chunks of 16 KB) ...
 constexpr int M_PF_STAGES = 5;   // ... used when fewer shared-memory stages than this fit
-constexpr size_t m_fixed_bytes(int kld) { return 1024 + gop_bytes(kld) + kBarBytes; }
+constexpr int M_PF_MODE = 1;     // 1: per 16 KB chunk (tensor), 2: per tile (bulk, contiguous rows)
+constexpr size_t m_fixed_bytes(int kld, int nb) { return 1024 + gop_bytes(kld, nb) + kBarBytes; }
 constexpr size_t kMaxSmem = 232448;  // opt-in limit per block
 
 // ------------------------------------------------------------------ E-pass
@@ -260,6 +267,7 @@ template <int KLD, bool RES>
 __global__ void __launch_bounds__(NT, 1)
     mstep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE,
                     const SegM* __restrict__ segs, const int* __restrict__ seg_off, int T, int S_N, int pf_dist,
+                    int gop_nb, const uint8_t* __restrict__ xbase, int64_t xrow_bytes,
                     __nv_bfloat16* __restrict__ Aout, float* __restrict__ gpart, int* status) {
   constexpr uint32_t X_BYTES = 128u * 128u;
   constexpr uint32_t E_CHUNK = (uint32_t)KLD * 128u;
@@ -273,7 +281,7 @@ __global__ void __launch_bounds__(NT, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* eres = smem + S_N * STAGE;                      // resident E[S] chunks (RES only)
   uint8_t* gop = eres + (RES ? (uint32_t)nk * E_CHUNK : 0u);  // Gram operand buffers
-  uint64_t* full = reinterpret_cast<uint64_t*>(gop + gop_bytes(KLD));
+  uint64_t* full = reinterpret_cast<uint64_t*>(gop + gop_bytes(KLD, gop_nb));
   uint64_t* empty = full + S_N;
   uint64_t* acc_full = empty + S_N;        // [2]
   uint64_t* acc_empty = acc_full + 2;      // [2]
@@ -290,13 +298,13 @@ __global__ void __launch_bounds__(NT, 1)
   auto gop_atom = [&](int b, int a) -> uint8_t* {
     return KLD == 64 ? gop + b * 16384 : gop + b * 32768 + a * 16384;
   };
-  auto gop_lbo = [&](int b) -> uint32_t { return KLD == 64 ? 32768u - 16384u * b : 16384u; };
+  auto gop_lbo = [&](int b) -> uint32_t { return KLD == 64 ? 16384u * (uint32_t)(gop_nb - b) : 16384u; };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g0 = seg_off[blockIdx.x], g1 = seg_off[blockIdx.x + 1];
 
   // zero the Gram operand buffers (with kld = 64 the shared atom 64..127 stays zero)
-  for (uint32_t e = threadIdx.x; e < gop_bytes(KLD) / 16; e += NT)
+  for (uint32_t e = threadIdx.x; e < gop_bytes(KLD, gop_nb) / 16; e += NT)
     reinterpret_cast<uint4*>(gop)[e] = make_uint4(0, 0, 0, 0);
   fence_proxy_async_smem();
   if (threadIdx.x == 0) {
@@ -351,7 +359,17 @@ __global__ void __launch_bounds__(NT, 1)
         while (pg < g1 && ptile >= segs[pg].tile_end)
           if (++pg < g1) ptile = segs[pg].tile_begin;
         if (pg >= g1 || pf_dist == 0) return;
-        tma_prefetch_l2_2d(&mapX, 64 * pkc, (int)(ptile * 128));
+        if (M_PF_MODE == 2) {
+          // a whole 128-row tile (contiguous rows) per prefetch, in 32 KB pieces
+          if (pkc == 0) {
+            const uint8_t* p = xbase + ptile * 128 * xrow_bytes;
+            const int64_t tot = 128 * xrow_bytes;
+            for (int64_t o = 0; o < tot; o += 32768)
+              bulk_prefetch_l2(p + o, (uint32_t)(tot - o < 32768 ? tot - o : 32768));
+          }
+        } else {
+          tma_prefetch_l2_2d(&mapX, 64 * pkc, (int)(ptile * 128));
+        }
         if (++pkc == nk) {
           pkc = 0;
           ++ptile;
@@ -455,7 +473,7 @@ __global__ void __launch_bounds__(NT, 1)
             break;
           }
           pv = true;
-          pb = b;
+          pb = (int)(n % gop_nb);
           pfirst = (tile == sg.tile_begin);
           plast = (tile == sg.tile_end - 1);
         }
@@ -480,11 +498,12 @@ __global__ void __launch_bounds__(NT, 1)
           break;
         }
         af_ph[b] ^= 1u;
-        if (!warp_wait(&gram_free[b], gf_ph[b] ^ 1u, abort_s, status)) {
+        const int gb = (int)(n % gop_nb);  // Gram operand buffer
+        if (!warp_wait(&gram_free[gb], gf_ph[gb] ^ 1u, abort_s, status)) {
           ok = false;
           break;
         }
-        gf_ph[b] ^= 1u;
+        gf_ph[gb] ^= 1u;
         tc_fence_after();
         __nv_bfloat16* arow = Aout + (tile * 128 + row) * (int64_t)KLD;
 
@@ -506,14 +525,14 @@ __global__ void __launch_bounds__(NT, 1)
             const uint4 v = make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
             ga[u] = v;
             const int phys = (cbase + u) ^ (row & 7);
-            *reinterpret_cast<uint4*>(gop_atom(b, atom) + row * 128 + phys * 16) = v;
+            *reinterpret_cast<uint4*>(gop_atom(gb, atom) + row * 128 + phys * 16) = v;
           }
         }
         fence_proxy_async_smem();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) {
-          mbar_arrive(&gram_ready[b]);
+          mbar_arrive(&gram_ready[gb]);
           mbar_arrive(&acc_empty[b]);
         }
         if (tile == sg.tile_end - 1) {
@@ -799,13 +818,28 @@ srm_status tc_setup(Ctx* c) {
   {
     // stage count from the shared-memory budget: resident E[S] if that still
     // leaves at least M_RES_MIN stages of X^ tiles, else streamed E[S] chunks
-    const size_t fixed = m_fixed_bytes(c->kld);
-    const size_t eres = (size_t)nk * c->kld * 128;
-    const long res_st = fixed + eres < kMaxSmem ? (long)((kMaxSmem - fixed - eres) / 16384) : 0;
-    const long str_st = (long)((kMaxSmem - fixed) / m_stage_bytes(c->kld));
+    // Two Gram buffers unless one buffer gives a deeper pipeline of at least
+    // M_PF_STAGES stages (measured: T = 1000, k = 50 runs faster with three
+    // stages, two buffers and L2 prefetch than with four stages and one
+    // buffer; T = 500 and T = 3500 gain from the extra stage).
     constexpr long M_RES_MIN = 3;
-    s->m_res = res_st >= M_RES_MIN;
-    s->m_stages = (int)std::min<long>(M_MAX_STAGES, s->m_res ? res_st : str_st);
+    const size_t eres = (size_t)nk * c->kld * 128;
+    auto plan = [&](int nb, bool& res, long& st) {
+      const size_t fixed = m_fixed_bytes(c->kld, nb);
+      const long res_st = fixed + eres < kMaxSmem ? (long)((kMaxSmem - fixed - eres) / 16384) : 0;
+      const long str_st = (long)((kMaxSmem - fixed) / m_stage_bytes(c->kld));
+      res = res_st >= M_RES_MIN;
+      st = std::min<long>(M_MAX_STAGES, res ? res_st : str_st);
+    };
+    bool res1, res2;
+    long st1, st2;
+    plan(1, res1, st1);
+    plan(2, res2, st2);
+    const bool one = (res1 == res2) && st1 > st2 && st1 >= M_PF_STAGES;
+    s->m_gop = one ? 1 : 2;
+    s->m_res = one ? res1 : res2;
+    s->m_stages = (int)(one ? st1 : st2);
+    const size_t fixed = m_fixed_bytes(c->kld, s->m_gop);
     s->m_smem = fixed + (s->m_res ? eres + (size_t)s->m_stages * 16384 : (size_t)s->m_stages * m_stage_bytes(c->kld));
   }
   // The E-pass leaves room on each SM for the M-step tail that runs beside it
@@ -856,7 +890,8 @@ cudaError_t launch_a_tc(Ctx* c) {
   auto* A = static_cast<__nv_bfloat16*>(c->A);
 #define M_LAUNCH(KLD, RES)                                                                                  \
   mstep_tc_kernel<KLD, RES><<<s->grid, NT, s->m_smem, c->stream>>>(s->mapXm, s->mapE, s->d_seg, s->d_seg_off, \
-                                                                   c->T, s->m_stages, s->m_stages < M_PF_STAGES ? M_PF : 0, A, \
+                                                                   c->T, s->m_stages, s->m_stages < M_PF_STAGES ? M_PF : 0, \
+                                                                   s->m_gop, static_cast<const uint8_t*>(c->Xh), (int64_t)c->ldT * 2, A, \
                                                                    c->Gpart, c->status)
   if (c->kld == 64) {
     if (s->m_res) M_LAUNCH(64, true);
