@@ -118,10 +118,27 @@ __global__ void __launch_bounds__(256) p_reduce_kernel(EReduceArgs ar) {
   static_assert(TCH * KLD / 4 == 256 * FW, "a thread owns FW float4 positions of a slot block");
   for (int i = i0; i < i1; ++i) {
     __syncthreads();  // the previous subject's tiles have been read
-    const float* Mi = M32 + (int64_t)i * KLD * KLD;
-    for (int e = tid; e < KLD * KLD; e += 256) {  // M_i is symmetric: row m read as column m
-      const int m = e / KLD, f = e - m * KLD;
-      Ms[e] = (f < k && m < k) ? Mi[e] : 0.f;
+    // M_i (symmetric: row m read as column m): KLD^2 / 4 float4, all of a thread's loads in flight
+    {
+      constexpr int NM4 = KLD * KLD / 4;          // 64 FW^2
+      constexpr int MJ = (NM4 + 255) / 256;
+      const float4* Mi4 = reinterpret_cast<const float4*>(M32 + (int64_t)i * KLD * KLD);
+      float4 mv[MJ];
+#pragma unroll
+      for (int j = 0; j < MJ; ++j)
+        mv[j] = (tid + 256 * j < NM4) ? __ldg(Mi4 + tid + 256 * j) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < MJ; ++j) {
+        if (tid + 256 * j >= NM4) continue;
+        const int e = 4 * (tid + 256 * j), m = e / KLD, f = e - m * KLD;
+        const bool rm = m < k;
+        float4 v = mv[j];
+        v.x = (rm && f < k) ? v.x : 0.f;
+        v.y = (rm && f + 1 < k) ? v.y : 0.f;
+        v.z = (rm && f + 2 < k) ? v.z : 0.f;
+        v.w = (rm && f + 3 < k) ? v.w : 0.f;
+        *reinterpret_cast<float4*>(Ms + e) = v;
+      }
     }
     const int b = src_off[i * nchunk + c], en = src_off[i * nchunk + c + 1];
     // slot offsets of this (subject, chunk) staged in shared memory

@@ -263,11 +263,11 @@ __global__ void __launch_bounds__(NT, 1)
 // RES: E[S] (all 64-column chunks, kld rows each) is loaded once per CTA and
 // stays in shared memory; the stages then carry X^ tiles only.  Otherwise
 // every stage carries an X^ tile and the matching E[S] chunk.
-template <int KLD, bool RES>
+template <int KLD, bool RES, int GNB>  // GNB: Gram operand buffers (1 or 2)
 __global__ void __launch_bounds__(NT, 1)
     mstep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE,
                     const SegM* __restrict__ segs, const int* __restrict__ seg_off, int T, int S_N, int pf_dist,
-                    int gop_nb, const uint8_t* __restrict__ xbase, int64_t xrow_bytes,
+                    const uint8_t* __restrict__ xbase, int64_t xrow_bytes,
                     __nv_bfloat16* __restrict__ Aout, float* __restrict__ gpart, int* status) {
   constexpr uint32_t X_BYTES = 128u * 128u;
   constexpr uint32_t E_CHUNK = (uint32_t)KLD * 128u;
@@ -276,6 +276,7 @@ __global__ void __launch_bounds__(NT, 1)
   constexpr uint32_t IDESC_MAIN = idesc_bf16(128, KLD, false, false);
   constexpr uint32_t IDESC_GRAM = idesc_bf16(128, KLD, true, true);
   const int nk = (T + 63) / 64;
+  constexpr int gop_nb = GNB;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -851,13 +852,16 @@ srm_status tc_setup(Ctx* c) {
                        cudaSharedmemCarveoutMaxShared);
   if (c->kld == 64) {
     cudaFuncSetAttribute(estep_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e_smem_bytes(64));
-    cudaFuncSetAttribute(mstep_tc_kernel<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
-    cudaFuncSetAttribute(mstep_tc_kernel<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+    cudaFuncSetAttribute(mstep_tc_kernel<64, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+    cudaFuncSetAttribute(mstep_tc_kernel<64, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+    cudaFuncSetAttribute(mstep_tc_kernel<64, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+    cudaFuncSetAttribute(mstep_tc_kernel<64, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
   } else {
     cudaFuncSetAttribute(estep_tc_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e_smem_bytes(128));
-    cudaFuncSetAttribute(mstep_tc_kernel<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kMaxSmem);
-    cudaFuncSetAttribute(mstep_tc_kernel<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+    cudaFuncSetAttribute(mstep_tc_kernel<128, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+    cudaFuncSetAttribute(mstep_tc_kernel<128, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+    cudaFuncSetAttribute(mstep_tc_kernel<128, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+    cudaFuncSetAttribute(mstep_tc_kernel<128, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core kernel attributes");
@@ -888,18 +892,30 @@ cudaError_t launch_p_tc(Ctx* c) {
 cudaError_t launch_a_tc(Ctx* c) {
   auto* s = static_cast<TcState*>(c->tc);
   auto* A = static_cast<__nv_bfloat16*>(c->A);
-#define M_LAUNCH(KLD, RES)                                                                                  \
-  mstep_tc_kernel<KLD, RES><<<s->grid, NT, s->m_smem, c->stream>>>(s->mapXm, s->mapE, s->d_seg, s->d_seg_off, \
-                                                                   c->T, s->m_stages, s->m_stages < M_PF_STAGES ? M_PF : 0, \
-                                                                   s->m_gop, static_cast<const uint8_t*>(c->Xh), (int64_t)c->ldT * 2, A, \
-                                                                   c->Gpart, c->status)
-  if (c->kld == 64) {
-    if (s->m_res) M_LAUNCH(64, true);
-    else M_LAUNCH(64, false);
-  } else {
-    if (s->m_res) M_LAUNCH(128, true);
-    else M_LAUNCH(128, false);
+#define M_LAUNCH(KLD, RES, GNB)                                                                                  \
+  mstep_tc_kernel<KLD, RES, GNB><<<s->grid, NT, s->m_smem, c->stream>>>(                                          \
+      s->mapXm, s->mapE, s->d_seg, s->d_seg_off, c->T, s->m_stages, s->m_stages < M_PF_STAGES ? M_PF : 0,          \
+      static_cast<const uint8_t*>(c->Xh), (int64_t)c->ldT * 2, A, c->Gpart, c->status)
+#define M_LAUNCH2(KLD, RES) \
+  if (s->m_gop == 1) {      \
+    M_LAUNCH(KLD, RES, 1);  \
+  } else {                  \
+    M_LAUNCH(KLD, RES, 2);  \
   }
+  if (c->kld == 64) {
+    if (s->m_res) {
+      M_LAUNCH2(64, true)
+    } else {
+      M_LAUNCH2(64, false)
+    }
+  } else {
+    if (s->m_res) {
+      M_LAUNCH2(128, true)
+    } else {
+      M_LAUNCH2(128, false)
+    }
+  }
+#undef M_LAUNCH2
 #undef M_LAUNCH
   return cudaGetLastError();
 }

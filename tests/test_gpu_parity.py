@@ -25,6 +25,9 @@ PLAIN_CASES = [
     # data of magnitude 1e4 (Gram entries near 1e20), k > 64: the eigen-solver path
     Case("k80-scaled-1e4", [3000, 2600], 400, 80, 4, seed=12, scale=1e4),
     Case("k50-scaled-1e4", [2500, 3100, 2000], 500, 50, 4, seed=13, scale=1e4),
+    # the largest k of the Newton-Schulz polar path (64) and the smallest past it (65)
+    Case("k64-boundary", [900, 1300], 130, 64, 4, seed=14),
+    Case("k65-eigen-path", [1000, 1200], 131, 65, 4, seed=15),
     # more subjects than E-step reduction groups: several subjects per group
     Case("grouped-subjects", [int(x) for x in np.random.default_rng(11).integers(40, 250, size=150)], 1500, 8, 4,
          seed=11),
