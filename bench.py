@@ -403,6 +403,53 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_k_sweep(args):
+    """Number of features k against throughput on the greeneyes-like shapes
+    (N = 16, v ~ U[2e4, 6e4], T = 1000; the paper's E3 runtime-vs-K, whose
+    values appear only in a figure): one JSON line per k with EM iterations/s
+    and each pass's GB/s.  k up to 128 (the library's limit)."""
+    import dataclasses
+
+    import torch
+
+    import paper_1608_04647_gb300 as srm
+    import synth
+    from paper_1608_04647_gb300 import _build
+    from synth.planted_torch import planted_dataset_torch
+
+    _build.build()
+    srm.load_library()
+    base = synth.config_spec(1)
+    vox = synth.draw_voxel_counts(base)
+    peaks = load_peaks()
+    for k in (10, 30, 60, 100, 128):
+        spec = dataclasses.replace(base, k=k, name=f"greeneyes-like N=16 v~U[2e4,6e4] T=1000 k={k}")
+        d = planted_dataset_torch(spec, vox, device="cuda")
+        stream = torch.cuda.Stream()
+        m = srm.SRM(d["X"], d["W0"], k, store="bf16", graph=True, max_iter=args.warmup + args.steps + 8,
+                    stream=stream)
+        ms = time_fit(m, stream, args.steps, args.warmup) / args.steps
+        m.close()
+        mp = srm.SRM(d["X"], d["W0"], k, store="bf16", graph=False, profile=True,
+                     max_iter=args.warmup + args.steps + 8, stream=stream)
+        mp.fit_async(args.warmup)
+        mp.kernel_times(reset=True)
+        mp.fit_async(args.steps)
+        kt = mp.kernel_times()
+        mp.close()
+        e_bytes, m_bytes = algorithmic_bytes(vox, spec.T, k, 2, 2)
+        te = kt["estep_tc"][1] / args.steps
+        tm = kt["mstep_tc"][1] / args.steps
+        print(json.dumps({"k_sweep": True, "k": k, "metric": METRIC, "value": round(1000.0 / ms, 3), "unit": UNIT,
+                          "ms_per_step": round(ms, 4), "estep_gbs": round(e_bytes / (te * 1e-3) / 1e9, 1),
+                          "mstep_gbs": round(m_bytes / (tm * 1e-3) / 1e9, 1), "peak_gbs": peaks["hbm_gbs"],
+                          "paper_gflops": round(paper_flops(vox, spec.T, k) / (ms * 1e-3) / 1e9, 1),
+                          "kernels_ms_per_step": {n: round(v[1] / args.steps, 4) for n, v in kt.items() if v[0]}}),
+              flush=True)
+        del d
+        torch.cuda.empty_cache()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -414,9 +461,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--k-sweep", action="store_true", help="throughput against k (extra lines, not the bench line)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.k_sweep:
+        run_k_sweep(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -149,6 +149,22 @@ SRM_API srm_status srm_transform(srm_ctx* ctx, int32_t subject, const void* X_ne
                          float* S_out_dev);
 
 /*
+ * srm_map -- map new data of subject `from` into the voxel space of subject
+ * `to` through the shared space (Sec. II-A, the orthogonality of the mappings
+ * gives the subject-to-subject map W_j W_i^T):
+ *   Y_out = W_to W_from^T (X_new - mean_t X_new).
+ *   from, to   0 <= from, to < N (equal: the projection onto span W_from)
+ *   X_new_dev  v_from x T_new row-major, cfg->in_dtype, device pointer
+ *   T_new      >= 1 columns
+ *   Y_out_dev  v_to x T_new row-major FP32, device pointer (written)
+ * Uses the mappings of the last M-step (W^0 before any).  Keeps a scratch
+ * buffer of 2 k T_new floats in the context (grown on demand; SRM_ERR_NOMEM
+ * if that allocation fails).  Asynchronous.
+ */
+SRM_API srm_status srm_map(srm_ctx* ctx, int32_t from, int32_t to, const void* X_new_dev, int32_t T_new,
+                           float* Y_out_dev);
+
+/*
  * srm_transform_noalloc -- the same result as srm_transform, for callers that
  * must not allocate device memory: code that runs while a CUDA stream is
  * being captured into a graph (an allocation there breaks the capture),

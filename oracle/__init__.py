@@ -16,6 +16,7 @@ from .psrm import (  # noqa: F401
     mstep,
     fit,
     transform,
+    map_subjects,
     ppca_fixed_point,
     State,
 )

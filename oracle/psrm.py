@@ -225,6 +225,13 @@ def transform(W_i: np.ndarray, X_new: np.ndarray) -> np.ndarray:
     return W_i.T @ Xh
 
 
+def map_subjects(W_i: np.ndarray, W_j: np.ndarray, X_new: np.ndarray) -> np.ndarray:
+    """Map new data of subject i into subject j's voxel space through the
+    shared space: W_j W_i^T (x - mean_t x) (Sec. II-A, the use the
+    orthogonality of the mappings makes simple)."""
+    return W_j @ transform(W_i, X_new)
+
+
 # ---------------------------------------------------------------- special case
 def ppca_fixed_point(Xhat: np.ndarray, k: int):
     """N = 1: the model is probabilistic PCA with orthonormal loadings

@@ -26,7 +26,7 @@ __all__ = [
     "srm_init", "srm_estep", "srm_mstep", "srm_fit", "srm_transform", "srm_get_w", "srm_get_s",
     "srm_get_params", "srm_get_ll", "srm_synchronize", "srm_get_state", "srm_set_state",
     "srm_get_kernel_times", "srm_layout", "srm_last_error", "srm_destroy", "srm_debug_mma",
-    "srm_transform_noalloc", "srm_debug_eig_sweeps",
+    "srm_transform_noalloc", "srm_debug_eig_sweeps", "srm_map",
 ]
 
 SRM_OK, SRM_ERR_ARG, SRM_ERR_CUDA, SRM_ERR_NOMEM, SRM_ERR_NUMERIC, SRM_ERR_STATE, SRM_ERR_UNSUPPORTED = range(7)
@@ -94,6 +94,7 @@ def load_library(path: Optional[str] = None):
         "srm_last_error": (ctypes.c_char_p, []),
         "srm_debug_mma": (st, [ctypes.c_int32, _P, _P, _P, ctypes.c_int32, ctypes.c_int32]),
         "srm_transform_noalloc": (st, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
+        "srm_map": (st, [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, _P]),
         "srm_debug_eig_sweeps": (st, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
         "srm_destroy": (None, [_P]),
     }
@@ -152,6 +153,10 @@ def srm_transform_noalloc(ctx: int, subject: int, X_new_ptr: int, T_new: int, S_
     comes from a fixed 16 MiB device array inside the library (see srm.h)."""
     _check(load_library().srm_transform_noalloc(_P(ctx), subject, _P(X_new_ptr), T_new, _P(S_out_ptr)),
            "srm_transform_noalloc")
+
+
+def srm_map(ctx: int, src: int, dst: int, X_new_ptr: int, T_new: int, Y_out_ptr: int):
+    _check(load_library().srm_map(_P(ctx), src, dst, _P(X_new_ptr), T_new, _P(Y_out_ptr)), "srm_map")
 
 
 def srm_get_w(ctx: int, subject: int, W_ptr: int):
@@ -323,6 +328,14 @@ class SRM:
         srm_transform(self.ctx, i, X_new.data_ptr(), int(X_new.shape[1]), S.data_ptr())
         self.synchronize()
         return S
+
+    def map(self, i: int, j: int, X_new):
+        """Subject i's new data in subject j's voxel space: W_j W_i^T (x - mean)."""
+        import torch
+        Y = torch.empty((self.voxels[j], int(X_new.shape[1])), dtype=torch.float32, device="cuda")
+        srm_map(self.ctx, i, j, X_new.data_ptr(), int(X_new.shape[1]), Y.data_ptr())
+        self.synchronize()
+        return Y
 
     def state(self) -> bytes:
         return srm_get_state(self.ctx)

@@ -99,7 +99,7 @@ void free_all(Ctx* c) {
   void* ptrs[] = {c->Xh, c->A, c->sqnorm, c->rowsq, c->d_off, c->d_v, c->rho2, c->Sigma, c->SigmaNext, c->L,
                   c->Phi, c->scal, c->M64, c->M32, c->Uwarm, c->G64, c->U64, c->H64, c->Xr64, c->eigv, c->Y,
                   c->ES64, c->ESt, c->ESb, c->esPart, c->ll, c->iter, c->status, c->Ppart, c->chunk_src, c->jac_sweeps, c->ns_fb,
-                  c->chunk_src_off, c->Ypart, c->ered_cnt, c->sPart, c->Gpart, c->gslot_off, c->tr_buf, c->tr_part};
+                  c->chunk_src_off, c->Ypart, c->ered_cnt, c->sPart, c->map_buf, c->Gpart, c->gslot_off, c->tr_buf, c->tr_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);

@@ -50,7 +50,7 @@ struct SegM {
 };
 
 struct TcState {
-  CUtensorMap mapXe, mapA, mapXm, mapE;
+  CUtensorMap mapXe, mapA, mapXm, mapE, mapAs;
   WorkE* d_work = nullptr;
   int* d_work_off = nullptr;
   SegM* d_seg = nullptr;
@@ -266,6 +266,7 @@ __global__ void __launch_bounds__(NT, 1)
 template <int KLD, bool RES, int GNB>  // GNB: Gram operand buffers (1 or 2)
 __global__ void __launch_bounds__(NT, 1)
     mstep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE,
+                    const __grid_constant__ CUtensorMap mapAs,
                     const SegM* __restrict__ segs, const int* __restrict__ seg_off, int T, int S_N, int pf_dist,
                     const uint8_t* __restrict__ xbase, int64_t xrow_bytes,
                     __nv_bfloat16* __restrict__ Aout, float* __restrict__ gpart, int* status) {
@@ -292,7 +293,8 @@ __global__ void __launch_bounds__(NT, 1)
   uint64_t* gram_empty = gram_full + 1;
   uint64_t* done = gram_empty + 1;
   uint64_t* e_full = done + 1;
-  uint32_t* tmem_s = reinterpret_cast<uint32_t*>(e_full + 1);
+  uint64_t* epi_bar = e_full + 1;          // the four epilogue warps meet here (bounded waits)
+  uint32_t* tmem_s = reinterpret_cast<uint32_t*>(epi_bar + 1);
   volatile int* abort_s = reinterpret_cast<volatile int*>(tmem_s + 1);
   // Gram operand buffer b, feature atom a (a = 1 only for kld = 128) and the
   // distance from atom 0 to atom 1 (the descriptor's leading-byte offset)
@@ -323,12 +325,14 @@ __global__ void __launch_bounds__(NT, 1)
     mbar_init(gram_full, 1);
     mbar_init(gram_empty, 4);
     mbar_init(done, 1);
+    mbar_init(epi_bar, 4);
     *abort_s = 0;
     fence_mbar_init();
   }
   if (threadIdx.x == 32) {
     tma_prefetch(&mapX);
     tma_prefetch(&mapE);
+    tma_prefetch(&mapAs);
   }
   if (warp == 1) {
     tmem_alloc(tmem_s, TMEM_COLS);
@@ -487,9 +491,17 @@ __global__ void __launch_bounds__(NT, 1)
   } else {
     const int q = warp & 3;
     const int row = q * 32 + lane;
-    uint32_t af_ph[2] = {0, 0}, gf_ph[2] = {0, 0}, gfl_ph = 0;
+    uint32_t af_ph[2] = {0, 0}, gf_ph[2] = {0, 0}, gfl_ph = 0, eb_ph = 0;
     int64_t n = 0;
     bool ok = true;
+    // all four epilogue warps arrive (lane 0 each) and wait, with the bounded wait
+    auto epi_sync = [&]() -> bool {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(epi_bar);
+      const bool r = warp_wait(epi_bar, eb_ph, abort_s, status);
+      eb_ph ^= 1u;
+      return r;
+    };
     for (int g = g0; g < g1 && ok; ++g) {
       const SegM sg = segs[g];
       for (int64_t tile = sg.tile_begin; tile < sg.tile_end; ++tile, ++n) {
@@ -506,7 +518,12 @@ __global__ void __launch_bounds__(NT, 1)
         }
         gf_ph[gb] ^= 1u;
         tc_fence_after();
-        __nv_bfloat16* arow = Aout + (tile * 128 + row) * (int64_t)KLD;
+        // the TMA store of the buffer's previous tile must have read it
+        if (threadIdx.x == 64) bulk_wait_read0();
+        if (!epi_sync()) {
+          ok = false;
+          break;
+        }
 
 #pragma unroll
         for (int cc = 0; cc < KLD / 32; ++cc) {
@@ -518,19 +535,28 @@ __global__ void __launch_bounds__(NT, 1)
             __nv_bfloat162 h = __floats2bfloat162_rn(r[2 * u], r[2 * u + 1]);
             pk[u] = *reinterpret_cast<uint32_t*>(&h);
           }
-          uint4* ga = reinterpret_cast<uint4*>(arow + cc * 32);
           const int atom = (cc * 32) >> 6;
           const int cbase = (cc & 1) * 4;
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const uint4 v = make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
-            ga[u] = v;
             const int phys = (cbase + u) ^ (row & 7);
             *reinterpret_cast<uint4*>(gop_atom(gb, atom) + row * 128 + phys * 16) = v;
           }
         }
         fence_proxy_async_smem();
         tc_fence_before();
+        // A_i tile to global memory: one TMA store per 64-feature atom of the
+        // 128B-swizzled copy (the same bytes the Gram MMA reads)
+        if (!epi_sync()) {
+          ok = false;
+          break;
+        }
+        if (threadIdx.x == 64) {
+#pragma unroll
+          for (int a = 0; a < KLD / 64; ++a) tma_store_2d(&mapAs, 64 * a, (int)(tile * 128), gop_atom(gb, a));
+          bulk_commit();
+        }
         __syncwarp();
         if (lane == 0) {
           mbar_arrive(&gram_ready[gb]);
@@ -560,6 +586,7 @@ __global__ void __launch_bounds__(NT, 1)
         }
       }
     }
+    if (threadIdx.x == 64) bulk_wait0();  // the A_i stores have landed
   }
   tc_fence_before();
   __syncthreads();
@@ -718,7 +745,8 @@ srm_status tc_setup(Ctx* c) {
   bool ok = make_map(&s->mapXe, c->Xh, c->T, c->Vpad_tot, (uint64_t)c->ldT * 2, 64, E_KR) &&
             make_map(&s->mapA, c->A, c->kld, c->Vpad_tot, (uint64_t)c->kld * 2, 64, E_KR) &&
             make_map(&s->mapXm, c->Xh, c->T, c->Vpad_tot, (uint64_t)c->ldT * 2, 64, 128) &&
-            make_map(&s->mapE, c->ESb, c->T, c->kld, (uint64_t)c->ldT * 2, 64, c->kld);
+            make_map(&s->mapE, c->ESb, c->T, c->kld, (uint64_t)c->ldT * 2, 64, c->kld) &&
+            make_map(&s->mapAs, c->A, c->kld, c->Vpad_tot, (uint64_t)c->kld * 2, 64, 128);
   if (!ok) {
     set_error("cuTensorMapEncodeTiled failed (driver entry point missing or bad layout)");
     return SRM_ERR_CUDA;
@@ -894,7 +922,8 @@ cudaError_t launch_a_tc(Ctx* c) {
   auto* A = static_cast<__nv_bfloat16*>(c->A);
 #define M_LAUNCH(KLD, RES, GNB)                                                                                  \
   mstep_tc_kernel<KLD, RES, GNB><<<s->grid, NT, s->m_smem, c->stream>>>(                                          \
-      s->mapXm, s->mapE, s->d_seg, s->d_seg_off, c->T, s->m_stages, s->m_stages < M_PF_STAGES ? M_PF : 0,          \
+      s->mapXm, s->mapE, s->mapAs, s->d_seg, s->d_seg_off, c->T, s->m_stages,                                      \
+      s->m_stages < M_PF_STAGES ? M_PF : 0,                                                                        \
       static_cast<const uint8_t*>(c->Xh), (int64_t)c->ldT * 2, A, c->Gpart, c->status)
 #define M_LAUNCH2(KLD, RES) \
   if (s->m_gop == 1) {      \

@@ -157,6 +157,8 @@ struct Ctx {
   int64_t tr_elems = 0;
   float* tr_part = nullptr;
   int64_t tr_part_elems = 0;
+  float* map_buf = nullptr;       // srm_map scratch (S and Z)
+  int64_t map_elems = 0;
 };
 
 // runs a deferred M-step tail (api.cu)

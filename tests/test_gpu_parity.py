@@ -102,6 +102,24 @@ def test_transform_matches_oracle():
         assert np.abs(S - So).max() / np.abs(So).max() <= 1e-5
 
 
+def test_map_between_subjects_matches_oracle():
+    """srm_map: W_j W_i^T (x - mean_t x) for new data, against the oracle's
+    mappings (the same fit), including i == j (the projection onto span W_i)."""
+    import oracle
+    import torch
+    case = PLAIN_CASES[1]
+    d = make_inputs(case)
+    o = run_oracle(d, case.n_iter, final_ll=False)
+    g = run_gpu(d, case.k, case.n_iter, store="f32", final_ll=False)
+    rng = np.random.default_rng(4)
+    for i, j in [(0, 1), (1, 1), (2, 0)]:
+        Xn = rng.standard_normal((d["X"][i].shape[0], 70)).astype(np.float32) - 1.0
+        Y = g["model"].map(i, j, torch.from_numpy(Xn).cuda()).cpu().numpy()
+        Yo = oracle.map_subjects(o["W"][i], o["W"][j], Xn.astype(np.float64))
+        assert Y.shape == Yo.shape
+        assert np.abs(Y - Yo).max() / np.abs(Yo).max() <= 1e-5
+
+
 def test_transform_before_fit_uses_w0():
     import oracle
     import torch

@@ -247,6 +247,25 @@ def test_transform_noise_free_closed_form():
     np.testing.assert_allclose(oracle.transform(W, X), S - S.mean(axis=1, keepdims=True), atol=1e-12)
 
 
+def test_map_subjects_closed_form_and_projection():
+    """Sec. II-A: x_it = W_i s_t + mu_i exactly -> W_j W_i^T (x - mean_t x) is
+    subject j's noise-free data W_j (s - mean_t s); and mapping a subject to
+    itself is the orthogonal projection onto span W_i (idempotent, residual
+    orthogonal to W_i)."""
+    rng = np.random.default_rng(17)
+    Wi = synth.random_orthonormal(rng, 60, 5)
+    Wj = synth.random_orthonormal(rng, 45, 5)
+    S = rng.standard_normal((5, 29))
+    X = Wi @ S + rng.standard_normal((60, 1))
+    np.testing.assert_allclose(oracle.map_subjects(Wi, Wj, X), Wj @ (S - S.mean(axis=1, keepdims=True)),
+                               atol=1e-12)
+    Y = rng.standard_normal((60, 29)) + 3.0
+    P = oracle.map_subjects(Wi, Wi, Y)
+    Yc = Y - Y.mean(axis=1, keepdims=True)
+    np.testing.assert_allclose(oracle.map_subjects(Wi, Wi, P), P, atol=1e-12)
+    np.testing.assert_allclose(Wi.T @ (Yc - P), np.zeros((5, 29)), atol=1e-12)
+
+
 def test_oracle_matches_committed_golden():
     """Regression pin: the oracle still reproduces the values its own script
     wrote for the raider-like workload (tests/golden/make_golden.py)."""
