@@ -44,7 +44,7 @@ void prof_begin(Ctx* c, int kind, int* ev0) {
 }
 
 // CUDA kernels behind one launcher call of each kind
-static const int kKernelsPerKind[KK_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 4, 4, 1, 1};
+static const int kKernelsPerKind[KK_COUNT] = {1, 1, 1, 2, 1, 1, 1, 1, 1, 4, 4, 1, 1};
 
 void prof_end(Ctx* c, int kind, int ev0) {
   const int ev1 = c->ev_next++;
@@ -99,7 +99,7 @@ void free_all(Ctx* c) {
   void* ptrs[] = {c->Xh, c->A, c->sqnorm, c->rowsq, c->d_off, c->d_v, c->rho2, c->Sigma, c->SigmaNext, c->L,
                   c->Phi, c->scal, c->M64, c->M32, c->Uwarm, c->G64, c->U64, c->H64, c->Xr64, c->eigv, c->Y,
                   c->ES64, c->ESt, c->ESb, c->esPart, c->ll, c->iter, c->status, c->Ppart, c->chunk_src, c->jac_sweeps, c->ns_fb,
-                  c->chunk_src_off, c->Ypart, c->ered_cnt, c->sPart, c->map_buf, c->Gpart, c->gslot_off, c->tr_buf, c->tr_part};
+                  c->chunk_src_off, c->Ypart, c->sPart, c->map_buf, c->Phi32, c->Gpart, c->gslot_off, c->tr_buf, c->tr_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -398,7 +398,7 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
   c->kld = batched ? (c->k <= 64 ? 64 : 128) : ((c->k + 15) / 16) * 16;
   c->ldT = ((c->T + 7) / 8) * 8;
   c->nchunk = (c->T + TCH - 1) / TCH;
-  c->nes_blk = c->nchunk;  // E[S] partials: one per 64-column chunk
+  c->nes_blk = es_blocks(c->T);  // E[S] partials: one per es block
   c->zgroups = zsum_groups(c->N, c->nchunk, c->num_sms);
   c->v.resize(c->N);
   c->vpad.resize(c->N);
@@ -450,11 +450,9 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
   AL(iter, 1, "iteration counter");
   AL(status, 1, "status");
   AL(esPart, c->nes_blk, "<y, E[S]> partials");
+  AL(Phi32, (int64_t)k * k, "Phi (FP32)");
   AL(sPart, (int64_t)c->nes_blk * k * k, "E[S] E[S]^T partials");
   AL(Ypart, (int64_t)c->zgroups * k * T, "subject-group reductions");
-  AL(ered_cnt, c->nchunk, "E-step arrival counters");
-  ce = cudaMemset(c->ered_cnt, 0, sizeof(int) * c->nchunk);
-  if (ce != cudaSuccess) return fail(cuda_fail(ce, "cudaMemset"));
   if (batched) {
     AL(ESb, (int64_t)c->kld * c->ldT, "E[S] bf16");
     ce = cudaMemset(c->ESb, 0, (size_t)c->kld * c->ldT * 2);

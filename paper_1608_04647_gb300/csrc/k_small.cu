@@ -54,43 +54,30 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 enum { SC_RHO0 = 0, SC_LOGDET = 1, SC_VLOGRHO = 2, SC_SQRHO = 3, SC_YPHIY = 4, SC_TRSIG = 5 };
 
 // ------------------------------------------------------------------ E-step
-// The whole E-step after the E-pass, in one launch.  grid (nchunk, G), 256
-// threads.
-// (A) Block (c, g) takes the subjects [N g / G, N (g + 1) / G) in order.  For
-//     each it sums the subject's partial blocks of t-chunk c in slot order
-//     into P (TCH x kld), forms Z_i = rho_i^-2 M_i P in FP32 (sum over m in
-//     order) and adds it to an FP64 accumulator; the block then writes
-//     ypart[g][f][t].  Thread (tx, ty) of the 16 x 16 grid holds the 4 x FW
-//     tile t = tx + 16 u, f = ty + 16 w, which reads P and M from shared
-//     memory at one load per two FMAs without bank conflicts (P rows padded
-//     to an odd stride, M stored m-major).
-// (B) The last of the G blocks of chunk c (an atomic arrival count; the sums
-//     themselves run in a fixed order, so results do not depend on which
-//     block is last) forms y = sum_g ypart[g] (FP64, groups in order),
-//     E[S] = Phi y for the chunk (FP32, the same tiling), the chunk's
-//     E[S] E[S]^T and <y, E[S]> partials, and the operand copies of E[S].
-// The arrival counters are reset by the blocks that consume them, so the
-// launch can be replayed (CUDA graphs).  Sigma_s^new and the log-likelihood
-// (sigma_kernel) are left to the M-step tail, which runs beside the next
-// E-pass: the M-pass needs only E[S].
+// p_reduce: grid (nchunk, G), 256 threads.  Block (c, g) takes the subjects
+// [N g / G, N (g + 1) / G) in order.  For each it sums the subject's partial
+// blocks of t-chunk c in slot order into P (TCH x kld), forms
+// Z_i = rho_i^-2 M_i P in FP32 (sum over m in order) and adds it to an
+// error-free FP32 accumulator (hi + lo); the block then writes ypart[g][f][t].
+// Thread (tx, ty) of the 16 x 16 grid holds the 4 x FW tile t = tx + 16 u,
+// f = ty + 16 w, which reads P and M from shared memory at one load per two
+// FMAs without bank conflicts (P rows padded to an odd stride, M stored
+// m-major).
+// es: y = sum_g ypart[g] (groups in order), E[S] = Phi y, the operand copies
+// and the E[S] E[S]^T / <y, E[S]> partials of ES_T columns per block, in FP32
+// (FP64 runs at about 2 FMA per clock per SM on this part).  Sigma_s^new and
+// the log-likelihood (sigma_kernel) are left to the M-step tail, which runs
+// beside the next E-pass: the M-pass needs only E[S].
 constexpr int PR_MAX_SLOTS = 64;  // slot offsets staged in shared memory per (subject, chunk)
 
 struct EReduceArgs {
-  int N, G, T, k, nchunk, ldT, kld;
+  int N, G, T, k, nchunk;
   const float* part;
   const ChunkSrc* src;
   const int* src_off;
   const float* M32;
   const double* rho2;
   float2* ypart;           // [G][k][T] (hi, lo)
-  const double* Phi;
-  double* ES64;
-  float* ESt;              // plain form operand (or null)
-  __nv_bfloat16* ESb;      // batched form operand (or null)
-  float* sPart;            // [nchunk][k*k] E[S] E[S]^T of each chunk
-  double* yePart;          // [nchunk] <y, E[S]> of each chunk
-  int* cnt;                // [nchunk] arrival counters (zero between launches)
-  int* status;
 };
 
 template <int FW>  // kld = 16 FW
@@ -223,133 +210,6 @@ __global__ void __launch_bounds__(256) p_reduce_kernel(EReduceArgs ar) {
       if (t < T) out[(int64_t)f * T + t] = make_float2(acc[u][w], accl[u][w]);
     }
   }
-  // ---- (B) the last group block of this chunk
-  __shared__ int s_last;
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    s_last = (atomicAdd(&ar.cnt[c], 1) == G - 1);
-  }
-  __syncthreads();
-  if (!s_last) return;
-  if (tid == 0) ar.cnt[c] = 0;
-  __threadfence();
-  // y = sum_g ypart[g] (hi + lo, groups in order) -> Ps[t][f] (FP32); Phi (symmetrised, FP32) -> Ms[m][f].
-  // A thread's KLD/4 elements are taken four at a time, eight groups per
-  // step: 32 independent loads in flight.
-  for (int jb = 0; jb < KLD / 4; jb += 4) {
-    int off[4];
-    float yh[4], yl[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int e = tid + 256 * (jb + j);
-      const int f = e / TCH, tt = e - f * TCH;
-      off[j] = (f < k && t0 + tt < T) ? f * T + t0 + tt : -1;
-      yh[j] = yl[j] = 0.f;
-    }
-    int q = 0;
-    for (; q + 8 <= G; q += 8) {
-      float2 v[4][8];
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          v[j][u] = off[j] >= 0 ? __ldcg(ypart + (int64_t)(q + u) * kT + off[j]) : make_float2(0.f, 0.f);
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          float hs, he;
-          two_sum(yh[j], v[j][u].x, hs, he);
-          yh[j] = hs;
-          yl[j] += he + v[j][u].y;
-        }
-    }
-    for (; q < G; ++q) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float2 v = off[j] >= 0 ? __ldcg(ypart + (int64_t)q * kT + off[j]) : make_float2(0.f, 0.f);
-        float hs, he;
-        two_sum(yh[j], v.x, hs, he);
-        yh[j] = hs;
-        yl[j] += he + v.y;
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int e = tid + 256 * (jb + j);
-      const int f = e / TCH, tt = e - f * TCH;
-      Ps[tt * (KLD + 1) + f] = off[j] >= 0 ? yh[j] + yl[j] : 0.f;
-    }
-  }
-  for (int e = tid; e < KLD * KLD; e += 256) {
-    const int m = e / KLD, f = e - m * KLD;
-    Ms[e] = (f < k && m < k) ? (float)(0.5 * (ar.Phi[m * k + f] + ar.Phi[f * k + m])) : 0.f;
-  }
-  __syncthreads();
-  float z[4][FW];
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int w = 0; w < FW; ++w) z[u][w] = 0.f;
-  for (int m = 0; m < k; ++m) {
-    float pv[4], mv[FW];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) pv[u] = Ps[(tx + 16 * u) * (KLD + 1) + m];
-#pragma unroll
-    for (int w = 0; w < FW; ++w) mv[w] = Ms[m * KLD + ty + 16 * w];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int w = 0; w < FW; ++w) z[u][w] = fmaf(mv[w], pv[u], z[u][w]);
-  }
-  // E[S] outputs and <y, E[S]> for the chunk
-  double ye = 0.0;
-#pragma unroll
-  for (int w = 0; w < FW; ++w) {
-    const int f = ty + 16 * w;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int tt = tx + 16 * u, t = t0 + tt;
-      if (f < k && t < T) {
-        const float ev = z[u][w];
-        ye += (double)Ps[tt * (KLD + 1) + f] * (double)ev;
-        ar.ES64[(int64_t)f * T + t] = (double)ev;
-        if (ar.ESt) ar.ESt[(int64_t)t * ar.kld + f] = ev;
-        if (ar.ESb) ar.ESb[(int64_t)f * ar.ldT + t] = __float2bfloat16_rn(ev);
-      }
-    }
-  }
-  __syncthreads();  // y no longer needed: E[S] tile into Ps[t][f] (zero outside the data)
-#pragma unroll
-  for (int w = 0; w < FW; ++w) {
-    const int f = ty + 16 * w;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int tt = tx + 16 * u;
-      Ps[tt * (KLD + 1) + f] = (f < k && t0 + tt < T) ? z[u][w] : 0.f;
-    }
-  }
-  __syncthreads();
-  float* pc = ar.sPart + (int64_t)c * k * k;
-  for (int e = tid; e < k * k; e += 256) {
-    const int a = e / k, b = e - a * k;
-    if (b < a) continue;
-    float sab = 0.f;
-    for (int tt = 0; tt < TCH; ++tt) sab = fmaf(Ps[tt * (KLD + 1) + a], Ps[tt * (KLD + 1) + b], sab);
-    pc[a * k + b] = sab;
-    pc[b * k + a] = sab;
-  }
-  {
-    __shared__ double red_ye[256];
-    red_ye[tid] = ye;
-    __syncthreads();
-    for (int st = 128; st > 0; st >>= 1) {
-      if (tid < st) red_ye[tid] += red_ye[tid + st];
-      __syncthreads();
-    }
-    if (tid == 0) ar.yePart[c] = red_ye[0];
-  }
 }
 
 
@@ -383,7 +243,7 @@ __global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __
                                                   const double* __restrict__ sqnorm,
                                                   const int64_t* __restrict__ vox, const double* __restrict__ Us,
                                                   const double* __restrict__ Gp, double* __restrict__ Phi,
-                                                  double* __restrict__ scal, int* status) {
+                                                  float* __restrict__ Phi32, double* __restrict__ scal, int* status) {
   extern __shared__ double ph_smem[];
   double* w = ph_smem;          // [k]  1 / (1 + rho0 lambda)
   double* ua = w + k;           // [k]  row a of U
@@ -427,6 +287,7 @@ __global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __
     for (int d = 0; d < k; ++d) s = fma(tv[d], Uss[cc * k + d], s);
     if (!isfinite(s)) flag(status, ST_NONFINITE);
     Phi[a * k + cc] = s;
+    Phi32[a * k + cc] = (float)s;
   }
   if (a == 0) {
     double ld = 0.0;
@@ -444,6 +305,89 @@ __global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __
       scal[SC_SQRHO] = s2;
     }
   }
+}
+
+constexpr int ES_T = 8;  // columns of E[S] per es block
+
+__global__ void __launch_bounds__(256) es_kernel(int G, int k, int T, int kld, int ldT, const float* __restrict__ Phi32,
+                                                 const float2* __restrict__ ypart, double* __restrict__ ES64,
+                                                 float* __restrict__ ESt, __nv_bfloat16* __restrict__ ESb,
+                                                 float* __restrict__ sPart, double* __restrict__ yePart) {
+  __shared__ float Ys[KMAX][ES_T];
+  __shared__ float Es[KMAX][ES_T];
+  __shared__ double red[256];
+  extern __shared__ float es_smem[];
+  float* Ps = es_smem;  // [k][k] Phi (symmetrised, FP32)
+  const int t0 = blockIdx.x * ES_T, tid = threadIdx.x;
+  const int64_t kT = (int64_t)k * T;
+  for (int e = tid; e < k * k; e += 256) {
+    const int f = e / k, m = e - f * k;
+    Ps[e] = 0.5f * (Phi32[e] + Phi32[m * k + f]);
+  }
+  // y: each thread owns up to two (f, t) elements; all group loads of a step in flight
+  for (int e = tid; e < k * ES_T; e += 256) {
+    const int f = e / ES_T, tt = e - f * ES_T, t = t0 + tt;
+    float yv = 0.f;
+    if (t < T) {
+      const float2* zp = ypart + (int64_t)f * T + t;
+      float yh = 0.f, yl = 0.f;
+      int q = 0;
+      for (; q + 8 <= G; q += 8) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldcg(zp + (int64_t)(q + u) * kT);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          float hs, he;
+          two_sum(yh, v[u].x, hs, he);
+          yh = hs;
+          yl += he + v[u].y;
+        }
+      }
+      for (; q < G; ++q) {
+        const float2 v = __ldcg(zp + (int64_t)q * kT);
+        float hs, he;
+        two_sum(yh, v.x, hs, he);
+        yh = hs;
+        yl += he + v.y;
+      }
+      yv = yh + yl;
+    }
+    Ys[f][tt] = yv;
+  }
+  __syncthreads();
+  double ye = 0.0;
+  for (int e = tid; e < k * ES_T; e += 256) {
+    const int f = e / ES_T, tt = e - f * ES_T, t = t0 + tt;
+    float s = 0.f;
+    for (int m = 0; m < k; ++m) s = fmaf(Ps[f * k + m], Ys[m][tt], s);
+    if (t >= T) s = 0.f;
+    Es[f][tt] = s;
+    if (t < T) {
+      ye += (double)Ys[f][tt] * (double)s;
+      ES64[(int64_t)f * T + t] = (double)s;
+      if (ESt) ESt[(int64_t)t * kld + f] = s;
+      if (ESb) ESb[(int64_t)f * ldT + t] = __float2bfloat16_rn(s);
+    }
+  }
+  __syncthreads();
+  float* pc = sPart + (int64_t)blockIdx.x * k * k;
+  for (int e = tid; e < k * k; e += 256) {
+    const int a = e / k, b = e - a * k;
+    if (b < a) continue;
+    float sab = 0.f;
+#pragma unroll
+    for (int tt = 0; tt < ES_T; ++tt) sab = fmaf(Es[a][tt], Es[b][tt], sab);
+    pc[a * k + b] = sab;
+    pc[b * k + a] = sab;
+  }
+  red[tid] = ye;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (tid < st) red[tid] += red[tid + st];
+    __syncthreads();
+  }
+  if (tid == 0) yePart[blockIdx.x] = red[0];
 }
 
 // Sigma_s^new = Phi + E[S] E[S]^T / T (eq:srm_variance_update_optimized) from
@@ -1373,6 +1317,7 @@ cudaError_t bgemm(Ctx* c, int nbatch, const double* A, int tA, const double* B, 
 
 
 void prepare_small_kernels(int max_smem) {
+  cudaFuncSetAttribute(es_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float) * KMAX * KMAX));
   // (these kernels also hold a few KB of static shared memory)
   cudaFuncSetAttribute(p_reduce_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
   cudaFuncSetAttribute(p_reduce_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
@@ -1409,22 +1354,13 @@ cudaError_t launch_p_reduce(Ctx* c) {
   ar.T = c->T;
   ar.k = c->k;
   ar.nchunk = c->nchunk;
-  ar.ldT = c->ldT;
-  ar.kld = c->kld;
   ar.part = c->Ppart;
   ar.src = c->chunk_src;
   ar.src_off = c->chunk_src_off;
   ar.M32 = c->M32;
   ar.rho2 = c->rho2;
   ar.ypart = c->Ypart;
-  ar.Phi = c->Phi;
-  ar.ES64 = c->ES64;
-  ar.ESt = c->batched ? nullptr : c->ESt;
-  ar.ESb = c->batched ? c->ESb : nullptr;
-  ar.sPart = c->sPart;
-  ar.yePart = c->esPart;
-  ar.cnt = c->ered_cnt;
-  ar.status = c->status;
+  cudaError_t e;
   switch (c->kld) {
 #define PR_CASE(FW) \
   case 16 * FW: p_reduce_kernel<FW><<<grid, 256, sm, c->stream>>>(ar); break;
@@ -1432,11 +1368,17 @@ cudaError_t launch_p_reduce(Ctx* c) {
 #undef PR_CASE
     default: return cudaErrorInvalidValue;
   }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  es_kernel<<<c->nes_blk, 256, sizeof(float) * c->k * c->k, c->stream>>>(
+      c->zgroups, c->k, c->T, c->kld, c->ldT, c->Phi32, c->Ypart, c->ES64, c->batched ? nullptr : c->ESt,
+      c->batched ? c->ESb : nullptr, c->sPart, c->esPart);
   return cudaGetLastError();
 }
 
+int es_blocks(int T) { return (T + ES_T - 1) / ES_T; }
+
 cudaError_t launch_sigma(Ctx* c) {
-  sigma_kernel<<<c->k, 256, 0, c->stream>>>(c->k, c->T, c->nchunk, (double)c->Vtot, c->Phi, c->sPart, c->esPart,
+  sigma_kernel<<<c->k, 256, 0, c->stream>>>(c->k, c->T, c->nes_blk, (double)c->Vtot, c->Phi, c->sPart, c->esPart,
                                             c->SigmaNext, c->scal, c->ll, c->iter, c->max_iter, c->status);
   return cudaGetLastError();
 }
@@ -1445,7 +1387,7 @@ cudaError_t launch_phi(Ctx* c) {
   const int64_t kk = (int64_t)c->k * c->k;
   const size_t sm = sizeof(double) * (3 * c->k + 2 * c->k * c->k);
   phi_kernel<<<c->k, 256, sm, c->stream>>>(c->N, c->k, c->rho2, c->sqnorm, c->d_v, c->Xr64 + c->N * kk,
-                                           c->G64 + c->N * kk, c->Phi, c->scal, c->status);
+                                           c->G64 + c->N * kk, c->Phi, c->Phi32, c->scal, c->status);
   return cudaGetLastError();
 }
 

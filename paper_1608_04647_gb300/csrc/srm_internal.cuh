@@ -90,6 +90,7 @@ struct Ctx {
   double* SigmaNext = nullptr;  // [k][k]
   double* L = nullptr;          // [k][k] Cholesky factor of I + rho0 Sigma
   double* Phi = nullptr;        // [k][k]
+  float* Phi32 = nullptr;       // [k][k] FP32 copy (the E[S] product)
   double* scal = nullptr;       // [16] scalars of the current E-step (see k_small.cu)
   double* M64 = nullptr;        // [N][k][k] (A_i^T A_i)^-1/2
   float* M32 = nullptr;         // [N][kld][kld] FP32 copy used by the reduction
@@ -106,9 +107,8 @@ struct Ctx {
   double* ES64 = nullptr;       // [k][T] E[S]
   float* ESt = nullptr;         // [ldT][kld] FP32 E[S]^T (plain-path operand)
   __nv_bfloat16* ESb = nullptr; // [kld][ldT] BF16 E[S] (tensor-core operand)
-  double* esPart = nullptr;     // [nes_blk] <y, E[S]> of each 64-column chunk
+  double* esPart = nullptr;     // [nes_blk] <y, E[S]> of each es block
   int nes_blk = 0;
-  int* ered_cnt = nullptr;      // [nchunk] arrival counters of the fused E-step reduction
   double* ll = nullptr;         // [max_iter]
   int* iter = nullptr;          // device E-step counter (index into ll)
   int* status = nullptr;        // device status word
@@ -119,7 +119,7 @@ struct Ctx {
   ChunkSrc* chunk_src = nullptr;  // device table
   int* chunk_src_off = nullptr;   // [N * nchunk + 1]
   float2* Ypart = nullptr;      // [zgroups][k][T] sum of rho_i^-2 M_i P_i over a group of subjects (hi, lo)
-  float* sPart = nullptr;       // [nchunk][k*k] E[S] E[S]^T of each 64-column chunk
+  float* sPart = nullptr;       // [nes_blk][k*k] E[S] E[S]^T of each es block
   float* Gpart = nullptr;       // M-pass Gram partials [..][kld][kld]
   int64_t Gpart_elems = 0;
   int* gslot_off = nullptr;     // [N+1] Gram slot ranges per subject
@@ -190,6 +190,7 @@ cudaError_t launch_a_simt(Ctx* c, int subject);
 
 // k_small.cu
 int zsum_groups(int N, int nchunk, int num_sms);
+int es_blocks(int T);
 cudaError_t launch_p_reduce(Ctx* c);
 cudaError_t launch_sigma(Ctx* c);
 cudaError_t launch_phi(Ctx* c);
