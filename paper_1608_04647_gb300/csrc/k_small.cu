@@ -401,11 +401,17 @@ __global__ void __launch_bounds__(256) sigma_kernel(int k, int T, int nchunk, do
                                                     int max_iter, int* status) {
   const int a = blockIdx.x, tid = threadIdx.x;
   const int64_t kk2 = (int64_t)k * k;
-  for (int b = tid; b < k; b += 256) {
-    const int e = a * k + b;
+  // four threads per element (adjacent lanes), each a contiguous quarter of
+  // the partials; the quarters are then added in order
+  const int sub = tid & 3;
+  const int q0 = (nchunk * sub) / 4, q1 = (nchunk * (sub + 1)) / 4;
+  for (int b0 = 0; b0 < k; b0 += 64) {
+    const int b = b0 + (tid >> 2);
+    const bool in = b < k;
+    const int e = a * k + (in ? b : 0);
     float sh = 0.f, sl = 0.f;
-    int q = 0;
-    for (; q + 8 <= nchunk; q += 8) {  // eight loads in flight, added in chunk order
+    int q = q0;
+    for (; q + 8 <= q1; q += 8) {  // eight loads in flight
       float v[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) v[u] = sPart[(int64_t)(q + u) * kk2 + e];
@@ -417,19 +423,47 @@ __global__ void __launch_bounds__(256) sigma_kernel(int k, int T, int nchunk, do
         sl += he;
       }
     }
-    for (; q < nchunk; ++q) {
+    for (; q < q1; ++q) {
       float hs, he;
       two_sum(sh, sPart[(int64_t)q * kk2 + e], hs, he);
       sh = hs;
       sl += he;
     }
-    const double v = 0.5 * (Phi[a * k + b] + Phi[b * k + a]) + ((double)sh + (double)sl) / (double)T;
-    if (!isfinite(v)) flag(status, ST_NONFINITE);
-    SigmaNext[e] = v;
+    // combine the four quarters in order (lanes 4j .. 4j + 3)
+    const int base = (tid & 31) & ~3;
+    float h[4], l[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      h[u] = __shfl_sync(0xffffffffu, sh, base + u);
+      l[u] = __shfl_sync(0xffffffffu, sl, base + u);
+    }
+    if (sub == 0 && in) {
+      float th = h[0], tl = l[0];
+#pragma unroll
+      for (int u = 1; u < 4; ++u) {
+        float hs, he;
+        two_sum(th, h[u], hs, he);
+        th = hs;
+        tl += he + l[u];
+      }
+      const double v = 0.5 * (Phi[a * k + b] + Phi[b * k + a]) + ((double)th + (double)tl) / (double)T;
+      if (!isfinite(v)) flag(status, ST_NONFINITE);
+      SigmaNext[e] = v;
+    }
   }
-  if (a == 0 && tid == 0) {
-    double yes = 0.0;
-    for (int q = 0; q < nchunk; ++q) yes += yePart[q];
+  if (a != 0) return;
+  // <y, Phi y>: the per-block partials summed by a fixed-order tree
+  __shared__ double yred[256];
+  double ys = 0.0;
+  for (int q = tid; q < nchunk; q += 256) ys += yePart[q];
+  yred[tid] = ys;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (tid < st) yred[tid] += yred[tid + st];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const double yes = yred[0];
     scal[SC_YPHIY] = yes;
     const double L = -0.5 * ((double)T * Vtot * 1.8378770664093454835606594728112 + (double)T * scal[SC_VLOGRHO] +
                              (double)T * scal[SC_LOGDET] + scal[SC_SQRHO] - yes);
@@ -785,10 +819,12 @@ constexpr double NS_CERT_F32 = 2e-6;
 constexpr double NS_CERT_BF16 = 1e-4;
 
 
-// C = A^T B for KP x KP row-major operands (KP <= 64, multiple of 4), 256 threads.
+// C = A^T B for KP x KP row-major operands (KP <= 64, multiple of 4), by the
+// 256 threads [base, base + 256) of the block.
 __device__ __forceinline__ void ns_mm(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ C,
-                                      int KP) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+                                      int KP, int base = 0) {
+  const int tid = (int)threadIdx.x - base, warp = tid >> 5, lane = tid & 31;
+  if (tid < 0 || tid >= 256) return;
   const int tr = (warp >> 1) * 4 + (lane >> 3), tc = (warp & 1) * 8 + (lane & 7);
   const int nt4 = KP / 4;
   if (tr >= nt4 || tc >= nt4) return;
@@ -821,7 +857,7 @@ __device__ __forceinline__ bool ns_mm2(const float* __restrict__ A, const float*
   const int tr = (warp >> 1) * 4 + (lane >> 3), tc = (warp & 1) * 8 + (lane & 7);
   r0 = 4 * tr;
   c0 = 4 * tc;
-  if (tr >= KP / 4 || tc >= KP / 4) return false;
+  if (tid >= 256 || tr >= KP / 4 || tc >= KP / 4) return false;
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -847,27 +883,29 @@ __device__ __forceinline__ bool ns_mm2(const float* __restrict__ A, const float*
   return true;
 }
 
-__device__ __forceinline__ float block_max_256(float v, float* red) {
+constexpr int NS_THREADS = 512;
+
+__device__ __forceinline__ float block_max_ns(float v, float* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
   float r = red[0];
 #pragma unroll
-  for (int w = 1; w < 8; ++w) r = fmaxf(r, red[w]);
+  for (int w = 1; w < NS_THREADS / 32; ++w) r = fmaxf(r, red[w]);
   __syncthreads();
   return r;
 }
 
-// Sum of three doubles over the 256 threads (fixed-order tree); every thread
-// gets the totals.
-__device__ void block_sum3_256(double& a, double& b, double& c, double (*red)[256]) {
+// Sum of three doubles over the NS_THREADS threads (fixed-order tree); every
+// thread gets the totals.
+__device__ void block_sum3_ns(double& a, double& b, double& c, double (*red)[NS_THREADS]) {
   const int tid = threadIdx.x;
   red[0][tid] = a;
   red[1][tid] = b;
   red[2][tid] = c;
   __syncthreads();
-  for (int st = 128; st > 0; st >>= 1) {
+  for (int st = NS_THREADS / 2; st > 0; st >>= 1) {
     if (tid < st) {
       red[0][tid] += red[0][tid + st];
       red[1][tid] += red[1][tid + st];
@@ -881,7 +919,7 @@ __device__ void block_sum3_256(double& a, double& b, double& c, double (*red)[25
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) polar_ns_kernel(int N, int k, int kld, int T, const float* __restrict__ gpart,
+__global__ void __launch_bounds__(NS_THREADS) polar_ns_kernel(int N, int k, int kld, int T, const float* __restrict__ gpart,
                                                        const int* __restrict__ gslot_off, double* __restrict__ G64,
                                                        double* __restrict__ M64, float* __restrict__ M32,
                                                        const double* __restrict__ sqnorm,
@@ -891,25 +929,27 @@ __global__ void __launch_bounds__(256) polar_ns_kernel(int N, int k, int kld, in
                                                        double* __restrict__ scal, int* __restrict__ iters_out,
                                                        int* __restrict__ fallback, double cert, int* status) {
   extern __shared__ __align__(16) float ns_smem[];
-  __shared__ float redf[8];
-  __shared__ double redd[3][256];
+  __shared__ float redf[NS_THREADS / 32];
+  __shared__ double redd[3][NS_THREADS];
   const int KP = (k + 3) & ~3;
   const int KK = KP * KP;
   float* B0 = ns_smem;
   float* B1 = B0 + KK;
   float* B2 = B1 + KK;
   float* B3 = B2 + KK;
+  float* B4 = B3 + KK;
   const int i = blockIdx.x, tid = threadIdx.x;
   double* Gi = G64 + (int64_t)i * k * k;
   float* Y = B0;
   float* Z = B1;
   float* Tm = B2;
   float* W = B3;
+  float* Xb = B4;
   // G (FP64) from the Gram partials (four slot loads in flight), kept as
   // FP32 hi + lo in W / Tm for the iteration's start; ||G||_F^2, tr Sigma_s^new
   const int s0 = gslot_off[i], s1 = gslot_off[i + 1];
   double fro = 0.0, tr = 0.0, z0 = 0.0;
-  for (int e = tid; e < KK; e += 256) {
+  for (int e = tid; e < KK; e += NS_THREADS) {
     const int a = e / KP, b = e - a * KP;
     double sum = 0.0;
     if (a < k && b < k) {
@@ -932,22 +972,22 @@ __global__ void __launch_bounds__(256) polar_ns_kernel(int N, int k, int kld, in
     Tm[e] = (float)(sum - (double)hi);
   }
   if (tid < k) tr = SigmaNext[tid * k + tid];
-  block_sum3_256(fro, tr, z0, redd);  // (its barriers also publish W, Tm)
+  block_sum3_ns(fro, tr, z0, redd);  // (its barriers also publish W, Tm)
   // ||sym(G)||_inf <= max_a sum_b (|G_ab| + |G_ba|) / 2, from the FP32 copy
   float rowmax = 0.f;
-  for (int a = tid; a < k; a += 256) {
+  for (int a = tid; a < k; a += NS_THREADS) {
     float rs = 0.f;
     for (int b = 0; b < k; ++b) rs += 0.5f * (fabsf(W[a * KP + b]) + fabsf(W[b * KP + a]));
     rowmax = fmaxf(rowmax, rs);
   }
-  const float ginf = block_max_256(rowmax, redf);
+  const float ginf = block_max_ns(rowmax, redf);
   const double trS = tr;
   double c = sqrt(fro);
   if ((double)ginf * (1.0 + 1e-5) < c) c = (double)ginf * (1.0 + 1e-5);  // both bound lambda_max from above
   const bool good_c = isfinite(c) && c > 0.0;
   const double cinv = good_c ? 1.0 / c : 0.0;
   // Y = sym(G) / c, Z = I (k block), zero padding
-  for (int e = tid; e < KK; e += 256) {
+  for (int e = tid; e < KK; e += NS_THREADS) {
     const int a = e / KP, b = e - a * KP;
     float y = 0.f, z = 0.f;
     if (a < k && b < k) {
@@ -966,7 +1006,7 @@ __global__ void __launch_bounds__(256) polar_ns_kernel(int N, int k, int kld, in
     __syncthreads();
     // T = (3I - (P + P^T)/2) / 2 on the k block (zero elsewhere); e = max |P - I|
     float emax = 0.f;
-    for (int e = tid; e < KK; e += 256) {
+    for (int e = tid; e < KK; e += NS_THREADS) {
       const int a = e / KP, b = e - a * KP;
       if (b < a) continue;
       float t = 0.f;
@@ -979,22 +1019,24 @@ __global__ void __launch_bounds__(256) polar_ns_kernel(int N, int k, int kld, in
       Tm[a * KP + b] = t;
       Tm[b * KP + a] = t;
     }
-    const float err = block_max_256(emax, redf);
+    const float err = block_max_ns(emax, redf);
     if (!(err == err)) break;  // non-finite
-    if (extra < 0 && err < NS_TOL) extra = 2;
+    if (extra < 0 && err < NS_TOL) extra = 1;
     if (extra == 0) {
       conv = true;
       break;
     }
     if (extra > 0) --extra;
-    ns_mm(Y, Tm, W, KP);  // Y T
+    // Y T and T Z at once, each by half of the block
+    ns_mm(Y, Tm, W, KP, 0);       // Y T
+    ns_mm(Tm, Z, Xb, KP, 256);    // T Z
     __syncthreads();
-    ns_mm(Tm, Z, Y, KP);  // T Z (into the old Y)
-    __syncthreads();
-    float* t = Z;
-    Z = Y;
+    float* t = Y;
     Y = W;
     W = t;
+    t = Z;
+    Z = Xb;
+    Xb = t;
   }
   // M_0 = sym(Z) / sqrt(c) into W; G = G_hi + G_lo into the buffers of Y and T
   float* Mb = W;
@@ -1003,7 +1045,7 @@ __global__ void __launch_bounds__(256) polar_ns_kernel(int N, int k, int kld, in
   float* Zb = Z;  // free once M_0 is formed
   {
     const float sc = (float)sqrt(cinv);
-    for (int e = tid; e < KK; e += 256) {
+    for (int e = tid; e < KK; e += NS_THREADS) {
       const int a = e / KP, b = e - a * KP;
       float m = 0.f, gh = 0.f, gl = 0.f;
       if (a < k && b < k) {
@@ -1050,8 +1092,8 @@ __global__ void __launch_bounds__(256) polar_ns_kernel(int N, int k, int kld, in
         corr += ev * (double)Ph[a * KP + b];  // R_ba = P_ab
       }
   }
-  for (int a = tid; a < k; a += 256) tmg += (double)Ph[a * KP + a] + (double)Pl[a * KP + a];
-  block_sum3_256(e2, tmg, corr, redd);
+  for (int a = tid; a < k; a += NS_THREADS) tmg += (double)Ph[a * KP + a] + (double)Pl[a * KP + a];
+  block_sum3_ns(e2, tmg, corr, redd);
   const double enorm = sqrt(e2);
   const bool ok = conv && good_c && enorm <= cert * sqrt((double)k) && isfinite(enorm);
   if (tid == 0) {
@@ -1068,7 +1110,7 @@ __global__ void __launch_bounds__(256) polar_ns_kernel(int N, int k, int kld, in
   if (ok) {
     double* Mi = M64 + (int64_t)i * k * k;
     float* M32i = M32 + (int64_t)i * kld * kld;
-    for (int e = tid; e < k * k; e += 256) {
+    for (int e = tid; e < k * k; e += NS_THREADS) {
       const int a = e / k, b = e - a * k;
       const float m = Mb[a * KP + b];
       Mi[e] = (double)m;
@@ -1076,12 +1118,12 @@ __global__ void __launch_bounds__(256) polar_ns_kernel(int N, int k, int kld, in
     }
   }
   if (i == 0)
-    for (int e = tid; e < k * k; e += 256) Sigma[e] = SigmaNext[e];
+    for (int e = tid; e < k * k; e += NS_THREADS) Sigma[e] = SigmaNext[e];
 }
 
 size_t ns_smem_bytes(int k) {
   const int KP = (k + 3) & ~3;
-  return sizeof(float) * 4 * (size_t)KP * KP;
+  return sizeof(float) * 5 * (size_t)KP * KP;
 }
 
 // ---------------------------------------------------------------- fused M-step tail
@@ -1430,7 +1472,7 @@ cudaError_t launch_refine(Ctx* c) {
 bool ns_supported(const Ctx* c) { return c->k <= NS_KMAX && c->k <= MT_KMAX; }
 
 cudaError_t launch_polar(Ctx* c) {
-  polar_ns_kernel<<<c->N, 256, ns_smem_bytes(c->k), c->stream>>>(
+  polar_ns_kernel<<<c->N, NS_THREADS, ns_smem_bytes(c->k), c->stream>>>(
       c->N, c->k, c->kld, c->T, c->Gpart, c->gslot_off, c->G64, c->M64, c->M32, c->sqnorm, c->d_v, c->SigmaNext,
       c->Sigma, c->rho2, c->scal, c->jac_sweeps, c->ns_fb, c->store == SRM_BF16 ? NS_CERT_BF16 : NS_CERT_F32,
       c->status);

@@ -50,7 +50,7 @@ struct SegM {
 };
 
 struct TcState {
-  CUtensorMap mapXe, mapA, mapXm, mapE, mapAs;
+  CUtensorMap mapXe, mapA, mapXm, mapE, mapAs, mapXp;
   WorkE* d_work = nullptr;
   int* d_work_off = nullptr;
   SegM* d_seg = nullptr;
@@ -91,7 +91,7 @@ __host__ __device__ constexpr uint32_t gop_bytes(int kld, int nb) {
 constexpr int M_MAX_STAGES = 8;  // runtime stage count of the M-pass is at most this
 constexpr int M_PF = 8;          // M-pass L2 prefetch distance (X^ chunks of 16 KB) ...
 constexpr int M_PF_STAGES = 5;   // ... used when fewer shared-memory stages than this fit
-constexpr int M_PF_MODE = 1;     // 1: per 16 KB chunk (tensor), 2: per tile (bulk, contiguous rows)
+constexpr int M_PF_MODE = 3;     // 1: per 16 KB chunk, 2: per tile (bulk), 3: per 4 chunks (one wide box)
 constexpr size_t m_fixed_bytes(int kld, int nb) { return 1024 + gop_bytes(kld, nb) + kBarBytes; }
 constexpr size_t kMaxSmem = 232448;  // opt-in limit per block
 
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(NT, 1)
 template <int KLD, bool RES, int GNB>  // GNB: Gram operand buffers (1 or 2)
 __global__ void __launch_bounds__(NT, 1)
     mstep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE,
-                    const __grid_constant__ CUtensorMap mapAs,
+                    const __grid_constant__ CUtensorMap mapAs, const __grid_constant__ CUtensorMap mapXp,
                     const SegM* __restrict__ segs, const int* __restrict__ seg_off, int T, int S_N, int pf_dist,
                     const uint8_t* __restrict__ xbase, int64_t xrow_bytes,
                     __nv_bfloat16* __restrict__ Aout, float* __restrict__ gpart, int* status) {
@@ -364,7 +364,10 @@ __global__ void __launch_bounds__(NT, 1)
         while (pg < g1 && ptile >= segs[pg].tile_end)
           if (++pg < g1) ptile = segs[pg].tile_begin;
         if (pg >= g1 || pf_dist == 0) return;
-        if (M_PF_MODE == 2) {
+        if (M_PF_MODE == 3) {
+          // four chunks of the same 128 rows in one box, once every four chunks
+          if ((pkc & 3) == 0) tma_prefetch_l2_2d(&mapXp, 64 * pkc, (int)(ptile * 128));
+        } else if (M_PF_MODE == 2) {
           // a whole 128-row tile (contiguous rows) per prefetch, in 32 KB pieces
           if (pkc == 0) {
             const uint8_t* p = xbase + ptile * 128 * xrow_bytes;
@@ -693,7 +696,7 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 
 // 2D BF16 tensor map, 128-byte swizzle; inner = contiguous extent (elements).
 bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes, uint32_t box_in,
-              uint32_t box_out) {
+              uint32_t box_out, bool swizzle = true) {
   auto enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[2] = {inner, outer};
@@ -701,8 +704,8 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, 
   cuuint32_t box[2] = {box_in, box_out};
   cuuint32_t es[2] = {1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
 
@@ -746,7 +749,9 @@ srm_status tc_setup(Ctx* c) {
             make_map(&s->mapA, c->A, c->kld, c->Vpad_tot, (uint64_t)c->kld * 2, 64, E_KR) &&
             make_map(&s->mapXm, c->Xh, c->T, c->Vpad_tot, (uint64_t)c->ldT * 2, 64, 128) &&
             make_map(&s->mapE, c->ESb, c->T, c->kld, (uint64_t)c->ldT * 2, 64, c->kld) &&
-            make_map(&s->mapAs, c->A, c->kld, c->Vpad_tot, (uint64_t)c->kld * 2, 64, 128);
+            make_map(&s->mapAs, c->A, c->kld, c->Vpad_tot, (uint64_t)c->kld * 2, 64, 128) &&
+            // L2 prefetch only (never lands in shared memory): 4 chunks x 128 rows per box
+            make_map(&s->mapXp, c->Xh, c->T, c->Vpad_tot, (uint64_t)c->ldT * 2, 256, 128, false);
   if (!ok) {
     set_error("cuTensorMapEncodeTiled failed (driver entry point missing or bad layout)");
     return SRM_ERR_CUDA;
@@ -922,7 +927,7 @@ cudaError_t launch_a_tc(Ctx* c) {
   auto* A = static_cast<__nv_bfloat16*>(c->A);
 #define M_LAUNCH(KLD, RES, GNB)                                                                                  \
   mstep_tc_kernel<KLD, RES, GNB><<<s->grid, NT, s->m_smem, c->stream>>>(                                          \
-      s->mapXm, s->mapE, s->mapAs, s->d_seg, s->d_seg_off, c->T, s->m_stages,                                      \
+      s->mapXm, s->mapE, s->mapAs, s->mapXp, s->d_seg, s->d_seg_off, c->T, s->m_stages,                            \
       s->m_stages < M_PF_STAGES ? M_PF : 0,                                                                        \
       static_cast<const uint8_t*>(c->Xh), (int64_t)c->ldT * 2, A, c->Gpart, c->status)
 #define M_LAUNCH2(KLD, RES) \
