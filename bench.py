@@ -202,7 +202,7 @@ def run_ours(args, rank, world):
 
     def make(store, graph=True, profile=False):
         return srm.SRM(d["X"], d["W0"], k, store=store, graph=graph, profile=profile, max_iter=max_iter,
-                       stream=stream)
+                       stream=stream, single_pass=args.single_pass)
 
     results = {}
     stores = [args.store] if args.store != "both" else ["bf16", "f32"]
@@ -462,6 +462,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--k-sweep", action="store_true", help="throughput against k (extra lines, not the bench line)")
+    ap.add_argument("--single-pass", action="store_true", help="one stream of X^ per EM iteration (SRM_SINGLE_PASS)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -74,6 +74,12 @@ typedef enum { SRM_F32 = 0, SRM_BF16 = 1 } srm_dtype;
                                     library streams them to the device subject by subject */
 #define SRM_PROFILE    (1u << 5) /* time every kernel with CUDA events on the context stream
                                     (srm_get_kernel_times); disables SRM_GRAPH */
+#define SRM_SINGLE_PASS (1u << 6) /* with SRM_BATCHED, k <= 64 and T <= 1024: each M-step
+                                    streams X^ once, producing A_i, its Gram and, for the
+                                    next E-step, A_i^T X^_i (W_i^T X^_i = M_i A_i^T X^_i,
+                                    Sec. II-B); E-steps that follow an M-step then read no
+                                    X^.  Ignored where unsupported (srm_layout out[5]
+                                    reports whether it is active) */
 
 typedef struct {
     int32_t n_subjects;      /* N >= 1 */
@@ -235,7 +241,8 @@ SRM_API srm_status srm_get_kernel_times(srm_ctx* ctx, const char** names, int64_
  * out[0] = padded row stride of the resident X^ (elements), out[1] = padded k
  * of the tensor-core operands, out[2] = total resident rows (all subjects, padded),
  * out[3] = bytes of the resident X^, out[4] = bytes of the per-subject
- * mapping factors A_i.  n = number of entries the caller's array holds.
+ * mapping factors A_i, out[5] = 1 if the single-pass form (SRM_SINGLE_PASS) is
+ * active, else 0.  n = number of entries the caller's array holds.
  */
 SRM_API srm_status srm_layout(srm_ctx* ctx, int64_t* out, int32_t n);
 

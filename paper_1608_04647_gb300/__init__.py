@@ -22,7 +22,7 @@ from . import _build
 
 __all__ = [
     "SRM", "SrmError", "load_library", "srm_config", "SRM_BATCHED", "SRM_GRAPH", "SRM_FINAL_LL",
-    "SRM_HOST_INPUT", "SRM_PROFILE", "SRM_F32", "SRM_BF16",
+    "SRM_HOST_INPUT", "SRM_PROFILE", "SRM_SINGLE_PASS", "SRM_F32", "SRM_BF16",
     "srm_init", "srm_estep", "srm_mstep", "srm_fit", "srm_transform", "srm_get_w", "srm_get_s",
     "srm_get_params", "srm_get_ll", "srm_synchronize", "srm_get_state", "srm_set_state",
     "srm_get_kernel_times", "srm_layout", "srm_last_error", "srm_destroy", "srm_debug_mma",
@@ -38,6 +38,7 @@ SRM_GRAPH = 1 << 1
 SRM_FINAL_LL = 1 << 3
 SRM_HOST_INPUT = 1 << 4
 SRM_PROFILE = 1 << 5
+SRM_SINGLE_PASS = 1 << 6
 
 
 class SrmError(RuntimeError):
@@ -216,9 +217,9 @@ def srm_get_kernel_times(ctx: int, reset: bool = False) -> dict:
 
 
 def srm_layout(ctx: int) -> dict:
-    out = (ctypes.c_int64 * 5)()
-    _check(load_library().srm_layout(_P(ctx), out, 5), "srm_layout")
-    keys = ["ldT", "kld", "rows_padded", "xhat_bytes", "a_bytes"]
+    out = (ctypes.c_int64 * 6)()
+    _check(load_library().srm_layout(_P(ctx), out, 6), "srm_layout")
+    keys = ["ldT", "kld", "rows_padded", "xhat_bytes", "a_bytes", "single_pass"]
     return dict(zip(keys, [int(x) for x in out]))
 
 
@@ -248,11 +249,13 @@ class SRM:
          tensors / NumPy arrays (pinned memory recommended).
     W0:  list of N torch CUDA float32 tensors (v_i x k) with orthonormal columns.
     store: "bf16" -> batched tensor-core form; "f32" -> plain per-subject form.
+    single_pass: with store="bf16", k <= 64 and T <= 1024, stream X^ once per
+         EM iteration (SRM_SINGLE_PASS); ignored elsewhere (see layout()).
     """
 
     def __init__(self, X: Sequence, W0: Sequence, k: int, store: str = "bf16", graph: bool = False,
                  final_ll: bool = False, profile: bool = False, host_input: bool = False,
-                 max_iter: int = 1024, stream=None):
+                 max_iter: int = 1024, stream=None, single_pass: bool = False):
         import torch
 
         self.N = len(X)
@@ -275,6 +278,8 @@ class SRM:
             flags |= SRM_PROFILE
         if host_input:
             flags |= SRM_HOST_INPUT
+        if single_pass:
+            flags |= SRM_SINGLE_PASS
         self.final_ll = final_ll
         self.cfg = srm_config(self.N, ctypes.cast(self._vox, ctypes.POINTER(ctypes.c_int64)), self.T, self.k,
                               in_dtype, SRM_BF16 if store == "bf16" else SRM_F32, flags, max_iter)

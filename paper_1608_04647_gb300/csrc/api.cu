@@ -21,7 +21,7 @@ thread_local std::string g_err;
 
 const char* const kKernelNames[KK_COUNT] = {
     "center", "estep_simt", "estep_tc", "ereduce", "sigma", "phi",
-    "mstep_simt", "mstep_tc", "eig", "refine", "rho", "mtail", "polar"};
+    "mstep_simt", "mstep_tc", "eig", "refine", "rho", "mtail", "polar", "fpass_tc"};
 
 void set_error(const std::string& msg) { g_err = msg; }
 
@@ -44,7 +44,7 @@ void prof_begin(Ctx* c, int kind, int* ev0) {
 }
 
 // CUDA kernels behind one launcher call of each kind
-static const int kKernelsPerKind[KK_COUNT] = {1, 1, 1, 2, 1, 1, 1, 1, 1, 4, 4, 1, 1};
+static const int kKernelsPerKind[KK_COUNT] = {1, 1, 1, 2, 1, 1, 1, 1, 1, 4, 4, 1, 1, 1};
 
 void prof_end(Ctx* c, int kind, int ev0) {
   const int ev1 = c->ev_next++;
@@ -95,11 +95,13 @@ __global__ void cast_kernel(const double* __restrict__ a, float* __restrict__ b,
   } while (0)
 
 void free_all(Ctx* c) {
+  if (c->fs) fused_destroy(c);
   if (c->tc) tc_destroy(c);
   void* ptrs[] = {c->Xh, c->A, c->sqnorm, c->rowsq, c->d_off, c->d_v, c->rho2, c->Sigma, c->SigmaNext, c->L,
                   c->Phi, c->scal, c->M64, c->M32, c->Uwarm, c->G64, c->U64, c->H64, c->Xr64, c->eigv, c->Y,
                   c->ES64, c->ESt, c->ESb, c->esPart, c->ll, c->iter, c->status, c->Ppart, c->chunk_src, c->jac_sweeps, c->ns_fb,
-                  c->chunk_src_off, c->Ypart, c->sPart, c->map_buf, c->Phi32, c->Gpart, c->gslot_off, c->tr_buf, c->tr_part};
+                  c->chunk_src_off, c->Ypart, c->sPart, c->map_buf, c->Phi32, c->Gpart, c->gslot_off, c->tr_buf, c->tr_part,
+                  c->f_ppart, c->f_chunk_src, c->f_chunk_src_off};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -233,14 +235,56 @@ srm_status flush_pending(Ctx* c) {
     c->sigma_pending = false;
   }
   if (!c->side_pending) return SRM_OK;
-  TRY(do_side_chain(c));
+  if (c->sig_eig_done) {
+    // single-pass form: Sigma_s's part of the tail already ran beside the pass
+    TRY(do_polar(c));
+    LAUNCH(c, KK_PHI, launch_phi(c));
+  } else {
+    TRY(do_side_chain(c));
+  }
   c->side_pending = false;
+  c->sig_eig_done = false;
   return SRM_OK;
 }
 
 namespace {
 
+// Single-pass form.  The M-step's pass leaves A_i^T X^_i behind, so the
+// E-step reads no X^: the polar factors (which need the pass's Gram) and Phi
+// run first, then the reduction.  Sigma_s^new and its eigen-decomposition ran
+// beside the pass.
+srm_status do_estep_fused(Ctx* c) {
+  if (c->side_pending || c->sigma_pending) TRY(flush_pending(c));
+  if (!c->p_from_f) LAUNCH(c, KK_P_TC, launch_p_tc(c));
+  LAUNCH(c, KK_P_REDUCE, launch_p_reduce(c));
+  c->sigma_pending = true;
+  return SRM_OK;
+}
+
+srm_status do_mstep_fused(Ctx* c) {
+  // Sigma_s^new (from the E-step just done) and its eigen-decomposition on a
+  // third stream beside the pass, joined at its end
+  CK(cudaEventRecord(c->ev_fork, c->stream));
+  CK(cudaStreamWaitEvent(c->side2, c->ev_fork, 0));
+  {
+    OnStream on(c, c->side2);
+    if (c->sigma_pending) {
+      LAUNCH(c, KK_SIGMA, launch_sigma(c));
+      c->sigma_pending = false;
+    }
+    if (ns_supported(c)) TRY(do_sigma_eig(c));
+  }
+  CK(cudaEventRecord(c->ev_join2, c->side2));
+  LAUNCH(c, KK_FPASS, launch_fpass(c));
+  CK(cudaStreamWaitEvent(c->stream, c->ev_join2, 0));
+  c->side_pending = true;
+  c->sig_eig_done = ns_supported(c);
+  c->p_from_f = true;
+  return SRM_OK;
+}
+
 srm_status do_estep(Ctx* c) {
+  if (c->fused) return do_estep_fused(c);
   const bool overlap = c->side_pending;
   if (!overlap && c->sigma_pending) {
     // an E-step followed by another without an M-step in between
@@ -288,6 +332,7 @@ srm_status do_estep(Ctx* c) {
 }
 
 srm_status do_mstep(Ctx* c) {
+  if (c->fused) return do_mstep_fused(c);
   if (c->batched) {
     LAUNCH(c, KK_A_TC, launch_a_tc(c));
   } else {
@@ -344,7 +389,7 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
     set_error("srm_init: SRM_BATCHED requires store_dtype SRM_BF16 and the plain form requires SRM_F32");
     return SRM_ERR_ARG;
   }
-  const uint32_t known = SRM_BATCHED | SRM_GRAPH | SRM_FINAL_LL | SRM_HOST_INPUT | SRM_PROFILE;
+  const uint32_t known = SRM_BATCHED | SRM_GRAPH | SRM_FINAL_LL | SRM_HOST_INPUT | SRM_PROFILE | SRM_SINGLE_PASS;
   if (cfg->flags & ~known) {
     set_error("srm_init: unknown flag bits");
     return SRM_ERR_ARG;
@@ -471,6 +516,10 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
   prepare_simt_kernels(prop.sharedMemPerBlockOptin);
   if (batched) {
     if ((st = tc_setup(c)) != SRM_OK) return fail(st);
+    if ((cfg->flags & SRM_SINGLE_PASS) && fused_supported(c)) {
+      if ((st = fused_setup(c)) != SRM_OK) return fail(st);
+      c->fused = true;
+    }
   } else {
     if ((st = setup_plain(c)) != SRM_OK) return fail(st);
   }
@@ -800,6 +849,8 @@ srm_status srm_set_state(srm_ctx* c, const void* buf, size_t bytes) {
   c->have_es = false;
   c->side_pending = false;
   c->sigma_pending = false;
+  c->sig_eig_done = false;
+  c->p_from_f = false;  // A_i changed: the next E-step streams X^ again
   CK(launch_phi(c));
   return check_status(c);
 }
@@ -842,10 +893,10 @@ srm_status srm_layout(srm_ctx* c, int64_t* out, int32_t n) {
     set_error("srm_layout: null output");
     return SRM_ERR_ARG;
   }
-  const int64_t vals[5] = {c->ldT, c->kld, c->Vpad_tot,
+  const int64_t vals[6] = {c->ldT, c->kld, c->Vpad_tot,
                            c->Vpad_tot * c->ldT * (c->store == SRM_BF16 ? 2 : 4),
-                           c->Vpad_tot * c->kld * (c->batched ? 2 : 4)};
-  for (int j = 0; j < n && j < 5; ++j) out[j] = vals[j];
+                           c->Vpad_tot * c->kld * (c->batched ? 2 : 4), c->fused ? 1 : 0};
+  for (int j = 0; j < n && j < 6; ++j) out[j] = vals[j];
   return SRM_OK;
 }
 

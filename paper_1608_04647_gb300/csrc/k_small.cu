@@ -1396,9 +1396,9 @@ cudaError_t launch_p_reduce(Ctx* c) {
   ar.T = c->T;
   ar.k = c->k;
   ar.nchunk = c->nchunk;
-  ar.part = c->Ppart;
-  ar.src = c->chunk_src;
-  ar.src_off = c->chunk_src_off;
+  ar.part = c->p_from_f ? c->f_ppart : c->Ppart;
+  ar.src = c->p_from_f ? c->f_chunk_src : c->chunk_src;
+  ar.src_off = c->p_from_f ? c->f_chunk_src_off : c->chunk_src_off;
   ar.M32 = c->M32;
   ar.rho2 = c->rho2;
   ar.ypart = c->Ypart;

@@ -43,6 +43,7 @@ enum KernelKind : int {
   KK_RHO,
   KK_MTAIL,
   KK_POLAR,
+  KK_FPASS,
   KK_COUNT
 };
 extern const char* const kKernelNames[KK_COUNT];
@@ -133,6 +134,14 @@ struct Ctx {
 
   // tensor-core path state (k_tc.cu)
   void* tc = nullptr;
+  // single-pass form (k_fused.cu): its state, its P partials and their table
+  void* fs = nullptr;
+  bool fused = false;
+  bool p_from_f = false;      // the current P partials come from the single pass
+  bool sig_eig_done = false;  // Sigma_s^new and its eigen-decomposition already ran beside that pass
+  float* f_ppart = nullptr;
+  ChunkSrc* f_chunk_src = nullptr;
+  int* f_chunk_src_off = nullptr;
 
   // ---- host bookkeeping
   int n_ll = 0;            // E-steps launched
@@ -217,6 +226,12 @@ srm_status tc_setup(Ctx* c);
 void tc_destroy(Ctx* c);
 cudaError_t launch_p_tc(Ctx* c);
 cudaError_t launch_a_tc(Ctx* c);
+
+// k_fused.cu (single pass over X^ per iteration)
+bool fused_supported(const Ctx* c);
+srm_status fused_setup(Ctx* c);
+void fused_destroy(Ctx* c);
+cudaError_t launch_fpass(Ctx* c);
 
 }  // namespace srm
 

@@ -99,3 +99,15 @@ def test_null_arguments(lib):
         assert getattr(lib, f)(None) == SRM_ERR_ARG
     assert lib.srm_fit(None, 1, None) == SRM_ERR_ARG
     lib.srm_destroy(None)  # no-op
+
+
+def test_flag_constants_match_header():
+    import re
+
+    import paper_1608_04647_gb300 as srm
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "srm.h")).read()
+    defs = {m.group(1): 1 << int(m.group(2)) for m in re.finditer(r"#define (SRM_[A-Z_]+)\s+\(1u << (\d+)\)", hdr)}
+    assert set(defs) >= {"SRM_BATCHED", "SRM_GRAPH", "SRM_FINAL_LL", "SRM_HOST_INPUT", "SRM_PROFILE",
+                         "SRM_SINGLE_PASS"}
+    for name, val in defs.items():
+        assert getattr(srm, name) == val, name

@@ -1,0 +1,122 @@
+"""GPU parity of the single-pass form (SRM_SINGLE_PASS: one stream of X^ per
+EM iteration produces A_i, its Gram and A_i^T X^_i for the next E-step)
+against the FP64 oracle, with the bar of the BF16 form (2e-2 relative).
+Shapes cover T <= 512 (one CTA per tile), 512 < T <= 1024 (a cluster of two
+CTAs splitting T, with the ragged edges T = 513 and T = 1024), ragged voxel
+tails, k from 1 to 64, many subjects, and a shape the form does not support
+(T > 1024), where the flag must be ignored."""
+import numpy as np
+import pytest
+
+from gpu_cases import Case, make_inputs, rel_errors, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+TOL_BF16 = 2e-2
+
+SP_CASES = [
+    Case("raider-like", [2000] * 4, 300, 10, 10, seed=0),
+    Case("uneven-k50", [2999, 4100, 3333], 333, 50, 8, seed=1),
+    Case("tiny", [7], 9, 1, 6, seed=5),
+    Case("k-odd", [130, 129, 257], 64, 17, 6, seed=6),
+    Case("many-subjects", [int(x) for x in np.random.default_rng(9).integers(150, 900, size=40)], 200, 12, 5,
+         seed=9),
+    Case("k64-boundary", [900, 1300], 130, 64, 4, seed=14),
+    Case("k50-scaled-1e4", [2500, 3100, 2000], 500, 50, 4, seed=13, scale=1e4),
+    Case("t512", [1700, 1200], 512, 30, 4, seed=21),
+    Case("t513-cluster", [1500, 2100], 513, 20, 5, seed=22),
+    Case("greeneyes-shape-small", [3000, 2500, 1800, 2222], 1000, 50, 5, seed=23),
+    Case("t1024-k64", [1500, 700], 1024, 64, 4, seed=24),
+    Case("t700-many", [int(x) for x in np.random.default_rng(25).integers(100, 700, size=24)], 700, 16, 4,
+         seed=25),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    from paper_1608_04647_gb300 import _build as b
+    b.build()
+
+
+@pytest.mark.parametrize("case", SP_CASES, ids=lambda c: c.name)
+def test_single_pass_matches_oracle(case):
+    d = make_inputs(case)
+    o = run_oracle(d, case.n_iter)
+    g = run_gpu(d, case.k, case.n_iter, store="bf16", single_pass=True)
+    assert g["model"].layout()["single_pass"] == 1
+    err = rel_errors(g, o)
+    print(case.name, {k: f"{v:.2e}" for k, v in err.items()})
+    for key, e in err.items():
+        assert e <= TOL_BF16, (key, e)
+    for w in g["W"]:
+        np.testing.assert_allclose(w.T @ w, np.eye(case.k), atol=2e-2)
+    assert np.all(np.diff(g["ll"]) >= -TOL_BF16 * np.abs(g["ll"][1:]))
+
+
+def test_single_pass_ignored_where_unsupported():
+    # T > 1024 and k > 64: the two-pass form runs and still matches the oracle
+    for case in (Case("t1100", [3000, 2500], 1100, 20, 4, seed=4),
+                 Case("k80", [3000, 2600], 400, 80, 3, seed=12)):
+        d = make_inputs(case)
+        o = run_oracle(d, case.n_iter)
+        g = run_gpu(d, case.k, case.n_iter, store="bf16", single_pass=True)
+        assert g["model"].layout()["single_pass"] == 0
+        for key, e in rel_errors(g, o).items():
+            assert e <= TOL_BF16, (case.name, key, e)
+
+
+def test_single_pass_deterministic_graph_and_steps():
+    # bitwise identical: eager iterations, CUDA-graph replay, a second run
+    case = SP_CASES[9]
+    d = make_inputs(case)
+    a = run_gpu(d, case.k, case.n_iter, store="bf16", single_pass=True, graph=False)
+    b = run_gpu(d, case.k, case.n_iter, store="bf16", single_pass=True, graph=True)
+    c = run_gpu(d, case.k, case.n_iter, store="bf16", single_pass=True, graph=True)
+    np.testing.assert_array_equal(a["ll"], b["ll"])
+    np.testing.assert_array_equal(b["ES"], c["ES"])
+    for x, y in zip(a["W"], c["W"]):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_single_pass_agrees_with_two_pass():
+    # the same iteration computed two ways: FP32 summation orders and the
+    # rounding of the BF16 A_i differ, so each sits within BF16 noise of the
+    # oracle and the two differ by up to the sum of those distances
+    case = SP_CASES[9]
+    d = make_inputs(case)
+    a = run_gpu(d, case.k, case.n_iter, store="bf16", single_pass=False)
+    b = run_gpu(d, case.k, case.n_iter, store="bf16", single_pass=True)
+    assert a["model"].layout()["single_pass"] == 0
+    err = rel_errors(b, a)
+    print({k: f"{v:.2e}" for k, v in err.items()})
+    for key, e in err.items():
+        assert e <= TOL_BF16, (key, e)
+
+
+def test_single_pass_steps_and_checkpoint():
+    import torch
+
+    import paper_1608_04647_gb300 as srm
+    case = SP_CASES[8]
+    d = make_inputs(case)
+    X = [torch.from_numpy(x).cuda() for x in d["X"]]
+    W0 = [torch.from_numpy(w).cuda() for w in d["W0"]]
+    ref = srm.SRM(X, W0, case.k, store="bf16", single_pass=True)
+    ref.fit(6)
+    # explicit E- and M-steps run the same launches as srm_fit
+    m = srm.SRM(X, W0, case.k, store="bf16", single_pass=True)
+    for _ in range(6):
+        m.estep()
+        m.mstep()
+    np.testing.assert_array_equal(m.get_w(1).cpu().numpy(), ref.get_w(1).cpu().numpy())
+    np.testing.assert_array_equal(m.params()[0], ref.params()[0])
+    # checkpoint after 3 iterations, restore into a fresh context, 3 more: the
+    # restored context's first E-step streams X^ (the pass's partials are not
+    # part of the state), so only summation orders differ
+    m1 = srm.SRM(X, W0, case.k, store="bf16", single_pass=True)
+    m1.fit(3)
+    st = m1.state()
+    m2 = srm.SRM(X, W0, case.k, store="bf16", single_pass=True)
+    m2.set_state(st)
+    m2.fit(3)
+    np.testing.assert_allclose(m2.ll(), ref.ll(), rtol=1e-4)
+    np.testing.assert_allclose(m2.get_w(0).cpu().numpy(), ref.get_w(0).cpu().numpy(), atol=2e-3)
