@@ -784,24 +784,26 @@ __global__ void __launch_bounds__(128) dk_rho_kernel(int N, int k, int T, const 
 // ---------------------------------------------------------------- polar factor by Newton-Schulz
 // For k <= NS_KMAX: M_i = (A_i^T A_i)^-1/2 and ||A_i||_* without an
 // eigen-decomposition when A_i^T A_i is well conditioned.  One CTA per
-// subject.  With G = A_i^T A_i (FP64 sum of the Gram partials) and
+// subject.  With G = A_i^T A_i (error-free sum of the Gram partials) and
 // c = min(||G||_F, ||G||_inf) >= lambda_max, the coupled Newton-Schulz
 // iteration on A = G / c,
 //     P = Z Y,  T = (3 I - P) / 2,  Y <- Y T,  Z <- T Z,   Y_0 = A, Z_0 = I,
 // converges quadratically to Y = A^1/2, Z = A^-1/2 for a symmetric positive
 // definite A (eigenvalues in (0, 1]); it is the stable, coupled form.  It
-// stops two steps after max |P - I| < NS_TOL; M_0 = sym(Z) / sqrt(c).
+// stops two steps after max |P - I| < NS_TOL; M_0 = Z / sqrt(c).
 //
 // FP32 arithmetic leaves M_0 with an error of about eps cond(G) in the
 // directions of the small eigenvalues, so each result is certified: with
 // E = M_0 G M_0 - I and delta = M_0 - G^-1/2, first order gives
 // E_ab = (sqrt(lambda_a) + sqrt(lambda_b)) delta_ab in the eigenbasis of G,
 // while the polar factor's error A_i delta has entries sqrt(lambda_a)
-// delta_ab; so ||A_i delta||_F <= ||E||_F.  E is formed in compensated FP32
-// (error-free products and sums, G split into two FP32 parts), and a subject
-// with ||E||_F > cert sqrt(k) (or no convergence) is marked for the
-// eigen-decomposition path (Jacobi + FP64 refinement), which then
-// overwrites its M_i and rho_i^2.
+// delta_ab; so ||A_i delta||_F <= ||E||_F.  For the FP32 store E is formed
+// in compensated FP32 (error-free products and sums, G split into two FP32
+// parts); for the BF16 store, whose threshold is 50 times larger, in plain
+// FP32 (its rounding, about k eps sqrt(cond G) per entry, can only make a
+// subject fail).  A subject with ||E||_F > cert sqrt(k) (or no convergence)
+// is marked for the eigen-decomposition path (Jacobi + FP64 refinement),
+// which then overwrites its M_i and rho_i^2.
 //
 // ||A_i||_* = tr(W^T A_i) for the polar factor W.  With W~ = A_i M_0 and
 // W = W~ (I + E)^-1/2 (orthonormal), tr(W^T A_i) = tr(M_0 G) - tr(E M_0 G)/2
@@ -810,7 +812,8 @@ __global__ void __launch_bounds__(128) dk_rho_kernel(int N, int k, int T, const 
 // Matrices are KP x KP (KP = k rounded up to 4) FP32 in shared memory with
 // zero padding; the products use 4 x 4 register tiles whose operands are
 // read as float4 (the left operand as its transpose, which for these
-// symmetric matrices is itself).
+// symmetric matrices is itself), each tile's inner index split over 2 or 4
+// lanes.
 constexpr int NS_KMAX = 64;
 constexpr int NS_MAXIT = 40;
 constexpr float NS_TOL = 1e-4f;
@@ -818,70 +821,6 @@ constexpr float NS_TOL = 1e-4f;
 constexpr double NS_CERT_F32 = 2e-6;
 constexpr double NS_CERT_BF16 = 1e-4;
 
-
-// C = A^T B for KP x KP row-major operands (KP <= 64, multiple of 4), by the
-// 256 threads [base, base + 256) of the block.
-__device__ __forceinline__ void ns_mm(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ C,
-                                      int KP, int base = 0) {
-  const int tid = (int)threadIdx.x - base, warp = tid >> 5, lane = tid & 31;
-  if (tid < 0 || tid >= 256) return;
-  const int tr = (warp >> 1) * 4 + (lane >> 3), tc = (warp & 1) * 8 + (lane & 7);
-  const int nt4 = KP / 4;
-  if (tr >= nt4 || tc >= nt4) return;
-  float acc[4][4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
-#pragma unroll 4
-  for (int m = 0; m < KP; ++m) {
-    const float4 a = *reinterpret_cast<const float4*>(A + m * KP + 4 * tr);
-    const float4 b = *reinterpret_cast<const float4*>(B + m * KP + 4 * tc);
-    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-    *reinterpret_cast<float4*>(C + (4 * tr + u) * KP + 4 * tc) = make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
-}
-
-// The same product with error-free accumulation of A^T B_hi plus A^T B_lo:
-// returns the 4 x 4 tile as hi + lo parts in registers.
-__device__ __forceinline__ bool ns_mm2(const float* __restrict__ A, const float* __restrict__ Bh,
-                                       const float* __restrict__ Bl, int KP, float (&hi)[4][4], float (&lo)[4][4],
-                                       int& r0, int& c0) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tr = (warp >> 1) * 4 + (lane >> 3), tc = (warp & 1) * 8 + (lane & 7);
-  r0 = 4 * tr;
-  c0 = 4 * tc;
-  if (tid >= 256 || tr >= KP / 4 || tc >= KP / 4) return false;
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) hi[u][v] = lo[u][v] = 0.f;
-  for (int m = 0; m < KP; ++m) {
-    const float4 a = *reinterpret_cast<const float4*>(A + m * KP + 4 * tr);
-    const float4 bh = *reinterpret_cast<const float4*>(Bh + m * KP + 4 * tc);
-    const float4 bl = *reinterpret_cast<const float4*>(Bl + m * KP + 4 * tc);
-    const float av[4] = {a.x, a.y, a.z, a.w}, bhv[4] = {bh.x, bh.y, bh.z, bh.w}, blv[4] = {bl.x, bl.y, bl.z, bl.w};
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const float p = av[u] * bhv[v];
-        const float pe = fmaf(av[u], bhv[v], -p);  // exact product error
-        float s, se;
-        two_sum(hi[u][v], p, s, se);
-        hi[u][v] = s;
-        lo[u][v] += se + pe;
-        lo[u][v] = fmaf(av[u], blv[v], lo[u][v]);
-      }
-  }
-  return true;
-}
 
 constexpr int NS_THREADS = 512;
 
@@ -897,127 +836,333 @@ __device__ __forceinline__ float block_max_ns(float v, float* red) {
   return r;
 }
 
-// Sum of three doubles over the NS_THREADS threads (fixed-order tree); every
-// thread gets the totals.
-__device__ void block_sum3_ns(double& a, double& b, double& c, double (*red)[NS_THREADS]) {
-  const int tid = threadIdx.x;
-  red[0][tid] = a;
-  red[1][tid] = b;
-  red[2][tid] = c;
-  __syncthreads();
-  for (int st = NS_THREADS / 2; st > 0; st >>= 1) {
-    if (tid < st) {
-      red[0][tid] += red[0][tid + st];
-      red[1][tid] += red[1][tid + st];
-      red[2][tid] += red[2][tid + st];
-    }
-    __syncthreads();
+// Sums of two floats over the NS_THREADS threads (fixed-order shuffle tree,
+// then the warp partials in warp order); every thread gets the totals.
+__device__ void block_sum2f_ns(float& a, float& b, float (*red)[NS_THREADS / 32]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
   }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = a;
+    red[1][threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
   a = red[0][0];
   b = red[1][0];
-  c = red[2][0];
+#pragma unroll
+  for (int w = 1; w < NS_THREADS / 32; ++w) {
+    a += red[0][w];
+    b += red[1][w];
+  }
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(NS_THREADS) polar_ns_kernel(int N, int k, int kld, int T, const float* __restrict__ gpart,
-                                                       const int* __restrict__ gslot_off, double* __restrict__ G64,
+// (h, l) += (bh, bl) in float-float arithmetic (renormalised)
+__device__ __forceinline__ void ff_add(float& h, float& l, float bh, float bl) {
+  float s, e;
+  two_sum(h, bh, s, e);
+  e += l + bl;
+  two_sum(s, e, h, l);
+}
+
+// ---- 4 x 4 register tiles of C = A^T B split over KS lanes along the inner
+// index (lanes l ^ 1, l ^ 2, ... hold the parts of one tile and add them by
+// shuffles).  With COMP the products are error-free (A^T B_hi in hi + lo
+// plus A^T B_lo), as in ns_mm2.
+template <int KS, bool COMP>
+__device__ __forceinline__ void tile_part(const float* __restrict__ A, const float* __restrict__ Bh,
+                                          const float* __restrict__ Bl, int KP, int tr, int tc, int q, bool valid,
+                                          float (&hi)[4][4], float (&lo)[4][4]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) hi[u][v] = lo[u][v] = 0.f;
+  if (!valid) return;
+  const int KQ = ((KP / 4 + KS - 1) / KS) * 4;
+  const int m0 = q * KQ, m1 = min(KP, m0 + KQ);
+#pragma unroll 2
+  for (int m = m0; m < m1; ++m) {
+    const float4 a = *reinterpret_cast<const float4*>(A + m * KP + 4 * tr);
+    const float4 b = *reinterpret_cast<const float4*>(Bh + m * KP + 4 * tc);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+    if (!COMP) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) hi[u][v] = fmaf(av[u], bv[v], hi[u][v]);
+    } else {
+      const float4 bl = *reinterpret_cast<const float4*>(Bl + m * KP + 4 * tc);
+      const float lv[4] = {bl.x, bl.y, bl.z, bl.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const float p = av[u] * bv[v];
+          const float pe = fmaf(av[u], bv[v], -p);  // exact product error
+          float sm, se;
+          two_sum(hi[u][v], p, sm, se);
+          hi[u][v] = sm;
+          lo[u][v] += se + pe;
+          lo[u][v] = fmaf(av[u], lv[v], lo[u][v]);
+        }
+    }
+  }
+}
+template <int KS, bool COMP>
+__device__ __forceinline__ void tile_combine(float (&hi)[4][4], float (&lo)[4][4]) {
+#pragma unroll
+  for (int o = 1; o < KS; o <<= 1)
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const float oh = __shfl_xor_sync(0xffffffffu, hi[u][v], o);
+        if (COMP) {
+          const float ol = __shfl_xor_sync(0xffffffffu, lo[u][v], o);
+          ff_add(hi[u][v], lo[u][v], oh, ol);
+        } else {
+          hi[u][v] += oh;
+        }
+      }
+}
+
+// C = A^T B for KP x KP operands whose product is symmetric (here: A, B
+// commuting symmetric polynomials of the same matrix, so C = A B = B A):
+// the upper tiles only, mirrored.  Threads [base, base + nth) of the block,
+// nth a multiple of 32; tiles from the upper-tile table `ut` (nut entries).
+template <int KS>
+__device__ __forceinline__ void sym_mm(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ C,
+                                       int KP, const uint16_t* __restrict__ ut, int nut, int base, int nth) {
+  const int lt = (int)threadIdx.x - base;
+  if (lt < 0 || lt >= nth) return;  // whole warps
+  const int per = nth / KS;
+  const int q = lt % KS;
+  for (int t0 = 0; t0 < nut; t0 += per) {
+    const int t = t0 + lt / KS;
+    const bool valid = t < nut;
+    const int tr = valid ? (ut[t] & 0xff) : 0, tc = valid ? (ut[t] >> 8) : 0;
+    float hi[4][4], lo[4][4];
+    tile_part<KS, false>(A, B, nullptr, KP, tr, tc, q, valid, hi, lo);
+    tile_combine<KS, false>(hi, lo);
+    if (valid && q == 0) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        *reinterpret_cast<float4*>(C + (4 * tr + u) * KP + 4 * tc) = make_float4(hi[u][0], hi[u][1], hi[u][2], hi[u][3]);
+      if (tc != tr) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          *reinterpret_cast<float4*>(C + (4 * tc + v) * KP + 4 * tr) = make_float4(hi[0][v], hi[1][v], hi[2][v], hi[3][v]);
+      }
+    }
+  }
+}
+
+// FP64 arithmetic runs at about 2 FMA per clock per SM on this GPU, so the
+// kernel keeps it to O(k) scalar work: sums of Gram partials, the
+// symmetrised G and tr(M_0 G) are carried as FP32 hi + lo pairs (error-free
+// transformations), the rest is plain FP32.  All iterates Y, Z, T are
+// polynomials in G, so every product of the iteration is symmetric and only
+// its upper 4 x 4 tiles are computed.  The certificate's products are
+// error-free for the FP32 store (comp = 1); for the BF16 store, whose
+// threshold is 50 times larger, plain FP32 products suffice (comp = 0).
+constexpr int NS_GE = 8;  // Gram elements per thread (KP * KP <= NS_GE * NS_THREADS)
+static_assert(NS_GE * NS_THREADS >= NS_KMAX * NS_KMAX, "polar: Gram elements per thread");
+
+template <bool COMP>
+__device__ __forceinline__ void ns_certificate(const float* __restrict__ Mb, const float* __restrict__ Gh,
+                                               const float* __restrict__ Gl, float* __restrict__ Ph,
+                                               float* __restrict__ Pl, int k, int KP,
+                                               const uint16_t* __restrict__ ut, int nut, float& e2, float& corr) {
+  const int tid = threadIdx.x, nt4 = KP / 4;
+  // R = M_0 G (all tiles), stored transposed: P = R^T = G M_0
+  {
+    constexpr int KS = 2;
+    const int per = NS_THREADS / KS, q = tid % KS, ntile = nt4 * nt4;
+    for (int t0 = 0; t0 < ntile; t0 += per) {
+      const int t = t0 + tid / KS;
+      const bool valid = t < ntile;
+      const int tr = valid ? t / nt4 : 0, tc = valid ? t - (t / nt4) * nt4 : 0;
+      float hi[4][4], lo[4][4];
+      tile_part<KS, COMP>(Mb, Gh, Gl, KP, tr, tc, q, valid, hi, lo);
+      tile_combine<KS, COMP>(hi, lo);
+      if (valid && q == 0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            Ph[(4 * tc + v) * KP + 4 * tr + u] = hi[u][v];
+            if (COMP) Pl[(4 * tc + v) * KP + 4 * tr + u] = lo[u][v];
+          }
+      }
+    }
+  }
+  __syncthreads();
+  // E = M_0 P - I (symmetric: upper tiles), ||E||_F^2 and
+  // tr(E M_0 G) = sum_ab E_ab R_ba = sum_ab E_ab P_ab
+  {
+    constexpr int KS = 4;
+    const int per = NS_THREADS / KS, q = tid % KS;
+    for (int t0 = 0; t0 < nut; t0 += per) {
+      const int t = t0 + tid / KS;
+      const bool valid = t < nut;
+      const int tr = valid ? (ut[t] & 0xff) : 0, tc = valid ? (ut[t] >> 8) : 0;
+      float hi[4][4], lo[4][4];
+      tile_part<KS, COMP>(Mb, Ph, Pl, KP, tr, tc, q, valid, hi, lo);
+      tile_combine<KS, COMP>(hi, lo);
+      if (valid && q == 0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int a = 4 * tr + u, b = 4 * tc + v;
+            if (a >= k || b >= k || b < a) continue;
+            const float ev = (hi[u][v] - (a == b ? 1.f : 0.f)) + lo[u][v];
+            if (a == b) {
+              e2 = fmaf(ev, ev, e2);
+              corr = fmaf(ev, Ph[a * KP + a], corr);
+            } else {
+              e2 = fmaf(2.f * ev, ev, e2);
+              corr = fmaf(ev, Ph[a * KP + b] + Ph[b * KP + a], corr);
+            }
+          }
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(NS_THREADS, 1) polar_ns_kernel(int N, int k, int kld, int T, const float* __restrict__ gpart,
+                                                       const int* __restrict__ gslot_off,
                                                        double* __restrict__ M64, float* __restrict__ M32,
                                                        const double* __restrict__ sqnorm,
                                                        const int64_t* __restrict__ vox,
                                                        const double* __restrict__ SigmaNext,
                                                        double* __restrict__ Sigma, double* __restrict__ rho2,
                                                        double* __restrict__ scal, int* __restrict__ iters_out,
-                                                       int* __restrict__ fallback, double cert, int* status) {
+                                                       int* __restrict__ fallback, double cert, int comp,
+                                                       int* status) {
   extern __shared__ __align__(16) float ns_smem[];
   __shared__ float redf[NS_THREADS / 32];
-  __shared__ double redd[3][NS_THREADS];
+  __shared__ float red2[2][NS_THREADS / 32];
+  __shared__ double trS_s;
+  __shared__ float tmg_s[2];
+  __shared__ uint16_t ut[(NS_KMAX / 4) * (NS_KMAX / 4 + 1) / 2];
   const int KP = (k + 3) & ~3;
   const int KK = KP * KP;
-  float* B0 = ns_smem;
-  float* B1 = B0 + KK;
-  float* B2 = B1 + KK;
-  float* B3 = B2 + KK;
-  float* B4 = B3 + KK;
+  const int nt4 = KP / 4, nut = nt4 * (nt4 + 1) / 2;
+  float* Y = ns_smem;
+  float* Z = Y + KK;
+  float* Tm = Z + KK;
+  float* W = Tm + KK;
+  float* Xb = W + KK;
+  float* Gh = Xb + KK;  // sym(G) = Gh + Gl, kept for the certificate
+  float* Gl = Gh + KK;
   const int i = blockIdx.x, tid = threadIdx.x;
-  double* Gi = G64 + (int64_t)i * k * k;
-  float* Y = B0;
-  float* Z = B1;
-  float* Tm = B2;
-  float* W = B3;
-  float* Xb = B4;
-  // G (FP64) from the Gram partials (four slot loads in flight), kept as
-  // FP32 hi + lo in W / Tm for the iteration's start; ||G||_F^2, tr Sigma_s^new
-  const int s0 = gslot_off[i], s1 = gslot_off[i + 1];
-  double fro = 0.0, tr = 0.0, z0 = 0.0;
-  for (int e = tid; e < KK; e += NS_THREADS) {
-    const int a = e / KP, b = e - a * KP;
-    double sum = 0.0;
-    if (a < k && b < k) {
-      const float* gp = gpart + a * kld + b;
-      int q = s0;
-      for (; q + 4 <= s1; q += 4) {
-        const float g0 = __ldg(gp + (int64_t)q * kld * kld), g1 = __ldg(gp + (int64_t)(q + 1) * kld * kld);
-        const float g2 = __ldg(gp + (int64_t)(q + 2) * kld * kld), g3 = __ldg(gp + (int64_t)(q + 3) * kld * kld);
-        sum += (double)g0;
-        sum += (double)g1;
-        sum += (double)g2;
-        sum += (double)g3;
-      }
-      for (; q < s1; ++q) sum += (double)__ldg(gp + (int64_t)q * kld * kld);
-      Gi[a * k + b] = sum;
-      fro += sum * sum;
+  for (int t = tid; t < nut; t += NS_THREADS) {  // upper tiles, row by row
+    int r = 0, rem = t;
+    while (rem >= nt4 - r) {
+      rem -= nt4 - r;
+      ++r;
     }
-    const float hi = (float)sum;
-    W[e] = hi;
-    Tm[e] = (float)(sum - (double)hi);
+    ut[t] = (uint16_t)(r | ((r + rem) << 8));
   }
-  if (tid < k) tr = SigmaNext[tid * k + tid];
-  block_sum3_ns(fro, tr, z0, redd);  // (its barriers also publish W, Tm)
-  // ||sym(G)||_inf <= max_a sum_b (|G_ab| + |G_ba|) / 2, from the FP32 copy
+  // G = hi + lo from the Gram partials (slot order, error-free; loads of
+  // four slots x NS_GE elements in flight); ||G||_F^2 from hi
+  const int s0 = gslot_off[i], s1 = gslot_off[i + 1];
+  const int64_t sst = (int64_t)kld * kld;
+  float fro = 0.f, unused = 0.f;
+  {
+    float gh[NS_GE], gl[NS_GE];
+    int off[NS_GE];
+#pragma unroll
+    for (int j = 0; j < NS_GE; ++j) {
+      const int e = tid + j * NS_THREADS;
+      const int a = e / KP, b = e - (e / KP) * KP;
+      off[j] = (e < KK && a < k && b < k) ? a * kld + b : -1;
+      gh[j] = gl[j] = 0.f;
+    }
+    for (int q = s0; q < s1; q += 4) {
+      float g[NS_GE][4];
+#pragma unroll
+      for (int j = 0; j < NS_GE; ++j)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+          g[j][jj] = (off[j] >= 0 && q + jj < s1) ? __ldg(gpart + (q + jj) * sst + off[j]) : 0.f;
+#pragma unroll
+      for (int j = 0; j < NS_GE; ++j)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          float sm, se;
+          two_sum(gh[j], g[j][jj], sm, se);
+          gh[j] = sm;
+          gl[j] += se;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NS_GE; ++j) {
+      const int e = tid + j * NS_THREADS;
+      if (e < KK) {
+        float sm, se;
+        two_sum(gh[j], gl[j], sm, se);
+        W[e] = sm;  // raw G (hi, lo) until symmetrised below
+        Xb[e] = se;
+        fro = fmaf(sm, sm, fro);
+      }
+    }
+  }
+  // tr Sigma_s^new: one warp, fixed-order FP64 tree over the diagonal
+  if (tid < 32) {
+    double t = 0.0;
+    for (int a = tid; a < k; a += 32) t += SigmaNext[a * k + a];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (tid == 0) trS_s = t;
+  }
+  block_sum2f_ns(fro, unused, red2);  // (its barriers also publish W, Xb, trS_s, ut)
+  const double trS = trS_s;
+  // sym(G) in float-float into Gh, Gl; Y = sym(G) / c below; Z = I
   float rowmax = 0.f;
   for (int a = tid; a < k; a += NS_THREADS) {
     float rs = 0.f;
     for (int b = 0; b < k; ++b) rs += 0.5f * (fabsf(W[a * KP + b]) + fabsf(W[b * KP + a]));
     rowmax = fmaxf(rowmax, rs);
   }
-  const float ginf = block_max_ns(rowmax, redf);
-  const double trS = tr;
-  double c = sqrt(fro);
-  if ((double)ginf * (1.0 + 1e-5) < c) c = (double)ginf * (1.0 + 1e-5);  // both bound lambda_max from above
-  const bool good_c = isfinite(c) && c > 0.0;
-  const double cinv = good_c ? 1.0 / c : 0.0;
-  // Y = sym(G) / c, Z = I (k block), zero padding
   for (int e = tid; e < KK; e += NS_THREADS) {
-    const int a = e / KP, b = e - a * KP;
-    float y = 0.f, z = 0.f;
-    if (a < k && b < k) {
-      const double gab = (double)W[e] + (double)Tm[e], gba = (double)W[b * KP + a] + (double)Tm[b * KP + a];
-      y = (float)(0.5 * (gab + gba) * cinv);
-      z = (a == b) ? 1.f : 0.f;
-    }
-    Y[e] = y;
-    Z[e] = z;
+    const int a = e / KP, b = e - (e / KP) * KP;
+    float h = W[e], l = Xb[e];
+    ff_add(h, l, W[b * KP + a], Xb[b * KP + a]);
+    Gh[e] = 0.5f * h;  // exact scaling
+    Gl[e] = 0.5f * l;
+  }
+  const float ginf = block_max_ns(rowmax, redf);  // (its barriers also publish Gh, Gl)
+  // both bound lambda_max from above (the margin covers FP32 rounding of the bounds)
+  const double c = fmin(sqrt((double)fro), (double)ginf) * (1.0 + 1e-5);
+  const bool good_c = isfinite(c) && c > 0.0;
+  const float cinv = good_c ? (float)(1.0 / c) : 0.f;
+  for (int e = tid; e < KK; e += NS_THREADS) {
+    const int a = e / KP, b = e - (e / KP) * KP;
+    Y[e] = (Gh[e] + Gl[e]) * cinv;
+    Z[e] = (a == b && a < k) ? 1.f : 0.f;
   }
   __syncthreads();
   int it = 0, extra = -1;
   bool conv = false;
   for (; good_c && it < NS_MAXIT; ++it) {
-    ns_mm(Z, Y, Tm, KP);  // P = Z^T Y
+    sym_mm<4>(Z, Y, Tm, KP, ut, nut, 0, NS_THREADS);  // P = Z Y
     __syncthreads();
-    // T = (3I - (P + P^T)/2) / 2 on the k block (zero elsewhere); e = max |P - I|
+    // T = (3I - P) / 2 on the k block (zero elsewhere); e = max |P - I|
     float emax = 0.f;
     for (int e = tid; e < KK; e += NS_THREADS) {
-      const int a = e / KP, b = e - a * KP;
-      if (b < a) continue;
+      const int a = e / KP, b = e - (e / KP) * KP;
       float t = 0.f;
       if (a < k && b < k) {
-        const float pab = Tm[a * KP + b], pba = Tm[b * KP + a];
         const float d = (a == b) ? 1.f : 0.f;
-        emax = fmaxf(emax, fmaxf(fabsf(pab - d), fabsf(pba - d)));
-        t = 1.5f * d - 0.25f * (pab + pba);
+        const float pab = Tm[e];
+        emax = fmaxf(emax, fabsf(pab - d));
+        t = 1.5f * d - 0.5f * pab;
       }
-      Tm[a * KP + b] = t;
-      Tm[b * KP + a] = t;
+      Tm[e] = t;
     }
     const float err = block_max_ns(emax, redf);
     if (!(err == err)) break;  // non-finite
@@ -1028,8 +1173,8 @@ __global__ void __launch_bounds__(NS_THREADS) polar_ns_kernel(int N, int k, int 
     }
     if (extra > 0) --extra;
     // Y T and T Z at once, each by half of the block
-    ns_mm(Y, Tm, W, KP, 0);       // Y T
-    ns_mm(Tm, Z, Xb, KP, 256);    // T Z
+    sym_mm<2>(Y, Tm, W, KP, ut, nut, 0, NS_THREADS / 2);
+    sym_mm<2>(Tm, Z, Xb, KP, ut, nut, NS_THREADS / 2, NS_THREADS / 2);
     __syncthreads();
     float* t = Y;
     Y = W;
@@ -1038,69 +1183,44 @@ __global__ void __launch_bounds__(NS_THREADS) polar_ns_kernel(int N, int k, int 
     Z = Xb;
     Xb = t;
   }
-  // M_0 = sym(Z) / sqrt(c) into W; G = G_hi + G_lo into the buffers of Y and T
+  // M_0 = Z / sqrt(c) into W; the certificate's product P = G M_0 into the
+  // buffers of Y (hi) and T (lo)
   float* Mb = W;
-  float* Gh = Y;
-  float* Gl = Tm;
-  float* Zb = Z;  // free once M_0 is formed
   {
-    const float sc = (float)sqrt(cinv);
-    for (int e = tid; e < KK; e += NS_THREADS) {
-      const int a = e / KP, b = e - a * KP;
-      float m = 0.f, gh = 0.f, gl = 0.f;
-      if (a < k && b < k) {
-        m = 0.5f * (Z[a * KP + b] + Z[b * KP + a]) * sc;
-        const double g = 0.5 * (Gi[a * k + b] + Gi[b * k + a]);
-        gh = (float)g;
-        gl = (float)(g - (double)gh);
-      }
-      Mb[e] = m;
-      Gh[e] = gh;
-      Gl[e] = gl;
+    const float sc = good_c ? (float)sqrt(1.0 / c) : 0.f;
+    for (int e = tid; e < KK; e += NS_THREADS) Mb[e] = Z[e] * sc;
+  }
+  __syncthreads();
+  float* Ph = Y;
+  float* Pl = Tm;
+  float e2 = 0.f, corr = 0.f;
+  if (comp)
+    ns_certificate<true>(Mb, Gh, Gl, Ph, Pl, k, KP, ut, nut, e2, corr);
+  else
+    ns_certificate<false>(Mb, Gh, Gl, Ph, Pl, k, KP, ut, nut, e2, corr);
+  // tr(M_0 G) = tr P in float-float (hi + lo with comp, hi alone without)
+  if (tid < 32) {
+    float h = 0.f, l = 0.f;
+    for (int a = tid; a < k; a += 32) ff_add(h, l, Ph[a * KP + a], comp ? Pl[a * KP + a] : 0.f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+      ff_add(h, l, oh, ol);
+    }
+    if (tid == 0) {
+      tmg_s[0] = h;
+      tmg_s[1] = l;
     }
   }
-  __syncthreads();
-  // R = M_0 G (hi + lo tiles), stored transposed: P = R^T = G M_0 (hi in Zb, lo in Gh)
-  float th[4][4], tl[4][4];
-  int r0, c0;
-  bool act = ns_mm2(Mb, Gh, Gl, KP, th, tl, r0, c0);
-  __syncthreads();
-  float* Ph = Zb;
-  float* Pl = Gh;
-  if (act) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        Ph[(c0 + v) * KP + r0 + u] = th[u][v];
-        Pl[(c0 + v) * KP + r0 + u] = tl[u][v];
-      }
-  }
-  __syncthreads();
-  // E = M_0 P - I (hi + lo), ||E||_F^2; tr(M_0 G) = tr P; tr(E M_0 G) = sum_ab E_ab P_ab^T... = sum_ab E_ab R_ba
-  double e2 = 0.0, tmg = 0.0, corr = 0.0;
-  act = ns_mm2(Mb, Ph, Pl, KP, th, tl, r0, c0);
-  if (act) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int a = r0 + u, b = c0 + v;
-        if (a >= k || b >= k) continue;
-        const double ev = ((double)th[u][v] - (a == b ? 1.0 : 0.0)) + (double)tl[u][v];
-        e2 += ev * ev;
-        corr += ev * (double)Ph[a * KP + b];  // R_ba = P_ab
-      }
-  }
-  for (int a = tid; a < k; a += NS_THREADS) tmg += (double)Ph[a * KP + a] + (double)Pl[a * KP + a];
-  block_sum3_ns(e2, tmg, corr, redd);
-  const double enorm = sqrt(e2);
+  block_sum2f_ns(e2, corr, red2);
+  const double tmg = (double)tmg_s[0] + (double)tmg_s[1];
+  const double enorm = sqrt((double)e2);
   const bool ok = conv && good_c && enorm <= cert * sqrt((double)k) && isfinite(enorm);
   if (tid == 0) {
     if (iters_out) iters_out[i] = it;
     fallback[i] = ok ? 0 : 1;
     if (ok) {
-      const double nuc = tmg - 0.5 * corr;
+      const double nuc = tmg - 0.5 * (double)corr;
       const double r = (sqnorm[i] - 2.0 * nuc + (double)T * trS) / ((double)T * (double)vox[i]);
       if (!(r > 0.0) || !isfinite(r)) flag(status, ST_NONFINITE);
       rho2[i] = r;
@@ -1123,7 +1243,7 @@ __global__ void __launch_bounds__(NS_THREADS) polar_ns_kernel(int N, int k, int 
 
 size_t ns_smem_bytes(int k) {
   const int KP = (k + 3) & ~3;
-  return sizeof(float) * 5 * (size_t)KP * KP;
+  return sizeof(float) * 7 * (size_t)KP * KP;
 }
 
 // ---------------------------------------------------------------- fused M-step tail
@@ -1473,9 +1593,9 @@ bool ns_supported(const Ctx* c) { return c->k <= NS_KMAX && c->k <= MT_KMAX; }
 
 cudaError_t launch_polar(Ctx* c) {
   polar_ns_kernel<<<c->N, NS_THREADS, ns_smem_bytes(c->k), c->stream>>>(
-      c->N, c->k, c->kld, c->T, c->Gpart, c->gslot_off, c->G64, c->M64, c->M32, c->sqnorm, c->d_v, c->SigmaNext,
+      c->N, c->k, c->kld, c->T, c->Gpart, c->gslot_off, c->M64, c->M32, c->sqnorm, c->d_v, c->SigmaNext,
       c->Sigma, c->rho2, c->scal, c->jac_sweeps, c->ns_fb, c->store == SRM_BF16 ? NS_CERT_BF16 : NS_CERT_F32,
-      c->status);
+      c->store == SRM_BF16 ? 0 : 1, c->status);
   return cudaGetLastError();
 }
 
