@@ -147,6 +147,13 @@ def algorithmic_bytes(vox, T, k, xbytes, abytes):
     return e_pass, m_pass
 
 
+def single_pass_bytes(vox, T, k, xbytes, abytes):
+    """Bytes one iteration of the single-pass form must move: X^ read once
+    and A_i written (the pass's second look at each tile is served by L2)."""
+    V = float(sum(vox))
+    return V * T * xbytes + V * k * abytes
+
+
 def paper_flops(vox, T, k):
     """Flop model of Sec. V-A per subject per iteration: two V_i x T x K
     products, one V_i x K x K product and a V_i x K economy SVD counted as
@@ -200,9 +207,27 @@ def run_ours(args, rank, world):
     stream = torch.cuda.Stream()
     max_iter = args.warmup + args.steps + 64
 
+    # launch plan of the batched form: tuned once on this device and these
+    # shapes (srm_autotune, before any timed region), then replayed from the
+    # cache file by every later context of the same shapes
+    tune = {"cache": None, "plan": None, "ms": None, "tuning_s": None}
+    if args.tune_cache:
+        tune["cache"] = args.tune_cache
+    else:
+        import tempfile
+        tune["cache"] = os.path.join(tempfile.gettempdir(), "srm_plans_bench_rank%d.txt" % rank)
+        if os.path.exists(tune["cache"]):
+            os.remove(tune["cache"])
+
     def make(store, graph=True, profile=False):
-        return srm.SRM(d["X"], d["W0"], k, store=store, graph=graph, profile=profile, max_iter=max_iter,
-                       stream=stream, single_pass=args.single_pass)
+        m = srm.SRM(d["X"], d["W0"], k, store=store, graph=graph, profile=profile, max_iter=max_iter,
+                    stream=stream, single_pass=args.single_pass)
+        if store == "bf16" and not args.no_autotune and not args.single_pass:
+            t0 = time.perf_counter()
+            plan, ms, _ = m.autotune(tune["cache"], iters=4)
+            if tune["plan"] is None:
+                tune.update(plan=plan, ms=round(ms, 4), tuning_s=round(time.perf_counter() - t0, 2))
+        return m
 
     results = {}
     stores = [args.store] if args.store != "both" else ["bf16", "f32"]
@@ -237,27 +262,29 @@ def run_ours(args, rank, world):
     xb = 2 if head == "bf16" else 4
     ab = 2 if head == "bf16" else 4
     e_bytes, m_bytes = algorithmic_bytes(vox, T, k, xb, ab)
+    f_bytes = single_pass_bytes(vox, T, k, xb, ab)
     ks = results[head]["kernels"]
-    kname_e = "estep_tc" if head == "bf16" else "estep_simt"
-    kname_m = "mstep_tc" if head == "bf16" else "mstep_simt"
+    single = bool(results[head]["layout"]["single_pass"])
     ms_step = results[head]["ms_per_step"]
     value = world * 1000.0 / ms_step
     roofline = None
-    if kname_e in ks and kname_m in ks:
-        # dominant kernel = the larger share of the two streaming passes
-        te = ks[kname_e]["ms"] / args.steps
-        tm = ks[kname_m]["ms"] / args.steps
-        name, t, b = (kname_e, te, e_bytes) if te >= tm else (kname_m, tm, m_bytes)
+    # dominant kernel = the streaming pass with the largest time per step
+    streaming = {"estep_tc": e_bytes, "mstep_tc": m_bytes, "fpass_tc": f_bytes} if head == "bf16" else \
+        {"estep_simt": e_bytes, "mstep_simt": m_bytes}
+    present = [(ks[n]["ms"], n) for n in streaming if n in ks]
+    if present:
+        _, name = max(present)
+        t = ks[name]["ms"] / ks[name]["launches"]
+        b = streaming[name]
         if head == "f32":
             b = b / len(vox)  # per launch (one launch per subject)
-            t = t / len(vox)
         achieved = b / (t * 1e-3) / 1e9
         traffic, tsrc = profiled_traffic(name, args.config) if head == "bf16" else (None, None)
         roofline = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                     "traffic_source": tsrc, "peak_source": peaks["source"] + " (burst copy)",
                     "bytes_per_launch": b, "ms_per_launch": t}
-    iter_bytes = e_bytes + m_bytes
+    iter_bytes = f_bytes if single else e_bytes + m_bytes
     kernels_per_step = sum(v["launches"] for v in ks.values()) / args.steps
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -268,7 +295,11 @@ def run_ours(args, rank, world):
                    "store": head, "l2": "inputs larger than L2 (resident X^ %.2f GB > 129 MB)" %
                    (results[head]["layout"]["xhat_bytes"] / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "graph": True},
+                   "graph": True, "single_pass": single,
+                   "plan": tune["plan"] if head == "bf16" else None,
+                   "autotune": None if head != "bf16" or tune["plan"] is None else
+                   {"tuned_ms_per_iteration": tune["ms"], "tuning_s": tune["tuning_s"],
+                    "note": "srm_autotune before the timed region; later contexts replay the cache"}},
         "hbm_gbs_iteration": round(iter_bytes / (ms_step * 1e-3) / 1e9, 1),
         "roofline": roofline,
         "paper_gflops": round(paper_flops(vox, T, k) / (ms_step * 1e-3) / 1e9, 1),
@@ -285,7 +316,8 @@ def run_ours(args, rank, world):
                                                      r["kernels"].items()}}
     in_bytes = sum(x.numel() * x.element_size() for x in d["X"])
     if not args.no_e2e and in_bytes <= 16e9:
-        out["e2e"] = run_e2e(args, d, spec, vox, stream, world)
+        out["e2e"] = run_e2e(args, d, spec, vox, stream, world,
+                             None if args.no_autotune or args.single_pass else tune["cache"])
     elif not args.no_e2e:
         out["e2e"] = {"value": None, "unit": UNIT, "skipped": "input of %.0f GB too large to pin on the host for "
                       "the end-to-end job" % (in_bytes / 1e9)}
@@ -294,7 +326,7 @@ def run_ours(args, rank, world):
     return out
 
 
-def run_e2e(args, d, spec, vox, stream, world):
+def run_e2e(args, d, spec, vox, stream, world, tune_cache=None):
     """One whole user job through the public API with host buffers: pinned
     host X -> srm_init (host input: H2D copy + centring) -> srm_fit(n_iter)
     -> parameters, E[S] and the log-likelihood back to the host.
@@ -309,8 +341,11 @@ def run_e2e(args, d, spec, vox, stream, world):
     for rep in range(2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        m = srm.SRM(Xh, d["W0"], spec.k, store=args.store if args.store != "both" else "bf16", graph=True,
-                    host_input=True, stream=stream, max_iter=n_iter + 4)
+        store = args.store if args.store != "both" else "bf16"
+        m = srm.SRM(Xh, d["W0"], spec.k, store=store, graph=True, host_input=True, stream=stream,
+                    max_iter=n_iter + 8, single_pass=args.single_pass)
+        if store == "bf16" and tune_cache:
+            m.autotune(tune_cache, iters=4)  # a cached plan: no timing, one file read
         ll = m.fit(n_iter)
         rho2, sig = m.params()
         S = m.get_s().cpu()
@@ -462,7 +497,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--k-sweep", action="store_true", help="throughput against k (extra lines, not the bench line)")
-    ap.add_argument("--single-pass", action="store_true", help="one stream of X^ per EM iteration (SRM_SINGLE_PASS)")
+    ap.add_argument("--single-pass", action="store_true", help="force the single-pass form (SRM_SINGLE_PASS), "
+                    "no autotuning")
+    ap.add_argument("--no-autotune", action="store_true", help="run the library's default launch plan")
+    ap.add_argument("--tune-cache", default=None, help="plan cache file kept across runs (default: a fresh one)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

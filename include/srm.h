@@ -246,6 +246,78 @@ SRM_API srm_status srm_get_kernel_times(srm_ctx* ctx, const char** names, int64_
  */
 SRM_API srm_status srm_layout(srm_ctx* ctx, int64_t* out, int32_t n);
 
+/*
+ * Launch plan of the batched form (SRM_BATCHED).  How the two contractions
+ * of Algorithm 1 (the E-step reduction sum_i W_i^T X^_i and the M-step's
+ * A_i = X^_i E[S]^T with its Gram) are cut into tiles and pipelined.  The
+ * mathematics is the same under every plan.  e_reserve and single_pass
+ * change the order of the FP32 partial sums, so results differ between such
+ * plans by rounding only.  Results under one fixed plan are bitwise
+ * reproducible.
+ */
+typedef struct {
+    int32_t single_pass;    /* 1: one stream of X^ per iteration (the SRM_SINGLE_PASS form;
+                               needs k <= 64 and T <= 1024), 0: two passes */
+    int32_t e_reserve;      /* SMs the E-pass leaves to the M-step tail that runs beside it;
+                               the E-pass runs (SMs - e_reserve) persistent CTAs, which
+                               split the voxel dimension (the split-v depth) */
+    int32_t m_stages;       /* M-pass shared-memory pipeline stages, 2..8 */
+    int32_t m_gram_bufs;    /* M-pass Gram operand buffers, 1 or 2 */
+    int32_t m_resident_es;  /* 1: E[S] stays resident in shared memory during the M-pass */
+    int32_t m_prefetch;     /* M-pass L2 prefetch distance in 64-column X^ chunks (0 = off) */
+    int32_t f_prefetch;     /* single-pass L2 prefetch distance in 128-row tiles (0 = off) */
+    int32_t reserved;       /* must be 0 */
+} srm_plan;
+
+/* srm_get_plan -- the plan the context runs.  SRM_ERR_UNSUPPORTED for the plain
+ * FP32 form, which has no plan. */
+SRM_API srm_status srm_get_plan(srm_ctx* ctx, srm_plan* plan);
+
+/*
+ * srm_set_plan -- run later iterations under `plan`.  Allowed between
+ * iterations only, so SRM_ERR_STATE if an E-step awaits its M-step.  A pending
+ * M-step tail is finished first under the old plan.  SRM_ERR_ARG if the
+ * M-pass plan does not fit in shared memory or a field is out of range.
+ * SRM_ERR_UNSUPPORTED for single_pass = 1 where that form is unsupported.
+ * SRM_ERR_NOMEM if the single-pass buffers, allocated on first use, do not
+ * fit.  Synchronises.
+ */
+SRM_API srm_status srm_set_plan(srm_ctx* ctx, const srm_plan* plan);
+
+/*
+ * srm_autotune -- choose the plan for this context's shapes (v_i, T, k) on
+ * this device by timing, then leave the context as srm_init left it.  The
+ * search has four stages:
+ *   1. every M-pass plan that fits in shared memory, timed launch by launch;
+ *   2. the single-pass prefetch distances, where that form is supported;
+ *   3. E-pass reserves (split-v depths), timed as whole EM iterations;
+ *   4. the two forms, timed as whole EM iterations.
+ * Iterations run through srm_fit's own path, with CUDA events on the
+ * context's stream.  Call it right after srm_init, before any E-step;
+ * otherwise SRM_ERR_STATE.  The W0 given to srm_init and the initial
+ * parameters are restored afterwards, so the fit that follows is the one an
+ * untuned context would run under the chosen plan.
+ *
+ *   cache_path    NULL, or a text file of tuned plans keyed by the device name,
+ *                 SM count, N, T, k and a hash of the v_i.  A matching line is
+ *                 applied without timing anything.  Otherwise the result is
+ *                 added to the file, written through a temporary file and a
+ *                 rename.  Concurrent tuners of one file may drop each
+ *                 other's lines.
+ *   iters         EM iterations timed per whole-iteration candidate (>= 1;
+ *                 2 more run untimed before each).  The log-likelihood trace
+ *                 must hold iters + 3 entries (srm_config.max_iter).
+ *   chosen        receives the chosen plan (may be NULL).
+ *   ms_per_iter   receives its milliseconds per EM iteration (may be NULL).
+ *   report        NULL, or a host buffer for a text table of every timing.
+ *                 It is truncated to report_bytes and NUL-terminated.
+ * Temporarily allocates one copy of the A_i (W0).  SRM_ERR_NOMEM if that
+ * copy does not fit.  SRM_ERR_UNSUPPORTED for the plain FP32 form.
+ * Synchronises.
+ */
+SRM_API srm_status srm_autotune(srm_ctx* ctx, const char* cache_path, int32_t iters, srm_plan* chosen,
+                                double* ms_per_iter, char* report, size_t report_bytes);
+
 /* Thread-local description of the last failure in this thread ("" if none). */
 SRM_API const char* srm_last_error(void);
 

@@ -26,7 +26,8 @@ __all__ = [
     "srm_init", "srm_estep", "srm_mstep", "srm_fit", "srm_transform", "srm_get_w", "srm_get_s",
     "srm_get_params", "srm_get_ll", "srm_synchronize", "srm_get_state", "srm_set_state",
     "srm_get_kernel_times", "srm_layout", "srm_last_error", "srm_destroy", "srm_debug_mma",
-    "srm_transform_noalloc", "srm_debug_eig_sweeps", "srm_map",
+    "srm_transform_noalloc", "srm_debug_eig_sweeps", "srm_map", "srm_plan", "srm_get_plan", "srm_set_plan",
+    "srm_autotune",
 ]
 
 SRM_OK, SRM_ERR_ARG, SRM_ERR_CUDA, SRM_ERR_NOMEM, SRM_ERR_NUMERIC, SRM_ERR_STATE, SRM_ERR_UNSUPPORTED = range(7)
@@ -58,6 +59,23 @@ class srm_config(ctypes.Structure):
         ("flags", ctypes.c_uint32),
         ("max_iter", ctypes.c_int32),
     ]
+
+
+class srm_plan(ctypes.Structure):
+    """Launch plan of the batched form (field meanings in include/srm.h)."""
+    _fields_ = [
+        ("single_pass", ctypes.c_int32),
+        ("e_reserve", ctypes.c_int32),
+        ("m_stages", ctypes.c_int32),
+        ("m_gram_bufs", ctypes.c_int32),
+        ("m_resident_es", ctypes.c_int32),
+        ("m_prefetch", ctypes.c_int32),
+        ("f_prefetch", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "reserved"}
 
 
 _lib = None
@@ -97,6 +115,10 @@ def load_library(path: Optional[str] = None):
         "srm_transform_noalloc": (st, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
         "srm_map": (st, [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, _P]),
         "srm_debug_eig_sweeps": (st, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
+        "srm_get_plan": (st, [_P, ctypes.POINTER(srm_plan)]),
+        "srm_set_plan": (st, [_P, ctypes.POINTER(srm_plan)]),
+        "srm_autotune": (st, [_P, ctypes.c_char_p, ctypes.c_int32, ctypes.POINTER(srm_plan),
+                              ctypes.POINTER(ctypes.c_double), ctypes.c_char_p, ctypes.c_size_t]),
         "srm_destroy": (None, [_P]),
     }
     for name, (res, args) in sig.items():
@@ -236,6 +258,26 @@ def srm_debug_eig_sweeps(ctx: int, n: int) -> np.ndarray:
     return out
 
 
+def srm_get_plan(ctx: int) -> srm_plan:
+    p = srm_plan()
+    _check(load_library().srm_get_plan(_P(ctx), ctypes.byref(p)), "srm_get_plan")
+    return p
+
+
+def srm_set_plan(ctx: int, plan: srm_plan):
+    _check(load_library().srm_set_plan(_P(ctx), ctypes.byref(plan)), "srm_set_plan")
+
+
+def srm_autotune(ctx: int, cache_path: Optional[str] = None, iters: int = 8):
+    """Returns (chosen srm_plan, ms per EM iteration, text report of every timing)."""
+    p = srm_plan()
+    ms = ctypes.c_double(0)
+    rep = ctypes.create_string_buffer(1 << 16)
+    _check(load_library().srm_autotune(_P(ctx), cache_path.encode() if cache_path else None, int(iters),
+                                       ctypes.byref(p), ctypes.byref(ms), rep, len(rep)), "srm_autotune")
+    return p, float(ms.value), rep.value.decode()
+
+
 def srm_destroy(ctx: int):
     load_library().srm_destroy(_P(ctx))
 
@@ -353,6 +395,21 @@ class SRM:
 
     def layout(self) -> dict:
         return srm_layout(self.ctx)
+
+    def plan(self) -> dict:
+        return srm_get_plan(self.ctx).as_dict()
+
+    def set_plan(self, **fields):
+        p = srm_get_plan(self.ctx)
+        for n, v in fields.items():
+            setattr(p, n, int(v))
+        srm_set_plan(self.ctx, p)
+
+    def autotune(self, cache_path: Optional[str] = None, iters: int = 8):
+        """Time candidate launch plans and keep the fastest (srm_autotune);
+        returns (plan dict, ms per EM iteration, report text)."""
+        p, ms, rep = srm_autotune(self.ctx, cache_path, iters)
+        return p.as_dict(), ms, rep
 
     def close(self):
         if getattr(self, "ctx", None):

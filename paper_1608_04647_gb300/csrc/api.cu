@@ -358,6 +358,52 @@ struct StateHeader {
 constexpr uint64_t kStateMagic = 0x314d5253'50534743ull;
 
 }  // namespace
+
+srm_status device_status(Ctx* c) { return check_status(c); }
+
+void drop_graph(Ctx* c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  c->graph_exec = nullptr;
+}
+
+// n_iter EM iterations (E-step then M-step each); the M-step tail of the last
+// one stays pending.  With SRM_GRAPH the steady-state iteration is replayed
+// as one CUDA graph.
+srm_status run_iterations(Ctx* c, int n_iter) {
+  const bool use_graph = (c->flags & SRM_GRAPH) && !c->profile;
+  for (int it = 0; it < n_iter; ++it) {
+    if (use_graph && c->side_pending) {
+      if (!c->graph_exec) {
+        // one steady-state iteration: [pending M-step tail || E-pass] -> E-step
+        // k x k work -> M-pass (whose tail stays pending)
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        srm_status s1 = do_estep(c);
+        srm_status s2 = s1 == SRM_OK ? do_mstep(c) : s1;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        c->side_pending = true;
+        if (s2 != SRM_OK) {
+          if (g) cudaGraphDestroy(g);
+          return s2;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+          c->graph_exec = nullptr;
+          return cuda_fail(e, "cudaGraphInstantiate");
+        }
+      }
+      CK(cudaGraphLaunch(c->graph_exec, c->stream));
+    } else {
+      TRY(do_estep(c));
+      TRY(do_mstep(c));
+    }
+    c->n_ll++;
+    c->iters_done++;
+  }
+  return SRM_OK;
+}
 }  // namespace srm
 
 using namespace srm;
@@ -518,7 +564,7 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
     if ((st = tc_setup(c)) != SRM_OK) return fail(st);
     if ((cfg->flags & SRM_SINGLE_PASS) && fused_supported(c)) {
       if ((st = fused_setup(c)) != SRM_OK) return fail(st);
-      c->fused = true;
+      fused_select(c, true);
     }
   } else {
     if ((st = setup_plain(c)) != SRM_OK) return fail(st);
@@ -605,38 +651,7 @@ srm_status srm_fit(srm_ctx* c, int32_t n_iter, double* ll_host) {
     return SRM_ERR_STATE;
   }
   const int ll0 = c->n_ll;
-  const bool use_graph = (c->flags & SRM_GRAPH) && !c->profile;
-  for (int it = 0; it < n_iter; ++it) {
-    if (use_graph && c->side_pending) {
-      if (!c->graph_exec) {
-        // one steady-state iteration: [pending M-step tail || E-pass] -> E-step
-        // k x k work -> M-pass (whose tail stays pending)
-        cudaGraph_t g = nullptr;
-        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        srm_status s1 = do_estep(c);
-        srm_status s2 = s1 == SRM_OK ? do_mstep(c) : s1;
-        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-        c->side_pending = true;
-        if (s2 != SRM_OK) {
-          if (g) cudaGraphDestroy(g);
-          return s2;
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-        e = cudaGraphInstantiate(&c->graph_exec, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
-          c->graph_exec = nullptr;
-          return cuda_fail(e, "cudaGraphInstantiate");
-        }
-      }
-      CK(cudaGraphLaunch(c->graph_exec, c->stream));
-    } else {
-      TRY(do_estep(c));
-      TRY(do_mstep(c));
-    }
-    c->n_ll++;
-    c->iters_done++;
-  }
+  TRY(run_iterations(c, n_iter));
   TRY(flush_pending(c));
   c->have_estep = false;
   if (n_iter > 0) c->have_es = true;

@@ -565,9 +565,16 @@ struct FState {
   SegF* d_seg = nullptr;
   int* d_seg_off = nullptr;
   int C = 1, clusters = 0;
-  // the two-pass M-pass's Gram buffers, replaced in the context by this pass's
+  int pf = F_PF;  // L2 prefetch distance (tiles)
+  // Gram slots of the two forms; the context points at the active form's
+  float* f_gpart = nullptr;
+  int* f_gslot_off = nullptr;
+  int f_ngslots = 0;
+  int64_t f_gel = 0;
   float* m_gpart = nullptr;
   int* m_gslot_off = nullptr;
+  int m_ngslots = 0;
+  int64_t m_gel = 0;
 };
 
 template <typename T>
@@ -691,22 +698,44 @@ srm_status fused_setup(Ctx* c) {
     set_error("cudaMalloc failed for single-pass partial slots");
     return SRM_ERR_NOMEM;
   }
-  // the polar-factor and eigen kernels read the Gram slots through the context
+  // the polar-factor and eigen kernels read the Gram slots through the
+  // context: fused_select points it at one form's
   f->m_gpart = c->Gpart;
   f->m_gslot_off = c->gslot_off;
-  c->Gpart = gp;
-  c->gslot_off = g_off;
-  c->n_gslots = (int)seg.size() * C;
-  c->Gpart_elems = gel;
+  f->m_ngslots = c->n_gslots;
+  f->m_gel = c->Gpart_elems;
+  f->f_gpart = gp;
+  f->f_gslot_off = g_off;
+  f->f_ngslots = (int)seg.size() * C;
+  f->f_gel = gel;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "single-pass setup");
   return SRM_OK;
 }
 
+void fused_select(Ctx* c, bool on) {
+  auto* f = static_cast<FState*>(c->fs);
+  if (!f) return;
+  c->Gpart = on ? f->f_gpart : f->m_gpart;
+  c->gslot_off = on ? f->f_gslot_off : f->m_gslot_off;
+  c->n_gslots = on ? f->f_ngslots : f->m_ngslots;
+  c->Gpart_elems = on ? f->f_gel : f->m_gel;
+  c->fused = on;
+}
+
+int fused_get_pf(const Ctx* c) { return c->fs ? static_cast<const FState*>(c->fs)->pf : 0; }
+
+void fused_set_pf(Ctx* c, int pf) {
+  if (c->fs) static_cast<FState*>(c->fs)->pf = pf;
+}
+
 void fused_destroy(Ctx* c) {
   auto* f = static_cast<FState*>(c->fs);
   if (!f) return;
-  void* p[] = {f->d_seg, f->d_seg_off, f->m_gpart, f->m_gslot_off};
+  // the context frees the active form's Gram slots; this frees the other's
+  const bool on = c->Gpart == f->f_gpart;
+  void* p[] = {f->d_seg, f->d_seg_off, on ? (void*)f->m_gpart : (void*)f->f_gpart,
+               on ? (void*)f->m_gslot_off : (void*)f->f_gslot_off};
   for (void* q : p)
     if (q) cudaFree(q);
   delete f;
@@ -718,7 +747,7 @@ cudaError_t launch_fpass(Ctx* c) {
   if (!f) return cudaErrorInvalidValue;
   if (f->C == 1) {
     fpass_kernel<1><<<f->clusters, FT, f_smem_bytes<1>(), c->stream>>>(
-        f->mapX, f->mapE, f->mapAs, f->mapXp, f->d_seg, f->d_seg_off, c->T, F_PF, c->f_ppart, c->Gpart, c->status);
+        f->mapX, f->mapE, f->mapAs, f->mapXp, f->d_seg, f->d_seg_off, c->T, f->pf, c->f_ppart, c->Gpart, c->status);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
@@ -734,7 +763,7 @@ cudaError_t launch_fpass(Ctx* c) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, fpass_kernel<2>, f->mapX, f->mapE, f->mapAs, f->mapXp, (const SegF*)f->d_seg,
-                            (const int*)f->d_seg_off, c->T, F_PF, c->f_ppart, c->Gpart, c->status);
+                            (const int*)f->d_seg_off, c->T, f->pf, c->f_ppart, c->Gpart, c->status);
 }
 
 }  // namespace srm

@@ -22,6 +22,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <array>
 #include <vector>
 
 #include "srm_internal.cuh"
@@ -60,6 +61,7 @@ struct TcState {
   bool m_res = false;   // M-pass keeps E[S] resident in shared memory
   int m_stages = 4;     // M-pass pipeline depth
   int m_gop = 2;        // M-pass Gram operand buffers
+  int m_pf = 0;         // M-pass L2 prefetch distance (X^ chunks; 0 = off)
   size_t m_smem = 0;
 };
 
@@ -723,40 +725,23 @@ srm_status upload(T** d, const std::vector<T>& h, const char* what) {
   return SRM_OK;
 }
 
-}  // namespace
-
-srm_status tc_setup(Ctx* c) {
-  if (c->kld != 64 && c->kld != 128) {
-    set_error("tensor-core form: padded k must be 64 or 128");
-    return SRM_ERR_UNSUPPORTED;
-  }
-  auto* s = new TcState();
-  c->tc = s;
-  const int G = c->num_sms;
-  s->grid = G;
-  // The E-pass leaves a few SMs to the M-step tail that runs beside it (the
-  // polar factors take one CTA per subject): the tail's blocks then run on
-  // otherwise idle SMs instead of slowing the E-pass CTAs they would share an
-  // SM with, whose fixed share of the work sets the pass's end.  132 of 152
-  // SMs still saturate HBM (greeneyes-like workload: E-pass 0.255 -> 0.217 ms,
-  // iteration 0.588 -> 0.548 ms).
+// E-pass schedule for GE persistent CTAs: the (T-block, subject, 32-row
+// chunk) steps split evenly, each CTA's share cut at subject and T-block
+// boundaries into work items with one partial slot each, and the table that
+// lists, for every (subject, 64-column chunk), its slots in a fixed order.
+// GE is the split-v depth: how many CTAs share the voxel range of the pass.
+srm_status build_e_schedule(Ctx* c, int GE) {
+  auto* s = static_cast<TcState*>(c->tc);
   const int N = c->N;
-  const int reserve = std::min(E_RESERVE_MAX, N + 4);
-  const int GE = std::max(1, c->num_sms - reserve);
+  void* old[] = {s->d_work, s->d_work_off, c->Ppart, c->chunk_src, c->chunk_src_off};
+  for (void* q : old)
+    if (q) cudaFree(q);
+  s->d_work = nullptr;
+  s->d_work_off = nullptr;
+  c->Ppart = nullptr;
+  c->chunk_src = nullptr;
+  c->chunk_src_off = nullptr;
   s->egrid = GE;
-  // tensor maps
-  bool ok = make_map(&s->mapXe, c->Xh, c->T, c->Vpad_tot, (uint64_t)c->ldT * 2, 64, E_KR) &&
-            make_map(&s->mapA, c->A, c->kld, c->Vpad_tot, (uint64_t)c->kld * 2, 64, E_KR) &&
-            make_map(&s->mapXm, c->Xh, c->T, c->Vpad_tot, (uint64_t)c->ldT * 2, 64, 128) &&
-            make_map(&s->mapE, c->ESb, c->T, c->kld, (uint64_t)c->ldT * 2, 64, c->kld) &&
-            make_map(&s->mapAs, c->A, c->kld, c->Vpad_tot, (uint64_t)c->kld * 2, 64, 128) &&
-            // L2 prefetch only (never lands in shared memory): 4 chunks x 128 rows per box
-            make_map(&s->mapXp, c->Xh, c->T, c->Vpad_tot, (uint64_t)c->ldT * 2, 256, 128, false);
-  if (!ok) {
-    set_error("cuTensorMapEncodeTiled failed (driver entry point missing or bad layout)");
-    return SRM_ERR_CUDA;
-  }
-  // ---- E-pass schedule: (T-block, subject, 32-row chunk) steps split evenly
   const int nTB = (c->T + E_TB - 1) / E_TB;
   int64_t U = 0;
   for (int i = 0; i < N; ++i) U += c->vpad[i] / E_KR;
@@ -786,7 +771,6 @@ srm_status tc_setup(Ctx* c) {
       }
     for (int q = cta + 1; q <= GE; ++q) work_off[q] = (int)work.size();
   }
-  // E-pass partial slots and the (subject, chunk) source table
   c->Ppart_elems = (int64_t)work.size() * E_TB * c->kld;
   std::vector<std::vector<int64_t>> lists((size_t)N * c->nchunk);
   for (const WorkE& w : work)
@@ -802,6 +786,108 @@ srm_status tc_setup(Ctx* c) {
     for (int64_t o : lists[j]) src.push_back({o});
   }
   src_off[lists.size()] = (int)src.size();
+  srm_status st;
+  if ((st = upload(&s->d_work, work, "E-pass schedule")) != SRM_OK) return st;
+  if ((st = upload(&s->d_work_off, work_off, "E-pass schedule offsets")) != SRM_OK) return st;
+  if ((st = upload(&c->chunk_src, src, "chunk table")) != SRM_OK) return st;
+  if ((st = upload(&c->chunk_src_off, src_off, "chunk table offsets")) != SRM_OK) return st;
+  if (cudaMalloc(&c->Ppart, sizeof(float) * std::max<int64_t>(1, c->Ppart_elems)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMalloc failed for E-pass partial slots");
+    return SRM_ERR_NOMEM;
+  }
+  return SRM_OK;
+}
+
+// Shared memory of an M-pass plan: nb Gram operand buffers, E[S] resident or
+// streamed, stages X^ stages.  0 if it does not fit.
+size_t m_plan_smem(const Ctx* c, int nb, bool res, int stages) {
+  if ((nb != 1 && nb != 2) || stages < 2 || stages > M_MAX_STAGES) return 0;
+  const size_t eres = (size_t)((c->T + 63) / 64) * c->kld * 128;
+  const size_t sm = m_fixed_bytes(c->kld, nb) +
+                    (res ? eres + (size_t)stages * 16384 : (size_t)stages * m_stage_bytes(c->kld));
+  return sm <= kMaxSmem ? sm : 0;
+}
+
+}  // namespace
+
+// The default E-pass reserve.  The E-pass leaves a few SMs to the M-step tail
+// that runs beside it (the polar factors take one CTA per subject): the
+// tail's blocks then run on otherwise idle SMs instead of slowing the E-pass
+// CTAs they would share an SM with, whose fixed share of the work sets the
+// pass's end.  132 of 152 SMs still saturate HBM (greeneyes-like workload:
+// E-pass 0.255 -> 0.217 ms, iteration 0.588 -> 0.548 ms).
+int tc_default_e_reserve(const Ctx* c) { return std::min(E_RESERVE_MAX, c->N + 4); }
+
+int tc_e_reserve(const Ctx* c) { return c->num_sms - static_cast<const TcState*>(c->tc)->egrid; }
+
+srm_status tc_set_e_reserve(Ctx* c, int reserve) {
+  if (reserve < 0 || reserve >= c->num_sms) {
+    set_error("plan: the E-pass reserve must leave at least one SM to the pass");
+    return SRM_ERR_ARG;
+  }
+  const int GE = c->num_sms - reserve;
+  if (static_cast<TcState*>(c->tc)->egrid == GE && c->Ppart) return SRM_OK;
+  return build_e_schedule(c, GE);
+}
+
+void tc_get_m_plan(const Ctx* c, int* nb, int* res, int* stages, int* pf) {
+  const auto* s = static_cast<const TcState*>(c->tc);
+  *nb = s->m_gop;
+  *res = s->m_res ? 1 : 0;
+  *stages = s->m_stages;
+  *pf = s->m_pf;
+}
+
+srm_status tc_set_m_plan(Ctx* c, int nb, int res, int stages, int pf) {
+  const size_t sm = m_plan_smem(c, nb, res != 0, stages);
+  if (!sm || pf < 0 || pf > 64) {
+    set_error("plan: the M-pass plan does not fit in shared memory (Gram buffers 1-2, stages 2-8, prefetch 0-64)");
+    return SRM_ERR_ARG;
+  }
+  auto* s = static_cast<TcState*>(c->tc);
+  s->m_gop = nb;
+  s->m_res = res != 0;
+  s->m_stages = stages;
+  s->m_pf = pf;
+  s->m_smem = sm;
+  return SRM_OK;
+}
+
+void tc_m_candidates(const Ctx* c, std::vector<std::array<int, 4>>& out) {
+  out.clear();
+  for (int nb = 1; nb <= 2; ++nb)
+    for (int res = 0; res <= 1; ++res)
+      for (int st = 2; st <= M_MAX_STAGES; ++st) {
+        if (!m_plan_smem(c, nb, res != 0, st)) continue;
+        out.push_back({nb, res, st, 0});
+        out.push_back({nb, res, st, M_PF});
+      }
+}
+
+srm_status tc_setup(Ctx* c) {
+  if (c->kld != 64 && c->kld != 128) {
+    set_error("tensor-core form: padded k must be 64 or 128");
+    return SRM_ERR_UNSUPPORTED;
+  }
+  auto* s = new TcState();
+  c->tc = s;
+  const int G = c->num_sms;
+  s->grid = G;
+  const int N = c->N;
+  const int GE = std::max(1, c->num_sms - tc_default_e_reserve(c));
+  // tensor maps
+  bool ok = make_map(&s->mapXe, c->Xh, c->T, c->Vpad_tot, (uint64_t)c->ldT * 2, 64, E_KR) &&
+            make_map(&s->mapA, c->A, c->kld, c->Vpad_tot, (uint64_t)c->kld * 2, 64, E_KR) &&
+            make_map(&s->mapXm, c->Xh, c->T, c->Vpad_tot, (uint64_t)c->ldT * 2, 64, 128) &&
+            make_map(&s->mapE, c->ESb, c->T, c->kld, (uint64_t)c->ldT * 2, 64, c->kld) &&
+            make_map(&s->mapAs, c->A, c->kld, c->Vpad_tot, (uint64_t)c->kld * 2, 64, 128) &&
+            // L2 prefetch only (never lands in shared memory): 4 chunks x 128 rows per box
+            make_map(&s->mapXp, c->Xh, c->T, c->Vpad_tot, (uint64_t)c->ldT * 2, 256, 128, false);
+  if (!ok) {
+    set_error("cuTensorMapEncodeTiled failed (driver entry point missing or bad layout)");
+    return SRM_ERR_CUDA;
+  }
   // ---- M-pass schedule: 128-row tiles split evenly, segments at subject boundaries
   const int64_t NTl = c->Vpad_tot / 128;
   std::vector<SegM> seg;
@@ -834,15 +920,11 @@ srm_status tc_setup(Ctx* c) {
   c->Gpart_elems = (int64_t)seg.size() * c->kld * c->kld;
 
   srm_status st;
-  if ((st = upload(&s->d_work, work, "E-pass schedule")) != SRM_OK) return st;
-  if ((st = upload(&s->d_work_off, work_off, "E-pass schedule offsets")) != SRM_OK) return st;
+  if ((st = build_e_schedule(c, GE)) != SRM_OK) return st;
   if ((st = upload(&s->d_seg, seg, "M-pass schedule")) != SRM_OK) return st;
   if ((st = upload(&s->d_seg_off, seg_off, "M-pass schedule offsets")) != SRM_OK) return st;
-  if ((st = upload(&c->chunk_src, src, "chunk table")) != SRM_OK) return st;
-  if ((st = upload(&c->chunk_src_off, src_off, "chunk table offsets")) != SRM_OK) return st;
   if ((st = upload(&c->gslot_off, gslot_off, "Gram slot table")) != SRM_OK) return st;
-  if (cudaMalloc(&c->Ppart, sizeof(float) * c->Ppart_elems) != cudaSuccess ||
-      cudaMalloc(&c->Gpart, sizeof(float) * std::max<int64_t>(1, c->Gpart_elems)) != cudaSuccess) {
+  if (cudaMalloc(&c->Gpart, sizeof(float) * std::max<int64_t>(1, c->Gpart_elems)) != cudaSuccess) {
     cudaGetLastError();
     set_error("cudaMalloc failed for tensor-core partial slots");
     return SRM_ERR_NOMEM;
@@ -873,8 +955,8 @@ srm_status tc_setup(Ctx* c) {
     s->m_gop = one ? 1 : 2;
     s->m_res = one ? res1 : res2;
     s->m_stages = (int)(one ? st1 : st2);
-    const size_t fixed = m_fixed_bytes(c->kld, s->m_gop);
-    s->m_smem = fixed + (s->m_res ? eres + (size_t)s->m_stages * 16384 : (size_t)s->m_stages * m_stage_bytes(c->kld));
+    s->m_pf = s->m_stages < M_PF_STAGES ? M_PF : 0;
+    s->m_smem = m_plan_smem(c, s->m_gop, s->m_res, s->m_stages);
   }
   // The E-pass leaves room on each SM for the M-step tail that runs beside it
   // on the second stream; ask for the largest shared-memory carve-out so that
@@ -928,7 +1010,7 @@ cudaError_t launch_a_tc(Ctx* c) {
 #define M_LAUNCH(KLD, RES, GNB)                                                                                  \
   mstep_tc_kernel<KLD, RES, GNB><<<s->grid, NT, s->m_smem, c->stream>>>(                                          \
       s->mapXm, s->mapE, s->mapAs, s->mapXp, s->d_seg, s->d_seg_off, c->T, s->m_stages,                            \
-      s->m_stages < M_PF_STAGES ? M_PF : 0,                                                                        \
+      s->m_pf,                                                                                                     \
       static_cast<const uint8_t*>(c->Xh), (int64_t)c->ldT * 2, A, c->Gpart, c->status)
 #define M_LAUNCH2(KLD, RES) \
   if (s->m_gop == 1) {      \

@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <array>
 #include <string>
 #include <vector>
 
@@ -172,6 +173,12 @@ struct Ctx {
 
 // runs a deferred M-step tail (api.cu)
 srm_status flush_pending(Ctx* c);
+// n_iter EM iterations through the graph path when enabled (api.cu)
+srm_status run_iterations(Ctx* c, int n_iter);
+// synchronises the stream and returns (and clears) the device status (api.cu)
+srm_status device_status(Ctx* c);
+// destroys the instantiated iteration graph, if any (api.cu)
+void drop_graph(Ctx* c);
 
 // error helpers (api.cu)
 void set_error(const std::string& msg);
@@ -224,6 +231,13 @@ void prepare_simt_kernels(int max_smem);
 // k_tc.cu (grouped persistent tensor-core form)
 srm_status tc_setup(Ctx* c);
 void tc_destroy(Ctx* c);
+int tc_default_e_reserve(const Ctx* c);
+int tc_e_reserve(const Ctx* c);
+srm_status tc_set_e_reserve(Ctx* c, int reserve);  // rebuilds the E-pass schedule
+void tc_get_m_plan(const Ctx* c, int* gram_bufs, int* resident_es, int* stages, int* prefetch);
+srm_status tc_set_m_plan(Ctx* c, int gram_bufs, int resident_es, int stages, int prefetch);
+// every M-pass plan that fits in shared memory: {gram_bufs, resident_es, stages, prefetch}
+void tc_m_candidates(const Ctx* c, std::vector<std::array<int, 4>>& out);
 cudaError_t launch_p_tc(Ctx* c);
 cudaError_t launch_a_tc(Ctx* c);
 
@@ -231,6 +245,9 @@ cudaError_t launch_a_tc(Ctx* c);
 bool fused_supported(const Ctx* c);
 srm_status fused_setup(Ctx* c);
 void fused_destroy(Ctx* c);
+void fused_select(Ctx* c, bool on);  // points the context at the single-pass (on) or two-pass Gram slots
+int fused_get_pf(const Ctx* c);
+void fused_set_pf(Ctx* c, int pf);
 cudaError_t launch_fpass(Ctx* c);
 
 }  // namespace srm
