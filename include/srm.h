@@ -266,7 +266,14 @@ typedef struct {
     int32_t m_resident_es;  /* 1: E[S] stays resident in shared memory during the M-pass */
     int32_t m_prefetch;     /* M-pass L2 prefetch distance in 64-column X^ chunks (0 = off) */
     int32_t f_prefetch;     /* single-pass L2 prefetch distance in 128-row tiles (0 = off) */
-    int32_t reserved;       /* must be 0 */
+    int32_t f_l2_hints;     /* single-pass L2 eviction hints, bits: 1 = a tile's first read
+                               evicts last, 2 = its second read (last use) evicts first,
+                               4 = A_i stores evict first */
+    int32_t f_first_stages; /* single pass: 32 KB stages (of 4) of the ring that streams each
+                               tile from HBM for A_i; the rest re-read it for A_i^T X^_i, 1..3;
+                               4 = one shared ring serving both reads in turn */
+    int32_t f_reserve;      /* SMs the single pass leaves to the Sigma_s chain that runs
+                               beside it (the pass runs on the rest, in whole clusters) */
 } srm_plan;
 
 /* srm_get_plan -- the plan the context runs.  SRM_ERR_UNSUPPORTED for the plain

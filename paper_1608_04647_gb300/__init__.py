@@ -71,11 +71,13 @@ class srm_plan(ctypes.Structure):
         ("m_resident_es", ctypes.c_int32),
         ("m_prefetch", ctypes.c_int32),
         ("f_prefetch", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("f_l2_hints", ctypes.c_int32),
+        ("f_first_stages", ctypes.c_int32),
+        ("f_reserve", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
-        return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "reserved"}
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
 
 
 _lib = None

@@ -27,8 +27,13 @@
 // (cluster, subject segment, CTA) and are summed in a fixed order by the
 // E-step reduction and the polar-factor kernel: results are reproducible.
 //
-// Warp roles (192 threads): warp 0 TMA loads, warp 1 TMEM owner and MMA
-// issue, warps 2-5 epilogue.  Every wait is bounded; a CTA that gives up
+// Warp roles (256 threads): warp 0 TMA loads of the first-read ring, warp 6
+// those of the second-read ring, warp 1 TMEM owner and phase-1 MMA issue,
+// warp 7 phase-2 MMA issue, warps 2-5 epilogue.  The two rings split the four
+// 32 KB stages (s_h and 4 - s_h), so the HBM stream of phase 1 never waits
+// behind the L2 re-reads and MMAs of phase 2.  With s_h = 4 the original
+// schedule runs instead: one ring, warp 0 loading and warp 1 issuing the
+// phases of consecutive tiles in turn (warps 6 and 7 idle).  Every wait is bounded; a CTA that gives up
 // raises the status word and stops issuing work.
 #include <cudaTypedefs.h>
 
@@ -44,7 +49,7 @@ using namespace tc;
 
 namespace {
 
-constexpr int FT = 192;               // threads per CTA
+constexpr int FT = 256;               // threads per CTA
 constexpr int F_TB = 512;             // t per CTA (one T-block)
 constexpr uint32_t F_BOX = 16384;     // 64 t x 128 voxel rows (BF16)
 constexpr uint32_t F_STAGE = 32768;   // two boxes: 128 t x 128 rows
@@ -53,6 +58,14 @@ constexpr uint32_t F_GOP = 16384;     // A_tile, 128 voxel rows x 64 features (B
 constexpr uint32_t F_EXCH = 16384;    // 64 rows x 64 FP32 partials
 constexpr int F_RESERVE = 10;         // SMs left to the Sigma_s chain that runs beside the pass
 constexpr int F_PF = 0;               // L2 prefetch distance (tiles)
+// L2 eviction hints (bits of the kernel's `hints`): phase-1 loads evict last,
+// phase-2 loads (the tile's last use) evict first, A_i stores evict first
+constexpr int F_HINT_KEEP = 1, F_HINT_DROP = 2, F_HINT_STORE = 4;
+constexpr int F_HINTS = 0;
+// Default ring split: with clusters (T > 512) one A_tile buffer fits, the
+// epilogue of tile n then waits for phase 2 of tile n - 1, and the shared ring
+// (4) is faster; one CTA per tile runs two rings of 2 stages each.
+constexpr int F_SH = 2;
 
 struct SegF {
   int64_t tile_begin, tile_end;  // 128-row tiles (global)
@@ -106,7 +119,7 @@ template <int C>
 __global__ void __launch_bounds__(FT, 1)
     fpass_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE,
                  const __grid_constant__ CUtensorMap mapAs, const __grid_constant__ CUtensorMap mapXp,
-                 const SegF* __restrict__ segs, const int* __restrict__ seg_off, int T, int pf_dist,
+                 const SegF* __restrict__ segs, const int* __restrict__ seg_off, int T, int s_h, int pf_dist, int hints,
                  float* __restrict__ ppart, float* __restrict__ gpart, int* status) {
   constexpr int S_N = f_stages<C>();
   constexpr int NG = f_gops<C>();
@@ -137,8 +150,8 @@ __global__ void __launch_bounds__(FT, 1)
   uint64_t* exch_full = gram_empty + 1;  // the other CTA's partial rows have arrived
   uint64_t* exch_free = exch_full + 1;   // the other CTA has read the rows this CTA sent
   uint64_t* e_full = exch_free + 1;
-  uint64_t* done = e_full + 1;
-  uint64_t* epi_bar = done + 1;
+  uint64_t* done = e_full + 1;          // [2] every MMA of the phase-1 / phase-2 issuer has completed
+  uint64_t* epi_bar = done + 2;
   uint64_t* own_bar = epi_bar + 1;
   uint32_t* tmem_s = reinterpret_cast<uint32_t*>(own_bar + 1);
   volatile int* abort_s = reinterpret_cast<volatile int*>(tmem_s + 1);
@@ -150,6 +163,8 @@ __global__ void __launch_bounds__(FT, 1)
   const int g0 = seg_off[pair], g1 = seg_off[pair + 1];
   const int t0 = F_TB * (int)rank;
   const int nk2 = min(4, (min(T, t0 + F_TB) - t0 + 127) / 128);  // 128-t stages per tile and phase
+  // s_h = S_N: the shared-ring schedule (warps 6 and 7 idle); otherwise two rings
+  const bool shared = s_h >= S_N;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S_N; ++s) {
@@ -169,7 +184,8 @@ __global__ void __launch_bounds__(FT, 1)
     mbar_init(exch_full, 1);
     mbar_init(exch_free, 1);
     mbar_init(e_full, 1);
-    mbar_init(done, 1);
+    mbar_init(&done[0], 1);
+    mbar_init(&done[1], 1);
     mbar_init(epi_bar, 4);
     mbar_init(own_bar, 2);
     *abort_s = 0;
@@ -191,12 +207,14 @@ __global__ void __launch_bounds__(FT, 1)
   if (C == 2) cluster_sync_all();  // the other CTA's barriers exist before anything arrives on them
   const uint32_t tmem = *tmem_s;
 
-  if (warp == 0) {
+  if (shared && warp == 0) {
+    // shared-ring schedule: one producer interleaves the first read of tile n
+    // and the second read of tile n - 1 in one ring of all S_N stages
     if (lane == 0) {
       int s = 0;
       uint32_t ph = 0;
-      int issued[4] = {0, 0, 0, 0};
-      uint32_t iss_ph[4] = {0, 0, 0, 0};
+      int issued[S_N] = {};
+      uint32_t iss_ph[S_N] = {};
       bool ok = true;
       if (g0 < g1) {
         mbar_arrive_expect_tx(e_full, (uint32_t)(2 * nk2) * F_ECH);
@@ -204,13 +222,16 @@ __global__ void __launch_bounds__(FT, 1)
       }
       // the tile's nk2 stages (the same loads serve phase 1 and, one tile
       // later, phase 2)
-      auto load_tile = [&](int64_t tile) -> bool {
+      const uint64_t pol_first = (hints & F_HINT_KEEP) ? l2_evict_last() : l2_evict_normal();
+      const uint64_t pol_again = (hints & F_HINT_DROP) ? l2_evict_first() : l2_evict_normal();
+      auto load_tile = [&](int64_t tile, bool again) -> bool {
+        const uint64_t pol = again ? pol_again : pol_first;
         for (int j = 0; j < nk2; ++j) {
           if (!mbar_wait(&empty[s], ph ^ 1u, abort_s, status, ST_TIMEOUT)) return false;
           uint8_t* st = smem + s * F_STAGE;
           mbar_arrive_expect_tx(&full[s], F_STAGE);
-          tma_load_2d(st, &mapX, t0 + 128 * j, (int)(tile * 128), &full[s]);
-          tma_load_2d(st + F_BOX, &mapX, t0 + 128 * j + 64, (int)(tile * 128), &full[s]);
+          tma_load_2d_hint(st, &mapX, t0 + 128 * j, (int)(tile * 128), &full[s], pol);
+          tma_load_2d_hint(st + F_BOX, &mapX, t0 + 128 * j + 64, (int)(tile * 128), &full[s], pol);
           issued[s] = 1;
           iss_ph[s] = ph;
           if (++s == S_N) {
@@ -235,10 +256,10 @@ __global__ void __launch_bounds__(FT, 1)
       for (int g = g0; g < g1 && ok; ++g)
         for (int64_t tile = segs[g].tile_begin; tile < segs[g].tile_end && ok; ++tile) {
           if (pf_dist > 0) pf_issue();
-          ok = load_tile(tile) && (prev < 0 || load_tile(prev));
+          ok = load_tile(tile, false) && (prev < 0 || load_tile(prev, true));
           prev = tile;
         }
-      if (ok && prev >= 0) ok = load_tile(prev);
+      if (ok && prev >= 0) ok = load_tile(prev, true);
       if (!ok) {
         for (int q = 0; q < S_N; ++q)
           if (issued[q])
@@ -247,7 +268,9 @@ __global__ void __launch_bounds__(FT, 1)
           for (uint32_t it = 0; it < (1u << 22) && !mbar_try_wait(e_full, 0); ++it) __nanosleep(128);
       }
     }
-  } else if (warp == 1) {
+  } else if (shared && warp == 1) {
+    // shared-ring schedule: one issuer interleaves phase 1 of tile n and
+    // phase 2 of tile n - 1
     if (lane == 0) {
       int s = 0;
       uint32_t ph = 0;
@@ -342,8 +365,194 @@ __global__ void __launch_bounds__(FT, 1)
       }
       if (ok && pv) ok = p2(n - 1, pfirst, plast);
       // everything issued must have completed before TMEM is freed
-      mma_commit(done);
-      for (uint32_t it = 0; it < (1u << 22) && !mbar_try_wait(done, 0); ++it) __nanosleep(64);
+      mma_commit(&done[0]);
+      for (uint32_t it = 0; it < (1u << 22) && !mbar_try_wait(&done[0], 0); ++it) __nanosleep(64);
+    }
+  } else if (shared && (warp == 6 || warp == 7)) {
+    // idle in the shared-ring schedule
+  } else if (warp == 0 || warp == 6) {
+    // TMA producers.  Warp 0 fills the first-read ring (stages [0, s_h):
+    // each tile's chunks for phase 1, from HBM); warp 6 fills the
+    // second-read ring (stages [s_h, S_N): the same chunks again for phase 2,
+    // normally from L2).  The rings are independent, so the HBM stream never
+    // waits behind phase 2.
+    if (lane == 0) {
+      const bool first = warp == 0;
+      const int nst = first ? s_h : S_N - s_h;
+      const int sbase = first ? 0 : s_h;
+      int s = 0;
+      uint32_t ph = 0;
+      int issued[S_N];
+      uint32_t iss_ph[S_N];
+      for (int q = 0; q < S_N; ++q) {
+        issued[q] = 0;
+        iss_ph[q] = 0;
+      }
+      bool ok = true;
+      if (first && g0 < g1) {
+        mbar_arrive_expect_tx(e_full, (uint32_t)(2 * nk2) * F_ECH);
+        for (int c2 = 0; c2 < 2 * nk2; ++c2) tma_load_2d(eres + c2 * F_ECH, &mapE, t0 + 64 * c2, 0, e_full);
+      }
+      // L2 policies: a tile's first read keeps its lines for the second, which
+      // is their last use in the pass
+      const uint64_t pol = first ? ((hints & F_HINT_KEEP) ? l2_evict_last() : l2_evict_normal())
+                                 : ((hints & F_HINT_DROP) ? l2_evict_first() : l2_evict_normal());
+      // L2 prefetch of the tiles pf_dist ahead in this CTA's list (first ring only)
+      int pg = g0;
+      int64_t ptile = g0 < g1 ? segs[g0].tile_begin : 0;
+      const int nwide = (nk2 + 1) / 2;  // 256-t boxes per tile
+      auto pf_issue = [&]() {
+        if (pg >= g1) return;
+        for (int w = 0; w < nwide; ++w) tma_prefetch_l2_2d(&mapXp, t0 + 256 * w, (int)(ptile * 128));
+        if (++ptile >= segs[pg].tile_end && ++pg < g1) ptile = segs[pg].tile_begin;
+      };
+      if (first)
+        for (int q = 0; q < pf_dist; ++q) pf_issue();
+      for (int g = g0; g < g1 && ok; ++g)
+        for (int64_t tile = segs[g].tile_begin; tile < segs[g].tile_end && ok; ++tile) {
+          if (first && pf_dist > 0) pf_issue();
+          for (int j = 0; j < nk2; ++j) {
+            const int si = sbase + s;
+            if (!mbar_wait(&empty[si], ph ^ 1u, abort_s, status, ST_TIMEOUT)) {
+              ok = false;
+              break;
+            }
+            uint8_t* st = smem + si * F_STAGE;
+            mbar_arrive_expect_tx(&full[si], F_STAGE);
+            tma_load_2d_hint(st, &mapX, t0 + 128 * j, (int)(tile * 128), &full[si], pol);
+            tma_load_2d_hint(st + F_BOX, &mapX, t0 + 128 * j + 64, (int)(tile * 128), &full[si], pol);
+            issued[si] = 1;
+            iss_ph[si] = ph;
+            if (++s == nst) {
+              s = 0;
+              ph ^= 1u;
+            }
+          }
+        }
+      if (!ok) {
+        for (int q = sbase; q < sbase + nst; ++q)
+          if (issued[q])
+            for (uint32_t it = 0; it < (1u << 22) && !mbar_try_wait(&full[q], iss_ph[q]); ++it) __nanosleep(128);
+        if (first && g0 < g1)
+          for (uint32_t it = 0; it < (1u << 22) && !mbar_try_wait(e_full, 0); ++it) __nanosleep(128);
+      }
+    }
+  } else if (warp == 1) {
+    // phase-1 MMA issue: A_tile partial over this CTA's t range, into one of
+    // two accumulators
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      uint32_t ae_ph[2] = {0, 0};
+      bool ok = true;
+      if (g0 < g1 && !mbar_wait(e_full, 0, abort_s, status, ST_TIMEOUT)) ok = false;
+      int64_t n = 0;
+      for (int g = g0; g < g1 && ok; ++g)
+        for (int64_t tile = segs[g].tile_begin; tile < segs[g].tile_end && ok; ++tile, ++n) {
+          const int b = (int)(n & 1);
+          if (!mbar_wait(&acc_empty[b], ae_ph[b] ^ 1u, abort_s, status, ST_TIMEOUT)) {
+            ok = false;
+            break;
+          }
+          ae_ph[b] ^= 1u;
+          tc_fence_after();
+          const uint32_t dacc = tmem + (uint32_t)b * 64u;
+          for (int j = 0; j < nk2; ++j) {
+            if (!mbar_wait(&full[s], ph, abort_s, status, ST_TIMEOUT)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t xs = smem_u32(smem + s * F_STAGE);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const uint32_t xb = xs + h * F_BOX;
+              const uint32_t eb = smem_u32(eres + (2 * j + h) * F_ECH);
+#pragma unroll
+              for (int kk = 0; kk < 4; ++kk)
+                mma_bf16(dacc, sdesc_sw128(xb + 32 * kk, 16, 1024), sdesc_sw128(eb + 32 * kk, 16, 1024), IDESC_KM,
+                         (j | h | kk) ? 1u : 0u);
+            }
+            mma_commit(&empty[s]);
+            if (++s == s_h) {
+              s = 0;
+              ph ^= 1u;
+            }
+          }
+          if (ok) mma_commit(&acc_full[b]);
+        }
+      // everything this thread issued completes before TMEM is freed
+      mma_commit(&done[0]);
+      for (uint32_t it = 0; it < (1u << 22) && !mbar_try_wait(&done[0], 0); ++it) __nanosleep(64);
+    }
+  } else if (warp == 7) {
+    // phase-2 MMA issue, one tile behind: Gram over this CTA's rows, then P
+    // over its t range, from the second-read ring
+    if (lane == 0) {
+      const int nst = S_N - s_h;
+      int s = 0;
+      uint32_t ph = 0;
+      uint32_t gf_ph[2] = {0, 0}, pe_ph = 0, ge_ph = 0;
+      bool ok = true;
+      int64_t n = 0;
+      for (int g = g0; g < g1 && ok; ++g) {
+        const SegF sg = segs[g];
+        for (int64_t tile = sg.tile_begin; tile < sg.tile_end && ok; ++tile, ++n) {
+          const bool first = tile == sg.tile_begin, last = tile == sg.tile_end - 1;
+          const int b = (int)(n % NG);
+          if (!mbar_wait_cluster(&gop_full[b], gf_ph[b], abort_s, status, ST_TIMEOUT)) {
+            ok = false;
+            break;
+          }
+          gf_ph[b] ^= 1u;
+          if (first) {
+            if (!mbar_wait(p_empty, pe_ph ^ 1u, abort_s, status, ST_TIMEOUT) ||
+                !mbar_wait(gram_empty, ge_ph ^ 1u, abort_s, status, ST_TIMEOUT)) {
+              ok = false;
+              break;
+            }
+            pe_ph ^= 1u;
+            ge_ph ^= 1u;
+          }
+          tc_fence_after();
+          const uint32_t ga = smem_u32(gop + b * F_GOP);
+          constexpr int JG = 8 / C;  // 16-row K steps of the Gram per CTA
+#pragma unroll
+          for (int j = 0; j < JG; ++j) {
+            const uint64_t d = sdesc_sw128(ga + (uint32_t)(rank * JG + j) * 2048u, F_GOP, 1024);
+            mma_bf16(tmem + T_GRAM, d, d, IDESC_MN, (first && j == 0) ? 0u : 1u);
+          }
+          for (int m = 0; m < nk2; ++m) {
+            const int si = s_h + s;
+            if (!mbar_wait(&full[si], ph, abort_s, status, ST_TIMEOUT)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t xs = smem_u32(smem + si * F_STAGE);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              mma_bf16(tmem + T_P + (uint32_t)m * 64u, sdesc_sw128(xs + j * 2048, F_BOX, 1024),
+                       sdesc_sw128(ga + j * 2048, F_GOP, 1024), IDESC_MN, (first && j == 0) ? 0u : 1u);
+            mma_commit(&empty[si]);
+            if (++s == nst) {
+              s = 0;
+              ph ^= 1u;
+            }
+          }
+          if (!ok) break;
+          if (C == 2)
+            mma_commit_mc(&gop_free[b], (uint16_t)0x3);
+          else
+            mma_commit(&gop_free[b]);
+          if (last) {
+            mma_commit(p_full);
+            mma_commit(gram_full);
+          }
+        }
+      }
+      mma_commit(&done[1]);
+      for (uint32_t it = 0; it < (1u << 22) && !mbar_try_wait(&done[1], 0); ++it) __nanosleep(64);
     }
   } else {
     const int q = warp & 3;  // TMEM lane quarter of this warp
@@ -368,6 +577,8 @@ __global__ void __launch_bounds__(FT, 1)
       ob_ph ^= 1u;
       return r;
     };
+    // A_i is not read again in the pass: its lines go first
+    const uint64_t pol_store = (hints & F_HINT_STORE) ? l2_evict_first() : l2_evict_normal();
     uint32_t peer_exch = 0, peer_exch_full = 0, peer_exch_free = 0;
     if (C == 2) {
       peer_exch = mapa_shared(smem_u32(exch), peer);
@@ -444,10 +655,10 @@ __global__ void __launch_bounds__(FT, 1)
           mbar_arrive_expect_tx(&gop_full[b], 64u * 128u);
           bulk_copy_to_cta(mapa_shared(smem_u32(gb + o), peer), gb + o, 64u * 128u,
                            mapa_shared(smem_u32(&gop_full[b]), peer));
-          tma_store_2d(&mapAs, 0, (int)(tile * 128 + 64 * (int64_t)rank), gb + o);
+          tma_store_2d_hint(&mapAs, 0, (int)(tile * 128 + 64 * (int64_t)rank), gb + o, pol_store);
         } else {
           mbar_arrive(&gop_full[b]);
-          tma_store_2d(&mapAs, 0, (int)(tile * 128), gb);
+          tma_store_2d_hint(&mapAs, 0, (int)(tile * 128), gb, pol_store);
         }
         bulk_commit();
       }
@@ -566,6 +777,8 @@ struct FState {
   int* d_seg_off = nullptr;
   int C = 1, clusters = 0;
   int pf = F_PF;  // L2 prefetch distance (tiles)
+  int hints = F_HINTS;
+  int s_h = F_SH;  // stages of the first-read ring (the second-read ring has the rest)
   // Gram slots of the two forms; the context points at the active form's
   float* f_gpart = nullptr;
   int* f_gslot_off = nullptr;
@@ -595,16 +808,11 @@ srm_status upload_vec(T** d, const std::vector<T>& h, const char* what) {
 
 bool fused_supported(const Ctx* c) { return c->batched && c->kld == 64 && c->T <= 2 * F_TB; }
 
-srm_status fused_setup(Ctx* c) {
-  if (!fused_supported(c)) {
-    set_error("single-pass form: needs the batched BF16 form, k <= 64 and T <= 1024");
-    return SRM_ERR_UNSUPPORTED;
-  }
-  auto* f = new FState();
-  c->fs = f;
-  const int C = c->T > F_TB ? 2 : 1;
-  f->C = C;
-  int clusters = std::max(1, (c->num_sms - F_RESERVE) / C);
+namespace {
+
+// Persistent clusters that fit beside `reserve` idle SMs.
+int fused_clusters(Ctx* c, int C, int reserve) {
+  int clusters = std::max(1, (c->num_sms - reserve) / C);
   if (C == 2) {
     // at most as many clusters as can be resident at once (persistent CTAs)
     cudaLaunchConfig_t cfg = {};
@@ -618,25 +826,35 @@ srm_status fused_setup(Ctx* c) {
     cfg.dynamicSmemBytes = f_smem_bytes<2>();
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaFuncSetAttribute(fpass_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f_smem_bytes<2>());
     int mc = 0;
     if (cudaOccupancyMaxActiveClusters(&mc, fpass_kernel<2>, &cfg) == cudaSuccess && mc > 0)
       clusters = std::min(clusters, mc);
     cudaGetLastError();
-  } else {
-    cudaFuncSetAttribute(fpass_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f_smem_bytes<1>());
   }
+  return clusters;
+}
+
+// Schedule, partial slots and reduction tables of the pass for `clusters`
+// clusters (replacing any earlier ones).
+srm_status fused_build(Ctx* c, int clusters) {
+  auto* f = static_cast<FState*>(c->fs);
+  const int C = f->C, N = c->N;
+  // the context points at the two-pass Gram slots while these are rebuilt
+  // (and stays so if the rebuild fails)
+  const bool was_on = c->fused;
+  if (was_on) fused_select(c, false);
+  c->p_from_f = false;  // the pass's partials are gone: the next E-step streams X^ again
+  void* old[] = {f->d_seg, f->d_seg_off, c->f_ppart, c->f_chunk_src, c->f_chunk_src_off, f->f_gpart, f->f_gslot_off};
+  for (void* q : old)
+    if (q) cudaFree(q);
+  f->d_seg = nullptr;
+  f->d_seg_off = nullptr;
+  c->f_ppart = nullptr;
+  c->f_chunk_src = nullptr;
+  c->f_chunk_src_off = nullptr;
+  f->f_gpart = nullptr;
+  f->f_gslot_off = nullptr;
   f->clusters = clusters;
-  const int N = c->N;
-  bool ok = bf16_map(&f->mapX, c->Xh, c->T, c->Vpad_tot, (uint64_t)c->ldT * 2, 64, 128) &&
-            bf16_map(&f->mapE, c->ESb, c->T, 64, (uint64_t)c->ldT * 2, 64, 64) &&
-            bf16_map(&f->mapAs, c->A, 64, c->Vpad_tot, 64 * 2, 64, 128 / C) &&
-            // L2 prefetch only (never lands in shared memory): 256 t x 128 rows per box
-            bf16_map(&f->mapXp, c->Xh, c->T, c->Vpad_tot, (uint64_t)c->ldT * 2, 256, 128, false);
-  if (!ok) {
-    set_error("cuTensorMapEncodeTiled failed for the single-pass form");
-    return SRM_ERR_CUDA;
-  }
   // 128-row tiles split evenly over the clusters, segments at subject boundaries
   const int64_t NTl = c->Vpad_tot / 128;
   std::vector<SegF> seg;
@@ -686,31 +904,72 @@ srm_status fused_setup(Ctx* c) {
   if ((st = upload_vec(&f->d_seg_off, seg_off, "single-pass schedule offsets")) != SRM_OK) return st;
   if ((st = upload_vec(&c->f_chunk_src, src, "single-pass chunk table")) != SRM_OK) return st;
   if ((st = upload_vec(&c->f_chunk_src_off, src_off, "single-pass chunk table offsets")) != SRM_OK) return st;
-  int* g_off = nullptr;
-  if ((st = upload_vec(&g_off, gslot_off, "single-pass Gram slot table")) != SRM_OK) return st;
+  if ((st = upload_vec(&f->f_gslot_off, gslot_off, "single-pass Gram slot table")) != SRM_OK) return st;
   const int64_t pel = (int64_t)seg.size() * C * F_TB * 64;
   const int64_t gel = (int64_t)seg.size() * C * 64 * 64;
-  float* gp = nullptr;
   if (cudaMalloc(&c->f_ppart, sizeof(float) * std::max<int64_t>(1, pel)) != cudaSuccess ||
-      cudaMalloc(&gp, sizeof(float) * std::max<int64_t>(1, gel)) != cudaSuccess) {
+      cudaMalloc(&f->f_gpart, sizeof(float) * std::max<int64_t>(1, gel)) != cudaSuccess) {
     cudaGetLastError();
-    if (g_off) cudaFree(g_off);
     set_error("cudaMalloc failed for single-pass partial slots");
     return SRM_ERR_NOMEM;
   }
-  // the polar-factor and eigen kernels read the Gram slots through the
-  // context: fused_select points it at one form's
+  f->f_ngslots = (int)seg.size() * C;
+  f->f_gel = gel;
+  // the polar-factor and eigen kernels read the Gram slots through the context
+  if (was_on) fused_select(c, true);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "single-pass setup");
+  return SRM_OK;
+}
+
+}  // namespace
+
+srm_status fused_setup(Ctx* c) {
+  if (!fused_supported(c)) {
+    set_error("single-pass form: needs the batched BF16 form, k <= 64 and T <= 1024");
+    return SRM_ERR_UNSUPPORTED;
+  }
+  auto* f = new FState();
+  c->fs = f;
+  const int C = c->T > F_TB ? 2 : 1;
+  f->C = C;
+  if (C == 2)
+    cudaFuncSetAttribute(fpass_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f_smem_bytes<2>());
+  else
+    cudaFuncSetAttribute(fpass_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f_smem_bytes<1>());
+  f->s_h = C == 2 ? 4 : F_SH;
+  bool ok = bf16_map(&f->mapX, c->Xh, c->T, c->Vpad_tot, (uint64_t)c->ldT * 2, 64, 128) &&
+            bf16_map(&f->mapE, c->ESb, c->T, 64, (uint64_t)c->ldT * 2, 64, 64) &&
+            bf16_map(&f->mapAs, c->A, 64, c->Vpad_tot, 64 * 2, 64, 128 / C) &&
+            // L2 prefetch only (never lands in shared memory): 256 t x 128 rows per box
+            bf16_map(&f->mapXp, c->Xh, c->T, c->Vpad_tot, (uint64_t)c->ldT * 2, 256, 128, false);
+  if (!ok) {
+    set_error("cuTensorMapEncodeTiled failed for the single-pass form");
+    return SRM_ERR_CUDA;
+  }
+  // the two-pass form's Gram slots, which fused_select swaps back in
   f->m_gpart = c->Gpart;
   f->m_gslot_off = c->gslot_off;
   f->m_ngslots = c->n_gslots;
   f->m_gel = c->Gpart_elems;
-  f->f_gpart = gp;
-  f->f_gslot_off = g_off;
-  f->f_ngslots = (int)seg.size() * C;
-  f->f_gel = gel;
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "single-pass setup");
-  return SRM_OK;
+  return fused_build(c, fused_clusters(c, C, F_RESERVE));
+}
+
+int fused_get_reserve(const Ctx* c) {
+  const auto* f = static_cast<const FState*>(c->fs);
+  return f ? c->num_sms - f->clusters * f->C : F_RESERVE;
+}
+
+srm_status fused_set_reserve(Ctx* c, int reserve) {
+  auto* f = static_cast<FState*>(c->fs);
+  if (!f) return SRM_OK;
+  if (reserve < 0 || reserve > c->num_sms - f->C) {
+    set_error("plan: the single-pass reserve must leave at least one cluster to the pass");
+    return SRM_ERR_ARG;
+  }
+  const int clusters = fused_clusters(c, f->C, reserve);
+  if (clusters == f->clusters && c->f_ppart) return SRM_OK;
+  return fused_build(c, clusters);
 }
 
 void fused_select(Ctx* c, bool on) {
@@ -723,10 +982,18 @@ void fused_select(Ctx* c, bool on) {
   c->fused = on;
 }
 
-int fused_get_pf(const Ctx* c) { return c->fs ? static_cast<const FState*>(c->fs)->pf : 0; }
+int fused_get_pf(const Ctx* c) { return c->fs ? static_cast<const FState*>(c->fs)->pf : F_PF; }
+int fused_get_hints(const Ctx* c) { return c->fs ? static_cast<const FState*>(c->fs)->hints : F_HINTS; }
+int fused_get_first_stages(const Ctx* c) { return c->fs ? static_cast<const FState*>(c->fs)->s_h : F_SH; }
+void fused_set_first_stages(Ctx* c, int s_h) {
+  if (c->fs) static_cast<FState*>(c->fs)->s_h = s_h;
+}
 
 void fused_set_pf(Ctx* c, int pf) {
   if (c->fs) static_cast<FState*>(c->fs)->pf = pf;
+}
+void fused_set_hints(Ctx* c, int hints) {
+  if (c->fs) static_cast<FState*>(c->fs)->hints = hints;
 }
 
 void fused_destroy(Ctx* c) {
@@ -747,7 +1014,7 @@ cudaError_t launch_fpass(Ctx* c) {
   if (!f) return cudaErrorInvalidValue;
   if (f->C == 1) {
     fpass_kernel<1><<<f->clusters, FT, f_smem_bytes<1>(), c->stream>>>(
-        f->mapX, f->mapE, f->mapAs, f->mapXp, f->d_seg, f->d_seg_off, c->T, f->pf, c->f_ppart, c->Gpart, c->status);
+        f->mapX, f->mapE, f->mapAs, f->mapXp, f->d_seg, f->d_seg_off, c->T, f->s_h, f->pf, f->hints, c->f_ppart, c->Gpart, c->status);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
@@ -763,7 +1030,7 @@ cudaError_t launch_fpass(Ctx* c) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, fpass_kernel<2>, f->mapX, f->mapE, f->mapAs, f->mapXp, (const SegF*)f->d_seg,
-                            (const int*)f->d_seg_off, c->T, f->pf, c->f_ppart, c->Gpart, c->status);
+                            (const int*)f->d_seg_off, c->T, f->s_h, f->pf, f->hints, c->f_ppart, c->Gpart, c->status);
 }
 
 }  // namespace srm

@@ -248,6 +248,12 @@ void fused_destroy(Ctx* c);
 void fused_select(Ctx* c, bool on);  // points the context at the single-pass (on) or two-pass Gram slots
 int fused_get_pf(const Ctx* c);
 void fused_set_pf(Ctx* c, int pf);
+int fused_get_hints(const Ctx* c);     // L2 eviction hints of the single pass (bits, 0..7)
+void fused_set_hints(Ctx* c, int hints);
+int fused_get_first_stages(const Ctx* c);  // stages of the single pass's first-read ring (1..3 of 4)
+void fused_set_first_stages(Ctx* c, int s_h);
+int fused_get_reserve(const Ctx* c);       // SMs the single pass leaves to the Sigma_s chain beside it
+srm_status fused_set_reserve(Ctx* c, int reserve);  // rebuilds the pass's schedule
 cudaError_t launch_fpass(Ctx* c);
 
 }  // namespace srm

@@ -40,12 +40,17 @@ srm_plan current_plan(const Ctx* c) {
   p.e_reserve = tc_e_reserve(c);
   tc_get_m_plan(c, &p.m_gram_bufs, &p.m_resident_es, &p.m_stages, &p.m_prefetch);
   p.f_prefetch = fused_get_pf(c);
+  p.f_l2_hints = fused_get_hints(c);
+  p.f_first_stages = fused_get_first_stages(c);
+  p.f_reserve = fused_get_reserve(c);
   return p;
 }
 
 srm_status apply_plan(Ctx* c, const srm_plan& p) {
-  if (p.reserved != 0 || (p.single_pass != 0 && p.single_pass != 1) || p.f_prefetch < 0 || p.f_prefetch > 16) {
-    set_error("srm_set_plan: field out of range (single_pass 0/1, f_prefetch 0-16, reserved 0)");
+  if ((p.single_pass != 0 && p.single_pass != 1) || p.f_prefetch < 0 || p.f_prefetch > 16 || p.f_l2_hints < 0 ||
+      p.f_l2_hints > 7 || p.f_first_stages < 1 || p.f_first_stages > 4) {
+    set_error("srm_set_plan: field out of range (single_pass 0/1, f_prefetch 0-16, f_l2_hints 0-7, "
+              "f_first_stages 1-4)");
     return SRM_ERR_ARG;
   }
   if (p.single_pass && !fused_supported(c)) {
@@ -68,7 +73,14 @@ srm_status apply_plan(Ctx* c, const srm_plan& p) {
   }
   if (p.single_pass && !c->fs) TTRY(fused_setup(c));
   if (c->fs) {
+    if (p.f_reserve < 0 || p.f_reserve >= c->num_sms) {
+      set_error("srm_set_plan: f_reserve must leave SMs to the single pass");
+      return SRM_ERR_ARG;
+    }
+    TTRY(fused_set_reserve(c, p.f_reserve));
     fused_set_pf(c, p.f_prefetch);
+    fused_set_hints(c, p.f_l2_hints);
+    fused_set_first_stages(c, p.f_first_stages);
     if (!p.single_pass) c->p_from_f = false;  // the next E-step streams X^ again
     fused_select(c, p.single_pass != 0);
   }
@@ -127,8 +139,9 @@ std::string signature(const Ctx* c) {
 
 std::string plan_line(const std::string& sig, const srm_plan& p, double ms) {
   char buf[320];
-  snprintf(buf, sizeof buf, "%s sp=%d er=%d mst=%d mgb=%d mres=%d mpf=%d fpf=%d ms=%.6f", sig.c_str(),
-           p.single_pass, p.e_reserve, p.m_stages, p.m_gram_bufs, p.m_resident_es, p.m_prefetch, p.f_prefetch, ms);
+  snprintf(buf, sizeof buf, "%s sp=%d er=%d mst=%d mgb=%d mres=%d mpf=%d fpf=%d fl2=%d fsh=%d fr=%d ms=%.6f",
+           sig.c_str(), p.single_pass, p.e_reserve, p.m_stages, p.m_gram_bufs, p.m_resident_es, p.m_prefetch,
+           p.f_prefetch, p.f_l2_hints, p.f_first_stages, p.f_reserve, ms);
   return buf;
 }
 
@@ -136,8 +149,10 @@ bool parse_line(const std::string& line, const std::string& sig, srm_plan* p, do
   if (line.compare(0, sig.size(), sig) != 0 || line.size() <= sig.size() || line[sig.size()] != ' ') return false;
   srm_plan q{};
   double t = 0;
-  if (sscanf(line.c_str() + sig.size(), " sp=%d er=%d mst=%d mgb=%d mres=%d mpf=%d fpf=%d ms=%lf", &q.single_pass,
-             &q.e_reserve, &q.m_stages, &q.m_gram_bufs, &q.m_resident_es, &q.m_prefetch, &q.f_prefetch, &t) != 8)
+  if (sscanf(line.c_str() + sig.size(),
+             " sp=%d er=%d mst=%d mgb=%d mres=%d mpf=%d fpf=%d fl2=%d fsh=%d fr=%d ms=%lf", &q.single_pass,
+             &q.e_reserve, &q.m_stages, &q.m_gram_bufs, &q.m_resident_es, &q.m_prefetch, &q.f_prefetch,
+             &q.f_l2_hints, &q.f_first_stages, &q.f_reserve, &t) != 11)
     return false;
   *p = q;
   *ms = t;
@@ -216,9 +231,10 @@ struct Report {
   std::ostringstream os;
   void add(const char* stage, const srm_plan& p, float ms, const char* unit) {
     char buf[200];
-    snprintf(buf, sizeof buf, "%-6s sp=%d er=%-3d mst=%d mgb=%d mres=%d mpf=%-2d fpf=%d  %9.4f %s\n", stage,
+    snprintf(buf, sizeof buf,
+             "%-6s sp=%d er=%-3d mst=%d mgb=%d mres=%d mpf=%-2d fpf=%d fl2=%d fsh=%d fr=%-2d  %9.4f %s\n", stage,
              p.single_pass, p.e_reserve, p.m_stages, p.m_gram_bufs, p.m_resident_es, p.m_prefetch, p.f_prefetch,
-             ms, unit);
+             p.f_l2_hints, p.f_first_stages, p.f_reserve, ms, unit);
     os << buf;
   }
 };
@@ -263,18 +279,26 @@ srm_status search(Ctx* c, int iters, srm_plan* best_out, float* best_ms_out, Rep
   if (fused_ok) {
     TTRY(apply_plan(c, bf));
     float best_f = 1e30f;
-    for (int pf : {0, 1, 2, 3, 4, 6}) {
-      fused_set_pf(c, pf);
-      float ms = 0;
-      TTRY(time_launches(c, launch_fpass, 3, e0, e1, &ms));
-      srm_plan p = bf;
-      p.f_prefetch = pf;
-      rep.add("fpass", p, ms, "ms/launch");
-      if (ms < best_f) {
-        best_f = ms;
-        bf.f_prefetch = pf;
+    srm_plan bfp = bf;
+    for (int sh : {1, 2, 3, 4})
+      for (int hints : {0, 7})
+        for (int pf : {0, 1, 2}) {
+        fused_set_pf(c, pf);
+        fused_set_hints(c, hints);
+        fused_set_first_stages(c, sh);
+        float ms = 0;
+        TTRY(time_launches(c, launch_fpass, 3, e0, e1, &ms));
+        srm_plan p = bf;
+        p.f_prefetch = pf;
+        p.f_l2_hints = hints;
+        p.f_first_stages = sh;
+        rep.add("fpass", p, ms, "ms/launch");
+        if (ms < best_f) {
+          best_f = ms;
+          bfp = p;
+        }
       }
-    }
+    bf = bfp;
   }
 
   // 3. E-pass reserves (split-v depths), as whole iterations of the two-pass form
@@ -297,16 +321,24 @@ srm_status search(Ctx* c, int iters, srm_plan* best_out, float* best_ms_out, Rep
     }
   }
 
-  // 4. the single-pass form with its best prefetch distance, as whole iterations
+  // 4. the single-pass form with its best pipeline, as whole iterations, for
+  // a few SM reserves beside it
   if (fused_ok) {
     bf.e_reserve = best.e_reserve;  // its first E-step still runs the E-pass
-    TTRY(apply_plan(c, bf));
-    float ms = 0;
-    TTRY(time_iterations(c, iters, e0, e1, &ms));
-    rep.add("iter", bf, ms, "ms/iteration");
-    if (ms < best_it) {
-      best_it = ms;
-      best = bf;
+    std::vector<int> fres = {0, 4, 10, bf.f_reserve};
+    std::sort(fres.begin(), fres.end());
+    fres.erase(std::unique(fres.begin(), fres.end()), fres.end());
+    for (int r : fres) {
+      srm_plan p = bf;
+      p.f_reserve = r;
+      TTRY(apply_plan(c, p));
+      float ms = 0;
+      TTRY(time_iterations(c, iters, e0, e1, &ms));
+      rep.add("iter", p, ms, "ms/iteration");
+      if (ms < best_it) {
+        best_it = ms;
+        best = p;
+      }
     }
   }
   *best_out = best;

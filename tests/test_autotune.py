@@ -81,7 +81,10 @@ def test_every_plan_matches_oracle():
     o = run_oracle(d, CASE.n_iter)
     plans = [dict(single_pass=0, e_reserve=0), dict(single_pass=0, e_reserve=32),
              dict(single_pass=0, m_stages=2, m_gram_bufs=1, m_resident_es=0, m_prefetch=0),
-             dict(single_pass=1, f_prefetch=0), dict(single_pass=1, f_prefetch=3)]
+             dict(single_pass=1, f_prefetch=0), dict(single_pass=1, f_prefetch=3, f_l2_hints=7),
+             dict(single_pass=1, f_prefetch=1, f_l2_hints=6), dict(single_pass=1, f_first_stages=1),
+             dict(single_pass=1, f_first_stages=3, f_prefetch=2), dict(single_pass=1, f_first_stages=4),
+             dict(single_pass=1, f_reserve=0), dict(single_pass=1, f_reserve=30, f_first_stages=1)]
     for fields in plans:
         m = _model(d, CASE.k, graph=True)
         m.set_plan(**fields)
@@ -94,15 +97,17 @@ def test_every_plan_matches_oracle():
             assert e <= TOL_BF16, (fields, key, e)
     # out-of-range plans are refused before anything runs
     m = _model(d, CASE.k)
-    for bad in (dict(m_stages=9), dict(m_gram_bufs=3), dict(e_reserve=-1), dict(f_prefetch=99)):
+    for bad in (dict(m_stages=9), dict(m_gram_bufs=3), dict(e_reserve=-1), dict(f_prefetch=99),
+                dict(f_l2_hints=8), dict(f_first_stages=0), dict(f_first_stages=5),
+                dict(single_pass=1, f_reserve=-1)):
         with pytest.raises(srm.SrmError) as ei:
             m.set_plan(**bad)
         assert ei.value.status == srm.SRM_ERR_ARG, bad
 
 
 def test_pipelining_plans_are_bitwise_identical():
-    # stages, Gram buffers, E[S] residency and prefetch change when bytes
-    # arrive, not the order of any sum
+    # stages, Gram buffers, E[S] residency, prefetch, L2 hints and the
+    # single pass's ring split change when bytes arrive, not the order of any sum
     d = make_inputs(CASE_T500)
     runs = []
     for fields in (dict(m_stages=2, m_gram_bufs=2, m_resident_es=0, m_prefetch=0),
@@ -111,11 +116,21 @@ def test_pipelining_plans_are_bitwise_identical():
         m = _model(d, CASE_T500.k)
         m.set_plan(single_pass=0, **fields)
         runs.append(_results(m, CASE_T500.n_iter))
-    for r in runs[1:]:
-        np.testing.assert_array_equal(runs[0]["ll"], r["ll"])
-        np.testing.assert_array_equal(runs[0]["ES"], r["ES"])
-        for a, b in zip(runs[0]["W"], r["W"]):
-            np.testing.assert_array_equal(a, b)
+    # the single pass: prefetch distance and L2 eviction hints
+    fused = []
+    for fields in (dict(f_prefetch=0, f_l2_hints=0, f_first_stages=2),
+                   dict(f_prefetch=2, f_l2_hints=7, f_first_stages=1),
+                   dict(f_prefetch=1, f_l2_hints=2, f_first_stages=3),
+                   dict(f_prefetch=0, f_l2_hints=7, f_first_stages=4)):
+        m = _model(d, CASE_T500.k)
+        m.set_plan(single_pass=1, **fields)
+        fused.append(_results(m, CASE_T500.n_iter))
+    for group in (runs, fused):
+        for r in group[1:]:
+            np.testing.assert_array_equal(group[0]["ll"], r["ll"])
+            np.testing.assert_array_equal(group[0]["ES"], r["ES"])
+            for a, b in zip(group[0]["W"], r["W"]):
+                np.testing.assert_array_equal(a, b)
 
 
 def test_plan_switch_between_iterations():
