@@ -105,20 +105,34 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def workload(config: int, rank: int):
+def workload(config: int, rank: int, subjects: int = 0):
+    """The config's planted spec and voxel counts; with subjects > 0 only the
+    first `subjects` subjects (a smaller case of the same shapes, for
+    profiling)."""
+    import dataclasses
+
     import synth
     spec = synth.config_spec(config)
     vox = synth.draw_voxel_counts(spec)
+    if subjects and subjects < len(vox):
+        vox = vox[:subjects]
+        spec = dataclasses.replace(spec, n_subjects=subjects,
+                                   name=spec.name + " (first %d subjects)" % subjects)
     return spec, vox
 
 
 # ncu captures committed under profiles/, by workload: DRAM bytes per launch of
 # a kernel, valid while the kernel's source file is unchanged (its SHA-1 is
 # recorded beside the number)
-PROFILE_TAGS = {1: "greeneyes_like_N16_T1000_k50"}
+PROFILE_TAGS = {1: "greeneyes_like_N16_T1000_k50", 3: "forrest_like_N8_T3500_k100",
+                4: "forrest1024_like_N1024_T500_k50"}
 
 
-def profiled_traffic(kernel: str, config: int):
+def profiled_traffic(kernel: str, config: int, voxels_total: int):
+    """DRAM bytes of one launch from the committed ncu summary of this kernel
+    on this workload.  A summary of a smaller case of the same shapes (the
+    first subjects only: `voxels_captured` below the workload's) is scaled
+    by voxel count, since every byte of these passes is per voxel row."""
     import hashlib
     import re
     tag = PROFILE_TAGS.get(config)
@@ -135,7 +149,13 @@ def profiled_traffic(kernel: str, config: int):
     src = os.path.join(ROOT, "paper_1608_04647_gb300", "csrc", ms.group(2))
     if not os.path.exists(src) or hashlib.sha1(open(src, "rb").read()).hexdigest() != ms.group(1):
         return None, os.path.relpath(path, ROOT) + " (stale: kernel source changed since the capture)"
-    return int(mt.group(1)), os.path.relpath(path, ROOT)
+    traffic = int(mt.group(1))
+    mv = re.search(r"voxels_captured: (\d+)", text)
+    if mv and int(mv.group(1)) != voxels_total:
+        traffic = int(round(traffic * voxels_total / int(mv.group(1))))
+        return traffic, os.path.relpath(path, ROOT) + " (smaller case, scaled by voxels x%.2f)" % (
+            voxels_total / int(mv.group(1)))
+    return traffic, os.path.relpath(path, ROOT)
 
 
 def algorithmic_bytes(vox, T, k, xbytes, abytes):
@@ -145,6 +165,15 @@ def algorithmic_bytes(vox, T, k, xbytes, abytes):
     e_pass = V * T * xbytes + V * k * abytes
     m_pass = V * T * xbytes + V * k * abytes
     return e_pass, m_pass
+
+
+def parse_plan(text: str) -> dict:
+    """'single_pass=1,f_l2_hints=7' -> {'single_pass': 1, 'f_l2_hints': 7}"""
+    out = {}
+    for item in filter(None, (x.strip() for x in text.split(","))):
+        key, val = item.split("=")
+        out[key.strip()] = int(val)
+    return out
 
 
 def single_pass_bytes(vox, T, k, xbytes, abytes):
@@ -200,7 +229,7 @@ def run_ours(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     srm.load_library()
-    spec, vox = workload(args.config, rank)
+    spec, vox = workload(args.config, rank, args.subjects)
     T, k = spec.T, spec.k
     peaks = load_peaks()
     d = planted_dataset_torch(spec, vox, device="cuda", seed_offset=rank)
@@ -227,6 +256,10 @@ def run_ours(args, rank, world):
             plan, ms, _ = m.autotune(tune["cache"], iters=4)
             if tune["plan"] is None:
                 tune.update(plan=plan, ms=round(ms, 4), tuning_s=round(time.perf_counter() - t0, 2))
+        if store == "bf16" and args.plan:
+            m.set_plan(**parse_plan(args.plan))
+            if tune["plan"] is None or tune.get("override") is None:
+                tune.update(plan=m.plan(), override=args.plan)
         return m
 
     results = {}
@@ -279,7 +312,7 @@ def run_ours(args, rank, world):
         if head == "f32":
             b = b / len(vox)  # per launch (one launch per subject)
         achieved = b / (t * 1e-3) / 1e9
-        traffic, tsrc = profiled_traffic(name, args.config) if head == "bf16" else (None, None)
+        traffic, tsrc = profiled_traffic(name, args.config, int(sum(vox))) if head == "bf16" else (None, None)
         roofline = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                     "traffic_source": tsrc, "peak_source": peaks["source"] + " (burst copy)",
@@ -297,8 +330,9 @@ def run_ours(args, rank, world):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "graph": True, "single_pass": single,
                    "plan": tune["plan"] if head == "bf16" else None,
-                   "autotune": None if head != "bf16" or tune["plan"] is None else
+                   "autotune": None if head != "bf16" or tune["ms"] is None else
                    {"tuned_ms_per_iteration": tune["ms"], "tuning_s": tune["tuning_s"],
+                    "plan_override": tune.get("override"),
                     "note": "srm_autotune before the timed region; later contexts replay the cache"}},
         "hbm_gbs_iteration": round(iter_bytes / (ms_step * 1e-3) / 1e9, 1),
         "roofline": roofline,
@@ -346,6 +380,8 @@ def run_e2e(args, d, spec, vox, stream, world, tune_cache=None):
                     max_iter=n_iter + 8, single_pass=args.single_pass)
         if store == "bf16" and tune_cache:
             m.autotune(tune_cache, iters=4)  # a cached plan: no timing, one file read
+        if store == "bf16" and args.plan:
+            m.set_plan(**parse_plan(args.plan))
         ll = m.fit(n_iter)
         rho2, sig = m.params()
         S = m.get_s().cpu()
@@ -413,7 +449,7 @@ def run_reference(args, rank, world):
     bounded sample of the same workload; each step one EM iteration over the
     sample, time scaled to the whole workload by voxel count."""
     import oracle
-    spec, vox = workload(args.config, rank)
+    spec, vox = workload(args.config, rank, args.subjects)
     sub, dd = oracle_sample(spec, vox, max_elems=2e7, max_subjects=2)
     Xh = [oracle.center(x)[0] for x in dd["X"]]
     for _ in range(args.warmup):
@@ -501,6 +537,10 @@ def main():
                     "no autotuning")
     ap.add_argument("--no-autotune", action="store_true", help="run the library's default launch plan")
     ap.add_argument("--tune-cache", default=None, help="plan cache file kept across runs (default: a fresh one)")
+    ap.add_argument("--plan", default="", help="launch-plan fields set after tuning, e.g. 'single_pass=0' "
+                    "(srm_set_plan; for profiling one form)")
+    ap.add_argument("--subjects", type=int, default=0, help="only the first K subjects of the workload (a smaller "
+                    "case of the same shapes, for ncu captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
