@@ -478,7 +478,8 @@ def run_k_sweep(args):
     """Number of features k against throughput on the greeneyes-like shapes
     (N = 16, v ~ U[2e4, 6e4], T = 1000; the paper's E3 runtime-vs-K, whose
     values appear only in a figure): one JSON line per k with EM iterations/s
-    and each pass's GB/s.  k up to 128 (the library's limit)."""
+    of the tuned batched form and each streaming pass's GB/s.  k up to 128
+    (the library's limit)."""
     import dataclasses
 
     import torch
@@ -499,21 +500,28 @@ def run_k_sweep(args):
         stream = torch.cuda.Stream()
         m = srm.SRM(d["X"], d["W0"], k, store="bf16", graph=True, max_iter=args.warmup + args.steps + 8,
                     stream=stream)
+        plan, _, _ = m.autotune(None, iters=4)
         ms = time_fit(m, stream, args.steps, args.warmup) / args.steps
         m.close()
         mp = srm.SRM(d["X"], d["W0"], k, store="bf16", graph=False, profile=True,
                      max_iter=args.warmup + args.steps + 8, stream=stream)
+        mp.set_plan(**plan)
         mp.fit_async(args.warmup)
         mp.kernel_times(reset=True)
         mp.fit_async(args.steps)
         kt = mp.kernel_times()
         mp.close()
         e_bytes, m_bytes = algorithmic_bytes(vox, spec.T, k, 2, 2)
-        te = kt["estep_tc"][1] / args.steps
-        tm = kt["mstep_tc"][1] / args.steps
+        f_bytes = single_pass_bytes(vox, spec.T, k, 2, 2)
+        passes = {}
+        for name, b in (("estep_tc", e_bytes), ("mstep_tc", m_bytes), ("fpass_tc", f_bytes)):
+            if kt.get(name, (0, 0))[0]:
+                t = kt[name][1] / kt[name][0]
+                passes[name] = {"ms": round(t, 4), "gbs": round(b / (t * 1e-3) / 1e9, 1),
+                                "frac": round(b / (t * 1e-3) / 1e9 / peaks["hbm_gbs"], 3)}
         print(json.dumps({"k_sweep": True, "k": k, "metric": METRIC, "value": round(1000.0 / ms, 3), "unit": UNIT,
-                          "ms_per_step": round(ms, 4), "estep_gbs": round(e_bytes / (te * 1e-3) / 1e9, 1),
-                          "mstep_gbs": round(m_bytes / (tm * 1e-3) / 1e9, 1), "peak_gbs": peaks["hbm_gbs"],
+                          "ms_per_step": round(ms, 4), "single_pass": bool(plan["single_pass"]), "passes": passes,
+                          "peak_gbs": peaks["hbm_gbs"],
                           "paper_gflops": round(paper_flops(vox, spec.T, k) / (ms * 1e-3) / 1e9, 1),
                           "kernels_ms_per_step": {n: round(v[1] / args.steps, 4) for n, v in kt.items() if v[0]}}),
               flush=True)

@@ -248,12 +248,10 @@ __global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __
   double* w = ph_smem;          // [k]  1 / (1 + rho0 lambda)
   double* ua = w + k;           // [k]  row a of U
   double* tv = ua + k;          // [k]  (U[a,:] B)
-  double* Uss = tv + k;         // [k][k] U
-  double* Gps = Uss + k * k;    // [k][k] G', symmetrised
+  double* Gps = tv + k;         // [k][k] G', symmetrised (U is read from global memory)
   const int a = blockIdx.x, tid = threadIdx.x;
   for (int e = tid; e < k * k; e += blockDim.x) {
     const int b = e / k, d = e % k;
-    Uss[e] = Us[e];
     Gps[e] = 0.5 * (Gp[b * k + d] + Gp[d * k + b]);
   }
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
@@ -284,7 +282,7 @@ __global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __
   __syncthreads();
   for (int cc = tid; cc < k; cc += blockDim.x) {
     double s = 0.0;
-    for (int d = 0; d < k; ++d) s = fma(tv[d], Uss[cc * k + d], s);
+    for (int d = 0; d < k; ++d) s = fma(tv[d], Us[cc * k + d], s);
     if (!isfinite(s)) flag(status, ST_NONFINITE);
     Phi[a * k + cc] = s;
     Phi32[a * k + cc] = (float)s;
@@ -1458,11 +1456,18 @@ __global__ void __launch_bounds__(256) transform_finish_kernel(int k, int kld, i
   S[e] = acc;
 }
 
+int g_max_smem = 232448;  // opt-in shared memory per block (set by prepare_small_kernels)
+
 int refine_bands(const Ctx* c, int nbatch) {
   int nb = (2 * c->num_sms + nbatch - 1) / nbatch;
   nb = nb < 1 ? 1 : nb;
   const int mx = c->k / 4 > 0 ? c->k / 4 : 1;
-  return nb > mx ? mx : nb;
+  nb = nb > mx ? mx : nb;
+  // B (k x (k+1)) and one band of A must fit in shared memory: at k = 128
+  // with many matrices (one band each) they would not
+  const int band_max = g_max_smem / (int)(sizeof(double) * (c->k + 1)) - c->k;
+  const int nb_min = band_max > 0 ? (c->k + band_max - 1) / band_max : c->k;
+  return nb < nb_min ? nb_min : nb;
 }
 
 cudaError_t bgemm(Ctx* c, int nbatch, const double* A, int tA, const double* B, int tB, double alpha,
@@ -1479,6 +1484,7 @@ cudaError_t bgemm(Ctx* c, int nbatch, const double* A, int tA, const double* B, 
 
 
 void prepare_small_kernels(int max_smem) {
+  g_max_smem = max_smem;
   cudaFuncSetAttribute(es_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float) * KMAX * KMAX));
   // (these kernels also hold a few KB of static shared memory)
   cudaFuncSetAttribute(p_reduce_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
@@ -1547,7 +1553,7 @@ cudaError_t launch_sigma(Ctx* c) {
 
 cudaError_t launch_phi(Ctx* c) {
   const int64_t kk = (int64_t)c->k * c->k;
-  const size_t sm = sizeof(double) * (3 * c->k + 2 * c->k * c->k);
+  const size_t sm = sizeof(double) * (3 * c->k + c->k * c->k);
   phi_kernel<<<c->k, 256, sm, c->stream>>>(c->N, c->k, c->rho2, c->sqnorm, c->d_v, c->Xr64 + c->N * kk,
                                            c->G64 + c->N * kk, c->Phi, c->Phi32, c->scal, c->status);
   return cudaGetLastError();

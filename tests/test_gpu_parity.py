@@ -28,6 +28,8 @@ PLAIN_CASES = [
     # the largest k of the Newton-Schulz polar path (64) and the smallest past it (65)
     Case("k64-boundary", [900, 1300], 130, 64, 4, seed=14),
     Case("k65-eigen-path", [1000, 1200], 131, 65, 4, seed=15),
+    # the largest k the library accepts (128; the k x k kernels' shared memory)
+    Case("k128-max", [1500, 1300], 300, 128, 3, seed=16),
     # more subjects than E-step reduction groups: several subjects per group
     Case("grouped-subjects", [int(x) for x in np.random.default_rng(11).integers(40, 250, size=150)], 1500, 8, 4,
          seed=11),
