@@ -1,0 +1,125 @@
+"""Parity at the full sizes of the benchmarked workloads, in the launch
+configuration bench.py times: the batched BF16 form, the autotuned plan and
+CUDA-graph iterations.
+
+The FP64 oracle cannot run whole EM fits at these sizes.  So each check
+starts from the GPU's own state after a fit.  From that state and the same
+seeded inputs, the oracle computes outputs it can afford one by one:
+
+* E-step: E[S] on sampled columns.  The reduced E-step acts on each column
+  t separately (y_t = sum_i rho_i^-2 W_i^T x^_it, E[s_t] = Phi y_t), so
+  oracle.estep on the columns {t} gives exactly those columns of E[S].
+* M-step: W_i and rho_i^2 of sampled subjects, from the GPU's E[S] and the
+  Sigma_s^new that the oracle forms from it.
+
+Properties that hold at any size are checked too: a log-likelihood that
+does not decrease, orthonormal W_i, positive rho_i^2, and a symmetric
+positive definite Sigma_s.  The bar is the BF16 form's 2e-2 relative
+(max-norm): the oracle consumes the unrounded FP32 input.  The sample means
+of the columns are prepared with PyTorch on the device (input preparation,
+not the library).  The oracle does the E-step and M-step arithmetic."""
+from collections.abc import Sequence
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+TOL_BF16 = 2e-2
+
+
+class _Lazy(Sequence):
+    """A sequence whose items are fetched when the oracle reads them, so that
+    a thousand subjects never sit on the host at once."""
+
+    def __init__(self, n, fetch):
+        self.n, self.fetch = n, fetch
+
+    def __len__(self):
+        return self.n
+
+    def __getitem__(self, i):
+        if i < 0 or i >= self.n:
+            raise IndexError(i)
+        return self.fetch(i)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    from paper_1608_04647_gb300 import _build as b
+    b.build()
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+# greeneyes-like (16 subjects, T = 1000) and forrest-1024-like (1024
+# subjects, T = 500, 41 GB resident): the workloads of the bench lines
+@pytest.mark.parametrize("config", [1, 4])
+def test_full_size_sampled_parity(config):
+    import torch
+
+    import oracle
+    import paper_1608_04647_gb300 as srm
+    import synth
+    from synth.planted_torch import planted_dataset_torch
+
+    spec = synth.config_spec(config)
+    vox = synth.draw_voxel_counts(spec)
+    N, T, k = len(vox), spec.T, spec.k
+    d = planted_dataset_torch(spec, vox, device="cuda")
+    m = srm.SRM(d["X"], d["W0"], k, store="bf16", graph=True, max_iter=spec.n_iter + 16)
+    plan, _, _ = m.autotune(None, iters=2)
+    ll = m.fit(spec.n_iter)
+    rho2, sig = m.params()
+    print(spec.name, plan)
+
+    # properties at any size
+    assert np.all(np.isfinite(ll)) and np.all(np.diff(ll) >= -1e-6 * np.abs(ll[1:])), ll
+    assert np.all(rho2 > 0)
+    np.testing.assert_allclose(sig, sig.T, rtol=0, atol=1e-12 * np.abs(sig).max())
+    assert np.linalg.eigvalsh(sig).min() > 0
+
+    # one more E-step on the GPU; the oracle's E-step on sampled columns
+    cols = [0, T // 3, T - 1]
+
+    def xcols(i):
+        x = d["X"][i]
+        mu = x.double().mean(dim=1, keepdim=True)
+        return (x[:, cols].double() - mu).cpu().numpy()
+
+    def wfetch(i):
+        return m.get_w(i).double().cpu().numpy()
+
+    est = oracle.estep(_Lazy(N, xcols), _Lazy(N, wfetch), rho2, sig)
+    m.estep()
+    es_gpu = m.get_s().double().cpu().numpy()
+    err_es = float(np.abs(es_gpu[:, cols] - est["ES"]).max() / np.abs(es_gpu).max())
+
+    # the M-step on the GPU; the oracle's M-step for sampled subjects from
+    # the GPU's E[S] (all columns) and the Sigma_s^new it implies
+    sub = sorted({0, N // 2, N - 1})
+    sig_new = oracle.sigma_update({"ES": es_gpu, "Phi": est["Phi"]}, T)
+    xh, sq = [], []
+    for i in sub:
+        x_i, _, s_i = oracle.center(d["X"][i].cpu().numpy())
+        xh.append(x_i)
+        sq.append(s_i)
+    w_o, r_o = oracle.mstep(xh, sq, es_gpu, sig_new)
+    m.mstep()
+    rho2_new, sig_gpu = m.params()
+    err_w = max(_rel(m.get_w(i).double().cpu().numpy(), w_o[j]) for j, i in enumerate(sub))
+    err_r = max(abs(rho2_new[i] - r_o[j]) / r_o[j] for j, i in enumerate(sub))
+    err_s = _rel(sig_gpu, sig_new)
+    print({"E[S] columns": f"{err_es:.2e}", "W": f"{err_w:.2e}", "rho2": f"{err_r:.2e}",
+           "Sigma_s": f"{err_s:.2e}"})
+    assert err_es <= TOL_BF16
+    assert err_w <= TOL_BF16
+    assert err_r <= TOL_BF16
+    assert err_s <= TOL_BF16
+    for i in sub:
+        w = m.get_w(i).double().cpu().numpy()
+        np.testing.assert_allclose(w.T @ w, np.eye(k), atol=1e-3)
+    m.close()
+    del d
+    torch.cuda.empty_cache()
