@@ -274,6 +274,8 @@ typedef struct {
                                4 = one shared ring serving both reads in turn */
     int32_t f_reserve;      /* SMs the single pass leaves to the Sigma_s chain that runs
                                beside it (the pass runs on the rest, in whole clusters) */
+    int32_t m_boxes;        /* M-pass: consecutive 64-column boxes of the same 128 rows of X^
+                               per stage, 1, 2 or 4 (longer contiguous reads per row) */
 } srm_plan;
 
 /* srm_get_plan -- the plan the context runs.  SRM_ERR_UNSUPPORTED for the plain

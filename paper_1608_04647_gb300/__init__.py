@@ -74,6 +74,7 @@ class srm_plan(ctypes.Structure):
         ("f_l2_hints", ctypes.c_int32),
         ("f_first_stages", ctypes.c_int32),
         ("f_reserve", ctypes.c_int32),
+        ("m_boxes", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:

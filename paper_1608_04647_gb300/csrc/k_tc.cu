@@ -62,6 +62,7 @@ struct TcState {
   int m_stages = 4;     // M-pass pipeline depth
   int m_gop = 2;        // M-pass Gram operand buffers
   int m_pf = 0;         // M-pass L2 prefetch distance (X^ chunks; 0 = off)
+  int m_bps = 1;        // M-pass 64-t boxes per stage (1, 2 or 4)
   size_t m_smem = 0;
 };
 
@@ -269,12 +270,14 @@ template <int KLD, bool RES, int GNB>  // GNB: Gram operand buffers (1 or 2)
 __global__ void __launch_bounds__(NT, 1)
     mstep_tc_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE,
                     const __grid_constant__ CUtensorMap mapAs, const __grid_constant__ CUtensorMap mapXp,
-                    const SegM* __restrict__ segs, const int* __restrict__ seg_off, int T, int S_N, int pf_dist,
-                    const uint8_t* __restrict__ xbase, int64_t xrow_bytes,
+                    const SegM* __restrict__ segs, const int* __restrict__ seg_off, int T, int S_N, int bps,
+                    int pf_dist, const uint8_t* __restrict__ xbase, int64_t xrow_bytes,
                     __nv_bfloat16* __restrict__ Aout, float* __restrict__ gpart, int* status) {
   constexpr uint32_t X_BYTES = 128u * 128u;
   constexpr uint32_t E_CHUNK = (uint32_t)KLD * 128u;
-  constexpr uint32_t STAGE = RES ? X_BYTES : m_stage_bytes(KLD);
+  // a stage holds bps consecutive 64-t boxes of the same 128 rows (X^ boxes
+  // first, then, unless E[S] is resident, the matching E[S] chunks)
+  const uint32_t STAGE = (uint32_t)bps * (RES ? X_BYTES : m_stage_bytes(KLD));
   constexpr uint32_t TMEM_COLS = (3 * KLD <= 256) ? 256 : 512;
   constexpr uint32_t IDESC_MAIN = idesc_bf16(128, KLD, false, false);
   constexpr uint32_t IDESC_GRAM = idesc_bf16(128, KLD, true, true);
@@ -389,16 +392,19 @@ __global__ void __launch_bounds__(NT, 1)
       for (int g = g0; g < g1 && ok; ++g) {
         const SegM sg = segs[g];
         for (int64_t tile = sg.tile_begin; tile < sg.tile_end && ok; ++tile) {
-          for (int kc = 0; kc < nk; ++kc) {
-            pf_next();
+          for (int kc0 = 0; kc0 < nk; kc0 += bps) {
+            const int nb = min(bps, nk - kc0);
+            for (int bb = 0; bb < nb; ++bb) pf_next();
             if (!mbar_wait(&empty[s], ph ^ 1u, abort_s, status, ST_TIMEOUT)) {
               ok = false;
               break;
             }
             uint8_t* st = smem + s * STAGE;
-            mbar_arrive_expect_tx(&full[s], STAGE);
-            tma_load_2d(st, &mapX, 64 * kc, (int)(tile * 128), &full[s]);
-            if (!RES) tma_load_2d(st + X_BYTES, &mapE, 64 * kc, 0, &full[s]);
+            mbar_arrive_expect_tx(&full[s], (uint32_t)nb * (RES ? X_BYTES : m_stage_bytes(KLD)));
+            for (int bb = 0; bb < nb; ++bb) {
+              tma_load_2d(st + bb * X_BYTES, &mapX, 64 * (kc0 + bb), (int)(tile * 128), &full[s]);
+              if (!RES) tma_load_2d(st + bps * X_BYTES + bb * E_CHUNK, &mapE, 64 * (kc0 + bb), 0, &full[s]);
+            }
             issued[s] = 1;
             iss_ph[s] = ph;
             if (++s == S_N) {
@@ -458,18 +464,23 @@ __global__ void __launch_bounds__(NT, 1)
           ae_ph[b] ^= 1u;
           tc_fence_after();
           const uint32_t dacc = tmem + b * KLD;
-          for (int kc = 0; kc < nk; ++kc) {
+          for (int kc0 = 0; kc0 < nk; kc0 += bps) {
+            const int nb = min(bps, nk - kc0);
             if (!mbar_wait(&full[s], ph, abort_s, status, ST_TIMEOUT)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            const uint32_t xs = smem_u32(smem + s * STAGE);
-            const uint32_t es = RES ? smem_u32(eres + kc * E_CHUNK) : xs + X_BYTES;
+            const uint32_t st = smem_u32(smem + s * STAGE);
+            for (int bb = 0; bb < nb; ++bb) {
+              const int kc = kc0 + bb;
+              const uint32_t xs = st + bb * X_BYTES;
+              const uint32_t es = RES ? smem_u32(eres + kc * E_CHUNK) : st + bps * X_BYTES + bb * E_CHUNK;
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-              mma_bf16(dacc, sdesc_sw128(xs + 32 * j, 16, 1024), sdesc_sw128(es + 32 * j, 16, 1024), IDESC_MAIN,
-                       (kc | j) ? 1u : 0u);
+              for (int j = 0; j < 4; ++j)
+                mma_bf16(dacc, sdesc_sw128(xs + 32 * j, 16, 1024), sdesc_sw128(es + 32 * j, 16, 1024), IDESC_MAIN,
+                         (kc | j) ? 1u : 0u);
+            }
             mma_commit(&empty[s]);
             if (++s == S_N) {
               s = 0;
@@ -801,11 +812,11 @@ srm_status build_e_schedule(Ctx* c, int GE) {
 
 // Shared memory of an M-pass plan: nb Gram operand buffers, E[S] resident or
 // streamed, stages X^ stages.  0 if it does not fit.
-size_t m_plan_smem(const Ctx* c, int nb, bool res, int stages) {
-  if ((nb != 1 && nb != 2) || stages < 2 || stages > M_MAX_STAGES) return 0;
+size_t m_plan_smem(const Ctx* c, int nb, bool res, int stages, int bps) {
+  if ((nb != 1 && nb != 2) || stages < 2 || stages > M_MAX_STAGES || (bps != 1 && bps != 2 && bps != 4)) return 0;
   const size_t eres = (size_t)((c->T + 63) / 64) * c->kld * 128;
-  const size_t sm = m_fixed_bytes(c->kld, nb) +
-                    (res ? eres + (size_t)stages * 16384 : (size_t)stages * m_stage_bytes(c->kld));
+  const size_t sm = m_fixed_bytes(c->kld, nb) + (res ? eres + (size_t)stages * bps * 16384
+                                                      : (size_t)stages * bps * m_stage_bytes(c->kld));
   return sm <= kMaxSmem ? sm : 0;
 }
 
@@ -831,18 +842,20 @@ srm_status tc_set_e_reserve(Ctx* c, int reserve) {
   return build_e_schedule(c, GE);
 }
 
-void tc_get_m_plan(const Ctx* c, int* nb, int* res, int* stages, int* pf) {
+void tc_get_m_plan(const Ctx* c, int* nb, int* res, int* stages, int* pf, int* bps) {
   const auto* s = static_cast<const TcState*>(c->tc);
   *nb = s->m_gop;
   *res = s->m_res ? 1 : 0;
   *stages = s->m_stages;
   *pf = s->m_pf;
+  *bps = s->m_bps;
 }
 
-srm_status tc_set_m_plan(Ctx* c, int nb, int res, int stages, int pf) {
-  const size_t sm = m_plan_smem(c, nb, res != 0, stages);
+srm_status tc_set_m_plan(Ctx* c, int nb, int res, int stages, int pf, int bps) {
+  const size_t sm = m_plan_smem(c, nb, res != 0, stages, bps);
   if (!sm || pf < 0 || pf > 64) {
-    set_error("plan: the M-pass plan does not fit in shared memory (Gram buffers 1-2, stages 2-8, prefetch 0-64)");
+    set_error("plan: the M-pass plan does not fit in shared memory (Gram buffers 1-2, stages 2-8, boxes per "
+              "stage 1, 2 or 4, prefetch 0-64)");
     return SRM_ERR_ARG;
   }
   auto* s = static_cast<TcState*>(c->tc);
@@ -850,19 +863,21 @@ srm_status tc_set_m_plan(Ctx* c, int nb, int res, int stages, int pf) {
   s->m_res = res != 0;
   s->m_stages = stages;
   s->m_pf = pf;
+  s->m_bps = bps;
   s->m_smem = sm;
   return SRM_OK;
 }
 
-void tc_m_candidates(const Ctx* c, std::vector<std::array<int, 4>>& out) {
+void tc_m_candidates(const Ctx* c, std::vector<std::array<int, 5>>& out) {
   out.clear();
-  for (int nb = 1; nb <= 2; ++nb)
-    for (int res = 0; res <= 1; ++res)
-      for (int st = 2; st <= M_MAX_STAGES; ++st) {
-        if (!m_plan_smem(c, nb, res != 0, st)) continue;
-        out.push_back({nb, res, st, 0});
-        out.push_back({nb, res, st, M_PF});
-      }
+  for (int bps : {1, 2, 4})
+    for (int nb = 1; nb <= 2; ++nb)
+      for (int res = 0; res <= 1; ++res)
+        for (int st = 2; st <= M_MAX_STAGES; ++st) {
+          if (!m_plan_smem(c, nb, res != 0, st, bps)) continue;
+          out.push_back({nb, res, st, 0, bps});
+          if (bps == 1) out.push_back({nb, res, st, M_PF, bps});
+        }
 }
 
 srm_status tc_setup(Ctx* c) {
@@ -956,7 +971,8 @@ srm_status tc_setup(Ctx* c) {
     s->m_res = one ? res1 : res2;
     s->m_stages = (int)(one ? st1 : st2);
     s->m_pf = s->m_stages < M_PF_STAGES ? M_PF : 0;
-    s->m_smem = m_plan_smem(c, s->m_gop, s->m_res, s->m_stages);
+    s->m_bps = 1;
+    s->m_smem = m_plan_smem(c, s->m_gop, s->m_res, s->m_stages, 1);
   }
   // The E-pass leaves room on each SM for the M-step tail that runs beside it
   // on the second stream; ask for the largest shared-memory carve-out so that
@@ -1009,7 +1025,7 @@ cudaError_t launch_a_tc(Ctx* c) {
   auto* A = static_cast<__nv_bfloat16*>(c->A);
 #define M_LAUNCH(KLD, RES, GNB)                                                                                  \
   mstep_tc_kernel<KLD, RES, GNB><<<s->grid, NT, s->m_smem, c->stream>>>(                                          \
-      s->mapXm, s->mapE, s->mapAs, s->mapXp, s->d_seg, s->d_seg_off, c->T, s->m_stages,                            \
+      s->mapXm, s->mapE, s->mapAs, s->mapXp, s->d_seg, s->d_seg_off, c->T, s->m_stages, s->m_bps,                 \
       s->m_pf,                                                                                                     \
       static_cast<const uint8_t*>(c->Xh), (int64_t)c->ldT * 2, A, c->Gpart, c->status)
 #define M_LAUNCH2(KLD, RES) \

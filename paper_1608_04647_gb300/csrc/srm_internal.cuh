@@ -234,10 +234,10 @@ void tc_destroy(Ctx* c);
 int tc_default_e_reserve(const Ctx* c);
 int tc_e_reserve(const Ctx* c);
 srm_status tc_set_e_reserve(Ctx* c, int reserve);  // rebuilds the E-pass schedule
-void tc_get_m_plan(const Ctx* c, int* gram_bufs, int* resident_es, int* stages, int* prefetch);
-srm_status tc_set_m_plan(Ctx* c, int gram_bufs, int resident_es, int stages, int prefetch);
-// every M-pass plan that fits in shared memory: {gram_bufs, resident_es, stages, prefetch}
-void tc_m_candidates(const Ctx* c, std::vector<std::array<int, 4>>& out);
+void tc_get_m_plan(const Ctx* c, int* gram_bufs, int* resident_es, int* stages, int* prefetch, int* boxes);
+srm_status tc_set_m_plan(Ctx* c, int gram_bufs, int resident_es, int stages, int prefetch, int boxes);
+// every M-pass plan that fits in shared memory: {gram_bufs, resident_es, stages, prefetch, boxes per stage}
+void tc_m_candidates(const Ctx* c, std::vector<std::array<int, 5>>& out);
 cudaError_t launch_p_tc(Ctx* c);
 cudaError_t launch_a_tc(Ctx* c);
 

@@ -38,7 +38,7 @@ srm_plan current_plan(const Ctx* c) {
   srm_plan p{};
   p.single_pass = c->fused ? 1 : 0;
   p.e_reserve = tc_e_reserve(c);
-  tc_get_m_plan(c, &p.m_gram_bufs, &p.m_resident_es, &p.m_stages, &p.m_prefetch);
+  tc_get_m_plan(c, &p.m_gram_bufs, &p.m_resident_es, &p.m_stages, &p.m_prefetch, &p.m_boxes);
   p.f_prefetch = fused_get_pf(c);
   p.f_l2_hints = fused_get_hints(c);
   p.f_first_stages = fused_get_first_stages(c);
@@ -62,13 +62,13 @@ srm_status apply_plan(Ctx* c, const srm_plan& p) {
   TCK(cudaStreamSynchronize(c->stream));
   TCK(cudaStreamSynchronize(c->side));
   TCK(cudaStreamSynchronize(c->side2));
-  int nb, res, st, pf;
-  tc_get_m_plan(c, &nb, &res, &st, &pf);
-  srm_status s = tc_set_m_plan(c, p.m_gram_bufs, p.m_resident_es, p.m_stages, p.m_prefetch);
+  int nb, res, st, pf, bx;
+  tc_get_m_plan(c, &nb, &res, &st, &pf, &bx);
+  srm_status s = tc_set_m_plan(c, p.m_gram_bufs, p.m_resident_es, p.m_stages, p.m_prefetch, p.m_boxes);
   if (s != SRM_OK) return s;
   s = tc_set_e_reserve(c, p.e_reserve);
   if (s != SRM_OK) {
-    tc_set_m_plan(c, nb, res, st, pf);
+    tc_set_m_plan(c, nb, res, st, pf, bx);
     return s;
   }
   if (p.single_pass && !c->fs) TTRY(fused_setup(c));
@@ -139,9 +139,9 @@ std::string signature(const Ctx* c) {
 
 std::string plan_line(const std::string& sig, const srm_plan& p, double ms) {
   char buf[320];
-  snprintf(buf, sizeof buf, "%s sp=%d er=%d mst=%d mgb=%d mres=%d mpf=%d fpf=%d fl2=%d fsh=%d fr=%d ms=%.6f",
+  snprintf(buf, sizeof buf, "%s sp=%d er=%d mst=%d mgb=%d mres=%d mpf=%d mbx=%d fpf=%d fl2=%d fsh=%d fr=%d ms=%.6f",
            sig.c_str(), p.single_pass, p.e_reserve, p.m_stages, p.m_gram_bufs, p.m_resident_es, p.m_prefetch,
-           p.f_prefetch, p.f_l2_hints, p.f_first_stages, p.f_reserve, ms);
+           p.m_boxes, p.f_prefetch, p.f_l2_hints, p.f_first_stages, p.f_reserve, ms);
   return buf;
 }
 
@@ -150,9 +150,9 @@ bool parse_line(const std::string& line, const std::string& sig, srm_plan* p, do
   srm_plan q{};
   double t = 0;
   if (sscanf(line.c_str() + sig.size(),
-             " sp=%d er=%d mst=%d mgb=%d mres=%d mpf=%d fpf=%d fl2=%d fsh=%d fr=%d ms=%lf", &q.single_pass,
-             &q.e_reserve, &q.m_stages, &q.m_gram_bufs, &q.m_resident_es, &q.m_prefetch, &q.f_prefetch,
-             &q.f_l2_hints, &q.f_first_stages, &q.f_reserve, &t) != 11)
+             " sp=%d er=%d mst=%d mgb=%d mres=%d mpf=%d mbx=%d fpf=%d fl2=%d fsh=%d fr=%d ms=%lf",
+             &q.single_pass, &q.e_reserve, &q.m_stages, &q.m_gram_bufs, &q.m_resident_es, &q.m_prefetch,
+             &q.m_boxes, &q.f_prefetch, &q.f_l2_hints, &q.f_first_stages, &q.f_reserve, &t) != 12)
     return false;
   *p = q;
   *ms = t;
@@ -232,9 +232,9 @@ struct Report {
   void add(const char* stage, const srm_plan& p, float ms, const char* unit) {
     char buf[200];
     snprintf(buf, sizeof buf,
-             "%-6s sp=%d er=%-3d mst=%d mgb=%d mres=%d mpf=%-2d fpf=%d fl2=%d fsh=%d fr=%-2d  %9.4f %s\n", stage,
-             p.single_pass, p.e_reserve, p.m_stages, p.m_gram_bufs, p.m_resident_es, p.m_prefetch, p.f_prefetch,
-             p.f_l2_hints, p.f_first_stages, p.f_reserve, ms, unit);
+             "%-6s sp=%d er=%-3d mst=%d mgb=%d mres=%d mpf=%-2d mbx=%d fpf=%d fl2=%d fsh=%d fr=%-2d  %9.4f %s\n",
+             stage, p.single_pass, p.e_reserve, p.m_stages, p.m_gram_bufs, p.m_resident_es, p.m_prefetch,
+             p.m_boxes, p.f_prefetch, p.f_l2_hints, p.f_first_stages, p.f_reserve, ms, unit);
     os << buf;
   }
 };
@@ -252,12 +252,12 @@ srm_status search(Ctx* c, int iters, srm_plan* best_out, float* best_ms_out, Rep
   TTRY(device_status(c));
 
   // 1. M-pass plans, launch by launch (the pass is idempotent: same E[S], same A_i)
-  std::vector<std::array<int, 4>> mc;
+  std::vector<std::array<int, 5>> mc;
   tc_m_candidates(c, mc);
   float best_m = 1e30f;
   srm_plan bm = base;
   for (const auto& m : mc) {
-    TTRY(tc_set_m_plan(c, m[0], m[1], m[2], m[3]));
+    TTRY(tc_set_m_plan(c, m[0], m[1], m[2], m[3], m[4]));
     float ms = 0;
     TTRY(time_launches(c, launch_a_tc, 3, e0, e1, &ms));
     srm_plan p = base;
@@ -265,6 +265,7 @@ srm_status search(Ctx* c, int iters, srm_plan* best_out, float* best_ms_out, Rep
     p.m_resident_es = m[1];
     p.m_stages = m[2];
     p.m_prefetch = m[3];
+    p.m_boxes = m[4];
     rep.add("mpass", p, ms, "ms/launch");
     if (ms < best_m) {
       best_m = ms;

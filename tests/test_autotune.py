@@ -81,6 +81,7 @@ def test_every_plan_matches_oracle():
     o = run_oracle(d, CASE.n_iter)
     plans = [dict(single_pass=0, e_reserve=0), dict(single_pass=0, e_reserve=32),
              dict(single_pass=0, m_stages=2, m_gram_bufs=1, m_resident_es=0, m_prefetch=0),
+             dict(single_pass=0, m_stages=2, m_gram_bufs=1, m_resident_es=0, m_prefetch=0, m_boxes=4),
              dict(single_pass=1, f_prefetch=0), dict(single_pass=1, f_prefetch=3, f_l2_hints=7),
              dict(single_pass=1, f_prefetch=1, f_l2_hints=6), dict(single_pass=1, f_first_stages=1),
              dict(single_pass=1, f_first_stages=3, f_prefetch=2), dict(single_pass=1, f_first_stages=4),
@@ -98,7 +99,7 @@ def test_every_plan_matches_oracle():
     # out-of-range plans are refused before anything runs
     m = _model(d, CASE.k)
     for bad in (dict(m_stages=9), dict(m_gram_bufs=3), dict(e_reserve=-1), dict(f_prefetch=99),
-                dict(f_l2_hints=8), dict(f_first_stages=0), dict(f_first_stages=5),
+                dict(f_l2_hints=8), dict(f_first_stages=0), dict(f_first_stages=5), dict(m_boxes=3),
                 dict(single_pass=1, f_reserve=-1)):
         with pytest.raises(srm.SrmError) as ei:
             m.set_plan(**bad)
@@ -110,9 +111,11 @@ def test_pipelining_plans_are_bitwise_identical():
     # single pass's ring split change when bytes arrive, not the order of any sum
     d = make_inputs(CASE_T500)
     runs = []
-    for fields in (dict(m_stages=2, m_gram_bufs=2, m_resident_es=0, m_prefetch=0),
-                   dict(m_stages=4, m_gram_bufs=1, m_resident_es=1, m_prefetch=8),
-                   dict(m_stages=6, m_gram_bufs=2, m_resident_es=1, m_prefetch=0)):
+    for fields in (dict(m_stages=2, m_gram_bufs=2, m_resident_es=0, m_prefetch=0, m_boxes=1),
+                   dict(m_stages=4, m_gram_bufs=1, m_resident_es=1, m_prefetch=8, m_boxes=1),
+                   dict(m_stages=6, m_gram_bufs=2, m_resident_es=1, m_prefetch=0, m_boxes=1),
+                   dict(m_stages=3, m_gram_bufs=1, m_resident_es=1, m_prefetch=0, m_boxes=2),
+                   dict(m_stages=2, m_gram_bufs=1, m_resident_es=0, m_prefetch=0, m_boxes=4)):
         m = _model(d, CASE_T500.k)
         m.set_plan(single_pass=0, **fields)
         runs.append(_results(m, CASE_T500.n_iter))
