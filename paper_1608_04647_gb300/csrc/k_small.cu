@@ -1030,7 +1030,11 @@ __device__ __forceinline__ void ns_certificate(const float* __restrict__ Mb, con
   }
 }
 
-__global__ void __launch_bounds__(NS_THREADS, 1) polar_ns_kernel(int N, int k, int kld, int T, const float* __restrict__ gpart,
+// MINB CTAs per SM: 1 when every subject has an SM of its own (latency), 2
+// when subjects outnumber the SMs (throughput: half the waves, at the cost of
+// a few spilled registers)
+template <int MINB>
+__global__ void __launch_bounds__(NS_THREADS, MINB) polar_ns_kernel(int N, int k, int kld, int T, const float* __restrict__ gpart,
                                                        const int* __restrict__ gslot_off,
                                                        double* __restrict__ M64, float* __restrict__ M32,
                                                        const double* __restrict__ sqnorm,
@@ -1501,8 +1505,11 @@ void prepare_small_kernels(int max_smem) {
   cudaFuncSetAttribute(eig_kernel<4>, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   cudaFuncSetAttribute(bgemm64_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   cudaFuncSetAttribute(mtail_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mtail_smem_bytes(MT_KMAX));
-  cudaFuncSetAttribute(polar_ns_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ns_smem_bytes(NS_KMAX));
-  cudaFuncSetAttribute(polar_ns_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+  cudaFuncSetAttribute(polar_ns_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ns_smem_bytes(NS_KMAX));
+  cudaFuncSetAttribute(polar_ns_kernel<1>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(polar_ns_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ns_smem_bytes(NS_KMAX));
+  cudaFuncSetAttribute(polar_ns_kernel<2>, cudaFuncAttributePreferredSharedMemoryCarveout,
                        cudaSharedmemCarveoutMaxShared);
   cudaFuncSetAttribute(mtail_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   cudaFuncSetAttribute(phi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
@@ -1598,10 +1605,18 @@ cudaError_t launch_refine(Ctx* c) {
 bool ns_supported(const Ctx* c) { return c->k <= NS_KMAX && c->k <= MT_KMAX; }
 
 cudaError_t launch_polar(Ctx* c) {
-  polar_ns_kernel<<<c->N, NS_THREADS, ns_smem_bytes(c->k), c->stream>>>(
-      c->N, c->k, c->kld, c->T, c->Gpart, c->gslot_off, c->M64, c->M32, c->sqnorm, c->d_v, c->SigmaNext,
-      c->Sigma, c->rho2, c->scal, c->jac_sweeps, c->ns_fb, c->store == SRM_BF16 ? NS_CERT_BF16 : NS_CERT_F32,
-      c->store == SRM_BF16 ? 0 : 1, c->status);
+  const size_t sm = ns_smem_bytes(c->k);
+  const double cert = c->store == SRM_BF16 ? NS_CERT_BF16 : NS_CERT_F32;
+  const int comp = c->store == SRM_BF16 ? 0 : 1;
+  // two CTAs per SM when the subjects outnumber the SMs and two fit
+  if (c->N > c->num_sms && 2 * (sm + 1024) <= (size_t)g_max_smem)
+    polar_ns_kernel<2><<<c->N, NS_THREADS, sm, c->stream>>>(
+        c->N, c->k, c->kld, c->T, c->Gpart, c->gslot_off, c->M64, c->M32, c->sqnorm, c->d_v, c->SigmaNext,
+        c->Sigma, c->rho2, c->scal, c->jac_sweeps, c->ns_fb, cert, comp, c->status);
+  else
+    polar_ns_kernel<1><<<c->N, NS_THREADS, sm, c->stream>>>(
+        c->N, c->k, c->kld, c->T, c->Gpart, c->gslot_off, c->M64, c->M32, c->sqnorm, c->d_v, c->SigmaNext,
+        c->Sigma, c->rho2, c->scal, c->jac_sweeps, c->ns_fb, cert, comp, c->status);
   return cudaGetLastError();
 }
 

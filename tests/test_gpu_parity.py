@@ -30,6 +30,9 @@ PLAIN_CASES = [
     Case("k65-eigen-path", [1000, 1200], 131, 65, 4, seed=15),
     # the largest k the library accepts (128; the k x k kernels' shared memory)
     Case("k128-max", [1500, 1300], 300, 128, 3, seed=16),
+    # more subjects than SMs: the polar factors run two CTAs per SM
+    Case("subjects-beyond-sms", [int(x) for x in np.random.default_rng(18).integers(80, 200, size=200)], 120, 30, 3,
+         seed=18),
     # more subjects than E-step reduction groups: several subjects per group
     Case("grouped-subjects", [int(x) for x in np.random.default_rng(11).integers(40, 250, size=150)], 1500, 8, 4,
          seed=11),

@@ -24,6 +24,9 @@ TC_CASES = [
     Case("k64-boundary", [900, 1300], 130, 64, 4, seed=14),
     Case("k65-eigen-path", [1000, 1200], 131, 65, 4, seed=15),
     Case("k50-scaled-1e4", [2500, 3100, 2000], 500, 50, 4, seed=13, scale=1e4),
+    # more subjects than SMs: the polar factors run two CTAs per SM
+    Case("subjects-beyond-sms", [int(x) for x in np.random.default_rng(18).integers(80, 200, size=200)], 120, 30, 3,
+         seed=18),
     # the largest k (128), and with 310 subjects: one band per matrix in the
     # FP64 k x k products would not fit in shared memory.  v_i >= 300: with
     # v_i close to k, A_i is nearly square and cond(A_i) amplifies the BF16
