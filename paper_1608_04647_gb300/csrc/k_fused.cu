@@ -62,9 +62,7 @@ constexpr int F_PF = 0;               // L2 prefetch distance (tiles)
 // phase-2 loads (the tile's last use) evict first, A_i stores evict first
 constexpr int F_HINT_KEEP = 1, F_HINT_DROP = 2, F_HINT_STORE = 4;
 constexpr int F_HINTS = 0;
-// Default ring split: with clusters (T > 512) one A_tile buffer fits, the
-// epilogue of tile n then waits for phase 2 of tile n - 1, and the shared ring
-// (4) is faster; one CTA per tile runs two rings of 2 stages each.
+// Default ring split (the tuner replaces it): two rings of 2 stages each.
 constexpr int F_SH = 2;
 
 struct SegF {
@@ -75,21 +73,21 @@ struct SegF {
   int pad;
 };
 
-// Four stages in both forms: with C = 2 the exchange buffer takes the room
-// of a second A_tile buffer, so phase 1's epilogue of tile n + 1 waits for
-// phase 2 of tile n to release the single one (it has phase 1 of tile n + 2
-// to finish before phase 2 of n + 1 needs it).
+// Four 32 KB stages in both forms.
 template <int C>
 constexpr int f_stages() {
   return 4;
 }
+// Two A_tile buffers in both forms.  With C = 2 the other CTA's FP32 partial
+// rows (64 rows x 64 features, 16 KB) land in the A_tile buffer that their
+// sum will fill, so no separate exchange buffer is needed.
 template <int C>
 constexpr int f_gops() {
-  return C == 1 ? 2 : 1;
+  return 2;
 }
 template <int C>
 constexpr size_t f_smem_bytes() {
-  return 1024 + (size_t)f_stages<C>() * F_STAGE + f_gops<C>() * F_GOP + (C == 2 ? F_EXCH : 0) + 8 * F_ECH + 256;
+  return 1024 + (size_t)f_stages<C>() * F_STAGE + f_gops<C>() * F_GOP + 8 * F_ECH + 256;
 }
 static_assert(f_smem_bytes<1>() <= 232448 && f_smem_bytes<2>() <= 232448, "fused pass shared memory");
 
@@ -135,8 +133,7 @@ __global__ void __launch_bounds__(FT, 1)
   // MMA reads M = 128 "features" from a tile and the 16 KB that follow it;
   // rows 64..127 of its accumulator are never read.
   uint8_t* gop = smem + S_N * F_STAGE;
-  uint8_t* exch = gop + NG * F_GOP;                      // C == 2 only
-  uint8_t* eres = exch + (C == 2 ? F_EXCH : 0u);          // E[S] chunks of this CTA's T-block
+  uint8_t* eres = gop + NG * F_GOP;                        // E[S] chunks of this CTA's T-block
   uint64_t* full = reinterpret_cast<uint64_t*>(eres + 8 * F_ECH);
   uint64_t* empty = full + S_N;
   uint64_t* acc_full = empty + S_N;    // [2] phase-1 accumulators
@@ -147,8 +144,8 @@ __global__ void __launch_bounds__(FT, 1)
   uint64_t* p_empty = p_full + 1;
   uint64_t* gram_full = p_empty + 1;
   uint64_t* gram_empty = gram_full + 1;
-  uint64_t* exch_full = gram_empty + 1;  // the other CTA's partial rows have arrived
-  uint64_t* exch_free = exch_full + 1;   // the other CTA has read the rows this CTA sent
+  uint64_t* exch_full = gram_empty + 1;  // the other CTA's partial rows have arrived (in the A_tile buffer)
+  uint64_t* exch_free = exch_full + 1;   // the other CTA has read the partial rows this CTA sent
   uint64_t* e_full = exch_free + 1;
   uint64_t* done = e_full + 1;          // [2] every MMA of the phase-1 / phase-2 issuer has completed
   uint64_t* epi_bar = done + 2;
@@ -560,7 +557,7 @@ __global__ void __launch_bounds__(FT, 1)
     const bool owner = C == 1 || (uint32_t)(row >> 6) == rank;
     const bool leader = C == 1 ? threadIdx.x == 64 : (owner && lane == 0 && (q & 1) == 0);
     uint32_t af_ph[2] = {0, 0}, gfr_ph[2] = {0, 0}, pf_ph = 0, gfl_ph = 0, ef_ph = 0, ex_ph = 0, eb_ph = 0,
-             ob_ph = 0;
+             ob_ph = 0, cp_ph = 0;
     bool used[2] = {false, false};  // A_tile buffers used (final wait for their release)
     bool ok = true;
     auto epi_sync = [&]() -> bool {  // the four epilogue warps
@@ -579,9 +576,9 @@ __global__ void __launch_bounds__(FT, 1)
     };
     // A_i is not read again in the pass: its lines go first
     const uint64_t pol_store = (hints & F_HINT_STORE) ? l2_evict_first() : l2_evict_normal();
-    uint32_t peer_exch = 0, peer_exch_full = 0, peer_exch_free = 0;
+    uint32_t peer_gop = 0, peer_exch_full = 0, peer_exch_free = 0;
     if (C == 2) {
-      peer_exch = mapa_shared(smem_u32(exch), peer);
+      peer_gop = mapa_shared(smem_u32(gop), peer);
       peer_exch_full = mapa_shared(smem_u32(exch_full), peer);
       peer_exch_free = mapa_shared(smem_u32(exch_free), peer);
     }
@@ -601,14 +598,21 @@ __global__ void __launch_bounds__(FT, 1)
       if (lane == 0) mbar_arrive(&acc_empty[a]);
       uint8_t* gb = gop + b * F_GOP;
       if (C == 2 && !owner) {
-        // partial row for the CTA that completes it
+        // partial row for the CTA that completes it, into that CTA's A_tile
+        // buffer b: free once phase 2 of tile n - NG is done in both CTAs
+        // (gop_free is signalled to both), and once the other CTA has read
+        // the partials of the previous tile (exch_full counts one tile's
+        // bytes at a time)
+        if (!warp_wait_cl(&gop_free[b], gfr_ph[b] ^ 1u, abort_s, status)) return false;
+        gfr_ph[b] ^= 1u;
         if (!warp_wait_cl(exch_free, ef_ph ^ 1u, abort_s, status)) return false;
         ef_ph ^= 1u;
         const int prow = row - 64 * (int)peer;
+        const uint32_t dst = peer_gop + (uint32_t)b * F_GOP;
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
           const uint32_t off = (uint32_t)prow * 256u + (uint32_t)((u ^ (prow & 15)) * 16);
-          st_async_v4(peer_exch + off, __float_as_uint(v[4 * u]), __float_as_uint(v[4 * u + 1]),
+          st_async_v4(dst + off, __float_as_uint(v[4 * u]), __float_as_uint(v[4 * u + 1]),
                       __float_as_uint(v[4 * u + 2]), __float_as_uint(v[4 * u + 3]), peer_exch_full);
         }
         return true;
@@ -622,7 +626,7 @@ __global__ void __launch_bounds__(FT, 1)
         if (!warp_wait_cl(exch_full, ex_ph, abort_s, status)) return false;
         ex_ph ^= 1u;
         const int orow = row - 64 * (int)rank;
-        const float4* src = reinterpret_cast<const float4*>(exch + orow * 256);
+        const float4* src = reinterpret_cast<const float4*>(gb + orow * 256);
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
           const float4 w = src[u ^ (orow & 15)];
@@ -631,7 +635,7 @@ __global__ void __launch_bounds__(FT, 1)
           v[4 * u + 2] += w.z;
           v[4 * u + 3] += w.w;
         }
-        if (!own_sync()) return false;  // every owner row has read the exchange buffer
+        if (!own_sync()) return false;  // every owner row has read the partials
         if (leader) mbar_arrive_remote(peer_exch_free);
       } else {
         if (!epi_sync()) return false;
@@ -648,6 +652,12 @@ __global__ void __launch_bounds__(FT, 1)
       }
       fence_proxy_async_smem();
       if (C == 2 ? !own_sync() : !epi_sync()) return false;
+      if (C == 2) {
+        // the other CTA has read the partials this CTA sent into its buffer b
+        // before this CTA's rows land there
+        if (!warp_wait_cl(exch_free, cp_ph, abort_s, status)) return false;
+        cp_ph ^= 1u;
+      }
       if (leader) {
         if (C == 2) {
           const uint32_t o = rank * 64u * 128u;
@@ -937,7 +947,7 @@ srm_status fused_setup(Ctx* c) {
     cudaFuncSetAttribute(fpass_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f_smem_bytes<2>());
   else
     cudaFuncSetAttribute(fpass_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f_smem_bytes<1>());
-  f->s_h = C == 2 ? 4 : F_SH;
+  f->s_h = F_SH;
   bool ok = bf16_map(&f->mapX, c->Xh, c->T, c->Vpad_tot, (uint64_t)c->ldT * 2, 64, 128) &&
             bf16_map(&f->mapE, c->ESb, c->T, 64, (uint64_t)c->ldT * 2, 64, 64) &&
             bf16_map(&f->mapAs, c->A, 64, c->Vpad_tot, 64 * 2, 64, 128 / C) &&
