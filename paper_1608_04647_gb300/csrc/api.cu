@@ -21,7 +21,7 @@ thread_local std::string g_err;
 
 const char* const kKernelNames[KK_COUNT] = {
     "center", "estep_simt", "estep_tc", "ereduce", "sigma", "phi",
-    "mstep_simt", "mstep_tc", "eig", "refine", "rho", "mtail", "polar", "fpass_tc"};
+    "mstep_simt", "mstep_tc", "eig", "refine", "rho", "mtail", "polar", "fpass_tc", "psum"};
 
 void set_error(const std::string& msg) { g_err = msg; }
 
@@ -44,7 +44,7 @@ void prof_begin(Ctx* c, int kind, int* ev0) {
 }
 
 // CUDA kernels behind one launcher call of each kind
-static const int kKernelsPerKind[KK_COUNT] = {1, 1, 1, 2, 1, 1, 1, 1, 1, 4, 4, 1, 1, 1};
+static const int kKernelsPerKind[KK_COUNT] = {1, 1, 1, 2, 1, 1, 1, 1, 1, 4, 4, 1, 1, 1, 1};
 
 void prof_end(Ctx* c, int kind, int ev0) {
   const int ev1 = c->ev_next++;
@@ -101,7 +101,7 @@ void free_all(Ctx* c) {
                   c->Phi, c->scal, c->M64, c->M32, c->Uwarm, c->G64, c->U64, c->H64, c->Xr64, c->eigv, c->Y,
                   c->ES64, c->ESt, c->ESb, c->esPart, c->ll, c->iter, c->status, c->Ppart, c->chunk_src, c->jac_sweeps, c->ns_fb,
                   c->chunk_src_off, c->Ypart, c->sPart, c->map_buf, c->Phi32, c->Gpart, c->gslot_off, c->tr_buf, c->tr_part,
-                  c->f_ppart, c->f_chunk_src, c->f_chunk_src_off};
+                  c->f_ppart, c->f_chunk_src, c->f_chunk_src_off, c->psum, c->psum_src, c->psum_src_off};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -254,6 +254,26 @@ namespace {
 // run first, then the reduction.  Sigma_s^new and its eigen-decomposition ran
 // beside the pass.
 srm_status do_estep_fused(Ctx* c) {
+  if (c->p_from_f && c->side_pending && c->sig_eig_done && !c->sigma_pending && c->psum) {
+    // after a single pass: its slot sums (which need no M_i) on the context
+    // stream beside the polar factors and Phi on the second, then the
+    // reduction from the sums
+    CK(cudaEventRecord(c->ev_fork, c->stream));
+    CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    {
+      OnStream on(c, c->side);
+      TRY(do_polar(c));
+      LAUNCH(c, KK_PHI, launch_phi(c));
+    }
+    CK(cudaEventRecord(c->ev_join, c->side));
+    LAUNCH(c, KK_P_SUM, launch_p_sum(c));
+    CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    c->side_pending = false;
+    c->sig_eig_done = false;
+    LAUNCH(c, KK_P_REDUCE, launch_p_reduce_from(c, true));
+    c->sigma_pending = true;
+    return SRM_OK;
+  }
   if (c->side_pending || c->sigma_pending) TRY(flush_pending(c));
   if (!c->p_from_f) LAUNCH(c, KK_P_TC, launch_p_tc(c));
   LAUNCH(c, KK_P_REDUCE, launch_p_reduce(c));

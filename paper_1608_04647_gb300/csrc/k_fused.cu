@@ -962,6 +962,26 @@ srm_status fused_setup(Ctx* c) {
   f->m_gslot_off = c->gslot_off;
   f->m_ngslots = c->n_gslots;
   f->m_gel = c->Gpart_elems;
+  // the pass's partials summed per (subject, chunk), and the table that
+  // gives the E-step reduction one source per (subject, chunk) among them
+  {
+    const int64_t nb = (int64_t)c->N * c->nchunk;
+    std::vector<ChunkSrc> src((size_t)nb);
+    std::vector<int> off((size_t)nb + 1);
+    for (int64_t j = 0; j < nb; ++j) {
+      src[(size_t)j].off = j * TCH * 64;
+      off[(size_t)j] = (int)j;
+    }
+    off[(size_t)nb] = (int)nb;
+    srm_status st;
+    if ((st = upload_vec(&c->psum_src, src, "slot-sum table")) != SRM_OK) return st;
+    if ((st = upload_vec(&c->psum_src_off, off, "slot-sum table offsets")) != SRM_OK) return st;
+    if (cudaMalloc(&c->psum, sizeof(float) * (size_t)nb * TCH * 64) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaMalloc failed for the single pass's slot sums");
+      return SRM_ERR_NOMEM;
+    }
+  }
   return fused_build(c, fused_clusters(c, C, F_RESERVE));
 }
 

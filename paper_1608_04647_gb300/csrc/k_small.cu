@@ -213,43 +213,85 @@ __global__ void __launch_bounds__(256) p_reduce_kernel(EReduceArgs ar) {
 }
 
 
-// Block reduction of three doubles over blockDim.x (a power of two <= 256) threads.
-__device__ void block_sum3(double& a, double& b, double& c) {
-  __shared__ double red[3][256];
-  const int tid = threadIdx.x;
-  red[0][tid] = a;
-  red[1][tid] = b;
-  red[2][tid] = c;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (tid < s) {
-      red[0][tid] += red[0][tid + s];
-      red[1][tid] += red[1][tid + s];
-      red[2][tid] += red[2][tid + s];
+
+// p_sum: grid (nchunk, N), 256 threads.  Block (c, i) sums subject i's
+// partial blocks of t-chunk c in slot order (the order p_reduce uses) into
+// psum[i][c].  It needs no M_i, so it runs beside the polar factors; p_reduce
+// then reads one block per (subject, chunk), and 0 + psum = psum exactly:
+// the result is bitwise that of p_reduce on the slots.
+template <int FW>
+__global__ void __launch_bounds__(256) p_sum_kernel(int nchunk, const float* __restrict__ part,
+                                                    const ChunkSrc* __restrict__ src,
+                                                    const int* __restrict__ src_off, float* __restrict__ psum) {
+  constexpr int KLD = 16 * FW;
+  const int c = blockIdx.x, i = blockIdx.y, tid = threadIdx.x;
+  const int b = src_off[i * nchunk + c], en = src_off[i * nchunk + c + 1];
+  float4 a4[FW];
+#pragma unroll
+  for (int j = 0; j < FW; ++j) a4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int q = b; q < en; q += 2) {
+    const int64_t o0 = src[q].off;
+    const bool two = q + 1 < en;
+    const int64_t o1 = two ? src[q + 1].off : o0;
+    float4 v0[FW], v1[FW];
+#pragma unroll
+    for (int j = 0; j < FW; ++j) {
+      v0[j] = __ldg(reinterpret_cast<const float4*>(part + o0) + tid + 256 * j);
+      v1[j] = two ? __ldg(reinterpret_cast<const float4*>(part + o1) + tid + 256 * j) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < FW; ++j) {
+      a4[j].x += v0[j].x;
+      a4[j].y += v0[j].y;
+      a4[j].z += v0[j].z;
+      a4[j].w += v0[j].w;
+      if (two) {
+        a4[j].x += v1[j].x;
+        a4[j].y += v1[j].y;
+        a4[j].z += v1[j].z;
+        a4[j].w += v1[j].w;
+      }
+    }
   }
-  a = red[0][0];
-  b = red[1][0];
-  c = red[2][0];
+  float4* out = reinterpret_cast<float4*>(psum + ((int64_t)i * nchunk + c) * TCH * KLD);
+#pragma unroll
+  for (int j = 0; j < FW; ++j) out[tid + 256 * j] = a4[j];
+}
+
+// Sum over the 256 threads of a block in a fixed order (warp shuffles, then
+// the eight warp sums in order); every thread receives the result.
+__device__ __forceinline__ double block_sum_fixed(double v, double* red8) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red8[threadIdx.x >> 5] = v;
   __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) s += red8[w];
+  __syncthreads();
+  return s;
 }
 
 // grid k blocks (row a of Phi), 256 threads.
 //   Sigma_s = U (Lambda + E) U^T with U = Us, G' = Lambda + E = Gp (k x k).
 //   Phi = U (g(Lambda) + F o E) U^T,  g(x) = x/(1 + rho0 x),
 //   F_bd = g[lambda_b, lambda_d] = 1 / ((1 + rho0 lambda_b)(1 + rho0 lambda_d)).
+// Each of the two k-term inner products per output is split over the lanes
+// of a warp and combined by shuffles: the kernel is latency-bound (FP64 at
+// about 2 FMA per clock per SM), so short dependent chains matter more than
+// the operation count.
 __global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __restrict__ rho2,
                                                   const double* __restrict__ sqnorm,
                                                   const int64_t* __restrict__ vox, const double* __restrict__ Us,
                                                   const double* __restrict__ Gp, double* __restrict__ Phi,
                                                   float* __restrict__ Phi32, double* __restrict__ scal, int* status) {
   extern __shared__ double ph_smem[];
+  __shared__ double red8[8];
   double* w = ph_smem;          // [k]  1 / (1 + rho0 lambda)
-  double* ua = w + k;           // [k]  row a of U
-  double* tv = ua + k;          // [k]  (U[a,:] B)
+  double* uw = w + k;           // [k]  U[a][b] w_b
+  double* tv = uw + k;          // [k]  (U[a,:] B)
   double* Gps = tv + k;         // [k][k] G', symmetrised (U is read from global memory)
-  const int a = blockIdx.x, tid = threadIdx.x;
+  const int a = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int e = tid; e < k * k; e += blockDim.x) {
     const int b = e / k, d = e % k;
     Gps[e] = 0.5 * (Gp[b * k + d] + Gp[d * k + b]);
@@ -264,28 +306,43 @@ __global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __
       s2 += sqnorm[i] / r;
     }
   }
-  block_sum3(s0, s1, s2);
-  const double rho0 = s0;
+  const double rho0 = block_sum_fixed(s0, red8);
+  if (a == 0) {
+    s1 = block_sum_fixed(s1, red8);
+    s2 = block_sum_fixed(s2, red8);
+  }
   for (int b = tid; b < k; b += blockDim.x) {
-    w[b] = 1.0 / (1.0 + rho0 * Gp[b * k + b]);
-    ua[b] = Us[a * k + b];
+    const double wb = 1.0 / (1.0 + rho0 * Gp[b * k + b]);
+    w[b] = wb;
+    uw[b] = Us[a * k + b] * wb;
   }
   __syncthreads();
-  // tv[d] = sum_b U[a][b] B[b][d],  B_bd = (b == d) ? lambda_b w_b : w_b w_d G'_bd
-  for (int d = tid; d < k; d += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < k; ++b) s = fma(ua[b] * w[b], Gps[b * k + d], s);
-    // the diagonal term: lambda_d w_d (not w_d^2 lambda_d)
-    s = (s - ua[d] * w[d] * Gps[d * k + d]) * w[d] + ua[d] * Gps[d * k + d] * w[d];
-    tv[d] = s;
+  // tv[d] = sum_b U[a][b] B[b][d],  B_bd = (b == d) ? lambda_b w_b : w_b w_d G'_bd;
+  // one warp per d, the b-sum over its lanes
+  for (int d = warp; d < k; d += 8) {
+    double sp = 0.0;
+    // G' is symmetric: read row d (consecutive b across the lanes, no bank conflicts)
+    for (int b = lane; b < k; b += 32) sp = fma(uw[b], Gps[d * k + b], sp);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
+    if (lane == 0) {
+      // the diagonal term: lambda_d w_d (not w_d^2 lambda_d)
+      const double gdd = Gps[d * k + d];
+      tv[d] = (sp - uw[d] * gdd) * w[d] + uw[d] * gdd;
+    }
   }
   __syncthreads();
-  for (int cc = tid; cc < k; cc += blockDim.x) {
-    double s = 0.0;
-    for (int d = 0; d < k; ++d) s = fma(tv[d], Us[cc * k + d], s);
-    if (!isfinite(s)) flag(status, ST_NONFINITE);
-    Phi[a * k + cc] = s;
-    Phi32[a * k + cc] = (float)s;
+  // Phi[a][c] = sum_d tv[d] U[c][d]: one warp per c, the d-sum over its lanes
+  for (int cc = warp; cc < k; cc += 8) {
+    double sp = 0.0;
+    for (int d = lane; d < k; d += 32) sp = fma(tv[d], Us[cc * k + d], sp);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
+    if (lane == 0) {
+      if (!isfinite(sp)) flag(status, ST_NONFINITE);
+      Phi[a * k + cc] = sp;
+      Phi32[a * k + cc] = (float)sp;
+    }
   }
   if (a == 0) {
     double ld = 0.0;
@@ -294,8 +351,7 @@ __global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __
       if (!(lam > 0.0)) flag(status, ST_NOT_PD);
       ld += log1p(rho0 * lam);
     }
-    double z0 = 0.0, z1 = 0.0;
-    block_sum3(ld, z0, z1);
+    ld = block_sum_fixed(ld, red8);
     if (tid == 0) {
       scal[SC_RHO0] = rho0;
       scal[SC_LOGDET] = ld;
@@ -1520,7 +1576,21 @@ int zsum_groups(int N, int nchunk, int num_sms) {
   return std::max(1, std::min(N, std::min(128, want)));
 }
 
-cudaError_t launch_p_reduce(Ctx* c) {
+cudaError_t launch_p_sum(Ctx* c) {
+  const dim3 grid(c->nchunk, c->N);
+  switch (c->kld) {
+#define PS_CASE(FW) \
+  case 16 * FW: p_sum_kernel<FW><<<grid, 256, 0, c->stream>>>(c->nchunk, c->f_ppart, c->f_chunk_src, c->f_chunk_src_off, c->psum); break;
+    PS_CASE(4)
+#undef PS_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_p_reduce(Ctx* c) { return launch_p_reduce_from(c, false); }
+
+cudaError_t launch_p_reduce_from(Ctx* c, bool from_sums) {
   const size_t sm = sizeof(float) * ((size_t)c->kld * c->kld + TCH * (c->kld + 1));
   const dim3 grid(c->nchunk, c->zgroups);
   EReduceArgs ar;
@@ -1529,9 +1599,9 @@ cudaError_t launch_p_reduce(Ctx* c) {
   ar.T = c->T;
   ar.k = c->k;
   ar.nchunk = c->nchunk;
-  ar.part = c->p_from_f ? c->f_ppart : c->Ppart;
-  ar.src = c->p_from_f ? c->f_chunk_src : c->chunk_src;
-  ar.src_off = c->p_from_f ? c->f_chunk_src_off : c->chunk_src_off;
+  ar.part = from_sums ? c->psum : c->p_from_f ? c->f_ppart : c->Ppart;
+  ar.src = from_sums ? c->psum_src : c->p_from_f ? c->f_chunk_src : c->chunk_src;
+  ar.src_off = from_sums ? c->psum_src_off : c->p_from_f ? c->f_chunk_src_off : c->chunk_src_off;
   ar.M32 = c->M32;
   ar.rho2 = c->rho2;
   ar.ypart = c->Ypart;

@@ -45,6 +45,7 @@ enum KernelKind : int {
   KK_MTAIL,
   KK_POLAR,
   KK_FPASS,
+  KK_P_SUM,
   KK_COUNT
 };
 extern const char* const kKernelNames[KK_COUNT];
@@ -143,6 +144,10 @@ struct Ctx {
   float* f_ppart = nullptr;
   ChunkSrc* f_chunk_src = nullptr;
   int* f_chunk_src_off = nullptr;
+  // its partials summed per (subject, chunk) and the one-source table over them
+  float* psum = nullptr;
+  ChunkSrc* psum_src = nullptr;
+  int* psum_src_off = nullptr;
 
   // ---- host bookkeeping
   int n_ll = 0;            // E-steps launched
@@ -208,6 +213,9 @@ cudaError_t launch_a_simt(Ctx* c, int subject);
 int zsum_groups(int N, int nchunk, int num_sms);
 int es_blocks(int T);
 cudaError_t launch_p_reduce(Ctx* c);
+// the single pass's slot sums (beside the polar factors), then the reduction from them
+cudaError_t launch_p_sum(Ctx* c);
+cudaError_t launch_p_reduce_from(Ctx* c, bool from_sums);
 cudaError_t launch_sigma(Ctx* c);
 cudaError_t launch_phi(Ctx* c);
 cudaError_t launch_eig(Ctx* c);
