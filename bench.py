@@ -340,6 +340,9 @@ def run_ours(args, rank, world):
         "gpu_launches": int(round(kernels_per_step * args.steps)),
         "clocks": clocks,
         "kernels_ms_per_step": {n: round(v["ms"] / args.steps, 4) for n, v in ks.items()},
+        "kernels_note": "CUDA-event time per step of each kernel kind on the stream it runs on (SRM_PROFILE run "
+                        "of the same steps); kinds on the second and third streams (sigma, eig, mtail, refine, rho, "
+                        "polar, phi where they run beside a streaming pass) include time spent waiting for SMs",
         "ll_monotone": results[head]["ll_monotone"],
     }
     if "f32" in results and head != "f32":
