@@ -276,6 +276,9 @@ typedef struct {
                                beside it (the pass runs on the rest, in whole clusters) */
     int32_t m_boxes;        /* M-pass: consecutive 64-column boxes of the same 128 rows of X^
                                per stage, 1, 2 or 4 (longer contiguous reads per row) */
+    int32_t f_lead;         /* single pass with two rings: tiles the first read of X^ may run
+                               ahead of the second (which then finds the tile in L2), 1..4;
+                               0 = no limit */
 } srm_plan;
 
 /* srm_get_plan -- the plan the context runs.  SRM_ERR_UNSUPPORTED for the plain

@@ -87,7 +87,7 @@ constexpr int f_gops() {
 }
 template <int C>
 constexpr size_t f_smem_bytes() {
-  return 1024 + (size_t)f_stages<C>() * F_STAGE + f_gops<C>() * F_GOP + 8 * F_ECH + 256;
+  return 1024 + (size_t)f_stages<C>() * F_STAGE + f_gops<C>() * F_GOP + 8 * F_ECH + 320;
 }
 static_assert(f_smem_bytes<1>() <= 232448 && f_smem_bytes<2>() <= 232448, "fused pass shared memory");
 
@@ -117,7 +117,8 @@ template <int C>
 __global__ void __launch_bounds__(FT, 1)
     fpass_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE,
                  const __grid_constant__ CUtensorMap mapAs, const __grid_constant__ CUtensorMap mapXp,
-                 const SegF* __restrict__ segs, const int* __restrict__ seg_off, int T, int s_h, int pf_dist, int hints,
+                 const SegF* __restrict__ segs, const int* __restrict__ seg_off, int T, int s_h, int lead,
+                 int pf_dist, int hints,
                  float* __restrict__ ppart, float* __restrict__ gpart, int* status) {
   constexpr int S_N = f_stages<C>();
   constexpr int NG = f_gops<C>();
@@ -150,7 +151,8 @@ __global__ void __launch_bounds__(FT, 1)
   uint64_t* done = e_full + 1;          // [2] every MMA of the phase-1 / phase-2 issuer has completed
   uint64_t* epi_bar = done + 2;
   uint64_t* own_bar = epi_bar + 1;
-  uint32_t* tmem_s = reinterpret_cast<uint32_t*>(own_bar + 1);
+  uint64_t* tdone = own_bar + 1;  // [4] phase 2 of tile n done (slot n % 4; two rings only)
+  uint32_t* tmem_s = reinterpret_cast<uint32_t*>(tdone + 4);
   volatile int* abort_s = reinterpret_cast<volatile int*>(tmem_s + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -183,6 +185,7 @@ __global__ void __launch_bounds__(FT, 1)
     mbar_init(e_full, 1);
     mbar_init(&done[0], 1);
     mbar_init(&done[1], 1);
+    for (int q = 0; q < 4; ++q) mbar_init(&tdone[q], 1);
     mbar_init(epi_bar, 4);
     mbar_init(own_bar, 2);
     *abort_s = 0;
@@ -405,9 +408,19 @@ __global__ void __launch_bounds__(FT, 1)
       };
       if (first)
         for (int q = 0; q < pf_dist; ++q) pf_issue();
+      int64_t tn = 0;  // tile counter
       for (int g = g0; g < g1 && ok; ++g)
-        for (int64_t tile = segs[g].tile_begin; tile < segs[g].tile_end && ok; ++tile) {
+        for (int64_t tile = segs[g].tile_begin; tile < segs[g].tile_end && ok; ++tile, ++tn) {
           if (first && pf_dist > 0) pf_issue();
+          // the first read of tile n waits for phase 2 of tile n - lead: the
+          // second read then comes soon enough to find the lines in L2
+          if (first && lead > 0 && tn >= lead) {
+            const int64_t m = tn - lead;
+            if (!mbar_wait(&tdone[m & 3], (uint32_t)((m >> 2) & 1), abort_s, status, ST_TIMEOUT)) {
+              ok = false;
+              break;
+            }
+          }
           for (int j = 0; j < nk2; ++j) {
             const int si = sbase + s;
             if (!mbar_wait(&empty[si], ph ^ 1u, abort_s, status, ST_TIMEOUT)) {
@@ -542,6 +555,7 @@ __global__ void __launch_bounds__(FT, 1)
             mma_commit_mc(&gop_free[b], (uint16_t)0x3);
           else
             mma_commit(&gop_free[b]);
+          mma_commit(&tdone[n & 3]);
           if (last) {
             mma_commit(p_full);
             mma_commit(gram_full);
@@ -789,6 +803,7 @@ struct FState {
   int pf = F_PF;  // L2 prefetch distance (tiles)
   int hints = F_HINTS;
   int s_h = F_SH;  // stages of the first-read ring (the second-read ring has the rest)
+  int lead = 0;    // tiles the first read may run ahead of phase 2 (0: no limit; two rings only)
   // Gram slots of the two forms; the context points at the active form's
   float* f_gpart = nullptr;
   int* f_gslot_off = nullptr;
@@ -1015,6 +1030,10 @@ void fused_select(Ctx* c, bool on) {
 int fused_get_pf(const Ctx* c) { return c->fs ? static_cast<const FState*>(c->fs)->pf : F_PF; }
 int fused_get_hints(const Ctx* c) { return c->fs ? static_cast<const FState*>(c->fs)->hints : F_HINTS; }
 int fused_get_first_stages(const Ctx* c) { return c->fs ? static_cast<const FState*>(c->fs)->s_h : F_SH; }
+int fused_get_lead(const Ctx* c) { return c->fs ? static_cast<const FState*>(c->fs)->lead : 0; }
+void fused_set_lead(Ctx* c, int lead) {
+  if (c->fs) static_cast<FState*>(c->fs)->lead = lead;
+}
 void fused_set_first_stages(Ctx* c, int s_h) {
   if (c->fs) static_cast<FState*>(c->fs)->s_h = s_h;
 }
@@ -1044,7 +1063,7 @@ cudaError_t launch_fpass(Ctx* c) {
   if (!f) return cudaErrorInvalidValue;
   if (f->C == 1) {
     fpass_kernel<1><<<f->clusters, FT, f_smem_bytes<1>(), c->stream>>>(
-        f->mapX, f->mapE, f->mapAs, f->mapXp, f->d_seg, f->d_seg_off, c->T, f->s_h, f->pf, f->hints, c->f_ppart, c->Gpart, c->status);
+        f->mapX, f->mapE, f->mapAs, f->mapXp, f->d_seg, f->d_seg_off, c->T, f->s_h, f->lead, f->pf, f->hints, c->f_ppart, c->Gpart, c->status);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
@@ -1060,7 +1079,7 @@ cudaError_t launch_fpass(Ctx* c) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, fpass_kernel<2>, f->mapX, f->mapE, f->mapAs, f->mapXp, (const SegF*)f->d_seg,
-                            (const int*)f->d_seg_off, c->T, f->s_h, f->pf, f->hints, c->f_ppart, c->Gpart, c->status);
+                            (const int*)f->d_seg_off, c->T, f->s_h, f->lead, f->pf, f->hints, c->f_ppart, c->Gpart, c->status);
 }
 
 }  // namespace srm

@@ -284,18 +284,22 @@ __global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __
                                                   const double* __restrict__ sqnorm,
                                                   const int64_t* __restrict__ vox, const double* __restrict__ Us,
                                                   const double* __restrict__ Gp, double* __restrict__ Phi,
-                                                  float* __restrict__ Phi32, double* __restrict__ scal, int* status) {
+                                                  float* __restrict__ Phi32, double* __restrict__ scal, int u_smem,
+                                                  int* status) {
   extern __shared__ double ph_smem[];
   __shared__ double red8[8];
   double* w = ph_smem;          // [k]  1 / (1 + rho0 lambda)
   double* uw = w + k;           // [k]  U[a][b] w_b
   double* tv = uw + k;          // [k]  (U[a,:] B)
-  double* Gps = tv + k;         // [k][k] G', symmetrised (U is read from global memory)
+  double* Gps = tv + k;         // [k][k] G', symmetrised
+  double* Uss = Gps + k * k;    // [k][k] U when it fits (u_smem), else U is read from global memory
   const int a = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int e = tid; e < k * k; e += blockDim.x) {
     const int b = e / k, d = e % k;
     Gps[e] = 0.5 * (Gp[b * k + d] + Gp[d * k + b]);
+    if (u_smem) Uss[e] = Us[e];
   }
+  const double* Ur = u_smem ? Uss : Us;
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
   for (int i = tid; i < N; i += blockDim.x) {
     const double r = rho2[i];
@@ -335,7 +339,7 @@ __global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __
   // Phi[a][c] = sum_d tv[d] U[c][d]: one warp per c, the d-sum over its lanes
   for (int cc = warp; cc < k; cc += 8) {
     double sp = 0.0;
-    for (int d = lane; d < k; d += 32) sp = fma(tv[d], Us[cc * k + d], sp);
+    for (int d = lane; d < k; d += 32) sp = fma(tv[d], Ur[cc * k + d], sp);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
     if (lane == 0) {
@@ -1630,9 +1634,13 @@ cudaError_t launch_sigma(Ctx* c) {
 
 cudaError_t launch_phi(Ctx* c) {
   const int64_t kk = (int64_t)c->k * c->k;
-  const size_t sm = sizeof(double) * (3 * c->k + c->k * c->k);
+  // U in shared memory beside G' when both fit (k <= 119 on this part)
+  const size_t sm1 = sizeof(double) * (3 * c->k + c->k * c->k);
+  const bool u_smem = sm1 + sizeof(double) * c->k * c->k + 8 * 1024 <= (size_t)g_max_smem;
+  const size_t sm = u_smem ? sm1 + sizeof(double) * c->k * c->k : sm1;
   phi_kernel<<<c->k, 256, sm, c->stream>>>(c->N, c->k, c->rho2, c->sqnorm, c->d_v, c->Xr64 + c->N * kk,
-                                           c->G64 + c->N * kk, c->Phi, c->Phi32, c->scal, c->status);
+                                           c->G64 + c->N * kk, c->Phi, c->Phi32, c->scal, u_smem ? 1 : 0,
+                                           c->status);
   return cudaGetLastError();
 }
 

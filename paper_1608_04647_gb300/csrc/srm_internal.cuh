@@ -260,6 +260,8 @@ int fused_get_hints(const Ctx* c);     // L2 eviction hints of the single pass (
 void fused_set_hints(Ctx* c, int hints);
 int fused_get_first_stages(const Ctx* c);  // stages of the single pass's first-read ring (1..3 of 4)
 void fused_set_first_stages(Ctx* c, int s_h);
+int fused_get_lead(const Ctx* c);          // tiles the first read may lead phase 2 (0: no limit)
+void fused_set_lead(Ctx* c, int lead);
 int fused_get_reserve(const Ctx* c);       // SMs the single pass leaves to the Sigma_s chain beside it
 srm_status fused_set_reserve(Ctx* c, int reserve);  // rebuilds the pass's schedule
 cudaError_t launch_fpass(Ctx* c);

@@ -43,14 +43,15 @@ srm_plan current_plan(const Ctx* c) {
   p.f_l2_hints = fused_get_hints(c);
   p.f_first_stages = fused_get_first_stages(c);
   p.f_reserve = fused_get_reserve(c);
+  p.f_lead = fused_get_lead(c);
   return p;
 }
 
 srm_status apply_plan(Ctx* c, const srm_plan& p) {
   if ((p.single_pass != 0 && p.single_pass != 1) || p.f_prefetch < 0 || p.f_prefetch > 16 || p.f_l2_hints < 0 ||
-      p.f_l2_hints > 7 || p.f_first_stages < 1 || p.f_first_stages > 4) {
+      p.f_l2_hints > 7 || p.f_first_stages < 1 || p.f_first_stages > 4 || p.f_lead < 0 || p.f_lead > 4) {
     set_error("srm_set_plan: field out of range (single_pass 0/1, f_prefetch 0-16, f_l2_hints 0-7, "
-              "f_first_stages 1-4)");
+              "f_first_stages 1-4, f_lead 0-4)");
     return SRM_ERR_ARG;
   }
   if (p.single_pass && !fused_supported(c)) {
@@ -81,6 +82,7 @@ srm_status apply_plan(Ctx* c, const srm_plan& p) {
     fused_set_pf(c, p.f_prefetch);
     fused_set_hints(c, p.f_l2_hints);
     fused_set_first_stages(c, p.f_first_stages);
+    fused_set_lead(c, p.f_lead);
     if (!p.single_pass) c->p_from_f = false;  // the next E-step streams X^ again
     fused_select(c, p.single_pass != 0);
   }
@@ -139,9 +141,9 @@ std::string signature(const Ctx* c) {
 
 std::string plan_line(const std::string& sig, const srm_plan& p, double ms) {
   char buf[320];
-  snprintf(buf, sizeof buf, "%s sp=%d er=%d mst=%d mgb=%d mres=%d mpf=%d mbx=%d fpf=%d fl2=%d fsh=%d fr=%d ms=%.6f",
+  snprintf(buf, sizeof buf, "%s sp=%d er=%d mst=%d mgb=%d mres=%d mpf=%d mbx=%d fpf=%d fl2=%d fsh=%d fr=%d fld=%d ms=%.6f",
            sig.c_str(), p.single_pass, p.e_reserve, p.m_stages, p.m_gram_bufs, p.m_resident_es, p.m_prefetch,
-           p.m_boxes, p.f_prefetch, p.f_l2_hints, p.f_first_stages, p.f_reserve, ms);
+           p.m_boxes, p.f_prefetch, p.f_l2_hints, p.f_first_stages, p.f_reserve, p.f_lead, ms);
   return buf;
 }
 
@@ -150,9 +152,9 @@ bool parse_line(const std::string& line, const std::string& sig, srm_plan* p, do
   srm_plan q{};
   double t = 0;
   if (sscanf(line.c_str() + sig.size(),
-             " sp=%d er=%d mst=%d mgb=%d mres=%d mpf=%d mbx=%d fpf=%d fl2=%d fsh=%d fr=%d ms=%lf",
+             " sp=%d er=%d mst=%d mgb=%d mres=%d mpf=%d mbx=%d fpf=%d fl2=%d fsh=%d fr=%d fld=%d ms=%lf",
              &q.single_pass, &q.e_reserve, &q.m_stages, &q.m_gram_bufs, &q.m_resident_es, &q.m_prefetch,
-             &q.m_boxes, &q.f_prefetch, &q.f_l2_hints, &q.f_first_stages, &q.f_reserve, &t) != 12)
+             &q.m_boxes, &q.f_prefetch, &q.f_l2_hints, &q.f_first_stages, &q.f_reserve, &q.f_lead, &t) != 13)
     return false;
   *p = q;
   *ms = t;
@@ -232,9 +234,9 @@ struct Report {
   void add(const char* stage, const srm_plan& p, float ms, const char* unit) {
     char buf[200];
     snprintf(buf, sizeof buf,
-             "%-6s sp=%d er=%-3d mst=%d mgb=%d mres=%d mpf=%-2d mbx=%d fpf=%d fl2=%d fsh=%d fr=%-2d  %9.4f %s\n",
+             "%-6s sp=%d er=%-3d mst=%d mgb=%d mres=%d mpf=%-2d mbx=%d fpf=%d fl2=%d fsh=%d fr=%-2d fld=%d  %9.4f %s\n",
              stage, p.single_pass, p.e_reserve, p.m_stages, p.m_gram_bufs, p.m_resident_es, p.m_prefetch,
-             p.m_boxes, p.f_prefetch, p.f_l2_hints, p.f_first_stages, p.f_reserve, ms, unit);
+             p.m_boxes, p.f_prefetch, p.f_l2_hints, p.f_first_stages, p.f_reserve, p.f_lead, ms, unit);
     os << buf;
   }
 };
@@ -282,17 +284,21 @@ srm_status search(Ctx* c, int iters, srm_plan* best_out, float* best_ms_out, Rep
     float best_f = 1e30f;
     srm_plan bfp = bf;
     for (int sh : {1, 2, 3, 4})
-      for (int hints : {0, 7})
-        for (int pf : {0, 1, 2}) {
+      for (int lead : {0, 3})
+        for (int hints : {0, 7})
+          for (int pf : {0, 1}) {
+        if (sh == 4 && lead != 0) continue;  // the shared ring keeps a lead of one tile by construction
         fused_set_pf(c, pf);
         fused_set_hints(c, hints);
         fused_set_first_stages(c, sh);
+        fused_set_lead(c, lead);
         float ms = 0;
         TTRY(time_launches(c, launch_fpass, 3, e0, e1, &ms));
         srm_plan p = bf;
         p.f_prefetch = pf;
         p.f_l2_hints = hints;
         p.f_first_stages = sh;
+        p.f_lead = lead;
         rep.add("fpass", p, ms, "ms/launch");
         if (ms < best_f) {
           best_f = ms;

@@ -85,7 +85,8 @@ def test_every_plan_matches_oracle():
              dict(single_pass=1, f_prefetch=0), dict(single_pass=1, f_prefetch=3, f_l2_hints=7),
              dict(single_pass=1, f_prefetch=1, f_l2_hints=6), dict(single_pass=1, f_first_stages=1),
              dict(single_pass=1, f_first_stages=3, f_prefetch=2), dict(single_pass=1, f_first_stages=4),
-             dict(single_pass=1, f_reserve=0), dict(single_pass=1, f_reserve=30, f_first_stages=1)]
+             dict(single_pass=1, f_reserve=0), dict(single_pass=1, f_reserve=30, f_first_stages=1),
+             dict(single_pass=1, f_first_stages=2, f_lead=1), dict(single_pass=1, f_first_stages=2, f_lead=3)]
     for fields in plans:
         m = _model(d, CASE.k, graph=True)
         m.set_plan(**fields)
@@ -100,7 +101,7 @@ def test_every_plan_matches_oracle():
     m = _model(d, CASE.k)
     for bad in (dict(m_stages=9), dict(m_gram_bufs=3), dict(e_reserve=-1), dict(f_prefetch=99),
                 dict(f_l2_hints=8), dict(f_first_stages=0), dict(f_first_stages=5), dict(m_boxes=3),
-                dict(single_pass=1, f_reserve=-1)):
+                dict(single_pass=1, f_reserve=-1), dict(f_lead=5)):
         with pytest.raises(srm.SrmError) as ei:
             m.set_plan(**bad)
         assert ei.value.status == srm.SRM_ERR_ARG, bad
@@ -124,7 +125,8 @@ def test_pipelining_plans_are_bitwise_identical():
     for fields in (dict(f_prefetch=0, f_l2_hints=0, f_first_stages=2),
                    dict(f_prefetch=2, f_l2_hints=7, f_first_stages=1),
                    dict(f_prefetch=1, f_l2_hints=2, f_first_stages=3),
-                   dict(f_prefetch=0, f_l2_hints=7, f_first_stages=4)):
+                   dict(f_prefetch=0, f_l2_hints=7, f_first_stages=4),
+                   dict(f_prefetch=0, f_l2_hints=7, f_first_stages=2, f_lead=2)):
         m = _model(d, CASE_T500.k)
         m.set_plan(single_pass=1, **fields)
         fused.append(_results(m, CASE_T500.n_iter))
