@@ -32,6 +32,19 @@ SRM_API srm_status srm_debug_mma(int32_t mn_major, const void* A, const void* B,
  * the host array out.  Synchronises.
  */
 SRM_API srm_status srm_debug_eig_sweeps(srm_ctx* ctx, int32_t* out, int32_t n);
+
+/*
+ * srm_debug_wait -- the bounded mbarrier wait of the tensor-core kernels,
+ * exercised on one CTA of the current device without any fault.  Two warps
+ * each wait on an mbarrier.  With arrive != 0 a thread arrives on both: the
+ * call returns SRM_OK.  With arrive == 0 nothing arrives.  The first waiter
+ * gives up after the library's limit of one second, raises the block's
+ * abort flag and the device status bit of a
+ * timed-out wait.  The other waiter stops on the abort flag.  The call then
+ * returns SRM_ERR_NUMERIC and srm_last_error() says which waits succeeded.
+ * Synchronous; the device stays usable afterwards.
+ */
+SRM_API srm_status srm_debug_wait(int32_t arrive);
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,7 @@ __all__ = [
     "srm_init", "srm_estep", "srm_mstep", "srm_fit", "srm_transform", "srm_get_w", "srm_get_s",
     "srm_get_params", "srm_get_ll", "srm_synchronize", "srm_get_state", "srm_set_state",
     "srm_get_kernel_times", "srm_layout", "srm_last_error", "srm_destroy", "srm_debug_mma",
-    "srm_transform_noalloc", "srm_debug_eig_sweeps", "srm_map", "srm_plan", "srm_get_plan", "srm_set_plan",
+    "srm_transform_noalloc", "srm_debug_eig_sweeps", "srm_debug_wait", "srm_map", "srm_plan", "srm_get_plan", "srm_set_plan",
     "srm_autotune",
 ]
 
@@ -119,6 +119,7 @@ def load_library(path: Optional[str] = None):
         "srm_transform_noalloc": (st, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
         "srm_map": (st, [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, _P]),
         "srm_debug_eig_sweeps": (st, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
+        "srm_debug_wait": (st, [ctypes.c_int32]),
         "srm_get_plan": (st, [_P, ctypes.POINTER(srm_plan)]),
         "srm_set_plan": (st, [_P, ctypes.POINTER(srm_plan)]),
         "srm_autotune": (st, [_P, ctypes.c_char_p, ctypes.c_int32, ctypes.POINTER(srm_plan),
@@ -252,6 +253,12 @@ def srm_layout(ctx: int) -> dict:
 def srm_debug_mma(mn_major: int, A_ptr: int, B_ptr: int, D_ptr: int, N: int, K: int):
     """Self-test of the tensor-core building blocks (include/srm_debug.h)."""
     _check(load_library().srm_debug_mma(int(mn_major), _P(A_ptr), _P(B_ptr), _P(D_ptr), N, K), "srm_debug_mma")
+
+
+def srm_debug_wait(arrive: bool):
+    """The bounded wait of the tensor-core kernels on one CTA (include/srm_debug.h):
+    raises SrmError(SRM_ERR_NUMERIC) when nothing arrives and the wait gives up."""
+    _check(load_library().srm_debug_wait(1 if arrive else 0), "srm_debug_wait")
 
 
 def srm_debug_eig_sweeps(ctx: int, n: int) -> np.ndarray:

@@ -263,9 +263,9 @@ __global__ void __launch_bounds__(FT, 1)
       if (!ok) {
         for (int q = 0; q < S_N; ++q)
           if (issued[q])
-            for (uint32_t it = 0; it < (1u << 22) && !mbar_try_wait(&full[q], iss_ph[q]); ++it) __nanosleep(128);
+            mbar_drain(&full[q], iss_ph[q], 128);
         if (g0 < g1)
-          for (uint32_t it = 0; it < (1u << 22) && !mbar_try_wait(e_full, 0); ++it) __nanosleep(128);
+          mbar_drain(e_full, 0, 128);
       }
     }
   } else if (shared && warp == 1) {
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(FT, 1)
       if (ok && pv) ok = p2(n - 1, pfirst, plast);
       // everything issued must have completed before TMEM is freed
       mma_commit(&done[0]);
-      for (uint32_t it = 0; it < (1u << 22) && !mbar_try_wait(&done[0], 0); ++it) __nanosleep(64);
+      mbar_drain(&done[0], 0, 64);
     }
   } else if (shared && (warp == 6 || warp == 7)) {
     // idle in the shared-ring schedule
@@ -442,9 +442,9 @@ __global__ void __launch_bounds__(FT, 1)
       if (!ok) {
         for (int q = sbase; q < sbase + nst; ++q)
           if (issued[q])
-            for (uint32_t it = 0; it < (1u << 22) && !mbar_try_wait(&full[q], iss_ph[q]); ++it) __nanosleep(128);
+            mbar_drain(&full[q], iss_ph[q], 128);
         if (first && g0 < g1)
-          for (uint32_t it = 0; it < (1u << 22) && !mbar_try_wait(e_full, 0); ++it) __nanosleep(128);
+          mbar_drain(e_full, 0, 128);
       }
     }
   } else if (warp == 1) {
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(FT, 1)
         }
       // everything this thread issued completes before TMEM is freed
       mma_commit(&done[0]);
-      for (uint32_t it = 0; it < (1u << 22) && !mbar_try_wait(&done[0], 0); ++it) __nanosleep(64);
+      mbar_drain(&done[0], 0, 64);
     }
   } else if (warp == 7) {
     // phase-2 MMA issue, one tile behind: Gram over this CTA's rows, then P
@@ -563,7 +563,7 @@ __global__ void __launch_bounds__(FT, 1)
         }
       }
       mma_commit(&done[1]);
-      for (uint32_t it = 0; it < (1u << 22) && !mbar_try_wait(&done[1], 0); ++it) __nanosleep(64);
+      mbar_drain(&done[1], 0, 64);
     }
   } else {
     const int q = warp & 3;  // TMEM lane quarter of this warp

@@ -84,6 +84,7 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 // if the phase did not complete within the limit.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status) {
   const uint32_t a = smem_u32(bar);
+  unsigned long long t0 = 0;
   for (uint32_t it = 0; it < (1u << 26); ++it) {
     uint32_t done;
     asm volatile(
@@ -92,7 +93,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
-    if (it > 64) __nanosleep(64);
+    if (it > 64) {
+      const unsigned long long now = global_ns();
+      if (t0 == 0)
+        t0 = now;
+      else if (now - t0 > kWaitLimitNs)
+        break;
+      __nanosleep(64);
+    }
   }
   atomicOr(status, ST_TIMEOUT);
   return false;

@@ -258,28 +258,34 @@ __global__ void __launch_bounds__(256) p_sum_kernel(int nchunk, const float* __r
   for (int j = 0; j < FW; ++j) out[tid + 256 * j] = a4[j];
 }
 
-// Sum over the 256 threads of a block in a fixed order (warp shuffles, then
-// the eight warp sums in order); every thread receives the result.
-__device__ __forceinline__ double block_sum_fixed(double v, double* red8) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) red8[threadIdx.x >> 5] = v;
+// Block reduction of three doubles over blockDim.x (a power of two <= 256) threads.
+__device__ void block_sum3(double& a, double& b, double& c) {
+  __shared__ double red[3][256];
+  const int tid = threadIdx.x;
+  red[0][tid] = a;
+  red[1][tid] = b;
+  red[2][tid] = c;
   __syncthreads();
-  double s = 0.0;
-#pragma unroll
-  for (int w = 0; w < 8; ++w) s += red8[w];
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (tid < s) {
+      red[0][tid] += red[0][tid + s];
+      red[1][tid] += red[1][tid + s];
+      red[2][tid] += red[2][tid + s];
+    }
+    __syncthreads();
+  }
+  a = red[0][0];
+  b = red[1][0];
+  c = red[2][0];
   __syncthreads();
-  return s;
 }
 
 // grid k blocks (row a of Phi), 256 threads.
 //   Sigma_s = U (Lambda + E) U^T with U = Us, G' = Lambda + E = Gp (k x k).
 //   Phi = U (g(Lambda) + F o E) U^T,  g(x) = x/(1 + rho0 x),
 //   F_bd = g[lambda_b, lambda_d] = 1 / ((1 + rho0 lambda_b)(1 + rho0 lambda_d)).
-// Each of the two k-term inner products per output is split over the lanes
-// of a warp and combined by shuffles: the kernel is latency-bound (FP64 at
-// about 2 FMA per clock per SM), so short dependent chains matter more than
-// the operation count.
+// U is staged in shared memory beside G' when both fit (u_smem), else read
+// from global memory (k close to 128).
 __global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __restrict__ rho2,
                                                   const double* __restrict__ sqnorm,
                                                   const int64_t* __restrict__ vox, const double* __restrict__ Us,
@@ -287,13 +293,12 @@ __global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __
                                                   float* __restrict__ Phi32, double* __restrict__ scal, int u_smem,
                                                   int* status) {
   extern __shared__ double ph_smem[];
-  __shared__ double red8[8];
   double* w = ph_smem;          // [k]  1 / (1 + rho0 lambda)
-  double* uw = w + k;           // [k]  U[a][b] w_b
-  double* tv = uw + k;          // [k]  (U[a,:] B)
+  double* ua = w + k;           // [k]  row a of U
+  double* tv = ua + k;          // [k]  (U[a,:] B)
   double* Gps = tv + k;         // [k][k] G', symmetrised
-  double* Uss = Gps + k * k;    // [k][k] U when it fits (u_smem), else U is read from global memory
-  const int a = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* Uss = Gps + k * k;    // [k][k] U (u_smem only)
+  const int a = blockIdx.x, tid = threadIdx.x;
   for (int e = tid; e < k * k; e += blockDim.x) {
     const int b = e / k, d = e % k;
     Gps[e] = 0.5 * (Gp[b * k + d] + Gp[d * k + b]);
@@ -310,43 +315,28 @@ __global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __
       s2 += sqnorm[i] / r;
     }
   }
-  const double rho0 = block_sum_fixed(s0, red8);
-  if (a == 0) {
-    s1 = block_sum_fixed(s1, red8);
-    s2 = block_sum_fixed(s2, red8);
-  }
+  block_sum3(s0, s1, s2);
+  const double rho0 = s0;
   for (int b = tid; b < k; b += blockDim.x) {
-    const double wb = 1.0 / (1.0 + rho0 * Gp[b * k + b]);
-    w[b] = wb;
-    uw[b] = Us[a * k + b] * wb;
+    w[b] = 1.0 / (1.0 + rho0 * Gp[b * k + b]);
+    ua[b] = Us[a * k + b];
   }
   __syncthreads();
-  // tv[d] = sum_b U[a][b] B[b][d],  B_bd = (b == d) ? lambda_b w_b : w_b w_d G'_bd;
-  // one warp per d, the b-sum over its lanes
-  for (int d = warp; d < k; d += 8) {
-    double sp = 0.0;
-    // G' is symmetric: read row d (consecutive b across the lanes, no bank conflicts)
-    for (int b = lane; b < k; b += 32) sp = fma(uw[b], Gps[d * k + b], sp);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
-    if (lane == 0) {
-      // the diagonal term: lambda_d w_d (not w_d^2 lambda_d)
-      const double gdd = Gps[d * k + d];
-      tv[d] = (sp - uw[d] * gdd) * w[d] + uw[d] * gdd;
-    }
+  // tv[d] = sum_b U[a][b] B[b][d],  B_bd = (b == d) ? lambda_b w_b : w_b w_d G'_bd
+  for (int d = tid; d < k; d += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < k; ++b) s = fma(ua[b] * w[b], Gps[b * k + d], s);
+    // the diagonal term: lambda_d w_d (not w_d^2 lambda_d)
+    s = (s - ua[d] * w[d] * Gps[d * k + d]) * w[d] + ua[d] * Gps[d * k + d] * w[d];
+    tv[d] = s;
   }
   __syncthreads();
-  // Phi[a][c] = sum_d tv[d] U[c][d]: one warp per c, the d-sum over its lanes
-  for (int cc = warp; cc < k; cc += 8) {
-    double sp = 0.0;
-    for (int d = lane; d < k; d += 32) sp = fma(tv[d], Ur[cc * k + d], sp);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
-    if (lane == 0) {
-      if (!isfinite(sp)) flag(status, ST_NONFINITE);
-      Phi[a * k + cc] = sp;
-      Phi32[a * k + cc] = (float)sp;
-    }
+  for (int cc = tid; cc < k; cc += blockDim.x) {
+    double s = 0.0;
+    for (int d = 0; d < k; ++d) s = fma(tv[d], Ur[cc * k + d], s);
+    if (!isfinite(s)) flag(status, ST_NONFINITE);
+    Phi[a * k + cc] = s;
+    Phi32[a * k + cc] = (float)s;
   }
   if (a == 0) {
     double ld = 0.0;
@@ -355,7 +345,8 @@ __global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __
       if (!(lam > 0.0)) flag(status, ST_NOT_PD);
       ld += log1p(rho0 * lam);
     }
-    ld = block_sum_fixed(ld, red8);
+    double z0 = 0.0, z1 = 0.0;
+    block_sum3(ld, z0, z1);
     if (tid == 0) {
       scal[SC_RHO0] = rho0;
       scal[SC_LOGDET] = ld;

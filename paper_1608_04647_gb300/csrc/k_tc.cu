@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(NT, 1)
         // let loads already in flight land before the block exits
         for (int q = 0; q < E_STAGES; ++q)
           if (issued[q]) {
-            for (uint32_t it2 = 0; it2 < (1u << 22) && !mbar_try_wait(&full[q], iss_ph[q]); ++it2) __nanosleep(128);
+            mbar_drain(&full[q], iss_ph[q], 128);
           }
       }
     }
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(NT, 1)
       }
       // everything issued must have completed before TMEM is freed
       mma_commit(done);
-      for (uint32_t it2 = 0; it2 < (1u << 22) && !mbar_try_wait(done, 0); ++it2) __nanosleep(64);
+      mbar_drain(done, 0, 64);
     }
   } else {
     const int q = warp & 3;
@@ -417,10 +417,10 @@ __global__ void __launch_bounds__(NT, 1)
       if (!ok) {
         for (int q = 0; q < S_N; ++q)
           if (issued[q]) {
-            for (uint32_t it2 = 0; it2 < (1u << 22) && !mbar_try_wait(&full[q], iss_ph[q]); ++it2) __nanosleep(128);
+            mbar_drain(&full[q], iss_ph[q], 128);
           }
         if (RES && g0 < g1)
-          for (uint32_t it2 = 0; it2 < (1u << 22) && !mbar_try_wait(e_full, 0); ++it2) __nanosleep(128);
+          mbar_drain(e_full, 0, 128);
       }
     }
   } else if (warp == 1) {
@@ -502,7 +502,7 @@ __global__ void __launch_bounds__(NT, 1)
       if (ok && pv) ok = do_gram(pb, pfirst, plast);
       // everything issued must have completed before TMEM is freed
       mma_commit(done);
-      for (uint32_t it2 = 0; it2 < (1u << 22) && !mbar_try_wait(done, 0); ++it2) __nanosleep(64);
+      mbar_drain(done, 0, 64);
     }
   } else {
     const int q = warp & 3;
@@ -1052,6 +1052,39 @@ cudaError_t launch_a_tc(Ctx* c) {
   return cudaGetLastError();
 }
 
+namespace {
+
+// The bounded wait of the tensor-core kernels, exercised alone: warp 0 waits
+// on one mbarrier, warp 1 on another.  With arrive != 0 a thread arrives on
+// both and the waits succeed.  With arrive == 0 nothing arrives on the first:
+// its waiter gives up after the library's poll limit and raises the abort
+// flag and the timeout bit.  The second waiter (on a barrier nothing arrives
+// on either) must then stop through the abort flag, well before its own
+// limit.  out[0..1]: 1 if the wait of warp 0 / warp 1 succeeded.
+__global__ void __launch_bounds__(64, 1) wait_selftest_kernel(int arrive, int* out, int* status) {
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  volatile int* abort_s = &abort_flag;
+  if (arrive && threadIdx.x == 0) {
+    mbar_arrive(&bar[0]);
+    mbar_arrive(&bar[1]);
+  }
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    const bool ok = mbar_wait(&bar[warp], 0, abort_s, status, ST_TIMEOUT);
+    out[warp] = ok ? 1 : 0;
+  }
+}
+
+}  // namespace
+
 }  // namespace srm
 
 // Self-test of the tensor-core building blocks (TMA 128-byte-swizzled loads,
@@ -1094,6 +1127,33 @@ extern "C" SRM_API srm_status srm_debug_mma(int32_t mn_major, const void* A, con
   if (st) {
     set_error("srm_debug_mma: a bounded wait gave up");
     return SRM_ERR_NUMERIC;
+  }
+  return SRM_OK;
+}
+
+// The bounded wait's give-up path, exercised without a fault; see srm_debug.h.
+extern "C" SRM_API srm_status srm_debug_wait(int32_t arrive) {
+  using namespace srm;
+  int* dev = nullptr;
+  if (cudaMalloc(&dev, 3 * sizeof(int)) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaMalloc");
+  cudaError_t e = cudaMemset(dev, 0, 3 * sizeof(int));
+  if (e == cudaSuccess) {
+    wait_selftest_kernel<<<1, 64>>>(arrive ? 1 : 0, dev, dev + 2);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int h[3] = {0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(h, dev, sizeof h, cudaMemcpyDeviceToHost);
+  cudaFree(dev);
+  if (e != cudaSuccess) return cuda_fail(e, "srm_debug_wait");
+  if (h[2] & ST_TIMEOUT) {
+    set_error(std::string("srm_debug_wait: a bounded wait gave up; waits ok: ") + std::to_string(h[0]) + ", " +
+              std::to_string(h[1]));
+    return SRM_ERR_NUMERIC;
+  }
+  if (!h[0] || !h[1]) {
+    set_error("srm_debug_wait: a wait failed without raising the timeout bit");
+    return SRM_ERR_STATE;
   }
   return SRM_OK;
 }

@@ -29,6 +29,19 @@ enum : int {
   ST_BOUNDS = 32,       // a kernel's own index check refused an access
 };
 
+// Bounded waits give up after this much elapsed time (the global timer).
+// Each mbarrier.try_wait may itself suspend the thread for a while, so a
+// limit on the number of polls alone would be far longer than it looks (2^24
+// polls measured about 63 s); the poll counts that remain are backstops.
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+#endif
+
 // Kernel kinds for SRM_PROFILE timing.
 enum KernelKind : int {
   KK_CENTER = 0,

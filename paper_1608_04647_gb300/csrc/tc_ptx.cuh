@@ -40,15 +40,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
-// Bounded wait.  Gives up (returns false) after ~2^24 polls with back-off
-// (well over a second) or as soon as another thread of the block has raised
-// *abort; the first thread to give up raises *abort and the status word.
+// Bounded wait.  Gives up (returns false) after kWaitLimitNs of waiting, or
+// as soon as another thread of the block has raised *abort; the first thread
+// to give up raises *abort and the status word.  The clock is read only once
+// the wait has polled 64 times, so waits that succeed at once pay nothing.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int* status,
                                           int timeout_bit) {
+  unsigned long long t0 = 0;
   for (uint32_t it = 0; it < (1u << 24); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 63) == 63) {
       if (*abort) return false;
+      const unsigned long long now = global_ns();
+      if (t0 == 0)
+        t0 = now;
+      else if (now - t0 > kWaitLimitNs)
+        break;
       __nanosleep(128);
     }
   }
@@ -57,15 +64,31 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   return false;
 }
 
+// Bounded wait without status (draining copies or MMAs already issued before
+// an exit): gives up after kWaitLimitNs.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity, uint32_t sleep_ns) {
+  const unsigned long long t0 = global_ns();
+  for (uint32_t it = 0; it < (1u << 22) && !mbar_try_wait(bar, parity); ++it) {
+    if (global_ns() - t0 > kWaitLimitNs) return;
+    __nanosleep(sleep_ns);
+  }
+}
+
 // Bounded wait for long waits (a whole work item): exponential back-off
 // from 64 ns to max_ns between polls, so that a waiting warp leaves the
 // issue slots to other work on the SM.  Same give-up rule as mbar_wait.
 __device__ __forceinline__ bool mbar_wait_patient(uint64_t* bar, uint32_t parity, volatile int* abort, int* status,
                                                   int timeout_bit, uint32_t max_ns) {
   uint32_t ns = 64;
+  unsigned long long t0 = 0;
   for (uint32_t it = 0; it < (1u << 22); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort) return false;
+    const unsigned long long now = global_ns();
+    if (t0 == 0)
+      t0 = now;
+    else if (now - t0 > kWaitLimitNs)
+      break;
     __nanosleep(ns);
     ns = ns < max_ns ? 2 * ns : max_ns;
   }
@@ -124,10 +147,16 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t pa
 // Bounded wait with cluster-scope acquire (data written by another CTA).
 __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, volatile int* abort, int* status,
                                                   int timeout_bit) {
+  unsigned long long t0 = 0;
   for (uint32_t it = 0; it < (1u << 24); ++it) {
     if (mbar_try_wait_cluster(bar, parity)) return true;
     if ((it & 63) == 63) {
       if (*abort) return false;
+      const unsigned long long now = global_ns();
+      if (t0 == 0)
+        t0 = now;
+      else if (now - t0 > kWaitLimitNs)
+        break;
       __nanosleep(128);
     }
   }
