@@ -66,6 +66,41 @@ int main(void) {{
     assert vals == py
 
 
+def test_plan_struct_layout_matches_c(lib):
+    """srm_plan: the binding's fields in the header's order, at the same offsets."""
+    from paper_1608_04647_gb300 import srm_plan
+    hdr = open(HEADER).read()
+    head = hdr[:hdr.index("} srm_plan;")]
+    body = head[head.rindex("typedef struct {"):]
+    fields = re.findall(r"int32_t\s+(\w+);", body)
+    assert fields == [n for n, _ in srm_plan._fields_]
+    offs = ", ".join(f"offsetof(srm_plan, {f})" for f in fields)
+    fmt = " ".join(["%zu"] * (len(fields) + 1))
+    src = f'''#include <stdio.h>
+#include <stddef.h>
+#include "{HEADER}"
+int main(void) {{
+  printf("{fmt}\\n", sizeof(srm_plan), {offs});
+  return 0;
+}}'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-o", exe, c], check=True)
+        vals = [int(x) for x in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
+    assert vals == [ctypes.sizeof(srm_plan)] + [getattr(srm_plan, f).offset for f in fields]
+
+
+def test_plan_calls_reject_bad_arguments_without_a_gpu(lib):
+    """The plan entry points check their arguments before any CUDA call."""
+    from paper_1608_04647_gb300 import SRM_ERR_ARG, srm_plan
+    p = srm_plan()
+    assert lib.srm_get_plan(None, ctypes.byref(p)) == SRM_ERR_ARG
+    assert lib.srm_set_plan(None, ctypes.byref(p)) == SRM_ERR_ARG
+    assert lib.srm_autotune(None, None, 4, None, None, None, 0) == SRM_ERR_ARG
+
+
 def _cfg(N=2, T=10, k=3, vox=(20, 30), store=0, flags=0):
     from paper_1608_04647_gb300 import srm_config
     arr = (ctypes.c_int64 * N)(*vox)
