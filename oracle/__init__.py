@@ -20,3 +20,4 @@ from .psrm import (  # noqa: F401
     ppca_fixed_point,
     State,
 )
+from .htfa import rbf_factors, residual as htfa_residual, residual_batch as htfa_residual_batch, zscore  # noqa: F401,E402
