@@ -532,6 +532,154 @@ def run_k_sweep(args):
         torch.cuda.empty_cache()
 
 
+HTFA_METRIC = "HTFA local cost evaluations/s (F_i of Eq. 14 and ||X_i - W_i F_i||_F^2 for every subject)"
+HTFA_UNIT = "evaluations/s"
+
+
+def fp32_alu_peak_tflops():
+    """FP32 FMA peak of the SIMT pipes: 152 SMs x 128 FP32 lanes x 2 flops
+    x the maximum SM clock (2070 MHz)."""
+    mhz = 2070.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def htfa_cpu_baseline(spec, d, budget_s=20.0, max_subjects=4):
+    """The FP64 oracle (as it stands) on the host cores: one cost evaluation
+    (factors, then residual) of the first subjects, time scaled by subject
+    count (every subject has the same shape)."""
+    import oracle
+    n = min(spec.n_subjects, max_subjects)
+    Xs = [(d["W"][i].astype(np.float64) @ oracle.rbf_factors(d["positions"][i], d["mu"][i], d["lam"][i])
+           + d["E"][i]) for i in range(n)]
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        for i in range(n):
+            F = oracle.rbf_factors(d["positions"][i], d["mu"][i], d["lam"][i])
+            oracle.htfa_residual(Xs[i], d["W"][i], F)
+        reps += 1
+        if time.perf_counter() - t0 > budget_s or reps >= 20:
+            break
+    dt = (time.perf_counter() - t0) / reps * spec.n_subjects / n
+    return {"value": round(1.0 / dt, 6), "unit": HTFA_UNIT, "cores": os.cpu_count(), "blas_threads": blas_threads(),
+            "kind": "oracle",
+            "sample": "%d subject(s) of %d (T = %d, V = %d, K = %d), %d evaluation(s) of the FP64 NumPy oracle; time "
+                      "scaled by subject count (x%.1f)" % (n, spec.n_subjects, spec.T, spec.V, spec.K, reps,
+                                                           spec.n_subjects / n)}
+
+
+def run_htfa(args):
+    """One step = the NLLS solver's cost evaluation for every subject of the
+    batch: F_i = srm_htfa_factors (Eq. 14), then r_i = srm_htfa_residual."""
+    import torch
+
+    import synth.htfa_inputs as hi
+    from paper_1608_04647_gb300 import _build, htfa
+    spec = hi.HTFA_CONFIGS[args.htfa_workload]
+    d = hi.draw(spec)
+    n, T, V, K = spec.n_subjects, spec.T, spec.V, spec.K
+    if args.impl == "reference":
+        cb = htfa_cpu_baseline(spec, d, budget_s=args.cpu_budget)
+        return {"impl": "reference", "metric": HTFA_METRIC, "value": cb["value"], "unit": HTFA_UNIT, "n_gpus": 0,
+                "higher_is_better": True, "dtype": "f64", "data": "synthetic (seeded HTFA-shaped inputs)",
+                "config": {"workload": spec.name, "n_subjects": n, "T": T, "V": V, "K": K}, "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": HTFA_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    _build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    X = torch.from_numpy(d["E"]).cuda()        # the data's values do not change the work
+    W = torch.from_numpy(d["W"]).cuda()
+    mu = torch.from_numpy(d["mu"]).cuda()
+    lam = torch.from_numpy(d["lam"]).cuda()
+    grid = htfa.GridPositions([torch.from_numpy(a) for a in d["axes"]], torch.from_numpy(d["vox"]).cuda())
+    F = torch.empty((n, K, V), device="cuda")
+    out = torch.empty((n,), dtype=torch.float64, device="cuda")
+    work = torch.empty(max(1, htfa.residual_workspace(n, K, T, V) // 8), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+
+    def step():
+        htfa.factors(grid, mu, lam, out=F)
+        htfa.residual(X, W, F, out=out, work=work)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(0) as cs:
+            e0.record(stream)
+            for _ in range(args.steps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms_step = e0.elapsed_time(e1) / args.steps
+        # per-call CUDA-event times on the same stream
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            htfa.factors(grid, mu, lam, out=F)
+            ev[i][1].record(stream)
+            htfa.residual(X, W, F, out=out, work=work)
+            ev[i][2].record(stream)
+        torch.cuda.synchronize()
+    t_f = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
+    t_r = sum(e[1].elapsed_time(e[2]) for e in ev) / args.steps
+    flops = 2.0 * n * T * V * K
+    peak = fp32_alu_peak_tflops()
+    achieved = flops / (t_r * 1e-3) / 1e12
+    f_bytes = n * K * V * 4 + n * V * 12
+    r_bytes = n * T * V * 4 + n * K * V * 4 + n * T * K * 4
+    hbm = load_peaks()["hbm_gbs"]
+    res = {
+        "metric": HTFA_METRIC, "value": round(1000.0 / ms_step, 3), "unit": HTFA_UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded HTFA-shaped inputs: grid voxels, centers, widths, weights, noise)",
+        "config": {"workload": spec.name, "n_subjects": n, "T": T, "V": V, "K": K,
+                   "l2": "inputs larger than L2 (X %.0f MB + F %.0f MB > 129 MB)" % (n * T * V * 4 / 1e6,
+                                                                                  n * K * V * 4 / 1e6)},
+        "roofline": {"kernel": "htfa_residual (tile + sum launches)", "bound": "alu", "achieved": round(achieved, 2),
+                     "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                     "traffic": None, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                     "flops_per_launch": flops, "ms_per_launch": round(t_r, 5),
+                     "hbm_gbs": round(r_bytes / (t_r * 1e-3) / 1e9, 1)},
+        "factors": {"ms_per_launch": round(t_f, 5), "bytes_per_launch": f_bytes,
+                    "achieved_gbs": round(f_bytes / (t_f * 1e-3) / 1e9, 1), "peak_gbs": hbm,
+                    "frac": round(f_bytes / (t_f * 1e-3) / 1e9 / hbm, 4)},
+        "gpu_launches": 3 * args.steps, "clocks": cs.summary(),
+    }
+    if not args.no_e2e:
+        Xh = X.cpu().pin_memory()
+        Wh, muh, lamh = W.cpu().pin_memory(), mu.cpu().pin_memory(), lam.cpu().pin_memory()
+        voxh = grid.vox.cpu().pin_memory()
+        outh = torch.empty((n,), dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for _ in range(args.steps):
+                X.copy_(Xh, non_blocking=True)
+                W.copy_(Wh, non_blocking=True)
+                mu.copy_(muh, non_blocking=True)
+                lam.copy_(lamh, non_blocking=True)
+                grid.vox.copy_(voxh, non_blocking=True)
+                step()
+                outh.copy_(out, non_blocking=True)
+                stream.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        h2d = sum(t.numel() * t.element_size() for t in (Xh, Wh, muh, lamh, voxh))
+        res["e2e"] = {"value": round(1.0 / dt, 3), "unit": HTFA_UNIT, "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(outh.numel() * 8),
+                      "note": "pinned host X, W, centers, widths and voxel indices copied in, the residuals copied "
+                              "out, every step"}
+    if not args.no_cpu_baseline:
+        res["cpu_baseline"] = htfa_cpu_baseline(spec, d, budget_s=args.cpu_budget)
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -552,9 +700,17 @@ def main():
                     "(srm_set_plan; for profiling one form)")
     ap.add_argument("--subjects", type=int, default=0, help="only the first K subjects of the workload (a smaller "
                     "case of the same shapes, for ncu captures)")
+    ap.add_argument("--htfa", action="store_true", help="the HTFA cost evaluation instead of the EM iteration "
+                    "(its own line)")
+    ap.add_argument("--htfa-workload", default="greeneyes-subsampled-like",
+                    help="greeneyes-subsampled-like | jacobian-example-like | ragged-small")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.htfa:
+        if int(os.environ.get("RANK", "0")) == 0:
+            print(json.dumps(run_htfa(args)))
+        return
     if args.k_sweep:
         run_k_sweep(args)
         return
