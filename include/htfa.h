@@ -47,17 +47,22 @@ extern "C" {
  * Because ||p - mu||^2 is a sum over the axes, each factor is the product of
  * one table entry per axis, exp(-(a - mu_c)^2 / lambda); the tables take
  * O(nx + ny + nz) exponentials per factor (the paper's per-axis cache of
- * squared differences, carried through the exponential).
+ * squared differences, carried through the exponential) and are built once
+ * per call in work_dev.
  *
  * flag_dev (one device int32, may be NULL) is OR-ed on the device with 1
  * when a voxel index lies outside its axis (that voxel's column of F is set
  * to NaN) and with 2 when a width is not a positive finite number (that
- * factor's row is set to NaN).  Requires 1 <= K, 1 <= nx, ny, nz <= 4096,
- * n_subj <= 65535, V <= 2^31 - 1.
+ * factor's row is set to NaN).  work_dev is caller-owned scratch for the
+ * tables, at least srm_htfa_factors_workspace() bytes, 16-byte aligned.
+ * Requires 1 <= K <= 2^20, 1 <= nx, ny, nz <= 4096, n_subj <= 65535,
+ * V <= 2^31 - 1.  Two launches: the tables, then F.
  */
+SRM_API size_t srm_htfa_factors_workspace(int32_t n_subj, int32_t K, int32_t nx, int32_t ny, int32_t nz);
 SRM_API srm_status srm_htfa_factors(int32_t n_subj, int32_t K, int32_t V, const float* axes_dev, int32_t nx,
                                     int32_t ny, int32_t nz, const int32_t* vox_dev, const float* mu_dev,
-                                    const float* lambda_dev, float* F_dev, int32_t* flag_dev, void* stream);
+                                    const float* lambda_dev, float* F_dev, int32_t* flag_dev, void* work_dev,
+                                    size_t work_bytes, void* stream);
 
 /*
  * srm_htfa_residual -- out_dev[i] = ||X_i - W_i F_i||_F^2 (FP64 result of

@@ -125,8 +125,10 @@ def load_library(path: Optional[str] = None):
         "srm_autotune": (st, [_P, ctypes.c_char_p, ctypes.c_int32, ctypes.POINTER(srm_plan),
                               ctypes.POINTER(ctypes.c_double), ctypes.c_char_p, ctypes.c_size_t]),
         "srm_destroy": (None, [_P]),
+        "srm_htfa_factors_workspace": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                         ctypes.c_int32, ctypes.c_int32]),
         "srm_htfa_factors": (st, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32,
-                                  ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, _P, _P]),
+                                  ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
         "srm_htfa_residual_workspace": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                           ctypes.c_int32]),
         "srm_htfa_residual": (st, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P, _P,

@@ -4,6 +4,7 @@
 // z-score.  Layouts follow the paper's HTFA notation: X_i is T x V (one
 // sample per row), W_i is T x K, F_i is K x V; a batch of equal-sized
 // subjects is stored back to back.
+#include <algorithm>
 #include <climits>
 #include <string>
 
@@ -18,74 +19,184 @@ __device__ __forceinline__ float qnan() { return __int_as_float(0x7fc00000); }
 
 // ---------------------------------------------------------------------------
 // Factor matrix (Eq. 14).  ||p - mu||^2 separates over the axes, so
-//   F[k][v] = Ex[k][ix] * Ey[k][iy] * Ez[k][iz],  Ec[k][a] = exp(-(a_c - mu_kc)^2 / lambda_k).
-// A block builds the tables of kc factors in shared memory (kc * (nx+ny+nz)
-// exponentials), then writes those kc rows for 1024 voxels: two multiplies
-// and one coalesced 4-byte store per element.
+//   F[k][v] = Ex[ix][k] * Ey[iy][k] * Ez[iz][k],  Ec[a][k] = exp(-(a_c - mu_kc)^2 / lambda_k).
+// The first kernel evaluates the tables of every subject once (n (nx+ny+nz)
+// K exponentials, laid out [n][a][Kp] with K padded to Kp, a multiple of 4,
+// so that four factors of one axis position are one 16-byte load).  The
+// second copies the tables of kc factors into shared memory and writes
+// those kc rows of F for 1024 voxels: per four factors of a voxel, three
+// 16-byte shared loads, eight multiplies and four coalesced stores.
 constexpr int FV_THREADS = 256;
 constexpr int FV_PER_BLOCK = 4 * FV_THREADS;
-constexpr int F_TABLE_FLOATS = 12288;  // 48 KB of tables per block
+constexpr int F_SMEM_DEFAULT = 48 * 1024;
 
-__global__ void __launch_bounds__(FV_THREADS) htfa_factors_kernel(int K, int V, int kc, const float* __restrict__ axes,
-                                                                  int nx, int ny, int nz, const int* __restrict__ vox,
-                                                                  const float* __restrict__ mu,
-                                                                  const float* __restrict__ lam, float* __restrict__ F,
-                                                                  int* flag) {
-  extern __shared__ float ftab[];  // [kn][na]
-  const int n = blockIdx.z;
-  const int k0 = blockIdx.y * kc;
-  const int kn = min(kc, K - k0);
+__global__ void __launch_bounds__(256) htfa_tables_kernel(int n_subj, int K, int Kp, const float* __restrict__ axes,
+                                                          int nx, int ny, int nz, const float* __restrict__ mu,
+                                                          const float* __restrict__ lam, float* __restrict__ tab,
+                                                          int* flag) {
   const int na = nx + ny + nz;
-  for (int e = threadIdx.x; e < kn * na; e += FV_THREADS) {
-    const int j = e / na, a = e - j * na;
-    const int axis = a < nx ? 0 : (a < nx + ny ? 1 : 2);
-    const int64_t f = (int64_t)n * K + k0 + j;
-    const float l = lam[f];
-    const bool ok = l > 0.f && l <= 3.402823466e38f;
-    const float d = axes[a] - mu[f * 3 + axis];
-    ftab[e] = ok ? expf(-(d * d) / l) : qnan();
-    if (!ok && a == 0 && flag) atomicOr(flag, 2);
-  }
-  __syncthreads();
-  const int64_t vb = (int64_t)blockIdx.x * FV_PER_BLOCK;
-#pragma unroll 1
-  for (int r = 0; r < 4; ++r) {
-    const int64_t v = vb + r * FV_THREADS + threadIdx.x;
-    if (v >= V) break;
-    const int* q = vox + ((int64_t)n * V + v) * 3;
-    const int ix = q[0], iy = q[1], iz = q[2];
-    float* out = F + ((int64_t)n * K + k0) * V + v;
-    if ((unsigned)ix < (unsigned)nx && (unsigned)iy < (unsigned)ny && (unsigned)iz < (unsigned)nz) {
-      const float* px = ftab + ix;
-      const float* py = ftab + nx + iy;
-      const float* pz = ftab + nx + ny + iz;
-      for (int j = 0; j < kn; ++j) out[(int64_t)j * V] = px[j * na] * py[j * na] * pz[j * na];
-    } else {
-      if (flag) atomicOr(flag, 1);
-      for (int j = 0; j < kn; ++j) out[(int64_t)j * V] = qnan();
+  const int64_t total = (int64_t)n_subj * na * Kp;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e % Kp);
+    const int64_t r = e / Kp;
+    const int a = (int)(r % na);
+    const int n = (int)(r / na);
+    float val = 0.f;
+    if (k < K) {
+      const int64_t f = (int64_t)n * K + k;
+      const float l = lam[f];
+      const bool ok = l > 0.f && l <= 3.402823466e38f;
+      const int axis = a < nx ? 0 : (a < nx + ny ? 1 : 2);
+      const float d = axes[a] - mu[f * 3 + axis];
+      val = ok ? expf(-(d * d) / l) : qnan();
+      if (!ok && a == 0 && flag) atomicOr(flag, 2);
     }
+    tab[e] = val;
   }
 }
 
+__global__ void __launch_bounds__(FV_THREADS) htfa_factors_kernel(int K, int Kp, int V, int kc, int ld, int nx, int ny,
+                                                                  int nz, const float* __restrict__ tab,
+                                                                  const int* __restrict__ vox, float* __restrict__ F,
+                                                                  int* flag) {
+  extern __shared__ __align__(16) float ftab[];  // [na][ld], factors k0 .. k0 + kc - 1
+  const int n = blockIdx.z;
+  const int k0 = blockIdx.y * kc;
+  const int kn = min(kc, K - k0);
+  const int q4 = (kn + 3) >> 2;
+  const int na = nx + ny + nz;
+  // the voxels' grid indices first, so that their loads overlap the copy
+  // of the tables
+  const int64_t vb = (int64_t)blockIdx.x * FV_PER_BLOCK + threadIdx.x;
+  int idx[4][3];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int64_t v = vb + r * FV_THREADS;
+    const int* q = vox + ((int64_t)n * V + (v < V ? v : 0)) * 3;
+    idx[r][0] = q[0];
+    idx[r][1] = q[1];
+    idx[r][2] = q[2];
+  }
+  const float* tn = tab + (int64_t)n * na * Kp + k0;
+  for (int e = threadIdx.x; e < na * q4; e += FV_THREADS) {
+    const int a = e / q4, j = (e - a * q4) * 4;
+    *reinterpret_cast<float4*>(&ftab[a * ld + j]) = *reinterpret_cast<const float4*>(&tn[(int64_t)a * Kp + j]);
+  }
+  __syncthreads();
+  // per voxel: its three table rows, or none (past V, or an index outside
+  // its axis: that column becomes NaN)
+  const float* px[4];
+  const float* py[4];
+  const float* pz[4];
+  float* out[4];
+  bool live[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int64_t v = vb + r * FV_THREADS;
+    const int ix = idx[r][0], iy = idx[r][1], iz = idx[r][2];
+    const bool inside = (unsigned)ix < (unsigned)nx && (unsigned)iy < (unsigned)ny && (unsigned)iz < (unsigned)nz;
+    out[r] = F + ((int64_t)n * K + k0) * V + (v < V ? v : 0);
+    live[r] = v < V && inside;
+    px[r] = ftab + (inside ? ix : 0) * ld;
+    py[r] = ftab + (nx + (inside ? iy : 0)) * ld;
+    pz[r] = ftab + (nx + ny + (inside ? iz : 0)) * ld;
+    if (v < V && !inside) {
+      if (flag) atomicOr(flag, 1);
+      for (int j = 0; j < kn; ++j) out[r][(int64_t)j * V] = qnan();
+    }
+  }
+  int j = 0;
+  for (; j + 4 <= kn; j += 4) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      if (!live[r]) continue;
+      const float4 x = *reinterpret_cast<const float4*>(px[r] + j);
+      const float4 y = *reinterpret_cast<const float4*>(py[r] + j);
+      const float4 z = *reinterpret_cast<const float4*>(pz[r] + j);
+      float* o = out[r] + (int64_t)j * V;
+      o[0] = x.x * y.x * z.x;
+      o[V] = x.y * y.y * z.y;
+      o[2 * (int64_t)V] = x.z * y.z * z.z;
+      o[3 * (int64_t)V] = x.w * y.w * z.w;
+    }
+  }
+  for (; j < kn; ++j)
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (live[r]) out[r][(int64_t)j * V] = px[r][j] * py[r][j] * pz[r][j];
+}
+
+// factors per block (a multiple of 4) and the table row stride (an odd
+// multiple of 4 floats, so that random rows spread over the banks)
+struct FactorPlan {
+  int Kp, kc, ld;
+  size_t smem;
+};
+
+FactorPlan factor_plan(int K, int na) {
+  FactorPlan p;
+  p.Kp = (K + 3) & ~3;
+  const int cap = F_SMEM_DEFAULT / (int)sizeof(float) / na;  // floats per table row that fit 48 KB
+  int kc = std::min(p.Kp, std::max(4, (cap - 4) & ~3));
+  p.kc = kc;
+  p.ld = ((kc >> 2) & 1) ? kc : kc + 4;
+  p.smem = (size_t)na * p.ld * sizeof(float);
+  return p;
+}
+
 // ---------------------------------------------------------------------------
-// Residual ||X - W F||_F^2.  A block owns a 64 (t) x 64 (v) tile of W F and
-// a thread a 4 x 4 piece of it (rows 4 ty .. 4 ty + 3, columns 4 tx ..
-// 4 tx + 3).  K is consumed in chunks of 16: W[t][k] is staged transposed
-// (Ws[k][t]) and F[k][v] as is, each thread then does 16 FMAs per pair of
-// 16-byte shared loads.  The squared residuals of the tile are summed in
-// FP32 per thread and in FP64 across the block (fixed order), one partial
-// per tile; a second kernel adds the partials of a subject in fixed order.
-constexpr int RT = 64, RV = 64, RK = 16, RPAD = 4;
+// Residual ||X - W F||_F^2.  A block of 128 threads owns a 64 (t) x 128 (v)
+// tile of W F and a thread an 8 x 8 piece of it: rows 4 ty + i and
+// 32 + 4 ty + i, columns 4 tx + j and 64 + 4 tx + j (i, j < 4; two 16-byte
+// groups each way, so that a warp's shared loads are broadcasts or cover 256
+// contiguous bytes).  K is consumed in chunks of 16, double-buffered in
+// shared memory: the copy of the next chunk (cp.async, no registers) is in
+// flight while the current one is multiplied, and one barrier per chunk
+// separates the buffers.  W[t][k] is staged transposed (Ws[k][t]) and F as
+// is; per k a thread does 64 FMAs for four 16-byte shared loads.  The
+// squared residuals of the tile are summed in FP32 per thread and in FP64
+// across the block (fixed order), one partial per tile; a second kernel
+// adds the partials of a subject in fixed order.
+constexpr int RT = 64, RV = 128, RK = 16, R_THREADS = 128;
+constexpr int WS_LD = RT + 4, FS_LD = RV + 4;  // floats per staged row
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// 4-byte global -> shared copy; ok == false writes zero and reads nothing
+__device__ __forceinline__ void cp_async4(uint32_t dst, const float* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+
+template <int KN>
+__device__ __forceinline__ void residual_mma_chunk(const float (*Ws)[WS_LD], const float (*Fs)[FS_LD], int kn, int ty,
+                                                   int tx, float (&acc)[8][8]) {
+#pragma unroll
+  for (int kk = 0; kk < (KN > 0 ? KN : RK); ++kk) {
+    if (KN == 0 && kk >= kn) break;
+    const float4 a0 = *reinterpret_cast<const float4*>(&Ws[kk][ty * 4]);
+    const float4 a1 = *reinterpret_cast<const float4*>(&Ws[kk][32 + ty * 4]);
+    const float4 b0 = *reinterpret_cast<const float4*>(&Fs[kk][tx * 4]);
+    const float4 b1 = *reinterpret_cast<const float4*>(&Fs[kk][64 + tx * 4]);
+    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+  }
+}
 
 template <bool VEC>
-__global__ void __launch_bounds__(256, 3) htfa_residual_kernel(int K, int T, int V, int tiles_v, int tiles,
-                                                               const float* __restrict__ X,
-                                                               const float* __restrict__ W,
-                                                               const float* __restrict__ F,
-                                                               double* __restrict__ part) {
-  __shared__ __align__(16) float Ws[RK][RT + RPAD];
-  __shared__ __align__(16) float Fs[RK][RV + RPAD];
-  __shared__ double red[8];
+__global__ void __launch_bounds__(R_THREADS, VEC ? 3 : 4) htfa_residual_kernel(int K, int T, int V, int tiles_v, int tiles,
+                                                                     const float* __restrict__ X,
+                                                                     const float* __restrict__ W,
+                                                                     const float* __restrict__ F,
+                                                                     double* __restrict__ part) {
+  __shared__ __align__(16) float Ws[2][RK][WS_LD];
+  __shared__ __align__(16) float Fs[2][RK][FS_LD];
+  __shared__ double red[R_THREADS / 32];
   const int n = blockIdx.y;
   const int tile = blockIdx.x;
   const int tt = tile / tiles_v, tv = tile - tt * tiles_v;
@@ -94,59 +205,97 @@ __global__ void __launch_bounds__(256, 3) htfa_residual_kernel(int K, int T, int
   const float* Wn = W + (int64_t)n * T * K;
   const float* Fn = F + (int64_t)n * K * V;
   const float* Xn = X + (int64_t)n * T * V;
-  float acc[4][4];
+  float acc[8][8];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
-  for (int k0 = 0; k0 < K; k0 += RK) {
+  // one chunk, global -> shared by cp.async (4-byte copies, zero-filled
+  // outside the matrices).  W tile 64 t x 16 k: this thread copies column
+  // k0 + wk of rows t0 + wt + 8 r (r < 8) into Ws[k][t].  F tile 16 k x
+  // 128 v: this thread copies column v0 + tid of rows k0 + r (r < 16).  The
+  // pointers and row predicates are formed once; a chunk only advances them.
+  const int wt = tid >> 4, wk = tid & 15;
+  unsigned wrows = 0;  // bit r: row t0 + wt + 8 r exists
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int e = tid + 256 * r;          // 0 .. 1023
-      const int wt = e >> 4, wk = e & 15;   // W tile: 64 t x 16 k, k fastest in memory
-      const int t = t0 + wt, k = k0 + wk;
-      Ws[wk][wt] = (t < T && k < K) ? Wn[(int64_t)t * K + k] : 0.f;
-      const int fk = e >> 6, fv = e & 63;   // F tile: 16 k x 64 v, v fastest in memory
-      const int kf = k0 + fk, v = v0 + fv;
-      Fs[fk][fv] = (kf < K && v < V) ? Fn[(int64_t)kf * V + v] : 0.f;
+  for (int r = 0; r < 8; ++r) wrows |= (t0 + wt + 8 * r < T ? 1u : 0u) << r;
+  const float* wsrc = Wn + (int64_t)min(t0 + wt, T - 1) * K + wk;
+  const int64_t wstep = (int64_t)8 * K;
+  const bool fcol = v0 + tid < V;
+  const float* fsrc = Fn + (fcol ? v0 + tid : 0);
+  const uint32_t wdst = smem_u32(&Ws[0][wk][wt]);
+  const uint32_t fdst = smem_u32(&Fs[0][0][tid]);
+  constexpr uint32_t WBUF = RK * WS_LD * 4, FBUF = RK * FS_LD * 4;
+  const bool interior = t0 + RT <= T && v0 + RV <= V;
+  auto issue_chunk = [&](int k0, int b) {
+    const uint32_t wd = wdst + b * WBUF, fd = fdst + b * FBUF;
+    const float* wp = wsrc + k0;
+    const float* fp = fsrc + (int64_t)k0 * V;
+    if (interior && k0 + RK <= K) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) cp_async4(wd + 32 * r, wp + r * wstep, true);
+#pragma unroll
+      for (int r = 0; r < 16; ++r) cp_async4(fd + r * (FS_LD * 4), fp + (int64_t)r * V, true);
+    } else {
+      const bool kw = k0 + wk < K;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const bool ok = kw && ((wrows >> r) & 1u);
+        cp_async4(wd + 32 * r, ok ? wp + r * wstep : Wn, ok);
+      }
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const bool ok = fcol && k0 + r < K;
+        cp_async4(fd + r * (FS_LD * 4), ok ? fp + (int64_t)r * V : Fn, ok);
+      }
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+
+  const int nch = (K + RK - 1) / RK;
+  issue_chunk(0, 0);
+  for (int c = 0; c < nch; ++c) {
+    const int b = c & 1;
+    // chunk c has landed; every thread is done with chunk c - 1, whose
+    // buffer the copy of chunk c + 1 now overwrites
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < RK; ++kk) {
-      const float4 a = *reinterpret_cast<const float4*>(&Ws[kk][ty * 4]);
-      const float4 b = *reinterpret_cast<const float4*>(&Fs[kk][tx * 4]);
-      const float av[4] = {a.x, a.y, a.z, a.w};
-      const float bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-    }
-    __syncthreads();
+    if (c + 1 < nch) issue_chunk((c + 1) * RK, b ^ 1);
+    const int kn = min(RK, K - c * RK);
+    if (kn == RK)
+      residual_mma_chunk<RK>(Ws[b], Fs[b], kn, ty, tx, acc);
+    else
+      residual_mma_chunk<0>(Ws[b], Fs[b], kn, ty, tx, acc);
   }
 
   float s = 0.f;
-  const int vc = v0 + tx * 4;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int t = t0 + ty * 4 + i;
-    if (t >= T) break;
-    const float* xr = Xn + (int64_t)t * V + vc;
-    if (VEC && vc < V) {
-      const float4 x = *reinterpret_cast<const float4*>(xr);
-      const float r0 = x.x - acc[i][0], r1 = x.y - acc[i][1], r2 = x.z - acc[i][2], r3 = x.w - acc[i][3];
-      s = fmaf(r0, r0, s);
-      s = fmaf(r1, r1, s);
-      s = fmaf(r2, r2, s);
-      s = fmaf(r3, r3, s);
-    } else if (!VEC) {
+  for (int i = 0; i < 8; ++i) {
+    const int t = t0 + (i < 4 ? 0 : 32) + ty * 4 + (i & 3);
+    if (t >= T) continue;
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (vc + j < V) {
-          const float r = xr[j] - acc[i][j];
-          s = fmaf(r, r, s);
+    for (int h = 0; h < 2; ++h) {
+      const int vc = v0 + 64 * h + tx * 4;
+      const float* xr = Xn + (int64_t)t * V + vc;
+      if (VEC) {
+        if (vc < V) {
+          const float4 x = *reinterpret_cast<const float4*>(xr);
+          const float r0 = x.x - acc[i][4 * h], r1 = x.y - acc[i][4 * h + 1];
+          const float r2 = x.z - acc[i][4 * h + 2], r3 = x.w - acc[i][4 * h + 3];
+          s = fmaf(r0, r0, s);
+          s = fmaf(r1, r1, s);
+          s = fmaf(r2, r2, s);
+          s = fmaf(r3, r3, s);
         }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (vc + j < V) {
+            const float r = xr[j] - acc[i][4 * h + j];
+            s = fmaf(r, r, s);
+          }
+      }
     }
   }
   double d = s;
@@ -156,7 +305,7 @@ __global__ void __launch_bounds__(256, 3) htfa_residual_kernel(int K, int T, int
   __syncthreads();
   if (tid == 0) {
     double tot = 0.0;
-    for (int w = 0; w < 8; ++w) tot += red[w];
+    for (int w = 0; w < R_THREADS / 32; ++w) tot += red[w];
     part[(int64_t)n * tiles + tile] = tot;
   }
 }
@@ -257,29 +406,45 @@ int64_t residual_tiles(int32_t T, int32_t V) {
 
 using namespace srm;
 
+extern "C" size_t srm_htfa_factors_workspace(int32_t n_subj, int32_t K, int32_t nx, int32_t ny, int32_t nz) {
+  if (n_subj <= 0 || K <= 0 || nx <= 0 || ny <= 0 || nz <= 0) return 0;
+  return (size_t)n_subj * (size_t)(nx + ny + nz) * (size_t)((K + 3) & ~3) * sizeof(float);
+}
+
 extern "C" srm_status srm_htfa_factors(int32_t n_subj, int32_t K, int32_t V, const float* axes, int32_t nx,
                                        int32_t ny, int32_t nz, const int32_t* vox, const float* mu,
-                                       const float* lambda, float* F, int32_t* flag, void* stream) {
-  if (n_subj < 0 || n_subj > 65535 || K < 1 || V < 0 || nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 ||
-      nz > 4096) {
-    set_error("srm_htfa_factors: need 0 <= n_subj <= 65535, K >= 1, V >= 0, 1 <= nx, ny, nz <= 4096");
+                                       const float* lambda, float* F, int32_t* flag, void* work, size_t work_bytes,
+                                       void* stream) {
+  if (n_subj < 0 || n_subj > 65535 || K < 1 || K > (1 << 20) || V < 0 || nx < 1 || ny < 1 || nz < 1 || nx > 4096 ||
+      ny > 4096 || nz > 4096) {
+    set_error("srm_htfa_factors: need 0 <= n_subj <= 65535, 1 <= K <= 2^20, V >= 0, 1 <= nx, ny, nz <= 4096");
     return SRM_ERR_ARG;
   }
   if (n_subj == 0 || V == 0) return SRM_OK;
-  if (!axes || !vox || !mu || !lambda || !F) {
-    set_error("srm_htfa_factors: null pointer");
+  const size_t need = srm_htfa_factors_workspace(n_subj, K, nx, ny, nz);
+  if (!axes || !vox || !mu || !lambda || !F || !work || (reinterpret_cast<uintptr_t>(work) & 15) ||
+      work_bytes < need) {
+    set_error("srm_htfa_factors: null pointer, workspace not 16-byte aligned or below " + std::to_string(need) +
+              " bytes");
     return SRM_ERR_ARG;
   }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int na = nx + ny + nz;
-  const int kc = std::max(1, std::min<int>(K, F_TABLE_FLOATS / na));
-  const dim3 grid((unsigned)((V + FV_PER_BLOCK - 1) / FV_PER_BLOCK), (unsigned)((K + kc - 1) / kc),
-                  (unsigned)n_subj);
-  if (grid.y > 65535) {
-    set_error("srm_htfa_factors: too many factor chunks (K = " + std::to_string(K) + ")");
-    return SRM_ERR_ARG;
+  const FactorPlan p = factor_plan(K, na);
+  float* tab = static_cast<float*>(work);
+  const int64_t total = (int64_t)n_subj * na * p.Kp;
+  const unsigned tb = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  htfa_tables_kernel<<<tb, 256, 0, s>>>(n_subj, K, p.Kp, axes, nx, ny, nz, mu, lambda, tab, flag);
+  srm_status st = launch_check("srm_htfa_factors: tables");
+  if (st != SRM_OK) return st;
+  if (p.smem > (size_t)F_SMEM_DEFAULT) {
+    const cudaError_t e = cudaFuncSetAttribute(htfa_factors_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)p.smem);
+    if (e != cudaSuccess) return cuda_fail(e, "srm_htfa_factors: cudaFuncSetAttribute");
   }
-  htfa_factors_kernel<<<grid, FV_THREADS, (size_t)kc * na * sizeof(float), static_cast<cudaStream_t>(stream)>>>(
-      K, V, kc, axes, nx, ny, nz, vox, mu, lambda, F, flag);
+  const dim3 grid((unsigned)((V + FV_PER_BLOCK - 1) / FV_PER_BLOCK), (unsigned)((K + p.kc - 1) / p.kc),
+                  (unsigned)n_subj);
+  htfa_factors_kernel<<<grid, FV_THREADS, p.smem, s>>>(K, p.Kp, V, p.kc, p.ld, nx, ny, nz, tab, vox, F, flag);
   return launch_check("srm_htfa_factors");
 }
 
@@ -322,9 +487,9 @@ extern "C" srm_status srm_htfa_residual(int32_t n_subj, int32_t K, int32_t T, in
   const dim3 grid((unsigned)tiles, (unsigned)n_subj);
   const bool vec = (V % 4 == 0) && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
   if (vec)
-    htfa_residual_kernel<true><<<grid, 256, 0, s>>>(K, T, V, tiles_v, (int)tiles, X, W, F, part);
+    htfa_residual_kernel<true><<<grid, R_THREADS, 0, s>>>(K, T, V, tiles_v, (int)tiles, X, W, F, part);
   else
-    htfa_residual_kernel<false><<<grid, 256, 0, s>>>(K, T, V, tiles_v, (int)tiles, X, W, F, part);
+    htfa_residual_kernel<false><<<grid, R_THREADS, 0, s>>>(K, T, V, tiles_v, (int)tiles, X, W, F, part);
   srm_status st = launch_check("srm_htfa_residual: tile kernel");
   if (st != SRM_OK) return st;
   htfa_residual_sum_kernel<<<(unsigned)n_subj, 256, 0, s>>>((int)tiles, part, out);

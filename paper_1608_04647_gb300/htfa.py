@@ -19,7 +19,8 @@ import torch
 
 from . import SrmError, _check, load_library  # noqa: F401
 
-__all__ = ["GridPositions", "factors", "residual", "zscore", "FLAG_BAD_VOXEL", "FLAG_BAD_WIDTH"]
+__all__ = ["GridPositions", "factors", "factors_workspace", "residual", "residual_workspace", "zscore",
+           "FLAG_BAD_VOXEL", "FLAG_BAD_WIDTH"]
 
 FLAG_BAD_VOXEL = 1
 FLAG_BAD_WIDTH = 2
@@ -60,11 +61,13 @@ class GridPositions:
 
 
 def factors(grid: GridPositions, mu: torch.Tensor, lam: torch.Tensor, out: Optional[torch.Tensor] = None,
-            flag: Optional[torch.Tensor] = None) -> torch.Tensor:
+            flag: Optional[torch.Tensor] = None, work: Optional[torch.Tensor] = None) -> torch.Tensor:
     """F (K x V, or n x K x V) with F[k][v] = exp(-||p_v - mu_k||^2 / lambda_k).
 
     mu: [K, 3] or [n, K, 3]; lam: [K] or [n, K]; flag: optional int32
-    device tensor of one element, OR-ed with FLAG_BAD_VOXEL / FLAG_BAD_WIDTH."""
+    device tensor of one element, OR-ed with FLAG_BAD_VOXEL / FLAG_BAD_WIDTH.
+    ``work`` (float64 device tensor of ``factors_workspace(...)`` bytes) may
+    be given instead of the cached scratch buffer."""
     lib = load_library()
     batched = grid.vox.dim() == 3
     _need(mu, "mu", torch.float32, (3,) if batched else (2,))
@@ -86,16 +89,30 @@ def factors(grid: GridPositions, mu: torch.Tensor, lam: torch.Tensor, out: Optio
         _need(flag, "flag", torch.int32, (0, 1))
         fptr = flag.data_ptr()
     nx, ny, nz = grid.n_axis
+    nbytes = lib.srm_htfa_factors_workspace(n, K, nx, ny, nz)
+    work = _scratch(work, mu.device, nbytes, "factors")
     _check(lib.srm_htfa_factors(n, K, V, grid.axes.data_ptr(), nx, ny, nz, grid.vox.data_ptr(), mu.data_ptr(),
-                                lam.data_ptr(), out.data_ptr(), fptr, _stream(mu)), "srm_htfa_factors")
+                                lam.data_ptr(), out.data_ptr(), fptr, work.data_ptr(), work.numel() * 8,
+                                _stream(mu)), "srm_htfa_factors")
     return out
+
+
+def factors_workspace(n: int, K: int, n_axis) -> int:
+    """Bytes of scratch ``factors`` needs (n subjects, K factors, axis sizes)."""
+    return int(load_library().srm_htfa_factors_workspace(n, K, *n_axis))
 
 
 _work_cache = {}
 
 
-def _workspace(device: torch.device, nbytes: int) -> torch.Tensor:
-    key = (device.type, device.index)
+def _scratch(work: Optional[torch.Tensor], device: torch.device, nbytes: int, use: str) -> torch.Tensor:
+    """The caller's scratch tensor, checked, or a cached one per device and
+    use (not safe for concurrent calls on several streams: pass ``work``)."""
+    if work is not None:
+        if work.dtype != torch.float64 or not work.is_cuda or work.numel() * 8 < nbytes:
+            raise ValueError(f"work must be a float64 CUDA tensor of at least {nbytes} bytes")
+        return work
+    key = (device.type, device.index, use)
     buf = _work_cache.get(key)
     if buf is None or buf.numel() * 8 < nbytes:
         buf = torch.empty(max(1, (nbytes + 7) // 8), device=device, dtype=torch.float64)
@@ -123,10 +140,7 @@ def residual(X: torch.Tensor, W: torch.Tensor, F: torch.Tensor, out: Optional[to
     if out is None:
         out = torch.empty((n,) if batched else (), device=X.device, dtype=torch.float64)
     nbytes = lib.srm_htfa_residual_workspace(n, K, T, V)
-    if work is None:
-        work = _workspace(X.device, nbytes)
-    elif work.dtype != torch.float64 or not work.is_cuda or work.numel() * 8 < nbytes:
-        raise ValueError(f"work must be a float64 CUDA tensor of at least {nbytes} bytes")
+    work = _scratch(work, X.device, nbytes, "residual")
     _check(lib.srm_htfa_residual(n, K, T, V, X.data_ptr(), W.data_ptr(), F.data_ptr(), out.data_ptr(),
                                  work.data_ptr(), work.numel() * 8, _stream(X)), "srm_htfa_residual")
     return out
