@@ -572,6 +572,28 @@ def htfa_cpu_baseline(spec, d, budget_s=20.0, max_subjects=4):
                                                            spec.n_subjects / n)}
 
 
+def htfa_profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes of one launch from the committed ncu summary of this HTFA
+    kernel on this workload, if the kernel source is unchanged since."""
+    import hashlib
+    import re
+    tag = {"greeneyes-subsampled-like": "greeneyes_subsampled_like_N40_T174_V6857_K100"}.get(workload)
+    if tag is None:
+        return None, None
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{tag}.md")
+    if not os.path.exists(path):
+        return None, None
+    text = open(path).read()
+    mt = re.search(r"traffic_bytes_per_launch: (\d+)", text)
+    ms = re.search(r"source_sha1: ([0-9a-f]{40}) \(([\w.]+) when captured\)", text)
+    if not mt or not ms:
+        return None, None
+    src = os.path.join(ROOT, "paper_1608_04647_gb300", "csrc", ms.group(2))
+    if not os.path.exists(src) or hashlib.sha1(open(src, "rb").read()).hexdigest() != ms.group(1):
+        return None, os.path.relpath(path, ROOT) + " (stale: kernel source changed since the capture)"
+    return int(mt.group(1)), os.path.relpath(path, ROOT)
+
+
 def run_htfa(args):
     """One step = the NLLS solver's cost evaluation for every subject of the
     batch: F_i = srm_htfa_factors (Eq. 14), then r_i = srm_htfa_residual."""
@@ -648,6 +670,7 @@ def run_htfa(args):
     f_bytes = n * K * V * 4 + n * V * 12
     r_bytes = n * T * V * 4 + n * K * V * 4 + n * T * K * 4
     hbm = load_peaks()["hbm_gbs"]
+    traffic, tsrc = htfa_profiled_traffic("htfa_residual", spec.name)
     res = {
         "metric": HTFA_METRIC, "value": round(1000.0 / ms_step, 3), "unit": HTFA_UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
@@ -659,7 +682,8 @@ def run_htfa(args):
         "timing_note": "per-call CUDA-event times over the first %d steps of a second run on the same stream" % n_ev,
         "roofline": {"kernel": "htfa_residual (tile + sum launches)", "bound": "alu", "achieved": round(achieved, 2),
                      "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                     "traffic": None, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                     "traffic": traffic, "traffic_source": tsrc, "algorithmic_bytes_per_launch": r_bytes,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
                      "flops_per_launch": flops, "ms_per_launch": round(t_r, 5),
                      "hbm_gbs": round(r_bytes / (t_r * 1e-3) / 1e9, 1)},
         "factors": {"ms_per_call": round(t_f, 5), "launches_per_call": 2, "bytes_per_call": f_bytes,

@@ -27,36 +27,39 @@ __device__ __forceinline__ float qnan() { return __int_as_float(0x7fc00000); }
 // those kc rows of F for 1024 voxels: per four factors of a voxel, three
 // 16-byte shared loads, eight multiplies and four coalesced stores.
 constexpr int FV_THREADS = 256;
-constexpr int FV_PER_BLOCK = 4 * FV_THREADS;
 constexpr int F_SMEM_DEFAULT = 48 * 1024;
 
-__global__ void __launch_bounds__(256) htfa_tables_kernel(int n_subj, int K, int Kp, const float* __restrict__ axes,
-                                                          int nx, int ny, int nz, const float* __restrict__ mu,
+// a block covers 32 axis positions of one subject; a thread owns one factor
+// (its center and width loaded once) and writes its 32 table entries
+constexpr int TAB_ROWS = 32;
+
+__global__ void __launch_bounds__(128) htfa_tables_kernel(int K, int Kp, int na, const float* __restrict__ axes,
+                                                          int nx, int ny, const float* __restrict__ mu,
                                                           const float* __restrict__ lam, float* __restrict__ tab,
                                                           int* flag) {
-  const int na = nx + ny + nz;
-  const int64_t total = (int64_t)n_subj * na * Kp;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int k = (int)(e % Kp);
-    const int64_t r = e / Kp;
-    const int a = (int)(r % na);
-    const int n = (int)(r / na);
-    float val = 0.f;
-    if (k < K) {
-      const int64_t f = (int64_t)n * K + k;
-      const float l = lam[f];
-      const bool ok = l > 0.f && l <= 3.402823466e38f;
-      const int axis = a < nx ? 0 : (a < nx + ny ? 1 : 2);
-      const float d = axes[a] - mu[f * 3 + axis];
-      val = ok ? expf(-(d * d) / l) : qnan();
-      if (!ok && a == 0 && flag) atomicOr(flag, 2);
+  const int n = blockIdx.y;
+  const int a0 = blockIdx.x * TAB_ROWS, a1 = min(na, a0 + TAB_ROWS);
+  for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
+    float* out = tab + (int64_t)n * na * Kp + k;
+    if (k >= K) {
+      for (int a = a0; a < a1; ++a) out[(int64_t)a * Kp] = 0.f;
+      continue;
     }
-    tab[e] = val;
+    const int64_t f = (int64_t)n * K + k;
+    const float l = lam[f];
+    const bool ok = l > 0.f && l <= 3.402823466e38f;
+    if (!ok && a0 == 0 && flag) atomicOr(flag, 2);
+    const float m0 = mu[f * 3], m1 = mu[f * 3 + 1], m2 = mu[f * 3 + 2];
+#pragma unroll 4
+    for (int a = a0; a < a1; ++a) {
+      const float d = axes[a] - (a < nx ? m0 : (a < nx + ny ? m1 : m2));
+      out[(int64_t)a * Kp] = ok ? expf(-(d * d) / l) : qnan();
+    }
   }
 }
 
-__global__ void __launch_bounds__(FV_THREADS) htfa_factors_kernel(int K, int Kp, int V, int kc, int ld, int nx, int ny,
-                                                                  int nz, const float* __restrict__ tab,
+__global__ void __launch_bounds__(FV_THREADS) htfa_factors_kernel(int K, int Kp, int V, int kc, int ld, int vpt, int nx,
+                                                                  int ny, int nz, const float* __restrict__ tab,
                                                                   const int* __restrict__ vox, float* __restrict__ F,
                                                                   int* flag) {
   extern __shared__ __align__(16) float ftab[];  // [na][ld], factors k0 .. k0 + kc - 1
@@ -67,11 +70,11 @@ __global__ void __launch_bounds__(FV_THREADS) htfa_factors_kernel(int K, int Kp,
   const int na = nx + ny + nz;
   // the voxels' grid indices first, so that their loads overlap the copy
   // of the tables
-  const int64_t vb = (int64_t)blockIdx.x * FV_PER_BLOCK + threadIdx.x;
+  const int64_t vb = (int64_t)blockIdx.x * vpt * FV_THREADS + threadIdx.x;
   int idx[4][3];
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    const int64_t v = vb + r * FV_THREADS;
+    const int64_t v = r < vpt ? vb + r * FV_THREADS : V;
     const int* q = vox + ((int64_t)n * V + (v < V ? v : 0)) * 3;
     idx[r][0] = q[0];
     idx[r][1] = q[1];
@@ -92,7 +95,7 @@ __global__ void __launch_bounds__(FV_THREADS) htfa_factors_kernel(int K, int Kp,
   bool live[4];
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    const int64_t v = vb + r * FV_THREADS;
+    const int64_t v = r < vpt ? vb + r * FV_THREADS : V;
     const int ix = idx[r][0], iy = idx[r][1], iz = idx[r][2];
     const bool inside = (unsigned)ix < (unsigned)nx && (unsigned)iy < (unsigned)ny && (unsigned)iz < (unsigned)nz;
     out[r] = F + ((int64_t)n * K + k0) * V + (v < V ? v : 0);
@@ -432,9 +435,8 @@ extern "C" srm_status srm_htfa_factors(int32_t n_subj, int32_t K, int32_t V, con
   const int na = nx + ny + nz;
   const FactorPlan p = factor_plan(K, na);
   float* tab = static_cast<float*>(work);
-  const int64_t total = (int64_t)n_subj * na * p.Kp;
-  const unsigned tb = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
-  htfa_tables_kernel<<<tb, 256, 0, s>>>(n_subj, K, p.Kp, axes, nx, ny, nz, mu, lambda, tab, flag);
+  htfa_tables_kernel<<<dim3((unsigned)((na + TAB_ROWS - 1) / TAB_ROWS), (unsigned)n_subj), 128, 0, s>>>(
+      K, p.Kp, na, axes, nx, ny, mu, lambda, tab, flag);
   srm_status st = launch_check("srm_htfa_factors: tables");
   if (st != SRM_OK) return st;
   if (p.smem > (size_t)F_SMEM_DEFAULT) {
@@ -442,9 +444,12 @@ extern "C" srm_status srm_htfa_factors(int32_t n_subj, int32_t K, int32_t V, con
                                                (int)p.smem);
     if (e != cudaSuccess) return cuda_fail(e, "srm_htfa_factors: cudaFuncSetAttribute");
   }
-  const dim3 grid((unsigned)((V + FV_PER_BLOCK - 1) / FV_PER_BLOCK), (unsigned)((K + p.kc - 1) / p.kc),
+  // four voxels a thread: one a thread (more, smaller blocks for a single
+  // subject) measured slower, each block copying the same tables
+  const int vpt = 4;
+  const dim3 grid((unsigned)((V + vpt * FV_THREADS - 1) / (vpt * FV_THREADS)), (unsigned)((K + p.kc - 1) / p.kc),
                   (unsigned)n_subj);
-  htfa_factors_kernel<<<grid, FV_THREADS, p.smem, s>>>(K, p.Kp, V, p.kc, p.ld, nx, ny, nz, tab, vox, F, flag);
+  htfa_factors_kernel<<<grid, FV_THREADS, p.smem, s>>>(K, p.Kp, V, p.kc, p.ld, vpt, nx, ny, nz, tab, vox, F, flag);
   return launch_check("srm_htfa_factors");
 }
 
