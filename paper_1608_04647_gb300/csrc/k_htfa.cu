@@ -256,6 +256,20 @@ __global__ void __launch_bounds__(R_THREADS, VEC ? 3 : 4) htfa_residual_kernel(i
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
 
+  // the X tile is read once, after the products: ask L2 for its lines now
+  // (one request per 128-byte line: threads with tx = 0 or 8)
+  if ((tx & 7) == 0) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int t = t0 + (i < 4 ? 0 : 32) + ty * 4 + (i & 3);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int vc = v0 + 64 * h + tx * 4;
+        if (t < T && vc < V) asm volatile("prefetch.global.L2 [%0];" ::"l"(Xn + (int64_t)t * V + vc));
+      }
+    }
+  }
+
   const int nch = (K + RK - 1) / RK;
   issue_chunk(0, 0);
   for (int c = 0; c < nch; ++c) {
@@ -290,6 +304,12 @@ __global__ void __launch_bounds__(R_THREADS, VEC ? 3 : 4) htfa_residual_kernel(i
           s = fmaf(r1, r1, s);
           s = fmaf(r2, r2, s);
           s = fmaf(r3, r3, s);
+        }
+      } else if (vc + 3 < V) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float r = xr[j] - acc[i][4 * h + j];
+          s = fmaf(r, r, s);
         }
       } else {
 #pragma unroll
