@@ -1,4 +1,6 @@
-"""FP64 CPU oracle for the pSRM EM iteration.
+"""FP64 CPU oracle for the pSRM EM iteration (``psrm``) and the HTFA
+local-step evaluations (``htfa``: the factor matrix of Eq. 14, the
+residual of the local objective and the z-score).
 
 TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import, call,
 link or run anything in this package; only ``tests/``, the smoke check in
