@@ -150,3 +150,20 @@ def test_zscore_constant_column_is_zero():
     np.testing.assert_array_equal(Z[:, 0], 0)
     np.testing.assert_array_equal(Z[:, 2], 0)
     assert Z[:, 1].std() == pytest.approx(1.0)
+
+
+def test_input_recipe_follows_the_subsampling_rule():
+    """The local step's subsample (Sec. V-A): the mean of 25 % of the voxels
+    and 3000, and of 10 % of the TRs and 300.  Greeneyes (42,855 voxels,
+    475 TRs): (10,713.75 + 3000) / 2 and (47.5 + 300) / 2."""
+    import synth.htfa_inputs as hi
+    assert hi.subsample_counts(42855, 475) == (6857, 174)
+    spec = hi.HTFA_CONFIGS["greeneyes-subsampled-like"]
+    assert (spec.n_subjects, spec.V, spec.T, spec.K) == (40, 6857, 174, 100)
+    d = hi.draw(hi.HTFA_CONFIGS["ragged-small"])
+    mask = {tuple(r) for r in hi.brain_mask(hi.HTFA_CONFIGS["ragged-small"].brain_voxels)}
+    assert all(tuple(r) in mask for r in d["vox"].reshape(-1, 3))        # voxels inside the brain
+    assert d["lam"].min() >= 0.04 * d["diameter"] and d["lam"].max() <= 1.8 * d["diameter"]
+    # positions are read off the axes by the indices
+    for a in range(3):
+        np.testing.assert_array_equal(d["positions"][..., a], d["axes"][a][d["vox"][..., a]])
