@@ -172,12 +172,12 @@ SRM_API srm_status srm_map(srm_ctx* ctx, int32_t from, int32_t to, const void* X
 
 /*
  * srm_transform_noalloc -- the same result as srm_transform, for callers that
- * must not allocate device memory: code that runs while a CUDA stream is
- * being captured into a graph (an allocation there breaks the capture),
- * real-time or latency-bound loops where a cudaMalloc would synchronise the
- * device, and hosts whose memory is pre-assigned by a pool or another
- * framework.  srm_transform allocates (and grows) its scratch on first use;
- * this entry point allocates nothing: no cudaMalloc, no cudaFree and no
+ * must not allocate device memory: real-time or latency-bound loops, where a
+ * cudaMalloc or cudaFree would synchronise the whole device and stall them,
+ * and hosts whose device memory is handed out by a pool or by another
+ * framework, so that an allocation from outside that pool fails or breaks
+ * its accounting.  srm_transform allocates (and grows) its scratch on first
+ * use; this entry point allocates nothing: no cudaMalloc, no cudaFree and no
  * allocating library routine.  The paper has no counterpart.
  *
  * Scratch lives in one fixed device array of 16 MiB compiled into the
@@ -188,12 +188,13 @@ SRM_API srm_status srm_map(srm_ctx* ctx, int32_t from, int32_t to, const void* X
  * form); larger requests return SRM_ERR_ARG with the sizes in
  * srm_last_error().  Arguments, layout and result are those of srm_transform.
  *
- * The first call on a device (with that device current) looks up the
- * device address of the array once; make that first call before any stream
- * capture.  Every call uses the same array and overwrites what it reads, so
- * nothing needs clearing, but calls whose work overlaps on the GPU (on
- * different streams, or from different contexts of one process on one
- * device) race on the array: order them on one stream.  Asynchronous.
+ * The context's device must be the current device (SRM_ERR_ARG otherwise).
+ * The first call on a device looks up the device address of the array once,
+ * with that device current; make that first call before any stream capture.
+ * Every call uses the same array and overwrites what it reads, so nothing
+ * needs clearing, but calls whose work overlaps on the GPU (on different
+ * streams, or from different contexts of one process on one device) race on
+ * the array: order them on one stream.  Asynchronous.
  */
 SRM_API srm_status srm_transform_noalloc(srm_ctx* ctx, int32_t subject, const void* X_new_dev, int32_t T_new,
                                          float* S_out_dev);

@@ -126,8 +126,8 @@ cudaError_t launch_p_centred_x(srm_dtype xt, int kld, dim3 grid, cudaStream_t st
   return launch_p_centred<TA, float>(kld, grid, st, A, static_cast<const float*>(X), mu, rows, T, nsplit, part);
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device (with that device current) and cached.
+// Device address of the scratch array on device `dev`, looked up once per
+// device and cached.  The caller has made `dev` the current device.
 srm_status scratch_address(int dev, void** out) {
   if (dev < 0 || dev >= kMaxDevices) {
     set_error("srm_transform_noalloc: device ordinal out of range");
@@ -172,11 +172,18 @@ extern "C" srm_status srm_transform_noalloc(srm_ctx* c, int32_t subject, const v
   int ns = std::max(1, 2 * c->num_sms / nchunk);
   ns = (int)std::min<int64_t>(ns, std::max<int64_t>(1, v / 64));
   ns = (int)std::min<int64_t>(ns, (int64_t)((kNoAllocScratchBytes - mu_bytes) / split_bytes));
+  // the array's address belongs to the context's device, which must be current
+  // (launches on the context's stream need it too)
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != c->device) {
+    set_error("srm_transform_noalloc: the context lives on device " + std::to_string(c->device) + " but device " +
+              std::to_string(dev) + " is current; make the context's device current first");
+    return SRM_ERR_ARG;
+  }
   void* base = nullptr;
-  srm_status st = scratch_address(dev, &base);
+  srm_status st = scratch_address(c->device, &base);
   if (st != SRM_OK) return st;
   // the transform reads the current A_i and M_i
   st = flush_pending(c);

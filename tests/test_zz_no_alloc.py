@@ -1,7 +1,13 @@
-"""srm_transform_noalloc (the transform for callers that must not allocate
-device memory) gives the result of srm_transform, on two calls in a row,
-for the plain FP32 and the batched BF16 forms; oversized requests are
-refused before anything runs.  Collected last on purpose."""
+"""srm_transform_noalloc is the transform for callers that must not allocate
+device memory: latency-bound loops, where an allocation would synchronise the
+device, and hosts whose device memory belongs to a pool.  These tests check
+three things.  It gives the result of srm_transform on two calls in a row, for
+the plain FP32 and the batched BF16 forms.  Those calls leave the device's
+free memory unchanged.  Oversized requests are refused before anything runs.
+
+The file name sorts last, so pytest collects it after every other test.  That
+is its only ordering need: if it fails under ``-x``, every other test has
+already run.  It depends on no other test and passes when run alone."""
 import numpy as np
 import pytest
 
@@ -32,10 +38,18 @@ def test_noalloc_transform_matches_transform(store):
     for i in range(len(X)):
         Xn = torch.from_numpy((rng.standard_normal((case.voxels[i], 97)) + 1.5).astype(np.float32)).cuda()
         ref = m.transform(i, Xn)
-        for _ in range(2):  # two calls in a row share the fixed scratch array
-            S = torch.full_like(ref, float("nan"))
+        outs = [torch.full_like(ref, float("nan")) for _ in range(2)]
+        for j, S in enumerate(outs):  # two calls in a row share the fixed scratch array
+            torch.cuda.synchronize()
+            before = torch.cuda.mem_get_info()[0]
             srm.srm_transform_noalloc(m.ctx, i, Xn.data_ptr(), int(Xn.shape[1]), S.data_ptr())
             m.synchronize()
+            after = torch.cuda.mem_get_info()[0]
+            # the very first call may load the kernels (lazy module loading can
+            # take device memory for code); every later call must leave the
+            # device's free memory exactly as it was
+            if i > 0 or j > 0:
+                assert after == before, (before, after)
             err = ((S - ref).abs().max() / ref.abs().max()).item()
             assert err <= TOL, err
     m.close()
