@@ -3,18 +3,28 @@
 One step = one EM iteration (E-pass, E-step k x k work, M-pass with the fused
 Gram, eigen / polar / rho update) over the whole resident workload.
 
-Default workload: the greeneyes-like case - 16 subjects with uneven voxel
-counts v_i ~ U[20000, 60000], T = 1000, k = 50 - on synthetic planted data
-(the paper's datasets are not available).  The headline ``value`` is EM
-iterations/s of the batched BF16-storage tensor-core form; the plain
-per-subject FP32 form is timed beside it on the same workload.
+Headline workload: forrest-1024-like - 1024 subjects with uneven voxel counts
+v_i ~ U[20000, 60000], T = 500, k = 50 (41 GB of BF16 X^ resident), the
+paper's thousand-subject weak-scaling shape (Sec. V-C), on synthetic planted
+data (the paper's datasets are not available).  The headline ``value`` is EM
+iterations/s of the batched BF16-storage tensor-core form, the median of
+several timed regions of K iterations; the plain per-subject FP32 form is
+timed beside it on the same workload (``fp32_plain``).  The same run times
+the forrest-like high-resolution shape (8 x 600000 voxels, T = 3500,
+k = 100) and the greeneyes-like shape (16 subjects, T = 1000, k = 50) under
+extra keys, each with its own roofline, clocks, end-to-end job and CPU
+baseline.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--config 1]
-                    [--impl ours|reference] [--store bf16|f32] [--no-cpu-baseline]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config 4]
+                    [--extra-configs 3,1] [--repeats 5]
+                    [--impl ours|reference] [--store bf16|f32|both] [--no-cpu-baseline]
 
-Under torchrun (N > 1) every rank runs an independent replica of the
-workload (its own seed) on its own GPU; the path's one exchange step (the
-k x T reduction of Algorithm 1) is not distributed here.
+Under torchrun (N > 1) the headline workload's subjects are spread over the
+ranks as Algorithm 1 spreads them over processes: each EM iteration is every
+rank's share of the E-step, one NCCL all-reduce of the k x T reduction y and
+four sums, the rest of the E-step and each rank's M-step (``--sharded``,
+strong scaling: value = whole-workload EM iterations/s).  ``--replicas``
+runs independent copies of the workload instead.
 """
 from __future__ import annotations
 
@@ -105,9 +115,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def workload(config: int, rank: int, subjects: int = 0):
+def workload(config: int, rank: int, subjects: int = 0, voxels_cap: int = 0):
     """The config's planted spec and voxel counts; with subjects > 0 only the
-    first `subjects` subjects (a smaller case of the same shapes, for
+    first `subjects` subjects, and with voxels_cap > 0 each subject cut to at
+    most that many voxels (smaller cases of the same T and k, for
     profiling)."""
     import dataclasses
 
@@ -118,6 +129,9 @@ def workload(config: int, rank: int, subjects: int = 0):
         vox = vox[:subjects]
         spec = dataclasses.replace(spec, n_subjects=subjects,
                                    name=spec.name + " (first %d subjects)" % subjects)
+    if voxels_cap and max(vox) > voxels_cap:
+        vox = [min(int(v), int(voxels_cap)) for v in vox]
+        spec = dataclasses.replace(spec, name=spec.name + " (voxels capped at %d)" % voxels_cap)
     return spec, vox
 
 
@@ -200,71 +214,92 @@ def max_over_ranks(ms: float, world: int, device="cuda") -> float:
     return float(t.item())
 
 
-def time_fit(model, stream, steps, warmup):
+def time_fit(model, stream, steps, warmup, repeats=1):
+    """W untimed warm-up iterations, then `repeats` timed regions of exactly
+    `steps` EM iterations each (CUDA events on the context's stream,
+    synchronised on both sides).  Returns the ms of each region."""
     import torch
     model.fit_async(warmup)
     model.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    model.fit_async(steps)
-    e1.record(stream)
-    e1.synchronize()
-    model.synchronize()
-    return e0.elapsed_time(e1)  # ms
+    out = []
+    for _ in range(max(1, repeats)):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        model.fit_async(steps)
+        e1.record(stream)
+        e1.synchronize()
+        model.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
 
 
-def run_ours(args, rank, world):
+def ll_monotonicity(ll):
+    """How far the log-likelihood trace ever fell from one iteration to the
+    next: the number of decreases, the largest one in nats, and that drop as
+    a fraction of the trace's own total increase (EM never decreases the
+    likelihood in exact arithmetic; the FP32 and BF16 sums may)."""
+    ll = np.asarray(ll, dtype=np.float64)
+    d = np.diff(ll)
+    drops = d[d < 0]
+    rise = float(ll.max() - ll[0]) if len(ll) else 0.0
+    worst = float(-drops.min()) if len(drops) else 0.0
+    return {"iterations": int(len(ll)), "decreases": int(len(drops)), "max_decrease_nats": worst,
+            "max_decrease_of_total_rise": (worst / rise) if rise > 0 else None,
+            "total_rise_nats": rise}
+
+
+def polar_diagnostics(model, n_iter):
+    """Per iteration of a fresh fit: how many subjects' Newton-Schulz polar
+    factors passed their accuracy certificate and how many fell back to the
+    eigen-decomposition path (srm_debug_eig_sweeps after each M-step)."""
+    import paper_1608_04647_gb300 as srm
+    per_iter = []
+    for _ in range(n_iter):
+        model.fit(1)
+        sw = srm.srm_debug_eig_sweeps(model.ctx, model.N + 1)[: model.N]
+        per_iter.append(int(np.sum(sw >= 256)))
+    return per_iter
+
+
+def bench_workload(args, config, rank, world, stores, dev, peaks, e2e=True, cpu=True, label=None):
+    """One workload: generate it on the device, tune the batched form, time
+    `repeats` regions of K EM iterations (median reported), profile the same
+    K iterations kernel by kernel, run one end-to-end job from pageable host
+    buffers, and time the FP64 oracle on a bounded sample."""
     import torch
 
     import paper_1608_04647_gb300 as srm
-    from paper_1608_04647_gb300 import _build
     from synth.planted_torch import planted_dataset_torch
 
-    dev = int(os.environ.get("LOCAL_RANK", 0))
-    torch.cuda.set_device(dev)
-    if rank == 0:
-        _build.build()
-    if world > 1:
-        torch.distributed.barrier()
-    srm.load_library()
-    spec, vox = workload(args.config, rank, args.subjects)
+    spec, vox = workload(config, rank, args.subjects, args.voxels_cap)
     T, k = spec.T, spec.k
-    peaks = load_peaks()
     d = planted_dataset_torch(spec, vox, device="cuda", seed_offset=rank)
     stream = torch.cuda.Stream()
-    max_iter = args.warmup + args.steps + 64
+    R = max(1, args.repeats)
+    max_iter = args.warmup + R * args.steps + 64
+    import tempfile
+    cache = args.tune_cache or os.path.join(tempfile.gettempdir(), "srm_plans_bench_c%d_rank%d.txt" % (config, rank))
+    if not args.tune_cache and os.path.exists(cache):
+        os.remove(cache)
+    tune = {"plan": None, "ms": None, "tuning_s": None}
 
-    # launch plan of the batched form: tuned once on this device and these
-    # shapes (srm_autotune, before any timed region), then replayed from the
-    # cache file by every later context of the same shapes
-    tune = {"cache": None, "plan": None, "ms": None, "tuning_s": None}
-    if args.tune_cache:
-        tune["cache"] = args.tune_cache
-    else:
-        import tempfile
-        tune["cache"] = os.path.join(tempfile.gettempdir(), "srm_plans_bench_rank%d.txt" % rank)
-        if os.path.exists(tune["cache"]):
-            os.remove(tune["cache"])
-
-    def make(store, graph=True, profile=False):
-        m = srm.SRM(d["X"], d["W0"], k, store=store, graph=graph, profile=profile, max_iter=max_iter,
-                    stream=stream, single_pass=args.single_pass)
+    def make(store, graph=True, profile=False, **kw):
+        m = srm.SRM(d["X"], d["W0"], k, store=store, graph=graph, profile=profile,
+                    max_iter=kw.pop("max_iter", max_iter), stream=stream, single_pass=args.single_pass, **kw)
         if store == "bf16" and not args.no_autotune and not args.single_pass:
             t0 = time.perf_counter()
-            plan, ms, _ = m.autotune(tune["cache"], iters=4)
+            plan, ms, _ = m.autotune(cache, iters=4)
             if tune["plan"] is None:
                 tune.update(plan=plan, ms=round(ms, 4), tuning_s=round(time.perf_counter() - t0, 2))
         if store == "bf16" and args.plan:
             m.set_plan(**parse_plan(args.plan))
-            if tune["plan"] is None or tune.get("override") is None:
+            if tune.get("override") is None:
                 tune.update(plan=m.plan(), override=args.plan)
         return m
 
     results = {}
-    stores = [args.store] if args.store != "both" else ["bf16", "f32"]
-    clocks = None
     for store in stores:
         m = make(store)
         lay = m.layout()
@@ -272,13 +307,12 @@ def run_ours(args, rank, world):
             torch.distributed.barrier()
         torch.cuda.synchronize()
         with ClockSampler(dev) as cs:
-            ms = time_fit(m, stream, args.steps, args.warmup)
-        ms = max_over_ranks(ms, world)
+            regions = time_fit(m, stream, args.steps, args.warmup, R if store == stores[0] else min(R, 2))
+        regions = [max_over_ranks(x, world) for x in regions]
+        ms = statistics.median(regions)
         ll = m.ll()
-        results[store] = {"ms_total": ms, "ms_per_step": ms / args.steps, "layout": lay,
-                          "ll_last": float(ll[-1]), "ll_monotone": bool(np.all(np.diff(ll) >= -1e-6 * np.abs(ll[1:])))}
-        if store == stores[0]:
-            clocks = cs.summary()
+        results[store] = {"ms_total": ms, "ms_per_step": ms / args.steps, "layout": lay, "clocks": cs.summary(),
+                          "regions_ms": [round(x, 4) for x in regions], "ll_monotone": ll_monotonicity(ll)}
         m.close()
         del m
         # per-kernel CUDA-event times over a profiled run of the same K steps
@@ -290,6 +324,13 @@ def run_ours(args, rank, world):
         mp.close()
         del mp
         results[store]["kernels"] = {n: {"launches": l, "ms": t} for n, (l, t) in kt.items() if l > 0}
+        # the workload's own schedule from W^0, one iteration at a time: the
+        # log-likelihood trace and the polar factors that needed the fallback
+        md = make(store, graph=False, max_iter=spec.n_iter + 8)
+        results[store]["polar_fallbacks_per_iteration"] = polar_diagnostics(md, spec.n_iter)
+        results[store]["schedule_ll"] = ll_monotonicity(md.ll())
+        md.close()
+        del md
         torch.cuda.empty_cache()
     head = stores[0]
     xb = 2 if head == "bf16" else 4
@@ -300,35 +341,23 @@ def run_ours(args, rank, world):
     single = bool(results[head]["layout"]["single_pass"])
     ms_step = results[head]["ms_per_step"]
     value = world * 1000.0 / ms_step
-    roofline = None
-    # dominant kernel = the streaming pass with the largest time per step
-    streaming = {"estep_tc": e_bytes, "mstep_tc": m_bytes, "fpass_tc": f_bytes} if head == "bf16" else \
-        {"estep_simt": e_bytes, "mstep_simt": m_bytes}
-    present = [(ks[n]["ms"], n) for n in streaming if n in ks]
-    if present:
-        _, name = max(present)
-        t = ks[name]["ms"] / ks[name]["launches"]
-        b = streaming[name]
-        if head == "f32":
-            b = b / len(vox)  # per launch (one launch per subject)
-        achieved = b / (t * 1e-3) / 1e9
-        traffic, tsrc = profiled_traffic(name, args.config, int(sum(vox))) if head == "bf16" else (None, None)
-        roofline = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
-                    "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
-                    "traffic_source": tsrc, "peak_source": peaks["source"] + " (burst copy)",
-                    "bytes_per_launch": b, "ms_per_launch": t}
+    roofline = roofline_of(ks, head, e_bytes, m_bytes, f_bytes, len(vox), config, int(sum(vox)), peaks)
     iter_bytes = f_bytes if single else e_bytes + m_bytes
     kernels_per_step = sum(v["launches"] for v in ks.values()) / args.steps
+    clocks = results[head]["clocks"]
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": head,
         "data": "synthetic planted (Sec. II-A model), generated on device",
-        "config": {"workload": spec.name, "N": len(vox), "T": T, "k": k, "voxels_total": int(sum(vox)),
+        "config": {"workload": label or spec.name, "N": len(vox), "T": T, "k": k, "voxels_total": int(sum(vox)),
                    "store": head, "l2": "inputs larger than L2 (resident X^ %.2f GB > 129 MB)" %
                    (results[head]["layout"]["xhat_bytes"] / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "graph": True, "single_pass": single,
+                   "timing": "median of %d timed regions of %d EM iterations each (after %d warm-up iterations); "
+                             "CUDA events on the context stream" % (R, args.steps, args.warmup),
+                   "regions_ms": results[head]["regions_ms"],
                    "plan": tune["plan"] if head == "bf16" else None,
                    "autotune": None if head != "bf16" or tune["ms"] is None else
                    {"tuned_ms_per_iteration": tune["ms"], "tuning_s": tune["tuning_s"],
@@ -339,46 +368,197 @@ def run_ours(args, rank, world):
         "paper_gflops": round(paper_flops(vox, T, k) / (ms_step * 1e-3) / 1e9, 1),
         "gpu_launches": int(round(kernels_per_step * args.steps)),
         "clocks": clocks,
+        "ms_x_sm_mhz": round(ms_step * clocks["sm_mhz"], 1) if clocks.get("sm_mhz") else None,
         "kernels_ms_per_step": {n: round(v["ms"] / args.steps, 4) for n, v in ks.items()},
         "kernels_note": "CUDA-event time per step of each kernel kind on the stream it runs on (SRM_PROFILE run "
                         "of the same steps); kinds on the second and third streams (sigma, eig, mtail, refine, rho, "
                         "polar, phi where they run beside a streaming pass) include time spent waiting for SMs",
         "ll_monotone": results[head]["ll_monotone"],
+        "schedule": {"n_iter": spec.n_iter, "ll": results[head]["schedule_ll"],
+                     "polar_fallbacks_per_iteration": results[head]["polar_fallbacks_per_iteration"],
+                     "note": "the workload's fixed schedule from W^0, one iteration at a time: subjects whose "
+                             "Newton-Schulz polar factor failed its certificate (eigen-decomposition fallback) "
+                             "out of %d" % len(vox)},
     }
     if "f32" in results and head != "f32":
         r = results["f32"]
+        ke, km = algorithmic_bytes(vox, T, k, 4, 4)
         out["fp32_plain"] = {"value": round(world * 1000.0 / r["ms_per_step"], 3), "ms_per_step":
-                             round(r["ms_per_step"], 4),
+                             round(r["ms_per_step"], 4), "regions_ms": r["regions_ms"], "clocks": r["clocks"],
+                             "roofline": roofline_of(r["kernels"], "f32", ke, km, ke, len(vox), config,
+                                                     int(sum(vox)), peaks),
+                             "ll_monotone": r["ll_monotone"],
+                             "schedule": {"ll": r["schedule_ll"],
+                                          "polar_fallbacks_per_iteration": r["polar_fallbacks_per_iteration"]},
                              "kernels_ms_per_step": {n: round(v["ms"] / args.steps, 4) for n, v in
                                                      r["kernels"].items()}}
-    in_bytes = sum(x.numel() * x.element_size() for x in d["X"])
-    if not args.no_e2e and in_bytes <= 16e9:
+    if e2e and not args.no_e2e:
         out["e2e"] = run_e2e(args, d, spec, vox, stream, world,
-                             None if args.no_autotune or args.single_pass else tune["cache"])
-    elif not args.no_e2e:
-        out["e2e"] = {"value": None, "unit": UNIT, "skipped": "input of %.0f GB too large to pin on the host for "
-                      "the end-to-end job" % (in_bytes / 1e9)}
-    if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(spec, vox, budget_s=args.cpu_budget)
+                             None if args.no_autotune or args.single_pass else cache, head)
+    if cpu and rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(spec, vox, d, budget_s=args.cpu_budget)
+    del d
+    torch.cuda.empty_cache()
     return out
 
 
-def run_e2e(args, d, spec, vox, stream, world, tune_cache=None):
-    """One whole user job through the public API with host buffers: pinned
-    host X -> srm_init (host input: H2D copy + centring) -> srm_fit(n_iter)
-    -> parameters, E[S] and the log-likelihood back to the host.
-    Value = EM iterations / job time."""
+def roofline_of(ks, store, e_bytes, m_bytes, f_bytes, n_subjects, config, voxels_total, peaks):
+    """The dominant streaming kernel (largest time per step) with its
+    algorithmic bytes per launch over its CUDA-event launch duration."""
+    streaming = {"estep_tc": e_bytes, "mstep_tc": m_bytes, "fpass_tc": f_bytes} if store == "bf16" else \
+        {"estep_simt": e_bytes, "mstep_simt": m_bytes}
+    present = [(ks[n]["ms"], n) for n in streaming if n in ks]
+    if not present:
+        return None
+    _, name = max(present)
+    t = ks[name]["ms"] / ks[name]["launches"]
+    b = streaming[name]
+    if store == "f32":
+        b = b / n_subjects  # per launch (one launch per subject; the mean subject)
+    achieved = b / (t * 1e-3) / 1e9
+    traffic, tsrc = profiled_traffic(name, config, voxels_total) if store == "bf16" else (None, None)
+    return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+            "traffic_source": tsrc, "peak_source": peaks["source"] + " (copy bandwidth)",
+            "bytes_per_launch": b, "ms_per_launch": t,
+            "traffic_over_algorithmic": round(traffic / b, 4) if traffic else None}
+
+
+def bench_sharded(args, rank, world, dev, peaks):
+    """The headline workload's subjects spread over the ranks (Algorithm 1,
+    D-SRM): each rank holds a context over its shard, and each EM iteration
+    is this rank's share of the E-step, one NCCL all-reduce of y (k x T) and
+    four sums, the rest of the E-step and the M-step of its own subjects
+    (shard.fit_sharded).  One step = one EM iteration of the whole workload,
+    so `value` is whole-workload EM iterations/s ("scaling": "strong")."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1608_04647_gb300 as srm
+    from paper_1608_04647_gb300.shard import fit_sharded, imbalance, shard_subjects
+    from synth.planted_torch import planted_dataset_torch
+
+    spec, vox = workload(args.config, rank, args.subjects, args.voxels_cap)
+    T, k = spec.T, spec.k
+    plan = shard_subjects(vox, world)
+    mine = plan[rank]
+    d = planted_dataset_torch(spec, vox, device="cuda", subjects=mine)
+    stream = torch.cuda.Stream()
+    R = max(1, args.repeats)
+    max_iter = args.warmup + R * args.steps + 64
+    import tempfile
+    cache = os.path.join(tempfile.gettempdir(), "srm_plans_bench_sharded_c%d_rank%d.txt" % (args.config, rank))
+    if os.path.exists(cache):
+        os.remove(cache)
+    m = srm.SRM(d["X"], d["W0"], k, store="bf16", graph=False, max_iter=max_iter, stream=stream)
+    if not args.no_autotune:
+        m.autotune(cache, iters=4)
+    fit_sharded(m, args.warmup, dist.all_reduce)
+    m.synchronize()
+    regions = []
+    with ClockSampler(dev) as cs:
+        for _ in range(R):
+            dist.barrier()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fit_sharded(m, args.steps, dist.all_reduce)
+            e1.record(stream)
+            e1.synchronize()
+            m.synchronize()
+            regions.append(max_over_ranks(e0.elapsed_time(e1), world))
+    ms_step = statistics.median(regions) / args.steps
+    ll = m.ll()
+    lay = m.layout()
+    m.close()
+    # per-kernel times of this rank over a profiled run of the same steps
+    mp = srm.SRM(d["X"], d["W0"], k, store="bf16", profile=True, max_iter=max_iter, stream=stream)
+    if not args.no_autotune:
+        mp.autotune(cache, iters=4)
+    fit_sharded(mp, args.warmup, dist.all_reduce)
+    mp.kernel_times(reset=True)
+    fit_sharded(mp, args.steps, dist.all_reduce)
+    kt = mp.kernel_times()
+    mp.close()
+    ks = {n: {"launches": l, "ms": t} for n, (l, t) in kt.items() if l > 0}
+    myvox = [vox[i] for i in mine]
+    e_bytes, m_bytes = algorithmic_bytes(myvox, T, k, 2, 2)
+    f_bytes = single_pass_bytes(myvox, T, k, 2, 2)
+    roofline = roofline_of(ks, "bf16", e_bytes, m_bytes, f_bytes, len(myvox), -1, int(sum(myvox)), peaks)
+    clocks = cs.summary()
+    out = {
+        "metric": METRIC, "value": round(1000.0 / ms_step, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic planted (Sec. II-A model), generated on device",
+        "config": {"workload": spec.name, "N": len(vox), "T": T, "k": k, "voxels_total": int(sum(vox)),
+                   "store": "bf16", "parallelism": "subjects sharded over %d ranks (Algorithm 1), one NCCL "
+                   "all-reduce of y and 4 sums per EM iteration" % world,
+                   "shard_imbalance": round(imbalance(vox, plan), 4), "subjects_per_rank": [len(p) for p in plan],
+                   "l2": "inputs larger than L2 (resident X^ %.2f GB per rank)" % (lay["xhat_bytes"] / 1e9),
+                   "timing": "median of %d timed regions of %d EM iterations, max over ranks" % (R, args.steps),
+                   "regions_ms": [round(x, 4) for x in regions]},
+        "roofline": roofline, "clocks": clocks,
+        "gpu_launches": int(round(sum(v["launches"] for v in ks.values()))),
+        "kernels_ms_per_step": {n: round(v["ms"] / args.steps, 4) for n, v in ks.items()},
+        "ll_monotone": ll_monotonicity(ll),
+        "e2e": {"value": None, "unit": UNIT, "skipped": "the sharded run reports device-resident throughput only"},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(spec, myvox, d, budget_s=args.cpu_budget)
+    return out
+
+
+def run_ours(args, rank, world):
     import torch
 
     import paper_1608_04647_gb300 as srm
-    Xh = [x.to("cpu").pin_memory() for x in d["X"]]
+    from paper_1608_04647_gb300 import _build
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    srm.load_library()
+    peaks = load_peaks()
+    if args.sharded:
+        return bench_sharded(args, rank, world, dev, peaks)
+    stores = [args.store] if args.store != "both" else ["bf16", "f32"]
+    out = bench_workload(args, args.config, rank, world, stores, dev, peaks)
+    extras = [int(x) for x in args.extra_configs.split(",") if x.strip() != ""] \
+        if args.subjects == 0 and args.voxels_cap == 0 else []
+    for c in extras:
+        if c == args.config:
+            continue
+        key = EXTRA_KEYS.get(c, "config_%d" % c)
+        out[key] = bench_workload(args, c, rank, world, stores, dev, peaks)
+    out["extra_keys"] = sorted(k for k in out if k not in ("metric", "value", "unit", "n_gpus", "steps", "warmup",
+                                                           "ms_per_step", "higher_is_better", "scaling",
+                                                           "vs_baseline", "dtype", "data", "config", "roofline",
+                                                           "cpu_baseline", "clocks", "e2e", "gpu_launches"))
+    return out
+
+
+EXTRA_KEYS = {0: "raider_like", 1: "greeneyes_like", 2: "batched_64", 3: "forrest_like", 4: "forrest1024_like"}
+
+
+def run_e2e(args, d, spec, vox, stream, world, tune_cache=None, store="bf16"):
+    """One whole user job through the public API with host buffers: pageable
+    host X (FP32, as a caller's NumPy arrays would be) -> srm_init with
+    SRM_HOST_INPUT (the library streams each subject through one staging
+    buffer and centres it) -> srm_fit(n_iter) -> parameters, E[S] and the
+    log-likelihood back to the host.  Value = EM iterations / job time."""
+    import torch
+
+    import paper_1608_04647_gb300 as srm
+    Xh = [x.to("cpu") for x in d["X"]]  # pageable host memory
     n_iter = spec.n_iter
     h2d = sum(x.numel() * x.element_size() for x in Xh)
     times = []
     for rep in range(2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        store = args.store if args.store != "both" else "bf16"
         m = srm.SRM(Xh, d["W0"], spec.k, store=store, graph=True, host_input=True, stream=stream,
                     max_iter=n_iter + 8, single_pass=args.single_pass)
         if store == "bf16" and tune_cache:
@@ -391,85 +571,152 @@ def run_e2e(args, d, spec, vox, stream, world, tune_cache=None):
         t1 = time.perf_counter()
         m.close()
         times.append(t1 - t0)
+    del Xh
     d2h = S.numel() * 4 + rho2.nbytes + sig.nbytes + ll.nbytes
     best = min(times)
     return {"value": round(world * n_iter / best, 3), "unit": UNIT, "job_s": round(best, 4),
+            "jobs_s": [round(t, 4) for t in times],
             "iterations_per_job": n_iter, "h2d_bytes_per_step": int(h2d / n_iter),
             "d2h_bytes_per_step": int(d2h / n_iter),
-            "note": "step = one EM iteration of a %d-iteration job; host->device copy of X from pinned memory, "
-                    "centring, fit and result read-back inside the timed region" % n_iter}
+            "note": "step = one EM iteration of a %d-iteration job; host->device copy of X from pageable host "
+                    "memory (FP32), centring, fit and result read-back inside the timed region; best of 2 jobs"
+                    % n_iter}
 
 
 def blas_threads():
+    """Threads of the BLAS the oracle's NumPy uses (threadpoolctl if present,
+    else the OpenBLAS entry point of the loaded library), or None."""
     try:
         from threadpoolctl import threadpool_info
         info = threadpool_info()
         return max((i.get("num_threads", 0) for i in info), default=None)
     except Exception:
-        return None
+        pass
+    try:
+        import ctypes
+        import numpy  # noqa: F401  (loads its BLAS)
+        libs = set()
+        with open("/proc/self/maps") as f:
+            for line in f:
+                p = line.split()[-1]
+                if "openblas" in os.path.basename(p).lower() and p.endswith(tuple(".so" + s for s in ("", ".0"))) \
+                        or ("openblas" in p.lower() and ".so" in p):
+                    libs.add(p)
+        for p in libs:
+            lib = ctypes.CDLL(p)
+            for fn in ("scipy_openblas_get_num_threads64_", "openblas_get_num_threads64_",
+                       "openblas_get_num_threads"):
+                if hasattr(lib, fn):
+                    return int(getattr(lib, fn)())
+    except Exception:
+        pass
+    return None
 
 
-def oracle_sample(spec, vox, max_elems=4e7, max_subjects=4):
-    """A bounded sample of the workload for the FP64 oracle: the first
-    subjects, each cut to at most max_elems / T voxel rows, at most
-    max_subjects of them, drawn from the same planted generator."""
-    import synth
-    rows = max(spec.k + 1, int(max_elems // spec.T))
-    sub = [min(int(v), rows) for v in vox[:max_subjects]]
-    while len(sub) > 1 and sum(sub) * spec.T > max_elems:
-        sub.pop()
-    dd = synth.planted_dataset(spec, voxel_counts=sub, dtype=np.float64)
-    return sub, dd
+def oracle_seconds_per_voxel(T, k):
+    """Estimated time of one FP64 oracle EM iteration per voxel row on this
+    kind of host (16 Grace cores: 2.8 ns per voxel x TR at k = 50, linear in
+    k), used only to size the bounded samples."""
+    return 2.8e-9 * T * max(k, 10) / 50.0
 
 
-def cpu_baseline(spec, vox, budget_s=20.0):
-    """The FP64 oracle (as it stands) on the host cores: EM iterations over a
-    bounded sample of the workload, time scaled to the whole workload by
-    voxel count (the oracle's per-iteration cost is linear in the voxels)."""
+def sample_rows(vox, T, k, target_s):
+    """A bounded sample of the workload for the oracle: its first subjects,
+    whole, while one EM iteration over them stays within about `target_s`
+    seconds; if even the first subject is larger, that subject cut to its
+    first rows.  Returns the voxel rows taken from each sampled subject."""
+    per = oracle_seconds_per_voxel(T, k)
+    rows, tot = [], 0.0
+    for v in vox:
+        if rows and tot + v * per > target_s:
+            break
+        rows.append(int(v))
+        tot += v * per
+    if len(rows) == 1 and rows[0] * per > target_s:
+        rows[0] = max(k + 1, int(target_s / per))
+    return rows
+
+
+def describe_sample(rows, vox, T, k):
+    cut = len(rows) == 1 and rows[0] < vox[0]
+    frac = float(sum(rows)) / float(sum(vox))
+    what = ("the first %d voxel rows of subject 0 (of %d)" % (rows[0], vox[0]) if cut else
+            "the first %d of %d subjects" % (len(rows), len(vox)))
+    return frac, "%s: %d of %d voxels (%.3f%% of the workload), T = %d, k = %d" % (
+        what, int(sum(rows)), int(sum(vox)), 100 * frac, T, k)
+
+
+def cpu_baseline(spec, vox, d, budget_s=20.0):
+    """The FP64 oracle as it stands, on this host's cores: consecutive whole
+    EM iterations (Algorithm 1: E-step then M-step over every sampled
+    subject) on a bounded sample of the workload, with the very data the
+    GPU fitted (copied down and up-cast) and the same W^0, until the budget
+    is spent or the workload's schedule ends.  The oracle's cost per
+    iteration is linear in the voxels, so EM iterations/s of the whole
+    workload = sample fraction / seconds per sample iteration."""
     import oracle
-    sub, dd = oracle_sample(spec, vox)
-    Xh = [oracle.center(x)[0] for x in dd["X"]]
-    del dd["X"]
+    rows = sample_rows(vox, spec.T, spec.k, budget_s / 3.0)
+    Xh = [oracle.center(d["X"][i][:r].double().cpu().numpy())[0] for i, r in enumerate(rows)]
+    W0 = []
+    for i, r in enumerate(rows):
+        w = d["W0"][i][:r].double().cpu().numpy()
+        if r < vox[i]:
+            w = np.linalg.qr(w)[0]  # a cut W^0 is re-orthonormalised (same cost per iteration)
+        W0.append(w)
+    state = {"W": W0, "rho2": None, "Sigma": None}
     t0 = time.perf_counter()
     iters = 0
-    while True:
-        oracle.fit(Xh, dd["W0"], 1, centered=True)
+    while iters < spec.n_iter:
+        r = oracle.fit(Xh, state["W"], 1, rho2_0=state["rho2"], Sigma_0=state["Sigma"], centered=True)
+        state = {"W": r["W"], "rho2": r["rho2"], "Sigma": r["Sigma_s"]}
         iters += 1
-        if time.perf_counter() - t0 > budget_s or iters >= 5:
+        if time.perf_counter() - t0 > budget_s:
             break
     dt = (time.perf_counter() - t0) / iters
-    scale = float(sum(vox)) / float(sum(sub))
-    per_iter_full = dt * scale
-    return {"value": round(1.0 / per_iter_full, 6), "unit": UNIT, "cores": os.cpu_count(),
+    frac, what = describe_sample(rows, vox, spec.T, spec.k)
+    return {"value": round(frac / dt, 6), "unit": UNIT, "cores": os.cpu_count(),
             "blas_threads": blas_threads(), "kind": "oracle",
-            "sample": "%d subject(s) of %d, %d voxels in all (of %d), T = %d, %d EM iteration(s) of the FP64 NumPy "
-                      "oracle; time scaled by total voxels (x%.1f)" % (len(sub), len(vox), int(sum(sub)),
-                                                                      int(sum(vox)), spec.T, iters, scale)}
+            "seconds_per_sample_iteration": round(dt, 4), "sample_iterations": iters,
+            "sample": "%s; %d consecutive EM iterations of the FP64 NumPy oracle from W^0 on the data the GPU "
+                      "fitted; value = sample fraction / seconds per sample iteration" % (what, iters)}
 
 
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle as it stands, on the host cores, on a
-    bounded sample of the same workload; each step one EM iteration over the
-    sample, time scaled to the whole workload by voxel count."""
+    bounded sample of the same workload.  Each step is one whole EM
+    iteration (Algorithm 1) of the oracle over the workload's first subjects
+    (all of it where one iteration of the whole workload is short), drawn on
+    the host by the same planted generator.  ms_per_step is the measured
+    time of one such step; value = EM iterations/s of the whole workload =
+    (sample voxels / workload voxels) / seconds per step, the oracle's cost
+    being linear in the voxels."""
     import oracle
-    spec, vox = workload(args.config, rank, args.subjects)
-    sub, dd = oracle_sample(spec, vox, max_elems=2e7, max_subjects=2)
+    import synth
+    spec, vox = workload(args.config, rank, args.subjects, args.voxels_cap)
+    rows = sample_rows(vox, spec.T, spec.k, args.ref_step_s)
+    dd = synth.planted_dataset(spec, voxel_counts=rows, dtype=np.float64)
     Xh = [oracle.center(x)[0] for x in dd["X"]]
+    del dd["X"]
+    state = {"W": dd["W0"], "rho2": None, "Sigma": None}
+
+    def step():
+        r = oracle.fit(Xh, state["W"], 1, rho2_0=state["rho2"], Sigma_0=state["Sigma"], centered=True)
+        state.update(W=r["W"], rho2=r["rho2"], Sigma=r["Sigma_s"])
+
     for _ in range(args.warmup):
-        oracle.fit(Xh, dd["W0"], 1, centered=True)
+        step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.fit(Xh, dd["W0"], 1, centered=True)
+        step()
     dt = (time.perf_counter() - t0) / args.steps
-    scale = float(sum(vox)) / float(sum(sub))
-    per_iter = dt * scale
-    value = 1.0 / per_iter
-    sample = ("%d subject(s) of %d, %d voxels in all (of %d) per step, one FP64 oracle EM iteration, time scaled by "
-              "total voxels (x%.1f)" % (len(sub), len(vox), int(sum(sub)), int(sum(vox)), scale))
+    frac, what = describe_sample(rows, vox, spec.T, spec.k)
+    value = frac / dt
+    sample = ("%s, drawn on the host by the same planted generator; each step one EM iteration of the FP64 NumPy "
+              "oracle over it, consecutive from W^0; value = sample fraction / seconds per step" % what)
     return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per_iter * 1e3, 3),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic planted (Sec. II-A model)",
+            "data": "synthetic planted (Sec. II-A model), drawn on the host",
             "config": {"workload": spec.name, "N": len(vox), "T": spec.T, "k": spec.k,
                        "voxels_total": int(sum(vox))},
             "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": os.cpu_count(),
@@ -730,12 +977,21 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--config", type=int, default=4, help="headline workload (4: forrest-1024-like)")
+    ap.add_argument("--extra-configs", default="3,1", help="workloads timed in the same run under extra keys "
+                    "(comma list; empty for none)")
+    ap.add_argument("--repeats", type=int, default=5, help="timed regions of K steps each; the median is reported")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--store", choices=["bf16", "f32", "both"], default="both")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sharded", action="store_true", help="spread the headline workload's subjects over the "
+                    "ranks with one NCCL all-reduce per EM iteration (the default under torchrun with N > 1)")
+    ap.add_argument("--replicas", action="store_true", help="under torchrun: independent replicas instead of "
+                    "the sharded workload")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle time for cpu_baseline")
+    ap.add_argument("--ref-step-s", type=float, default=1.0, help="reference arm: about this many seconds of "
+                    "oracle work per step (the sample size)")
     ap.add_argument("--k-sweep", action="store_true", help="throughput against k (extra lines, not the bench line)")
     ap.add_argument("--single-pass", action="store_true", help="force the single-pass form (SRM_SINGLE_PASS), "
                     "no autotuning")
@@ -743,6 +999,8 @@ def main():
     ap.add_argument("--tune-cache", default=None, help="plan cache file kept across runs (default: a fresh one)")
     ap.add_argument("--plan", default="", help="launch-plan fields set after tuning, e.g. 'single_pass=0' "
                     "(srm_set_plan; for profiling one form)")
+    ap.add_argument("--voxels-cap", type=int, default=0, help="cut every subject to at most this many voxels (a "
+                    "smaller case of the same T and k, for ncu captures)")
     ap.add_argument("--subjects", type=int, default=0, help="only the first K subjects of the workload (a smaller "
                     "case of the same shapes, for ncu captures)")
     ap.add_argument("--htfa", action="store_true", help="the HTFA cost evaluation instead of the EM iteration "
@@ -766,12 +1024,18 @@ def main():
             return
         print(json.dumps(run_reference(args, rank, world)))
         return
-    if world > 1:
+    if world > 1 and not args.replicas:
+        args.sharded = True
+    if world > 1 or args.sharded:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29511")
+        os.environ.setdefault("RANK", str(rank))
+        os.environ.setdefault("WORLD_SIZE", str(world))
         torch.distributed.init_process_group("nccl")
     out = run_ours(args, rank, world)
-    if world > 1:
+    if world > 1 or args.sharded:
         import torch
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
