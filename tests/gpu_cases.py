@@ -60,3 +60,33 @@ def rel_errors(g, o):
     el = np.max(np.abs(g["ll"] - o["ll"]) / np.abs(o["ll"]))
     esg = np.abs(g["Sigma_s"] - o["Sigma_s"]).max() / np.abs(o["Sigma_s"]).max()
     return {"W": ew, "ES": es, "rho2": er, "ll": el, "Sigma_s": esg}
+
+
+# Largest log-likelihood decrease accepted per iteration, as a fraction of
+# |LL|.  EM never decreases the likelihood in exact arithmetic.  The FP32
+# form evaluates the quadratic terms of the LL (sum_i ||X^_i||^2 / rho_i^2
+# and <y, Phi y>, each at most |LL|) from FP32 sums: 2^-20 |LL| allows a few
+# ulps of FP32 on them.  The BF16 form also takes its M-step's polar factor
+# from the BF16-rounded A_i, which is not the exact maximiser of the
+# Q-function; the loss is second order in that rounding, u_bf16^2 = 2^-18 of
+# the quadratic terms, so 2^-16 |LL| allows a factor of 4 on it.
+LL_DROP = {"f32": 2.0 ** -20, "bf16": 2.0 ** -16}
+
+
+def check_ll_trace(g_ll, o_ll, store, rel_inc=2e-2):
+    """The GPU's log-likelihood trace against EM's monotonicity and against
+    the oracle's per-iteration increments.  Every decrease is reported; none
+    may exceed LL_DROP[store] |LL|.  Where the oracle's own increment is
+    large against that bound (100 x), the GPU's increment must match it to
+    `rel_inc` relative.  Returns the decreases (iteration, nats)."""
+    g_ll = np.asarray(g_ll, dtype=np.float64)
+    o_ll = np.asarray(o_ll, dtype=np.float64)
+    dg, do = np.diff(g_ll), np.diff(o_ll)
+    bound = LL_DROP[store] * np.abs(g_ll[1:])
+    drops = [(j + 1, float(-x)) for j, x in enumerate(dg) if x < 0]
+    if drops:
+        print("log-likelihood decreases (iteration, nats):", drops, "bound", bound.max())
+    assert np.all(dg >= -bound), (drops, bound)
+    big = do > 100 * bound
+    assert np.all(np.abs(dg[big] - do[big]) <= rel_inc * do[big]), list(zip(dg[big], do[big]))
+    return drops

@@ -2,9 +2,16 @@
 configuration bench.py times: the batched BF16 form, the autotuned plan and
 CUDA-graph iterations.
 
-The FP64 oracle cannot run whole EM fits at these sizes.  So each check
-starts from the GPU's own state after a fit.  From that state and the same
-seeded inputs, the oracle computes outputs it can afford one by one:
+Whole fits are compared with the oracle in tests/test_config_scale.py: the
+greeneyes-like workload in full, and the forrest-like shape on three
+subjects.  Here the workloads run at their full sizes: greeneyes-like,
+batched (64 subjects), forrest-like (8 x 600000 voxels, T = 3500, k = 100,
+34 GB resident) and forrest-1024-like (1024 subjects, 41 GB).  A whole FP64
+oracle fit of the larger ones would take many minutes (about a minute per
+iteration on 16 host cores for forrest-1024-like) and more host memory than
+the box has in FP64.  So each check starts from the GPU's own state after
+the workload's fit.  From that state and the same seeded inputs, the oracle
+computes outputs it can afford one by one:
 
 * E-step: E[S] on sampled columns.  The reduced E-step acts on each column
   t separately (y_t = sum_i rho_i^-2 W_i^T x^_it, E[s_t] = Phi y_t), so
@@ -13,15 +20,20 @@ seeded inputs, the oracle computes outputs it can afford one by one:
   Sigma_s^new that the oracle forms from it.
 
 Properties that hold at any size are checked too: a log-likelihood that
-does not decrease, orthonormal W_i, positive rho_i^2, and a symmetric
-positive definite Sigma_s.  The bar is the BF16 form's 2e-2 relative
-(max-norm): the oracle consumes the unrounded FP32 input.  The sample means
-of the columns are prepared with PyTorch on the device (input preparation,
-not the library).  The oracle does the E-step and M-step arithmetic."""
+does not decrease beyond the rounding bound of the BF16 form, orthonormal
+W_i, positive rho_i^2, and a symmetric positive definite Sigma_s.  The bar
+is the BF16 form's 2e-2 relative (max-norm): the oracle consumes the
+unrounded FP32 input.  The sample means of the columns are prepared with
+PyTorch on the device (input preparation, not the library).  The oracle
+does the E-step and M-step arithmetic.  The number of subjects whose polar
+factor failed its Newton-Schulz certificate in the last M-step is
+printed."""
 from collections.abc import Sequence
 
 import numpy as np
 import pytest
+
+from gpu_cases import LL_DROP
 
 pytestmark = pytest.mark.gpu
 TOL_BF16 = 2e-2
@@ -53,9 +65,10 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / np.abs(b).max())
 
 
-# greeneyes-like (16 subjects, T = 1000) and forrest-1024-like (1024
-# subjects, T = 500, 41 GB resident): the workloads of the bench lines
-@pytest.mark.parametrize("config", [1, 4])
+# greeneyes-like (16 subjects, T = 1000), batched (64 subjects of
+# 10,000-200,000 voxels), forrest-like (T = 3500, k = 100, 34 GB resident) and
+# forrest-1024-like (1024 subjects, T = 500, 41 GB resident)
+@pytest.mark.parametrize("config", [1, 2, 3, 4])
 def test_full_size_sampled_parity(config):
     import torch
 
@@ -74,8 +87,12 @@ def test_full_size_sampled_parity(config):
     rho2, sig = m.params()
     print(spec.name, plan)
 
+    sweeps = srm.srm_debug_eig_sweeps(m.ctx, N + 1)[:N]
+    print("polar factors of the last M-step: %d certified Newton-Schulz, %d eigen-decomposition fallbacks"
+          % (int(np.sum(sweeps < 256)), int(np.sum(sweeps >= 256))))
+
     # properties at any size
-    assert np.all(np.isfinite(ll)) and np.all(np.diff(ll) >= -1e-6 * np.abs(ll[1:])), ll
+    assert np.all(np.isfinite(ll)) and np.all(np.diff(ll) >= -LL_DROP["bf16"] * np.abs(ll[1:])), ll
     assert np.all(rho2 > 0)
     np.testing.assert_allclose(sig, sig.T, rtol=0, atol=1e-12 * np.abs(sig).max())
     assert np.linalg.eigvalsh(sig).min() > 0
@@ -100,12 +117,13 @@ def test_full_size_sampled_parity(config):
     # the GPU's E[S] (all columns) and the Sigma_s^new it implies
     sub = sorted({0, N // 2, N - 1})
     sig_new = oracle.sigma_update({"ES": es_gpu, "Phi": est["Phi"]}, T)
-    xh, sq = [], []
-    for i in sub:
+    w_o, r_o = [], []
+    for i in sub:  # one subject at a time: a forrest-like subject is 17 GB in FP64
         x_i, _, s_i = oracle.center(d["X"][i].cpu().numpy())
-        xh.append(x_i)
-        sq.append(s_i)
-    w_o, r_o = oracle.mstep(xh, sq, es_gpu, sig_new)
+        w, r = oracle.mstep([x_i], [s_i], es_gpu, sig_new)
+        w_o.append(w[0])
+        r_o.append(r[0])
+        del x_i
     m.mstep()
     rho2_new, sig_gpu = m.params()
     err_w = max(_rel(m.get_w(i).double().cpu().numpy(), w_o[j]) for j, i in enumerate(sub))

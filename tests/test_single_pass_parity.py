@@ -8,7 +8,7 @@ tails, k from 1 to 64, many subjects, and a shape the form does not support
 import numpy as np
 import pytest
 
-from gpu_cases import Case, make_inputs, rel_errors, run_gpu, run_oracle
+from gpu_cases import Case, check_ll_trace, make_inputs, rel_errors, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 TOL_BF16 = 2e-2
@@ -49,7 +49,7 @@ def test_single_pass_matches_oracle(case):
         assert e <= TOL_BF16, (key, e)
     for w in g["W"]:
         np.testing.assert_allclose(w.T @ w, np.eye(case.k), atol=2e-2)
-    assert np.all(np.diff(g["ll"]) >= -TOL_BF16 * np.abs(g["ll"][1:]))
+    check_ll_trace(g["ll"], o["ll"], "bf16")
 
 
 def test_single_pass_ignored_where_unsupported():
