@@ -91,6 +91,8 @@ typedef struct {
     uint32_t flags;          /* SRM_* flags above */
     int32_t max_iter;        /* capacity of the log-likelihood trace (>= total iterations
                                 run over the context's life; 0 -> 1024) */
+    uint64_t seed;           /* seed of the random orthogonal W^0 that srm_init draws when
+                                it is given no W0 (see srm_init) */
 } srm_config;
 
 typedef struct srm_ctx srm_ctx;  /* opaque; created by srm_init, freed by srm_destroy */
@@ -106,7 +108,18 @@ typedef struct srm_ctx srm_ctx;  /* opaque; created by srm_init, freed by srm_de
  *             the library keeps its own demeaned copy in cfg->store_dtype.
  *   W0_dev    N device pointers; W0_dev[i] is v_i x k row-major FP32 with
  *             orthonormal columns (Algorithm 1: "a random orthogonal matrix").
- *             Read during the call only.
+ *             Read during the call only.  NULL: the library draws W^0 itself
+ *             from the Haar distribution, as the Q factor (with a positive-
+ *             diagonal R) of a v_i x k matrix G_i of standard normals from the
+ *             counter-based generator Philox4x64-10 (Salmon et al., SC 2011):
+ *             key (cfg->seed, 0), counter (b, i, 0, 0) for block b of subject
+ *             i; each output word w gives u = ((w >> 12) + 1/2) 2^-52; the
+ *             word pairs (w0, w1), (w2, w3) of block b give entries 4b..4b+3
+ *             of G_i (row-major) by Box-Muller, sqrt(-2 ln u_a) cos(2 pi u_b)
+ *             and sqrt(-2 ln u_a) sin(2 pi u_b).  Any implementation of this
+ *             definition draws the same W^0 (to rounding).  Q is formed by two
+ *             Cholesky-QR passes in FP64 in a temporary workspace
+ *             (about 20 v_max k bytes).
  *   stream    cudaStream_t the context runs on, or NULL for a library-owned
  *             non-blocking stream.  The device is the current CUDA device.
  *   out       receives the context.
@@ -141,6 +154,41 @@ SRM_API srm_status srm_mstep(srm_ctx* ctx);
  * otherwise the call is asynchronous.
  */
 SRM_API srm_status srm_fit(srm_ctx* ctx, int32_t n_iter, double* ll_host);
+
+/*
+ * Sharded E-step (Algorithm 1, D-SRM: subjects are spread over processes and
+ * the E-step's one exchange is the Reduce of eq:srm_mean_distributed).  Each
+ * process holds a context over its own subjects.  Per iteration:
+ *   srm_estep_partial(ctx, y, sums)   this context's share;
+ *   the caller sums y and sums over all contexts (an all-reduce, e.g. NCCL);
+ *   srm_estep_finish(ctx, y, sums)    the rest of the E-step from the totals;
+ *   srm_mstep(ctx)                    W_i and rho_i^2 of this context's subjects.
+ * Every context then holds the same Sigma_s, E[S] and log-likelihood trace,
+ * equal (to rounding) to one context over all subjects.  Sigma_s and E[S]
+ * are formed redundantly in every context, so no broadcast follows.
+ *
+ * srm_estep_partial -- the pending M-step tail, the E-pass and the reduction
+ * over this context's subjects, stopped before Phi:
+ *   y     k x T row-major FP64, device pointer (written):
+ *         y = sum over this context's subjects of rho_i^-2 W_i^T X^_i.
+ *   sums  4 FP64, device pointer (written): { sum rho_i^-2 (eq:srm_wt_psi_w),
+ *         sum v_i ln rho_i^2, sum ||X^_i||_F^2 / rho_i^2, sum v_i } over this
+ *         context's subjects (the log-likelihood's sums over subjects).
+ * Asynchronous on the context's stream; the caller must order its reduction
+ * after it (e.g. on the same stream).  SRM_ERR_STATE while a partial E-step
+ * awaits its finish; until srm_estep_finish, srm_estep, srm_mstep, srm_fit,
+ * srm_set_plan, srm_autotune and the state calls return SRM_ERR_STATE.
+ *
+ * srm_estep_finish -- Phi = (Sigma_s^-1 + rho_0 I)^-1 with rho_0 = sums[0]
+ * (eq:srm_inversion_opt), E[S] = Phi y (eq:srm_mean_distributed), and, with
+ * the next M-step, Sigma_s^new (eq:srm_variance_update_optimized) and the
+ * log-likelihood of the parameters this E-step used, over all subjects.
+ *   y, sums  the totals over every context, laid out as above (device
+ *            pointers, read by launches on the context's stream).
+ * SRM_ERR_STATE without a preceding srm_estep_partial.  Asynchronous.
+ */
+SRM_API srm_status srm_estep_partial(srm_ctx* ctx, double* y_dev, double* sums_dev);
+SRM_API srm_status srm_estep_finish(srm_ctx* ctx, const double* y_dev, const double* sums_dev);
 
 /*
  * srm_transform -- map new data of one subject to the shared space

@@ -1,4 +1,5 @@
-"""FP64 CPU oracle for the pSRM EM iteration (``psrm``) and the HTFA
+"""FP64 CPU oracle for the pSRM EM iteration (``psrm``; ``init``: Algorithm
+1's random orthogonal W^0 drawn from a seed, as the library draws it) and the HTFA
 local-step evaluations (``htfa``: the factor matrix of Eq. 14, the
 residual of the local objective and the z-score).
 
@@ -23,3 +24,4 @@ from .psrm import (  # noqa: F401
     State,
 )
 from .htfa import rbf_factors, residual as htfa_residual, residual_batch as htfa_residual_batch, zscore  # noqa: F401,E402
+from .init import haar_w0, philox4x64_10, standard_normals  # noqa: F401,E402

@@ -27,7 +27,7 @@ __all__ = [
     "srm_get_params", "srm_get_ll", "srm_synchronize", "srm_get_state", "srm_set_state",
     "srm_get_kernel_times", "srm_layout", "srm_last_error", "srm_destroy", "srm_debug_mma",
     "srm_transform_noalloc", "srm_debug_eig_sweeps", "srm_debug_wait", "srm_map", "srm_plan", "srm_get_plan", "srm_set_plan",
-    "srm_autotune",
+    "srm_autotune", "srm_estep_partial", "srm_estep_finish",
 ]
 
 SRM_OK, SRM_ERR_ARG, SRM_ERR_CUDA, SRM_ERR_NOMEM, SRM_ERR_NUMERIC, SRM_ERR_STATE, SRM_ERR_UNSUPPORTED = range(7)
@@ -58,6 +58,7 @@ class srm_config(ctypes.Structure):
         ("store_dtype", ctypes.c_int),
         ("flags", ctypes.c_uint32),
         ("max_iter", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
     ]
 
 
@@ -101,6 +102,8 @@ def load_library(path: Optional[str] = None):
                           ctypes.POINTER(_P)]),
         "srm_estep": (st, [_P]),
         "srm_mstep": (st, [_P]),
+        "srm_estep_partial": (st, [_P, _P, _P]),
+        "srm_estep_finish": (st, [_P, _P, _P]),
         "srm_fit": (st, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
         "srm_transform": (st, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
         "srm_get_w": (st, [_P, ctypes.c_int32, _P]),
@@ -153,11 +156,12 @@ def _check(status: int, where: str):
 
 
 # ---------------------------------------------------------------- C names
-def srm_init(cfg: srm_config, X_ptrs: Sequence[int], W0_ptrs: Sequence[int], stream: int = 0) -> int:
+def srm_init(cfg: srm_config, X_ptrs: Sequence[int], W0_ptrs: Optional[Sequence[int]], stream: int = 0) -> int:
+    """W0_ptrs None: the library draws a seeded random orthogonal W^0 (cfg.seed; include/srm.h)."""
     lib = load_library()
     n = len(X_ptrs)
     xa = (_P * n)(*X_ptrs)
-    wa = (_P * n)(*W0_ptrs)
+    wa = (_P * n)(*W0_ptrs) if W0_ptrs is not None else None
     out = _P()
     _check(lib.srm_init(ctypes.byref(cfg), xa, wa, _P(stream or None), ctypes.byref(out)), "srm_init")
     return out.value
@@ -169,6 +173,18 @@ def srm_estep(ctx: int):
 
 def srm_mstep(ctx: int):
     _check(load_library().srm_mstep(_P(ctx)), "srm_mstep")
+
+
+def srm_estep_partial(ctx: int, y_ptr: int, sums_ptr: int):
+    """This context's share of a sharded E-step (include/srm.h): y (k x T
+    FP64) and the four sums over its subjects, both device buffers."""
+    _check(load_library().srm_estep_partial(_P(ctx), _P(y_ptr), _P(sums_ptr)), "srm_estep_partial")
+
+
+def srm_estep_finish(ctx: int, y_ptr: int, sums_ptr: int):
+    """The rest of a sharded E-step from y and the sums totalled over all
+    contexts (device buffers)."""
+    _check(load_library().srm_estep_finish(_P(ctx), _P(y_ptr), _P(sums_ptr)), "srm_estep_finish")
 
 
 def srm_fit(ctx: int, n_iter: int, n_out: int) -> np.ndarray:
@@ -303,13 +319,23 @@ def srm_destroy(ctx: int):
 
 
 # ---------------------------------------------------------------- wrapper
+def _check_buffers(m, y, sums):
+    import torch
+    if not (y.is_cuda and sums.is_cuda and y.dtype == torch.float64 and sums.dtype == torch.float64
+            and y.is_contiguous() and tuple(y.shape) == (m.k, m.T) and sums.numel() >= 4):
+        raise ValueError("sharded E-step buffers: y must be a contiguous CUDA float64 (k, T) tensor and sums a "
+                         "CUDA float64 tensor of 4")
+
+
 class SRM:
     """One pSRM context on the current CUDA device.
 
     X:   list of N subject matrices (v_i x T, row-major): torch CUDA tensors
          (float32 or bfloat16), or with ``host_input=True`` contiguous CPU
          tensors / NumPy arrays (pinned memory recommended).
-    W0:  list of N torch CUDA float32 tensors (v_i x k) with orthonormal columns.
+    W0:  list of N torch CUDA float32 tensors (v_i x k) with orthonormal columns,
+         or None: the library draws Algorithm 1's random orthogonal W^0 from
+         `seed` (Philox4x64-10 normals, Q of their QR; see include/srm.h).
     store: "bf16" -> batched tensor-core form; "f32" -> plain per-subject form.
     single_pass: with store="bf16", k <= 64 and T <= 1024, stream X^ once per
          EM iteration (SRM_SINGLE_PASS); ignored elsewhere (see layout()).
@@ -317,7 +343,7 @@ class SRM:
 
     def __init__(self, X: Sequence, W0: Sequence, k: int, store: str = "bf16", graph: bool = False,
                  final_ll: bool = False, profile: bool = False, host_input: bool = False,
-                 max_iter: int = 1024, stream=None, single_pass: bool = False):
+                 max_iter: int = 1024, stream=None, single_pass: bool = False, seed: int = 0):
         import torch
 
         self.N = len(X)
@@ -344,12 +370,12 @@ class SRM:
             flags |= SRM_SINGLE_PASS
         self.final_ll = final_ll
         self.cfg = srm_config(self.N, ctypes.cast(self._vox, ctypes.POINTER(ctypes.c_int64)), self.T, self.k,
-                              in_dtype, SRM_BF16 if store == "bf16" else SRM_F32, flags, max_iter)
+                              in_dtype, SRM_BF16 if store == "bf16" else SRM_F32, flags, max_iter, int(seed))
         if host_input:
             xp = [x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr() for x in X]
         else:
             xp = [x.data_ptr() for x in X]
-        wp = [w.data_ptr() for w in W0]
+        wp = [w.data_ptr() for w in W0] if W0 is not None else None
         self._stream = stream
         s = stream.cuda_stream if stream is not None else 0
         self.ctx = srm_init(self.cfg, xp, wp, s)
@@ -359,6 +385,23 @@ class SRM:
 
     def mstep(self):
         srm_mstep(self.ctx)
+
+    def shard_buffers(self):
+        """Device buffers for a sharded E-step: y (k x T) and the 4 sums, FP64."""
+        import torch
+        return (torch.empty((self.k, self.T), dtype=torch.float64, device="cuda"),
+                torch.empty(4, dtype=torch.float64, device="cuda"))
+
+    def estep_partial(self, y, sums):
+        """This context's share of a sharded E-step into the device tensors
+        y (k x T) and sums (4), FP64 (see include/srm.h)."""
+        _check_buffers(self, y, sums)
+        srm_estep_partial(self.ctx, y.data_ptr(), sums.data_ptr())
+
+    def estep_finish(self, y, sums):
+        """Finish a sharded E-step from y and sums totalled over all contexts."""
+        _check_buffers(self, y, sums)
+        srm_estep_finish(self.ctx, y.data_ptr(), sums.data_ptr())
 
     def fit(self, n_iter: int) -> np.ndarray:
         return srm_fit(self.ctx, n_iter, n_iter + (1 if self.final_ll else 0))

@@ -362,6 +362,15 @@ srm_status do_mstep(Ctx* c) {
   return SRM_OK;
 }
 
+// A partial (sharded) E-step must be finished before anything else steps the EM.
+srm_status no_partial(srm_ctx* c, const char* who) {
+  if (c->shard_partial) {
+    set_error(std::string(who) + ": a sharded E-step awaits srm_estep_finish");
+    return SRM_ERR_STATE;
+  }
+  return SRM_OK;
+}
+
 srm_status valid_ctx(srm_ctx* ctx) {
   if (!ctx) {
     set_error("null context");
@@ -436,7 +445,7 @@ const char* srm_last_error(void) { return g_err.c_str(); }
 srm_status srm_init(const srm_config* cfg, const void* const* X, const float* const* W0_dev, void* stream,
                     srm_ctx** out) {
   g_err.clear();
-  if (!cfg || !X || !W0_dev || !out || !cfg->voxels) {
+  if (!cfg || !X || !out || !cfg->voxels) {
     set_error("srm_init: null argument");
     return SRM_ERR_ARG;
   }
@@ -465,7 +474,7 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
       set_error("srm_init: voxel count of subject " + std::to_string(i) + " must be in [k, 2^31]");
       return SRM_ERR_ARG;
     }
-    if (!X[i] || !W0_dev[i]) {
+    if (!X[i] || (W0_dev && !W0_dev[i])) {
       set_error("srm_init: null data or W0 pointer for subject " + std::to_string(i));
       return SRM_ERR_ARG;
     }
@@ -605,6 +614,17 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
       return fail(SRM_ERR_NOMEM);
     }
   }
+  // Algorithm 1's random orthogonal W^0 drawn here when the caller gives none
+  void* haar_work = nullptr;
+  if (!W0_dev && ce == cudaSuccess) {
+    ce = cudaMalloc(&haar_work, haar_workspace_bytes(c));
+    if (ce != cudaSuccess) {
+      cudaGetLastError();
+      if (stage) cudaFree(stage);
+      set_error("srm_init: cannot allocate the workspace of the random initial mappings");
+      return fail(SRM_ERR_NOMEM);
+    }
+  }
   for (int i = 0; i < N; ++i) {
     const void* src = X[i];
     if (stage) {
@@ -617,7 +637,7 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
     ce = launch_center(c, i, src, cfg->in_dtype, T);
     if (ce != cudaSuccess) break;
     if (c->profile) prof_end(c, KK_CENTER, ev0);
-    ce = launch_load_w0(c, i, W0_dev[i]);
+    ce = W0_dev ? launch_load_w0(c, i, W0_dev[i]) : launch_haar_w0(c, i, cfg->seed, haar_work);
     if (ce != cudaSuccess) break;
   }
   if (ce == cudaSuccess) ce = launch_sqnorm_reduce(c);
@@ -625,6 +645,7 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
   if (ce == cudaSuccess) ce = launch_phi(c);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
   if (stage) cudaFree(stage);
+  if (haar_work) cudaFree(haar_work);
   if (ce != cudaSuccess) return fail(cuda_fail(ce, "srm_init: centring / initialisation"));
   cudaFree(c->rowsq);
   c->rowsq = nullptr;
@@ -635,6 +656,7 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
 
 srm_status srm_estep(srm_ctx* c) {
   TRY(valid_ctx(c));
+  TRY(no_partial(c, "srm_estep"));
   if (c->n_ll >= c->max_iter) {
     set_error("srm_estep: log-likelihood trace is full (raise max_iter)");
     return SRM_ERR_STATE;
@@ -648,6 +670,7 @@ srm_status srm_estep(srm_ctx* c) {
 
 srm_status srm_mstep(srm_ctx* c) {
   TRY(valid_ctx(c));
+  TRY(no_partial(c, "srm_mstep"));
   if (!c->have_estep) {
     set_error("srm_mstep: no E-step precedes this M-step");
     return SRM_ERR_STATE;
@@ -660,6 +683,7 @@ srm_status srm_mstep(srm_ctx* c) {
 
 srm_status srm_fit(srm_ctx* c, int32_t n_iter, double* ll_host) {
   TRY(valid_ctx(c));
+  TRY(no_partial(c, "srm_fit"));
   if (n_iter < 0) {
     set_error("srm_fit: n_iter < 0");
     return SRM_ERR_ARG;
@@ -697,6 +721,48 @@ srm_status srm_fit(srm_ctx* c, int32_t n_iter, double* ll_host) {
     CK(cudaMemcpyAsync(ll_host, c->ll + ll0, sizeof(double) * (c->n_ll - ll0), cudaMemcpyDeviceToHost, c->stream));
     TRY(check_status(c));
   }
+  return SRM_OK;
+}
+
+srm_status srm_estep_partial(srm_ctx* c, double* y, double* sums) {
+  TRY(valid_ctx(c));
+  TRY(no_partial(c, "srm_estep_partial"));
+  if (!y || !sums) {
+    set_error("srm_estep_partial: null y or sums");
+    return SRM_ERR_ARG;
+  }
+  if (c->n_ll >= c->max_iter) {
+    set_error("srm_estep_partial: log-likelihood trace is full (raise max_iter)");
+    return SRM_ERR_STATE;
+  }
+  c->shard_y = y;
+  c->shard_sums = sums;
+  const srm_status st = do_estep(c);
+  c->shard_y = nullptr;
+  c->shard_sums = nullptr;
+  // nothing of E[S] exists yet: Sigma_s^new and the likelihood follow srm_estep_finish
+  c->sigma_pending = false;
+  if (st != SRM_OK) return st;
+  c->shard_partial = true;
+  return SRM_OK;
+}
+
+srm_status srm_estep_finish(srm_ctx* c, const double* y, const double* sums) {
+  TRY(valid_ctx(c));
+  if (!c->shard_partial) {
+    set_error("srm_estep_finish: no srm_estep_partial awaits its finish");
+    return SRM_ERR_STATE;
+  }
+  if (!y || !sums) {
+    set_error("srm_estep_finish: null y or sums");
+    return SRM_ERR_ARG;
+  }
+  LAUNCH(c, KK_PHI, launch_estep_finish(c, y, sums));
+  c->shard_partial = false;
+  c->sigma_pending = true;
+  c->n_ll++;
+  c->have_estep = true;
+  c->have_es = true;
   return SRM_OK;
 }
 
@@ -792,6 +858,7 @@ srm_status srm_synchronize(srm_ctx* c) {
 
 srm_status srm_get_state(srm_ctx* c, void* buf, size_t* bytes) {
   TRY(valid_ctx(c));
+  TRY(no_partial(c, "srm_get_state"));
   if (!bytes) {
     set_error("srm_get_state: null size");
     return SRM_ERR_ARG;
@@ -840,6 +907,7 @@ srm_status srm_get_state(srm_ctx* c, void* buf, size_t* bytes) {
 
 srm_status srm_set_state(srm_ctx* c, const void* buf, size_t bytes) {
   TRY(valid_ctx(c));
+  TRY(no_partial(c, "srm_set_state"));
   if (!buf || bytes < sizeof(StateHeader)) {
     set_error("srm_set_state: buffer too small");
     return SRM_ERR_ARG;

@@ -51,7 +51,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 // scal[] layout
-enum { SC_RHO0 = 0, SC_LOGDET = 1, SC_VLOGRHO = 2, SC_SQRHO = 3, SC_YPHIY = 4, SC_TRSIG = 5 };
+enum { SC_RHO0 = 0, SC_LOGDET = 1, SC_VLOGRHO = 2, SC_SQRHO = 3, SC_YPHIY = 4, SC_TRSIG = 5, SC_VTOT = 6 };
 
 // ------------------------------------------------------------------ E-step
 // p_reduce: grid (nchunk, G), 256 threads.  Block (c, g) takes the subjects
@@ -286,12 +286,16 @@ __device__ void block_sum3(double& a, double& b, double& c) {
 //   F_bd = g[lambda_b, lambda_d] = 1 / ((1 + rho0 lambda_b)(1 + rho0 lambda_d)).
 // U is staged in shared memory beside G' when both fit (u_smem), else read
 // from global memory (k close to 128).
+// With sums != nullptr (a sharded E-step) rho_0 and the likelihood's sums
+// over subjects are taken from sums = {sum rho_i^-2, sum v_i ln rho_i^2,
+// sum ||X^_i||^2 / rho_i^2, sum v_i} over all shards instead of this
+// context's subjects.
 __global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __restrict__ rho2,
                                                   const double* __restrict__ sqnorm,
                                                   const int64_t* __restrict__ vox, const double* __restrict__ Us,
                                                   const double* __restrict__ Gp, double* __restrict__ Phi,
                                                   float* __restrict__ Phi32, double* __restrict__ scal, int u_smem,
-                                                  int* status) {
+                                                  int* status, double vtot, const double* __restrict__ sums) {
   extern __shared__ double ph_smem[];
   double* w = ph_smem;          // [k]  1 / (1 + rho0 lambda)
   double* ua = w + k;           // [k]  row a of U
@@ -306,16 +310,24 @@ __global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __
   }
   const double* Ur = u_smem ? Uss : Us;
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-  for (int i = tid; i < N; i += blockDim.x) {
-    const double r = rho2[i];
-    s0 += 1.0 / r;
-    if (a == 0) {
-      if (!(r > 0.0) || !isfinite(r)) flag(status, ST_NONFINITE);
-      s1 += (double)vox[i] * log(r);
-      s2 += sqnorm[i] / r;
+  if (sums) {
+    s0 = sums[0];
+    s1 = sums[1];
+    s2 = sums[2];
+    vtot = sums[3];
+    if (!(s0 > 0.0) || !isfinite(s0) || !isfinite(s1) || !isfinite(s2) || !(vtot > 0.0)) flag(status, ST_NONFINITE);
+  } else {
+    for (int i = tid; i < N; i += blockDim.x) {
+      const double r = rho2[i];
+      s0 += 1.0 / r;
+      if (a == 0) {
+        if (!(r > 0.0) || !isfinite(r)) flag(status, ST_NONFINITE);
+        s1 += (double)vox[i] * log(r);
+        s2 += sqnorm[i] / r;
+      }
     }
+    block_sum3(s0, s1, s2);
   }
-  block_sum3(s0, s1, s2);
   const double rho0 = s0;
   for (int b = tid; b < k; b += blockDim.x) {
     w[b] = 1.0 / (1.0 + rho0 * Gp[b * k + b]);
@@ -352,7 +364,57 @@ __global__ void __launch_bounds__(256) phi_kernel(int N, int k, const double* __
       scal[SC_LOGDET] = ld;
       scal[SC_VLOGRHO] = s1;
       scal[SC_SQRHO] = s2;
+      scal[SC_VTOT] = vtot;
     }
+  }
+}
+
+// A sharded E-step (Algorithm 1's Reduce, done by the caller between
+// shards): this context's share of y = sum_i rho_i^-2 W_i^T X^_i, the group
+// partials summed in group order exactly as es_kernel sums them (error-free
+// FP32), written as FP64 hi + lo; one thread per (f, t).
+__global__ void __launch_bounds__(256) ysum_kernel(int G, int k, int T, const float2* __restrict__ ypart,
+                                                   double* __restrict__ y) {
+  const int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x, kT = (int64_t)k * T;
+  if (e >= kT) return;
+  float yh = 0.f, yl = 0.f;
+  for (int q = 0; q < G; ++q) {
+    const float2 v = __ldcg(ypart + (int64_t)q * kT + e);
+    float hs, he;
+    two_sum(yh, v.x, hs, he);
+    yh = hs;
+    yl += he + v.y;
+  }
+  y[e] = (double)yh + (double)yl;
+}
+
+// This context's share of the E-step's sums over subjects:
+// {sum rho_i^-2 (eq:srm_wt_psi_w), sum v_i ln rho_i^2, sum ||X^_i||^2 / rho_i^2,
+// sum v_i}; one block, a fixed-order tree.
+__global__ void __launch_bounds__(256) shard_sums_kernel(int N, const double* __restrict__ rho2,
+                                                         const double* __restrict__ sqnorm,
+                                                         const int64_t* __restrict__ vox, double* __restrict__ out) {
+  __shared__ double v4[256];
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  for (int i = threadIdx.x; i < N; i += 256) {
+    const double r = rho2[i];
+    s0 += 1.0 / r;
+    s1 += (double)vox[i] * log(r);
+    s2 += sqnorm[i] / r;
+    s3 += (double)vox[i];
+  }
+  block_sum3(s0, s1, s2);
+  v4[threadIdx.x] = s3;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (threadIdx.x < st) v4[threadIdx.x] += v4[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = s0;
+    out[1] = s1;
+    out[2] = s2;
+    out[3] = v4[0];
   }
 }
 
@@ -361,7 +423,8 @@ constexpr int ES_T = 8;  // columns of E[S] per es block
 __global__ void __launch_bounds__(256) es_kernel(int G, int k, int T, int kld, int ldT, const float* __restrict__ Phi32,
                                                  const float2* __restrict__ ypart, double* __restrict__ ES64,
                                                  float* __restrict__ ESt, __nv_bfloat16* __restrict__ ESb,
-                                                 float* __restrict__ sPart, double* __restrict__ yePart) {
+                                                 float* __restrict__ sPart, double* __restrict__ yePart,
+                                                 const double* __restrict__ y64) {
   __shared__ float Ys[KMAX][ES_T];
   __shared__ float Es[KMAX][ES_T];
   __shared__ double red[256];
@@ -377,7 +440,9 @@ __global__ void __launch_bounds__(256) es_kernel(int G, int k, int T, int kld, i
   for (int e = tid; e < k * ES_T; e += 256) {
     const int f = e / ES_T, tt = e - f * ES_T, t = t0 + tt;
     float yv = 0.f;
-    if (t < T) {
+    if (t < T && y64) {
+      yv = (float)y64[(int64_t)f * T + t];  // the y of a sharded E-step, reduced over the shards
+    } else if (t < T) {
       const float2* zp = ypart + (int64_t)f * T + t;
       float yh = 0.f, yl = 0.f;
       int q = 0;
@@ -443,7 +508,7 @@ __global__ void __launch_bounds__(256) es_kernel(int G, int k, int T, int kld, i
 // the chunk partials (summed in chunk order, error-free FP32 accumulation),
 // and the log-likelihood of the E-step that produced them.  grid k blocks
 // (row a), 256 threads; block 0 also finishes the likelihood.
-__global__ void __launch_bounds__(256) sigma_kernel(int k, int T, int nchunk, double Vtot, const double* __restrict__ Phi,
+__global__ void __launch_bounds__(256) sigma_kernel(int k, int T, int nchunk, const double* __restrict__ Phi,
                                                     const float* __restrict__ sPart,
                                                     const double* __restrict__ yePart, double* __restrict__ SigmaNext,
                                                     double* __restrict__ scal, double* __restrict__ ll, int* iter,
@@ -514,6 +579,7 @@ __global__ void __launch_bounds__(256) sigma_kernel(int k, int T, int nchunk, do
   if (tid == 0) {
     const double yes = yred[0];
     scal[SC_YPHIY] = yes;
+    const double Vtot = scal[SC_VTOT];  // all subjects' voxels (all shards' in a sharded E-step)
     const double L = -0.5 * ((double)T * Vtot * 1.8378770664093454835606594728112 + (double)T * scal[SC_VLOGRHO] +
                              (double)T * scal[SC_LOGDET] + scal[SC_SQRHO] - yes);
     if (!isfinite(L)) flag(status, ST_NONFINITE);
@@ -1609,21 +1675,40 @@ cudaError_t launch_p_reduce_from(Ctx* c, bool from_sums) {
     default: return cudaErrorInvalidValue;
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (c->shard_y) {
+    // a sharded E-step stops at this context's share of y and of the sums
+    ysum_kernel<<<nblocks((int64_t)c->k * c->T, 256), 256, 0, c->stream>>>(c->zgroups, c->k, c->T, c->Ypart,
+                                                                              c->shard_y);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    shard_sums_kernel<<<1, 256, 0, c->stream>>>(c->N, c->rho2, c->sqnorm, c->d_v, c->shard_sums);
+    return cudaGetLastError();
+  }
   es_kernel<<<c->nes_blk, 256, sizeof(float) * c->k * c->k, c->stream>>>(
       c->zgroups, c->k, c->T, c->kld, c->ldT, c->Phi32, c->Ypart, c->ES64, c->batched ? nullptr : c->ESt,
-      c->batched ? c->ESb : nullptr, c->sPart, c->esPart);
+      c->batched ? c->ESb : nullptr, c->sPart, c->esPart, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_estep_finish(Ctx* c, const double* y, const double* sums) {
+  cudaError_t e = launch_phi_from(c, sums);
+  if (e != cudaSuccess) return e;
+  es_kernel<<<c->nes_blk, 256, sizeof(float) * c->k * c->k, c->stream>>>(
+      c->zgroups, c->k, c->T, c->kld, c->ldT, c->Phi32, c->Ypart, c->ES64, c->batched ? nullptr : c->ESt,
+      c->batched ? c->ESb : nullptr, c->sPart, c->esPart, y);
   return cudaGetLastError();
 }
 
 int es_blocks(int T) { return (T + ES_T - 1) / ES_T; }
 
 cudaError_t launch_sigma(Ctx* c) {
-  sigma_kernel<<<c->k, 256, 0, c->stream>>>(c->k, c->T, c->nes_blk, (double)c->Vtot, c->Phi, c->sPart, c->esPart,
+  sigma_kernel<<<c->k, 256, 0, c->stream>>>(c->k, c->T, c->nes_blk, c->Phi, c->sPart, c->esPart,
                                             c->SigmaNext, c->scal, c->ll, c->iter, c->max_iter, c->status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_phi(Ctx* c) {
+cudaError_t launch_phi(Ctx* c) { return launch_phi_from(c, nullptr); }
+
+cudaError_t launch_phi_from(Ctx* c, const double* sums) {
   const int64_t kk = (int64_t)c->k * c->k;
   // U in shared memory beside G' when both fit (k <= 119 on this part)
   const size_t sm1 = sizeof(double) * (3 * c->k + c->k * c->k);
@@ -1631,7 +1716,7 @@ cudaError_t launch_phi(Ctx* c) {
   const size_t sm = u_smem ? sm1 + sizeof(double) * c->k * c->k : sm1;
   phi_kernel<<<c->k, 256, sm, c->stream>>>(c->N, c->k, c->rho2, c->sqnorm, c->d_v, c->Xr64 + c->N * kk,
                                            c->G64 + c->N * kk, c->Phi, c->Phi32, c->scal, u_smem ? 1 : 0,
-                                           c->status);
+                                           c->status, (double)c->Vtot, sums);
   return cudaGetLastError();
 }
 

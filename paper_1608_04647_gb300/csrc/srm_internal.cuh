@@ -162,6 +162,11 @@ struct Ctx {
   ChunkSrc* psum_src = nullptr;
   int* psum_src_off = nullptr;
 
+  // ---- sharded E-step (srm_estep_partial / srm_estep_finish)
+  double* shard_y = nullptr;     // caller's k x T buffer while a partial E-step is launched
+  double* shard_sums = nullptr;  // caller's 4 sums while a partial E-step is launched
+  bool shard_partial = false;    // a partial E-step awaits srm_estep_finish
+
   // ---- host bookkeeping
   int n_ll = 0;            // E-steps launched
   bool have_estep = false; // an E-step result is pending for an M-step
@@ -214,6 +219,9 @@ cudaError_t launch_center_generic(const void* X, srm_dtype in_dtype, int64_t row
 cudaError_t launch_sqnorm_reduce(Ctx* c);
 cudaError_t launch_load_w0(Ctx* c, int subject, const float* W0);
 cudaError_t launch_get_w(Ctx* c, int subject, float* W);
+// k_init.cu: Algorithm 1's random orthogonal W^0 drawn in the library (seeded Haar)
+size_t haar_workspace_bytes(const Ctx* c);
+cudaError_t launch_haar_w0(Ctx* c, int subject, uint64_t seed, void* work);
 cudaError_t launch_init_params(Ctx* c);
 
 // k_simt.cu (plain per-subject FP32 form)
@@ -231,6 +239,10 @@ cudaError_t launch_p_sum(Ctx* c);
 cudaError_t launch_p_reduce_from(Ctx* c, bool from_sums);
 cudaError_t launch_sigma(Ctx* c);
 cudaError_t launch_phi(Ctx* c);
+// Phi and the likelihood's scalars from sums over all shards (sums != nullptr)
+cudaError_t launch_phi_from(Ctx* c, const double* sums);
+// the rest of a sharded E-step: Phi from the reduced sums, E[S] = Phi y
+cudaError_t launch_estep_finish(Ctx* c, const double* y, const double* sums);
 cudaError_t launch_eig(Ctx* c);
 cudaError_t launch_refine(Ctx* c);
 cudaError_t launch_rho(Ctx* c);

@@ -386,7 +386,7 @@ srm_status srm_set_plan(srm_ctx* c, const srm_plan* plan) {
     set_error("srm_set_plan: the plain FP32 form has no launch plan");
     return SRM_ERR_UNSUPPORTED;
   }
-  if (c->have_estep) {
+  if (c->have_estep || c->shard_partial) {
     set_error("srm_set_plan: an E-step awaits its M-step; change the plan between iterations");
     return SRM_ERR_STATE;
   }
@@ -407,7 +407,7 @@ srm_status srm_autotune(srm_ctx* c, const char* cache_path, int32_t iters, srm_p
     set_error("srm_autotune: iters must be >= 1");
     return SRM_ERR_ARG;
   }
-  if (c->n_ll != 0 || c->iters_done != 0 || c->have_estep) {
+  if (c->n_ll != 0 || c->iters_done != 0 || c->have_estep || c->shard_partial) {
     set_error("srm_autotune: call it right after srm_init, before any E-step");
     return SRM_ERR_STATE;
   }

@@ -34,3 +34,41 @@ def imbalance(voxels: Sequence[int], plan: List[List[int]]) -> float:
     loads = [sum(int(voxels[i]) for i in p) for p in plan]
     mean = sum(loads) / len(loads)
     return max(loads) / mean if mean > 0 else 1.0
+
+
+def fit_sharded(model, n_iter: int, all_reduce) -> None:
+    """Algorithm 1 (D-SRM) with this process's subjects in `model`: per
+    iteration, this process's share of the E-step (``estep_partial``: y and
+    the four sums over its subjects), one sum over all processes of each
+    (``all_reduce``, in place: the paper's Reduce, which every process
+    receives, so no Bcast follows), the rest of the E-step from the totals
+    (``estep_finish``) and the M-step of its own subjects (``mstep``).
+
+    ``model`` is an :class:`~paper_1608_04647_gb300.SRM` context over this
+    process's subjects, or any object with the same members (``shard_buffers``,
+    ``estep_partial``, ``estep_finish``, ``mstep``).  For a context the
+    reduction is ordered after the E-pass on the context's stream: the
+    context's stream is made current for ``all_reduce`` (NCCL's
+    ``torch.distributed.all_reduce`` waits for that stream), and a context on
+    a library-owned stream is synchronised first."""
+    y, sums = model.shard_buffers()
+    stream = getattr(model, "_stream", None)
+    on_gpu = getattr(y, "is_cuda", False)
+    for _ in range(n_iter):
+        model.estep_partial(y, sums)
+        if on_gpu and stream is not None:
+            import torch
+            with torch.cuda.stream(stream):
+                all_reduce(y)
+                all_reduce(sums)
+        elif on_gpu:
+            import torch
+            model.synchronize()
+            all_reduce(y)
+            all_reduce(sums)
+            torch.cuda.current_stream().synchronize()
+        else:
+            all_reduce(y)
+            all_reduce(sums)
+        model.estep_finish(y, sums)
+        model.mstep()

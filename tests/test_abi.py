@@ -48,10 +48,10 @@ def test_config_struct_layout_matches_c(lib):
 #include <stddef.h>
 #include "{HEADER}"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(srm_config), offsetof(srm_config, n_subjects),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(srm_config), offsetof(srm_config, n_subjects),
          offsetof(srm_config, voxels), offsetof(srm_config, T), offsetof(srm_config, k),
          offsetof(srm_config, in_dtype), offsetof(srm_config, store_dtype), offsetof(srm_config, flags),
-         offsetof(srm_config, max_iter));
+         offsetof(srm_config, max_iter), offsetof(srm_config, seed));
   return 0;
 }}'''
     with tempfile.TemporaryDirectory() as d:
@@ -62,7 +62,7 @@ int main(void) {{
         vals = [int(x) for x in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
     py = [ctypes.sizeof(srm_config)] + [getattr(srm_config, f).offset for f in
                                         ["n_subjects", "voxels", "T", "k", "in_dtype", "store_dtype", "flags",
-                                         "max_iter"]]
+                                         "max_iter", "seed"]]
     assert vals == py
 
 

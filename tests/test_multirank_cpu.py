@@ -1,7 +1,9 @@
 """Multi-rank logic on CPU (gloo, world size 2, 127.0.0.1): the subject
 sharding of Algorithm 1 (D-SRM) with its one exchange per iteration gives the
 single-process EM result, and bench.py's max-over-ranks timing agrees on all
-ranks.  No GPU is used."""
+ranks.  No GPU is used.  The sharded fit runs through the library's host
+driver (shard.fit_sharded) and the contract of its sharded E-step calls; an
+oracle-backed stand-in implements that contract on the CPU."""
 import os
 import socket
 
@@ -34,48 +36,59 @@ def test_shard_plan_balanced_and_complete():
     assert shard_subjects([5, 5, 5, 5], 2) == [[0, 2], [1, 3]]
 
 
+class OracleShard:
+    """The sharded E-step contract of the library (srm_estep_partial /
+    srm_estep_finish / srm_mstep, include/srm.h) over one process's subjects,
+    with the FP64 oracle's arithmetic on CPU tensors: test infrastructure
+    that lets the host driver (shard.fit_sharded) and its all-reduce run over
+    gloo without a GPU."""
+
+    def __init__(self, X, W0, mine):
+        self.mine = list(mine)
+        self.Xh = [oracle.center(X[i])[0] for i in self.mine]
+        self.sq = [float(np.sum(x * x)) for x in self.Xh]
+        self.W = [W0[i].astype(np.float64) for i in self.mine]
+        self.rho2 = np.ones(len(self.mine))
+        self.k, self.T = W0[0].shape[1], X[0].shape[1]
+        self.Sigma = np.eye(self.k)
+        self.ll = []
+
+    def shard_buffers(self):
+        return torch.zeros((self.k, self.T), dtype=torch.float64), torch.zeros(4, dtype=torch.float64)
+
+    def estep_partial(self, y, sums):
+        yl = np.zeros((self.k, self.T))
+        for x, w, r in zip(self.Xh, self.W, self.rho2):
+            yl += (w.T @ x) / r
+        y.copy_(torch.from_numpy(yl))
+        v = np.array([x.shape[0] for x in self.Xh], dtype=np.float64)
+        sums.copy_(torch.tensor([np.sum(1.0 / self.rho2), np.sum(v * np.log(self.rho2)),
+                                 np.sum(np.array(self.sq) / self.rho2), np.sum(v)]))
+
+    def estep_finish(self, y, sums):
+        y, s = y.numpy(), sums.numpy()
+        k, T = self.k, self.T
+        rho0 = s[0]
+        Phi = np.linalg.inv(np.linalg.inv(self.Sigma) + rho0 * np.eye(k))
+        est = {"y": y, "rho0": rho0, "Phi": Phi, "ES": self.Sigma @ (np.eye(k) - rho0 * Phi) @ y}
+        ld = np.linalg.slogdet(np.eye(k) + rho0 * self.Sigma)[1]
+        self.ll.append(-0.5 * (T * s[3] * np.log(2 * np.pi) + T * s[1] + T * ld + s[2] - np.sum(y * (Phi @ y))))
+        self.est = est
+
+    def mstep(self):
+        self.Sigma = oracle.sigma_update(self.est, self.T)
+        self.W, self.rho2 = oracle.mstep(self.Xh, self.sq, self.est["ES"], self.Sigma)
+
+
 def _sharded_em(rank, world, port, X, W0, n_iter, out):
+    from paper_1608_04647_gb300.shard import fit_sharded
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    N = len(X)
     plan = shard_subjects([x.shape[0] for x in X], world)
-    mine = plan[rank]
-    Xh = {i: oracle.center(X[i])[0] for i in mine}
-    sq = {i: float(np.sum(Xh[i] ** 2)) for i in mine}
-    W = {i: W0[i].astype(np.float64) for i in mine}
-    rho2 = np.ones(N)
-    k, T = W0[0].shape[1], X[0].shape[1]
-    Sigma = np.eye(k)
-    V = float(sum(x.shape[0] for x in X))
-    lls = []
-    for _ in range(n_iter):
-        # local part of the reduction y = sum_i rho_i^-2 W_i^T X_i and the scalars
-        y = np.zeros((k, T))
-        s = np.zeros(3)  # sum rho^-2, sum v ln rho^2, sum ||X||^2 / rho^2
-        for i in mine:
-            y += W[i].T @ Xh[i] / rho2[i]
-            s += [1.0 / rho2[i], Xh[i].shape[0] * np.log(rho2[i]), sq[i] / rho2[i]]
-        ty, ts = torch.from_numpy(y), torch.from_numpy(s)
-        dist.all_reduce(ty)
-        dist.all_reduce(ts)
-        y, s = ty.numpy(), ts.numpy()
-        rho0 = s[0]
-        est = {"y": y, "rho0": rho0, "Phi": np.linalg.inv(np.linalg.inv(Sigma) + rho0 * np.eye(k))}
-        est["ES"] = Sigma @ (np.eye(k) - rho0 * est["Phi"]) @ y
-        ld = np.linalg.slogdet(np.eye(k) + rho0 * Sigma)[1]
-        lls.append(-0.5 * (T * V * np.log(2 * np.pi) + T * s[1] + T * ld + s[2] - np.sum(y * (est["Phi"] @ y))))
-        Sigma = oracle.sigma_update(est, T)
-        Wl, rl = oracle.mstep([Xh[i] for i in mine], [sq[i] for i in mine], est["ES"], Sigma)
-        new_rho = np.zeros(N)
-        for j, i in enumerate(mine):
-            W[i] = Wl[j]
-            new_rho[i] = rl[j]
-        tr = torch.from_numpy(new_rho)
-        dist.all_reduce(tr)
-        rho2 = tr.numpy()
-    if rank == 0:
-        out.put((np.array(lls), rho2, Sigma))
+    model = OracleShard(X, W0, plan[rank])
+    fit_sharded(model, n_iter, dist.all_reduce)
+    out.put((rank, np.array(model.ll), dict(zip(model.mine, model.rho2)), model.Sigma))
     dist.destroy_process_group()
 
 
@@ -89,13 +102,18 @@ def test_sharded_em_equals_single_process():
     procs = [ctx.Process(target=_sharded_em, args=(r, 2, port, d["X"], d["W0"], case.n_iter, q)) for r in range(2)]
     for p in procs:
         p.start()
-    lls, rho2, Sigma = q.get(timeout=120)
+    res = [q.get(timeout=120) for _ in range(2)]
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    np.testing.assert_allclose(lls, ref["ll"], rtol=1e-10)
+    rho2 = np.zeros(len(d["X"]))
+    for rank, lls, r, Sigma in res:
+        # every rank holds the whole likelihood trace and Sigma_s
+        np.testing.assert_allclose(lls, ref["ll"], rtol=1e-10)
+        np.testing.assert_allclose(Sigma, ref["Sigma_s"], rtol=1e-8, atol=1e-12)
+        for i, v in r.items():
+            rho2[i] = v
     np.testing.assert_allclose(rho2, ref["rho2"], rtol=1e-9)
-    np.testing.assert_allclose(Sigma, ref["Sigma_s"], rtol=1e-8, atol=1e-12)
 
 
 def _bench_max(rank, world, port, out):
