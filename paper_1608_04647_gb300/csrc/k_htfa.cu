@@ -333,8 +333,11 @@ __global__ void __launch_bounds__(R_THREADS, VEC ? 3 : 4) htfa_residual_kernel(i
   }
 }
 
+// out[n] = sum of subject n's `tiles` partials in a fixed order; NaN when a
+// bounded wait of the tensor-core kernel gave up (status != 0).
 __global__ void __launch_bounds__(256) htfa_residual_sum_kernel(int tiles, const double* __restrict__ part,
-                                                                double* __restrict__ out) {
+                                                                double* __restrict__ out,
+                                                                const int* __restrict__ status) {
   __shared__ double red[8];
   const int n = blockIdx.x;
   double s = 0.0;
@@ -346,7 +349,7 @@ __global__ void __launch_bounds__(256) htfa_residual_sum_kernel(int tiles, const
   if (threadIdx.x == 0) {
     double tot = 0.0;
     for (int w = 0; w < 8; ++w) tot += red[w];
-    out[n] = tot;
+    out[n] = (status && *status) ? __longlong_as_double(0x7ff8000000000000ll) : tot;
   }
 }
 
@@ -473,10 +476,16 @@ extern "C" srm_status srm_htfa_factors(int32_t n_subj, int32_t K, int32_t V, con
   return launch_check("srm_htfa_factors");
 }
 
+// Partials per subject of the form that runs for K: the FP32 SIMT tiles, or
+// four per tensor-core tile (one per epilogue warp).
+int64_t residual_parts(int32_t K, int32_t T, int32_t V) {
+  return htfa_tc_supported(K) ? 4 * htfa_tc_tiles(T, V) : residual_tiles(T, V);
+}
+
 extern "C" size_t srm_htfa_residual_workspace(int32_t n_subj, int32_t K, int32_t T, int32_t V) {
-  (void)K;
   if (n_subj <= 0 || T <= 0 || V <= 0) return 0;
-  return (size_t)n_subj * (size_t)residual_tiles(T, V) * sizeof(double);
+  // the partials, then one status word (16 bytes) for the tensor-core form
+  return (size_t)n_subj * (size_t)residual_parts(K, T, V) * sizeof(double) + 16;
 }
 
 extern "C" srm_status srm_htfa_residual(int32_t n_subj, int32_t K, int32_t T, int32_t V, const float* X,
@@ -496,9 +505,9 @@ extern "C" srm_status srm_htfa_residual(int32_t n_subj, int32_t K, int32_t T, in
     const cudaError_t e = cudaMemsetAsync(out, 0, (size_t)n_subj * sizeof(double), s);
     return e == cudaSuccess ? SRM_OK : cuda_fail(e, "srm_htfa_residual: cudaMemsetAsync");
   }
-  const int64_t tiles = residual_tiles(T, V);
-  if (tiles > INT_MAX) {
-    set_error("srm_htfa_residual: T x V has more than 2^31 - 1 tiles of 64 x 64");
+  const int64_t tiles = residual_parts(K, T, V);
+  if (tiles > INT_MAX / 4) {
+    set_error("srm_htfa_residual: T x V has too many tiles");
     return SRM_ERR_ARG;
   }
   if (!X || !W || !F || !work || (reinterpret_cast<uintptr_t>(work) & 7) ||
@@ -508,6 +517,15 @@ extern "C" srm_status srm_htfa_residual(int32_t n_subj, int32_t K, int32_t T, in
     return SRM_ERR_ARG;
   }
   double* part = static_cast<double*>(work);
+  if (htfa_tc_supported(K)) {
+    int* st_word = reinterpret_cast<int*>(part + (size_t)n_subj * (size_t)tiles);
+    cudaError_t e = cudaMemsetAsync(st_word, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "srm_htfa_residual: cudaMemsetAsync");
+    e = launch_htfa_residual_tc(n_subj, K, T, V, X, W, F, part, st_word, s);
+    if (e != cudaSuccess) return cuda_fail(e, "srm_htfa_residual: tensor-core kernel");
+    htfa_residual_sum_kernel<<<(unsigned)n_subj, 256, 0, s>>>((int)tiles, part, out, st_word);
+    return launch_check("srm_htfa_residual: sum kernel");
+  }
   const int tiles_v = (V + RV - 1) / RV;
   const dim3 grid((unsigned)tiles, (unsigned)n_subj);
   const bool vec = (V % 4 == 0) && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
@@ -517,7 +535,7 @@ extern "C" srm_status srm_htfa_residual(int32_t n_subj, int32_t K, int32_t T, in
     htfa_residual_kernel<false><<<grid, R_THREADS, 0, s>>>(K, T, V, tiles_v, (int)tiles, X, W, F, part);
   srm_status st = launch_check("srm_htfa_residual: tile kernel");
   if (st != SRM_OK) return st;
-  htfa_residual_sum_kernel<<<(unsigned)n_subj, 256, 0, s>>>((int)tiles, part, out);
+  htfa_residual_sum_kernel<<<(unsigned)n_subj, 256, 0, s>>>((int)tiles, part, out, nullptr);
   return launch_check("srm_htfa_residual: sum kernel");
 }
 

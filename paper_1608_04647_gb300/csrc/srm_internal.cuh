@@ -219,6 +219,12 @@ cudaError_t launch_center_generic(const void* X, srm_dtype in_dtype, int64_t row
 cudaError_t launch_sqnorm_reduce(Ctx* c);
 cudaError_t launch_load_w0(Ctx* c, int subject, const float* W0);
 cudaError_t launch_get_w(Ctx* c, int subject, float* W);
+// k_htfa_tc.cu: the HTFA residual on the tensor cores (K <= 128)
+bool htfa_tc_supported(int K);
+int64_t htfa_tc_tiles(int T, int V);
+size_t htfa_tc_smem_bytes();
+cudaError_t launch_htfa_residual_tc(int n_subj, int K, int T, int V, const float* X, const float* W, const float* F,
+                                    double* part, int* status, cudaStream_t s);
 // k_init.cu: Algorithm 1's random orthogonal W^0 drawn in the library (seeded Haar)
 size_t haar_workspace_bytes(const Ctx* c);
 cudaError_t launch_haar_w0(Ctx* c, int subject, uint64_t seed, void* work);

@@ -17,11 +17,14 @@ SRM_OK, SRM_ERR_ARG = 0, 1
 P = ctypes.c_void_p(16)  # a non-null pointer that the checks below never dereference
 
 
-def test_residual_workspace_is_one_double_per_tile(lib):
-    # tiles of 64 samples x 128 voxels
-    assert lib.srm_htfa_residual_workspace(40, 100, 174, 6857) == 40 * 3 * 54 * 8
-    assert lib.srm_htfa_residual_workspace(1, 100, 2000, 50000) == 32 * 391 * 8
-    assert lib.srm_htfa_residual_workspace(2, 7, 64, 128) == 2 * 1 * 1 * 8
+def test_residual_workspace_holds_the_partials(lib):
+    # K <= 128 (tensor cores): four doubles per tile of 128 samples x 64 voxels,
+    # then a 16-byte status word; K > 128 (FP32 FMA): one double per tile of
+    # 64 samples x 128 voxels, then the same 16 bytes
+    assert lib.srm_htfa_residual_workspace(40, 100, 174, 6857) == 40 * 4 * 2 * 108 * 8 + 16
+    assert lib.srm_htfa_residual_workspace(1, 100, 2000, 50000) == 4 * 16 * 782 * 8 + 16
+    assert lib.srm_htfa_residual_workspace(2, 7, 64, 128) == 2 * 4 * 1 * 2 * 8 + 16
+    assert lib.srm_htfa_residual_workspace(2, 150, 64, 128) == 2 * 1 * 1 * 8 + 16
     assert lib.srm_htfa_residual_workspace(0, 7, 64, 128) == 0
     assert lib.srm_htfa_residual_workspace(3, 7, 0, 128) == 0
 

@@ -11,10 +11,15 @@ the oracle's data (u = 2^-24, twice the bound for margin):
   two products add 14u: |F - F_o| <= 2 (4 a + 14) u F_o + 2^-125, with
   a = ||p - mu||^2 / lambda.  The absolute term covers results below the
   FP32 normal range;
-* residual: per element the FMA chain over K carries at most
-  gamma_K sum_k |w_tk| |f_kv|, the difference one more u |r|; squaring and
-  summing 16 terms per thread add gamma_16 r^2:
-  |R - R_o| <= 2 sum (2 |r| (u |r| + gamma_K (|W| |F|)_tv) + gamma_16 r^2);
+* residual: per element the product carries at most g (|W| |F|)_tv and
+  the difference one more u |r|; squaring and summing 64 terms per thread
+  add gamma_64 r^2:
+  |R - R_o| <= 2 sum (2 |r| (u |r| + g (|W| |F|)_tv) + gamma_64 r^2).
+  For K > 128 the FP32 FMA chain runs, g = gamma_K.  For K <= 128 the
+  tensor cores form W F from three BF16 pieces of each operand, which leave
+  at most 4 u |W| |F| (the pieces' remainders and three dropped products).
+  Their FP32 accumulator rounds once per MMA, 6 ceil(K / 16) times, each
+  allowed 2 u (a truncating rounding), so g = (4 + 12 ceil(K / 16)) u;
 * z-score: the shifted sums over at most ceil(T/8) + 8 terms bound the
   error of the mean by (T/8 + 10) u max|x - x_0| and that of the variance
   likewise; the bound on z follows.
@@ -57,12 +62,18 @@ def _check_factors(d, F_gpu):
     return worst
 
 
+def _product_gamma(K):
+    if K <= 128:  # tensor cores, three BF16 pieces per operand
+        return (4 + 12 * math.ceil(K / 16)) * U
+    return K * U / (1 - K * U)
+
+
 def _residual_bound(X, W, F, K):
     X, W, F = (np.asarray(a, dtype=np.float64) for a in (X, W, F))
     r = X - W @ F
-    gk = K * U / (1 - K * U)
-    g16 = 16 * U / (1 - 16 * U)
-    per = 2 * np.abs(r) * (U * np.abs(r) + gk * (np.abs(W) @ np.abs(F))) + g16 * r * r
+    gk = _product_gamma(K)
+    g64 = 64 * U / (1 - 64 * U)
+    per = 2 * np.abs(r) * (U * np.abs(r) + gk * (np.abs(W) @ np.abs(F))) + g64 * r * r
     return 2 * float(per.sum()) + 1e-300
 
 
@@ -178,7 +189,10 @@ def test_residual_matches_oracle(name, V):
     print(name, "relative error", float(np.max(np.abs(r1 - oracle.htfa_residual_batch(X, W, F)) / r1)))
 
 
-@pytest.mark.parametrize("T,V,K", [(1, 1, 1), (1, 5, 3), (65, 63, 17), (64, 64, 16), (3, 1000, 1)])
+# tensor-core tiles (128 x 64, K in steps of 16): ragged in T, V and K, two K
+# atoms (K > 64), the largest K of that path (128); and K > 128 (FP32 FMA path)
+@pytest.mark.parametrize("T,V,K", [(1, 1, 1), (1, 5, 3), (65, 63, 17), (64, 64, 16), (3, 1000, 1),
+                                   (129, 65, 65), (300, 513, 100), (128, 64, 128), (70, 200, 150)])
 def test_residual_small_shapes(T, V, K):
     import oracle
     from paper_1608_04647_gb300 import htfa
