@@ -917,7 +917,7 @@ def run_htfa(args):
     f_bytes = n * K * V * 4 + n * V * 12
     r_bytes = n * T * V * 4 + n * K * V * 4 + n * T * K * 4
     hbm = load_peaks()["hbm_gbs"]
-    traffic, tsrc = htfa_profiled_traffic("htfa_residual", spec.name)
+    traffic, tsrc = htfa_profiled_traffic("htfa_residual_tc" if K <= 128 else "htfa_residual", spec.name)
     res = {
         "metric": HTFA_METRIC, "value": round(1000.0 / ms_step, 3), "unit": HTFA_UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,

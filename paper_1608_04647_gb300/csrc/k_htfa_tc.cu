@@ -53,39 +53,18 @@ constexpr size_t ht_smem_bytes() {
 }
 static_assert(ht_smem_bytes() <= 232448, "HTFA residual shared memory");
 
-__device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
-  a = __float2bfloat16_rn(x);
-  const float r1 = x - __bfloat162float(a);
-  b = __float2bfloat16_rn(r1);
-  const float r2 = r1 - __bfloat162float(b);
-  c = __float2bfloat16_rn(r2);
-}
-
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
-// eight consecutive values -> one 16-byte chunk of each of the three pieces
-__device__ __forceinline__ void store_split8(const float (&x)[8], uint8_t* p0, uint8_t* p1, uint8_t* p2,
-                                             uint32_t off) {
-  __nv_bfloat16 a[8], b[8], c[8];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) split3(x[j], a[j], b[j], c[j]);
-  *reinterpret_cast<uint4*>(p0 + off) = make_uint4(pack2(a[0], a[1]), pack2(a[2], a[3]), pack2(a[4], a[5]),
-                                                   pack2(a[6], a[7]));
-  *reinterpret_cast<uint4*>(p1 + off) = make_uint4(pack2(b[0], b[1]), pack2(b[2], b[3]), pack2(b[4], b[5]),
-                                                   pack2(b[6], b[7]));
-  *reinterpret_cast<uint4*>(p2 + off) = make_uint4(pack2(c[0], c[1]), pack2(c[2], c[3]), pack2(c[4], c[5]),
-                                                   pack2(c[6], c[7]));
-}
-
-// one value -> its 2-byte slot (byte offset off) in each of the three pieces
-__device__ __forceinline__ void store_split1(float x, uint8_t* p0, uint32_t piece_bytes, uint32_t off) {
-  __nv_bfloat16 a, b, c;
-  split3(x, a, b, c);
-  *reinterpret_cast<__nv_bfloat16*>(p0 + off) = a;
-  *reinterpret_cast<__nv_bfloat16*>(p0 + piece_bytes + off) = b;
-  *reinterpret_cast<__nv_bfloat16*>(p0 + 2 * piece_bytes + off) = c;
+// two values -> their adjacent 2-byte slots (4-byte aligned offset off) in
+// each of the three pieces, with paired conversions
+__device__ __forceinline__ void store_split2(float x0, float x1, uint8_t* p0, uint32_t piece_bytes, uint32_t off) {
+  const __nv_bfloat162 a = __floats2bfloat162_rn(x0, x1);
+  const float2 af = __bfloat1622float2(a);
+  const float r0 = x0 - af.x, r1 = x1 - af.y;
+  const __nv_bfloat162 b = __floats2bfloat162_rn(r0, r1);
+  const float2 bf = __bfloat1622float2(b);
+  const __nv_bfloat162 c = __floats2bfloat162_rn(r0 - bf.x, r1 - bf.y);
+  *reinterpret_cast<__nv_bfloat162*>(p0 + off) = a;
+  *reinterpret_cast<__nv_bfloat162*>(p0 + piece_bytes + off) = b;
+  *reinterpret_cast<__nv_bfloat162*>(p0 + 2 * piece_bytes + off) = c;
 }
 
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int* status) {
@@ -145,11 +124,11 @@ __global__ void __launch_bounds__(HT_THREADS, 1)
   const float* Fn = F + (int64_t)n * K * V;
 
   if (warp < HT_CONV / 32) {
-    // ---- converters (HT_CONV threads): lane = consecutive columns of one row,
-    // so every warp load reads 128 contiguous bytes; each value is split and
-    // stored in its 2-byte slots of the three swizzled pieces.  The loads of a
-    // batch of rows are all issued before any is used, and the F rows of the
-    // tile after next are requested from L2.
+    // ---- converters (HT_CONV threads): lane = two adjacent columns of one row,
+    // so a warp's two loads cover 256 contiguous bytes; each pair is split with
+    // paired conversions and stored in its 4-byte slots of the three swizzled
+    // pieces.  The loads of a batch of rows are all issued before any is used,
+    // and the F rows of the tile after next are requested from L2.
     const int cw = warp;  // converter warp
     constexpr int NCW = HT_CONV / 32;
     auto prefetch_f = [&](int vt) {
@@ -170,8 +149,8 @@ __global__ void __launch_bounds__(HT_THREADS, 1)
       for (int b = 0; b < 8; ++b) {
         const int r = r0 + NCW * b, t = t0 + r;
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const int k = 32 * h + lane;
+        for (int h = 0; h < 4; ++h) {  // k = 64 (h / 2) + 2 lane + h % 2
+          const int k = 64 * (h >> 1) + 2 * lane + (h & 1);
           x[b][h] = (r < HT_M && t < T && k < K) ? __ldg(Wn + (int64_t)t * K + k) : 0.f;
         }
       }
@@ -180,13 +159,13 @@ __global__ void __launch_bounds__(HT_THREADS, 1)
         const int r = r0 + NCW * b;
         if (r >= HT_M) continue;
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const int k = 32 * h + lane;
+        for (int a = 0; a < 2; ++a) {  // the two K atoms
+          const int k = 64 * a + 2 * lane;
           if (k >= Kp) continue;
-          const int kk = k & 63;
-          const uint32_t off = (uint32_t)(k >> 6) * W_ATOM + (uint32_t)r * 128u +
+          const int kk = 2 * lane;
+          const uint32_t off = (uint32_t)a * W_ATOM + (uint32_t)r * 128u +
                                (uint32_t)((((kk >> 3) ^ (r & 7)) << 4) + ((kk & 7) << 1));
-          store_split1(x[b][h], wp, W_PIECE, off);
+          store_split2(x[b][2 * a], x[b][2 * a + 1], wp, W_PIECE, off);
         }
       }
     }
@@ -202,13 +181,13 @@ __global__ void __launch_bounds__(HT_THREADS, 1)
     for (int vt = vt0, j = 0; vt < vt1; ++vt, ++j) {
       const int b = j & 1;
       const int v0 = vt * HT_N;
-      float x[FR][2];
+      float x[FR][2];  // columns 2 lane and 2 lane + 1 of each of the warp's rows
 #pragma unroll
       for (int i = 0; i < FR; ++i) {
         const int k = cw + NCW * i;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int v = v0 + 32 * h + lane;
+          const int v = v0 + 2 * lane + h;
           x[i][h] = (k < K && v < V) ? __ldg(Fn + (int64_t)k * V + v) : 0.f;
         }
       }
@@ -222,12 +201,9 @@ __global__ void __launch_bounds__(HT_THREADS, 1)
       for (int i = 0; i < FR; ++i) {
         const int k = cw + NCW * i;
         if (k >= Kp) continue;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int vl = 32 * h + lane;
-          const uint32_t off = (uint32_t)k * 128u + (uint32_t)((((vl >> 3) ^ (k & 7)) << 4) + ((vl & 7) << 1));
-          store_split1(x[i][h], fb, F_PIECE, off);
-        }
+        const int vl = 2 * lane;
+        const uint32_t off = (uint32_t)k * 128u + (uint32_t)((((vl >> 3) ^ (k & 7)) << 4) + ((vl & 7) << 1));
+        store_split2(x[i][0], x[i][1], fb, F_PIECE, off);
       }
       fence_proxy_async_smem();
       __syncwarp();
