@@ -24,14 +24,26 @@ SRM_API srm_status srm_debug_mma(int32_t mn_major, const void* A, const void* B,
 
 /*
  * srm_debug_eig_sweeps -- diagnostics of the last M-step, one int per
- * symmetric matrix.  Entries 0..N-1 (the subjects' A_i^T A_i): for k <= 64
- * the number of Newton-Schulz steps of the polar factor, or 256 + the number
- * of Jacobi sweeps when that result failed its accuracy certificate and the
- * eigen-decomposition path took over; for k > 64 the number of Jacobi
- * sweeps.  Entry N (Sigma_s): Jacobi sweeps.  Writes min(n, N + 1) ints to
+ * symmetric matrix.  Entries 0..N-1 (the subjects' A_i^T A_i): the number of
+ * Newton-Schulz steps of the polar factor, or 256 + the number of Jacobi
+ * sweeps when that result failed its accuracy certificate and the
+ * eigen-decomposition path took over.  Entry N (Sigma_s): Jacobi sweeps for
+ * k <= 64; for k > 64 Sigma_s is not decomposed (Phi comes from a Cholesky
+ * factorisation) and entry N is not defined.  Writes min(n, N + 1) ints to
  * the host array out.  Synchronises.
  */
 SRM_API srm_status srm_debug_eig_sweeps(srm_ctx* ctx, int32_t* out, int32_t n);
+
+/*
+ * srm_debug_force_eig_polar -- with on != 0, every later M-step of ctx fails
+ * each subject's Newton-Schulz certificate on purpose, so that all polar
+ * factors (eq:srm_mapping_update) and rho_i^2 come from the
+ * eigen-decomposition path (Jacobi + FP64 refinement) that otherwise serves
+ * only the subjects whose certificate fails; on == 0 restores the default.
+ * For tests of that path.  Flushes pending work; returns SRM_ERR_ARG for a
+ * bad context.
+ */
+SRM_API srm_status srm_debug_force_eig_polar(srm_ctx* ctx, int32_t on);
 
 /*
  * srm_debug_wait -- the bounded mbarrier wait of the tensor-core kernels,

@@ -26,7 +26,7 @@ __all__ = [
     "srm_init", "srm_estep", "srm_mstep", "srm_fit", "srm_transform", "srm_get_w", "srm_get_s",
     "srm_get_params", "srm_get_ll", "srm_synchronize", "srm_get_state", "srm_set_state",
     "srm_get_kernel_times", "srm_layout", "srm_last_error", "srm_destroy", "srm_debug_mma",
-    "srm_transform_noalloc", "srm_debug_eig_sweeps", "srm_debug_wait", "srm_map", "srm_plan", "srm_get_plan", "srm_set_plan",
+    "srm_transform_noalloc", "srm_debug_eig_sweeps", "srm_debug_force_eig_polar", "srm_debug_wait", "srm_map", "srm_plan", "srm_get_plan", "srm_set_plan",
     "srm_autotune", "srm_estep_partial", "srm_estep_finish",
 ]
 
@@ -122,6 +122,7 @@ def load_library(path: Optional[str] = None):
         "srm_transform_noalloc": (st, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P]),
         "srm_map": (st, [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32, _P]),
         "srm_debug_eig_sweeps": (st, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]),
+        "srm_debug_force_eig_polar": (st, [_P, ctypes.c_int32]),
         "srm_debug_wait": (st, [ctypes.c_int32]),
         "srm_get_plan": (st, [_P, ctypes.POINTER(srm_plan)]),
         "srm_set_plan": (st, [_P, ctypes.POINTER(srm_plan)]),
@@ -292,6 +293,11 @@ def srm_debug_eig_sweeps(ctx: int, n: int) -> np.ndarray:
     _check(load_library().srm_debug_eig_sweeps(_P(ctx), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), n),
            "srm_debug_eig_sweeps")
     return out
+
+
+def srm_debug_force_eig_polar(ctx: int, on: bool) -> None:
+    """Route every later polar factor through the eigen-decomposition path."""
+    _check(load_library().srm_debug_force_eig_polar(_P(ctx), int(bool(on))), "srm_debug_force_eig_polar")
 
 
 def srm_get_plan(ctx: int) -> srm_plan:

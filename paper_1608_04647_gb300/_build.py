@@ -20,7 +20,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "lib")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsrm.so")
-SOURCES = ["api.cu", "k_center.cu", "k_simt.cu", "k_small.cu", "k_tc.cu", "k_noalloc.cu", "k_map.cu", "k_fused.cu", "tune.cu", "k_htfa.cu", "k_init.cu", "k_htfa_tc.cu"]
+SOURCES = ["api.cu", "k_center.cu", "k_simt.cu", "k_small.cu", "k_tc.cu", "k_noalloc.cu", "k_map.cu", "k_fused.cu", "tune.cu", "k_htfa.cu", "k_init.cu", "k_htfa_tc.cu", "k_tail.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", INCLUDE]

@@ -194,6 +194,7 @@ struct OnStream {
 // needed by the next E-pass (which reads only A_i), so it runs on a second
 // stream beside that pass when an iteration follows.
 srm_status do_sigma_eig(Ctx* c) {
+  if (!sigma_eig_supported(c)) return SRM_OK;  // k > 64: Phi by Cholesky, after the polar factors
   LAUNCH(c, KK_EIG, launch_eig_sigma(c));
   LAUNCH(c, KK_MTAIL, launch_mtail_sigma(c));
   return SRM_OK;
@@ -1013,6 +1014,14 @@ srm_status srm_debug_eig_sweeps(srm_ctx* c, int32_t* out, int32_t n) {
   TRY(check_status(c));
   const int m = std::min(n, c->N + 1);
   if (m > 0) CK(cudaMemcpy(out, c->jac_sweeps, sizeof(int) * m, cudaMemcpyDeviceToHost));
+  return SRM_OK;
+}
+
+srm_status srm_debug_force_eig_polar(srm_ctx* c, int32_t on) {
+  TRY(valid_ctx(c));
+  TRY(flush_pending(c));
+  c->force_eig_polar = on != 0;
+  drop_graph(c);  // a captured iteration holds the launch arguments
   return SRM_OK;
 }
 

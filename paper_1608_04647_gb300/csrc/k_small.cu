@@ -33,25 +33,11 @@
 
 #include <algorithm>
 
-#include "srm_internal.cuh"
+#include "kk_util.cuh"
 
 namespace srm {
 
 namespace {
-
-inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
-
-__device__ __forceinline__ void flag(int* status, int bits) { atomicOr(status, bits); }
-
-// Error-free sum: s + e == a + b exactly (Knuth).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float z = s - a;
-  e = (a - (s - z)) + (b - z);
-}
-
-// scal[] layout
-enum { SC_RHO0 = 0, SC_LOGDET = 1, SC_VLOGRHO = 2, SC_SQRHO = 3, SC_YPHIY = 4, SC_TRSIG = 5, SC_VTOT = 6 };
 
 // ------------------------------------------------------------------ E-step
 // p_reduce: grid (nchunk, G), 256 threads.  Block (c, g) takes the subjects
@@ -787,12 +773,15 @@ int eig_threads(int k) {
 // D_b = alpha op(A_b) op(B_b) + beta C_b for a batch of k x k FP64 matrices.
 // grid (nband, nbatch), 256 threads.  op(B) is staged in shared memory as
 // [m][c] and the band of op(A) as [r][m]; with sym != 0 only c >= r is
-// computed and mirrored (the product is known to be symmetric).
+// computed and mirrored (the product is known to be symmetric).  With
+// only != nullptr, matrices b with only[b] == 0 are skipped.
 __global__ void __launch_bounds__(256) bgemm64_kernel(int k, int nband, const double* __restrict__ A, int tA,
                                                       const double* __restrict__ B, int tB, double alpha,
                                                       const double* __restrict__ C, double beta,
-                                                      double* __restrict__ D, int sym) {
+                                                      double* __restrict__ D, int sym,
+                                                      const int* __restrict__ only) {
   extern __shared__ double bg_smem[];
+  if (only && only[blockIdx.y] == 0) return;  // matrix not selected
   const int ldb = k + 1;
   double* Bs = bg_smem;              // [k][k+1]
   double* As = Bs + k * ldb;         // [band][k+1]
@@ -835,8 +824,9 @@ __global__ void __launch_bounds__(128) dk_rho_kernel(int N, int k, int T, const 
                                                      const int64_t* __restrict__ vox,
                                                      const double* __restrict__ SigmaNext, double* __restrict__ Sigma,
                                                      double* __restrict__ rho2, double* __restrict__ scal,
-                                                     int* status) {
+                                                     int* status, const int* __restrict__ only) {
   __shared__ double sq[KMAX];
+  if (only && (blockIdx.x >= N || only[blockIdx.x] == 0)) return;  // subject not selected
   __shared__ double red[3][128];
   const int i = blockIdx.x, tid = threadIdx.x;
   const double* G = Gp + (int64_t)i * k * k;
@@ -930,11 +920,6 @@ __global__ void __launch_bounds__(128) dk_rho_kernel(int N, int k, int T, const 
 // symmetric matrices is itself), each tile's inner index split over 2 or 4
 // lanes.
 constexpr int NS_KMAX = 64;
-constexpr int NS_MAXIT = 40;
-constexpr float NS_TOL = 1e-4f;
-// accepted ||E||_F / sqrt(k): FP32 store (results compared at 1e-5) and BF16 store (2e-2)
-constexpr double NS_CERT_F32 = 2e-6;
-constexpr double NS_CERT_BF16 = 1e-4;
 
 
 constexpr int NS_THREADS = 512;
@@ -972,14 +957,6 @@ __device__ void block_sum2f_ns(float& a, float& b, float (*red)[NS_THREADS / 32]
     b += red[1][w];
   }
   __syncthreads();
-}
-
-// (h, l) += (bh, bl) in float-float arithmetic (renormalised)
-__device__ __forceinline__ void ff_add(float& h, float& l, float bh, float bl) {
-  float s, e;
-  two_sum(h, bh, s, e);
-  e += l + bl;
-  two_sum(s, e, h, l);
 }
 
 // ---- 4 x 4 register tiles of C = A^T B split over KS lanes along the inner
@@ -1025,24 +1002,6 @@ __device__ __forceinline__ void tile_part(const float* __restrict__ A, const flo
     }
   }
 }
-template <int KS, bool COMP>
-__device__ __forceinline__ void tile_combine(float (&hi)[4][4], float (&lo)[4][4]) {
-#pragma unroll
-  for (int o = 1; o < KS; o <<= 1)
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const float oh = __shfl_xor_sync(0xffffffffu, hi[u][v], o);
-        if (COMP) {
-          const float ol = __shfl_xor_sync(0xffffffffu, lo[u][v], o);
-          ff_add(hi[u][v], lo[u][v], oh, ol);
-        } else {
-          hi[u][v] += oh;
-        }
-      }
-}
-
 // C = A^T B for KP x KP operands whose product is symmetric (here: A, B
 // commuting symmetric polynomials of the same matrix, so C = A B = B A):
 // the upper tiles only, mirrored.  Threads [base, base + nth) of the block,
@@ -1548,12 +1507,14 @@ size_t mtail_smem_bytes(int k) {
   return sizeof(double) * ((size_t)2 * k * kp + (size_t)MT_RMAX * kp + k);
 }
 
-// M32 (padded, FP32) from M64; Uwarm <- FP32 copy of the refined U (N + 1 matrices).
+// M32 (padded, FP32) from M64; Uwarm <- FP32 copy of the refined U (N + 1
+// matrices, or the subjects selected by only).
 __global__ void finish_m_kernel(int N, int k, int kld, const double* __restrict__ M64, const double* __restrict__ U,
-                                float* __restrict__ M32, float* __restrict__ Uwarm) {
+                                float* __restrict__ M32, float* __restrict__ Uwarm, const int* __restrict__ only) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)(N + 1) * k * k) return;
   const int64_t i = e / ((int64_t)k * k);
+  if (only && (i >= N || only[i] == 0)) return;  // subject not selected
   const int w = (int)(e % ((int64_t)k * k));
   const int a = w / k, b = w % k;
   if (i < N) M32[i * kld * kld + a * kld + b] = (float)M64[e];
@@ -1592,12 +1553,12 @@ int refine_bands(const Ctx* c, int nbatch) {
 }
 
 cudaError_t bgemm(Ctx* c, int nbatch, const double* A, int tA, const double* B, int tB, double alpha,
-                  const double* C, double beta, double* D, int sym) {
+                  const double* C, double beta, double* D, int sym, const int* only = nullptr) {
   const int k = c->k;
   const int nb = refine_bands(c, nbatch);
   const int band = (k + nb - 1) / nb;
   const size_t sm = sizeof(double) * (size_t)(k + band) * (k + 1);
-  bgemm64_kernel<<<dim3(nb, nbatch), 256, sm, c->stream>>>(k, nb, A, tA, B, tB, alpha, C, beta, D, sym);
+  bgemm64_kernel<<<dim3(nb, nbatch), 256, sm, c->stream>>>(k, nb, A, tA, B, tB, alpha, C, beta, D, sym, only);
   return cudaGetLastError();
 }
 
@@ -1606,6 +1567,7 @@ cudaError_t bgemm(Ctx* c, int nbatch, const double* A, int tA, const double* B, 
 
 void prepare_small_kernels(int max_smem) {
   g_max_smem = max_smem;
+  prepare_tail_kernels();
   cudaFuncSetAttribute(es_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float) * KMAX * KMAX));
   // (these kernels also hold a few KB of static shared memory)
   cudaFuncSetAttribute(p_reduce_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
@@ -1709,6 +1671,7 @@ cudaError_t launch_sigma(Ctx* c) {
 cudaError_t launch_phi(Ctx* c) { return launch_phi_from(c, nullptr); }
 
 cudaError_t launch_phi_from(Ctx* c, const double* sums) {
+  if (!sigma_eig_supported(c)) return launch_phi_chol(c, sums);
   const int64_t kk = (int64_t)c->k * c->k;
   // U in shared memory beside G' when both fit (k <= 119 on this part)
   const size_t sm1 = sizeof(double) * (3 * c->k + c->k * c->k);
@@ -1743,25 +1706,40 @@ cudaError_t launch_eig(Ctx* c) { return launch_eig_from(c, 0, c->N + 1, nullptr)
 cudaError_t launch_eig_sigma(Ctx* c) { return launch_eig_from(c, c->N, 1, nullptr); }
 cudaError_t launch_eig_fallback(Ctx* c) { return launch_eig_from(c, 0, c->N, c->ns_fb); }
 
-cudaError_t launch_refine(Ctx* c) {
-  const int n1 = c->N + 1;
+// The FP64 refinement of the Jacobi eigenvectors: N + 1 matrices, or the
+// subjects selected by only (n1 = N).
+cudaError_t launch_refine_from(Ctx* c, const int* only) {
+  const int n1 = only ? c->N : c->N + 1;
   cudaError_t e;
   // H = U0^T U0 (symmetric)
-  if ((e = bgemm(c, n1, c->U64, 1, c->U64, 0, 1.0, nullptr, 0.0, c->H64, 1)) != cudaSuccess) return e;
+  if ((e = bgemm(c, n1, c->U64, 1, c->U64, 0, 1.0, nullptr, 0.0, c->H64, 1, only)) != cudaSuccess) return e;
   // X = U0 (3I - U0^T U0) / 2 = 1.5 U0 - 0.5 U0 H
-  if ((e = bgemm(c, n1, c->U64, 0, c->H64, 0, -0.5, c->U64, 1.5, c->Xr64, 0)) != cudaSuccess) return e;
+  if ((e = bgemm(c, n1, c->U64, 0, c->H64, 0, -0.5, c->U64, 1.5, c->Xr64, 0, only)) != cudaSuccess) return e;
   // H = G X
-  if ((e = bgemm(c, n1, c->G64, 0, c->Xr64, 0, 1.0, nullptr, 0.0, c->H64, 0)) != cudaSuccess) return e;
+  if ((e = bgemm(c, n1, c->G64, 0, c->Xr64, 0, 1.0, nullptr, 0.0, c->H64, 0, only)) != cudaSuccess) return e;
   // G' = X^T H (symmetric)
-  return bgemm(c, n1, c->Xr64, 1, c->H64, 0, 1.0, nullptr, 0.0, c->G64, 1);
+  return bgemm(c, n1, c->Xr64, 1, c->H64, 0, 1.0, nullptr, 0.0, c->G64, 1, only);
 }
 
-bool ns_supported(const Ctx* c) { return c->k <= NS_KMAX && c->k <= MT_KMAX; }
+cudaError_t launch_refine(Ctx* c) { return launch_refine_from(c, nullptr); }
+
+cudaError_t launch_rho_from(Ctx* c, const int* only);
+
+// Newton-Schulz polar factors: one CTA per subject for k <= 64, a cluster per
+// subject above (k_tail.cu).
+bool ns_supported(const Ctx* c) { return (c->k <= NS_KMAX && c->k <= MT_KMAX) || polar_cl_supported(c); }
+
+// Sigma_s's eigen-decomposition (and Phi from it) for k <= 64; above, Phi
+// comes from a Cholesky factorisation and Sigma_s is not decomposed.
+bool sigma_eig_supported(const Ctx* c) { return c->k <= MT_KMAX; }
 
 cudaError_t launch_polar(Ctx* c) {
   const size_t sm = ns_smem_bytes(c->k);
-  const double cert = c->store == SRM_BF16 ? NS_CERT_BF16 : NS_CERT_F32;
+  // a negative threshold fails every certificate (all subjects take the
+  // eigen-decomposition path)
+  const double cert = c->force_eig_polar ? -1.0 : c->store == SRM_BF16 ? NS_CERT_BF16 : NS_CERT_F32;
   const int comp = c->store == SRM_BF16 ? 0 : 1;
+  if (c->k > NS_KMAX) return launch_polar_cl(c, cert, comp);
   // two CTAs per SM when the subjects outnumber the SMs and two fit
   if (c->N > c->num_sms && 2 * (sm + 1024) <= (size_t)g_max_smem)
     polar_ns_kernel<2><<<c->N, NS_THREADS, sm, c->stream>>>(
@@ -1785,22 +1763,31 @@ cudaError_t launch_mtail_from(Ctx* c, int first, int count, const int* only) {
 
 cudaError_t launch_mtail(Ctx* c) { return launch_mtail_from(c, 0, c->N + 1, nullptr); }
 cudaError_t launch_mtail_sigma(Ctx* c) { return launch_mtail_from(c, c->N, 1, nullptr); }
-cudaError_t launch_mtail_fallback(Ctx* c) { return launch_mtail_from(c, 0, c->N, c->ns_fb); }
+cudaError_t launch_mtail_fallback(Ctx* c) {
+  if (mtail_supported(c)) return launch_mtail_from(c, 0, c->N, c->ns_fb);
+  // k > 64: the FP64 refinement and M_i, rho_i^2 for the subjects whose
+  // Newton-Schulz certificate failed
+  cudaError_t e = launch_refine_from(c, c->ns_fb);
+  if (e != cudaSuccess) return e;
+  return launch_rho_from(c, c->ns_fb);
+}
 
-cudaError_t launch_rho(Ctx* c) {
+cudaError_t launch_rho_from(Ctx* c, const int* only) {
   const int k = c->k, N = c->N;
-  dk_rho_kernel<<<N + 1, 128, 0, c->stream>>>(N, k, c->T, c->G64, c->H64, c->eigv, c->sqnorm, c->d_v, c->SigmaNext,
-                                              c->Sigma, c->rho2, c->scal, c->status);
+  dk_rho_kernel<<<only ? N : N + 1, 128, 0, c->stream>>>(N, k, c->T, c->G64, c->H64, c->eigv, c->sqnorm, c->d_v,
+                                                          c->SigmaNext, c->Sigma, c->rho2, c->scal, c->status, only);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // subjects only; entry N of G64 / Xr64 (Sigma_s) is kept for the next E-step.
   // T1 = X B (into G64) ; M = T1 X^T (symmetric)
-  if ((e = bgemm(c, N, c->Xr64, 0, c->H64, 0, 1.0, nullptr, 0.0, c->G64, 0)) != cudaSuccess) return e;
-  if ((e = bgemm(c, N, c->G64, 0, c->Xr64, 1, 1.0, nullptr, 0.0, c->M64, 1)) != cudaSuccess) return e;
+  if ((e = bgemm(c, N, c->Xr64, 0, c->H64, 0, 1.0, nullptr, 0.0, c->G64, 0, only)) != cudaSuccess) return e;
+  if ((e = bgemm(c, N, c->G64, 0, c->Xr64, 1, 1.0, nullptr, 0.0, c->M64, 1, only)) != cudaSuccess) return e;
   const int64_t n = (int64_t)(N + 1) * k * k;
-  finish_m_kernel<<<nblocks(n, 256), 256, 0, c->stream>>>(N, k, c->kld, c->M64, c->Xr64, c->M32, c->Uwarm);
+  finish_m_kernel<<<nblocks(n, 256), 256, 0, c->stream>>>(N, k, c->kld, c->M64, c->Xr64, c->M32, c->Uwarm, only);
   return cudaGetLastError();
 }
+
+cudaError_t launch_rho(Ctx* c) { return launch_rho_from(c, nullptr); }
 
 cudaError_t launch_transform_finish(Ctx* c, int i, const float* part, int nsplit, int T_new, float* S_out) {
   const int nchunk = (T_new + TCH - 1) / TCH;

@@ -1,0 +1,873 @@
+// The k x k steps of an EM iteration for 64 < k <= 128 that would otherwise
+// take an eigen-decomposition per subject and one of Sigma_s (Algorithm 1):
+//
+// polar_ns_cl  the M-step's polar factor W_i = A_i (A_i^T A_i)^-1/2
+//              (eq:srm_mapping_update), ||A_i||_* and rho_i^2 (eq:srm_rho_update)
+//              by the certified coupled Newton-Schulz iteration, on a cluster
+//              of NC_C CTAs per subject (the matrices of one subject do not fit
+//              one CTA's shared memory at k = 128);
+// phi_chol,    the E-step's Phi = (Sigma_s^-1 + rho_0 I)^-1 (eq:srm_inversion_opt)
+// phi_solve    written as B^-1 Sigma_s with B = I + rho_0 Sigma_s, from the
+//              Cholesky factor B = L L^T in float-float arithmetic; ln det B =
+//              sum ln L_jj^2 gives the log-likelihood's ln det(I + rho_0
+//              Sigma_s), and a failed factorisation reports B as not positive
+//              definite.
+//
+// Newton-Schulz (as for k <= 64): with G = A_i^T A_i (error-free sum of the
+// Gram partials, symmetrised) and c = min(||G||_F, ||G||_inf) >= lambda_max,
+// the iteration on A = G / c,
+//     P = Z Y,  T = (3 I - P) / 2,  Y <- T Y,  Z <- T Z,   Y_0 = A, Z_0 = I,
+// converges to Y = A^1/2, Z = A^-1/2 (all iterates are polynomials in G, so
+// T Y = Y T); it stops two steps after max |P - I| < NS_TOL; M_0 = Z / sqrt(c).
+// The certificate E = M_0 G M_0 - I bounds the polar factor's error
+// (||A_i (M_0 - G^-1/2)||_F <= ||E||_F to first order); a subject with
+// ||E||_F > cert sqrt(k) goes through the eigen-decomposition path.  For the
+// FP32 store E is formed in float-float arithmetic (G kept as hi + lo), for
+// the BF16 store, whose threshold is 50 times larger, in plain FP32.
+// ||A_i||_* = tr(M_0 G) - tr(E M_0 G) / 2 + O(|E|^2).
+//
+// Cluster layout: CTA r of the cluster owns the 4-row tiles tr = r + NC_C l of
+// every matrix (rows a = 4 tr + u).  Each CTA keeps full copies of Y and Z
+// (the right operands) and computes its own rows of each product; after a
+// step the new rows are stored into every CTA's copies (distributed shared
+// memory) between cluster barriers.  Every control decision is taken from
+// values that all CTAs reduce in the same order, so the CTAs of a cluster
+// run the same sequence of barriers.
+#include <math.h>
+
+#include "kk_util.cuh"
+#include "tc_ptx.cuh"
+
+namespace srm {
+
+namespace {
+
+using tc::cluster_ctarank;
+using tc::cluster_sync_all;
+using tc::mapa_shared;
+using tc::smem_u32;
+
+__device__ __forceinline__ void st_cluster_f4(uint32_t raddr, float4 v) {
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(raddr), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ void st_cluster_f32(uint32_t raddr, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(raddr), "f"(v) : "memory");
+}
+
+constexpr int NC_C = 8;                                   // CTAs per subject
+constexpr int NC_KMAX = 128;
+constexpr int NC_THREADS = 512;
+constexpr int NC_TRMAX = (NC_KMAX / 4 + NC_C - 1) / NC_C;  // own 4-row tiles per CTA
+constexpr int NC_RMAX = 4 * NC_TRMAX;                      // own rows per CTA
+constexpr int NC_NW = NC_THREADS / 32;
+
+// 4 x 4 tile C[u][v] = sum_m A[m][ac + u] B[m][bc + v] over this lane's share
+// of m (KS adjacent lanes split the inner index in blocks of 4).  A is
+// m-major with leading dimension lda, B row-major with leading dimension KP.
+// With CA (CB) A (B) carries a low part: the products of the high parts are
+// error-free (hi + lo), the low parts' products are added to lo.
+template <int KS, bool CA, bool CB>
+__device__ __forceinline__ void cl_tile(const float* __restrict__ Ah, const float* __restrict__ Al, int lda, int ac,
+                                        const float* __restrict__ Bh, const float* __restrict__ Bl, int KP, int bc,
+                                        int q, bool valid, float (&hi)[4][4], float (&lo)[4][4]) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) hi[u][v] = lo[u][v] = 0.f;
+  if (!valid) return;
+  const int KQ = ((KP / 4 + KS - 1) / KS) * 4;
+  const int m0 = q * KQ, m1 = min(KP, m0 + KQ);
+#pragma unroll 2
+  for (int m = m0; m < m1; ++m) {
+    const float4 a = *reinterpret_cast<const float4*>(Ah + m * lda + ac);
+    const float4 b = *reinterpret_cast<const float4*>(Bh + m * KP + bc);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+    if (!CA && !CB) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) hi[u][v] = fmaf(av[u], bv[v], hi[u][v]);
+    } else {
+      float alv[4] = {0.f, 0.f, 0.f, 0.f}, blv[4] = {0.f, 0.f, 0.f, 0.f};
+      if (CA) {
+        const float4 t = *reinterpret_cast<const float4*>(Al + m * lda + ac);
+        alv[0] = t.x, alv[1] = t.y, alv[2] = t.z, alv[3] = t.w;
+      }
+      if (CB) {
+        const float4 t = *reinterpret_cast<const float4*>(Bl + m * KP + bc);
+        blv[0] = t.x, blv[1] = t.y, blv[2] = t.z, blv[3] = t.w;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const float p = av[u] * bv[v];
+          const float pe = fmaf(av[u], bv[v], -p);  // exact product error
+          float sm, se;
+          two_sum(hi[u][v], p, sm, se);
+          hi[u][v] = sm;
+          lo[u][v] += se + pe;
+          if (CB) lo[u][v] = fmaf(av[u], blv[v], lo[u][v]);
+          if (CA) lo[u][v] = fmaf(alv[u], bv[v], lo[u][v]);
+        }
+    }
+  }
+}
+
+__device__ __forceinline__ float block_max_cl(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float r = red[0];
+#pragma unroll
+  for (int w = 1; w < NC_NW; ++w) r = fmaxf(r, red[w]);
+  __syncthreads();
+  return r;
+}
+
+// Sums of two floats over the block (fixed-order shuffle tree, then the warp
+// partials in warp order); every thread gets the totals.
+__device__ __forceinline__ void block_sum2_cl(float& a, float& b, float (*red)[NC_NW]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = a;
+    red[1][threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  a = red[0][0];
+  b = red[1][0];
+#pragma unroll
+  for (int w = 1; w < NC_NW; ++w) {
+    a += red[0][w];
+    b += red[1][w];
+  }
+  __syncthreads();
+}
+
+// Stores `v` into slot `rank` of the array `slots` in every CTA of the cluster.
+__device__ __forceinline__ void cl_publish(float* slots, uint32_t rank, float v) {
+  const uint32_t a = smem_u32(slots + rank);
+#pragma unroll
+  for (int d = 0; d < NC_C; ++d) st_cluster_f32(mapa_shared(a, (uint32_t)d), v);
+}
+
+// Copies this CTA's rows of S (row-major [own row][KP]) into rows 4 tr + u of
+// the full matrix F in every CTA of the cluster.
+__device__ __forceinline__ void cl_broadcast_rows(const float* __restrict__ S, float* F, int KP, uint32_t r,
+                                                  int nown) {
+  const int nq = KP / 4;
+  const int n = nown * 4 * nq;
+  for (int e = threadIdx.x; e < n; e += NC_THREADS) {
+    const int lr = e / nq, j = e - lr * nq;
+    const int a = 4 * ((int)r + NC_C * (lr >> 2)) + (lr & 3);
+    const float4 v = *reinterpret_cast<const float4*>(S + lr * KP + 4 * j);
+    const uint32_t dst = smem_u32(F + a * KP + 4 * j);
+#pragma unroll
+    for (int d = 0; d < NC_C; ++d) st_cluster_f4(mapa_shared(dst, (uint32_t)d), v);
+  }
+}
+
+// grid (NC_C, N), cluster (NC_C, 1, 1), NC_THREADS threads.
+// gscr: per subject 2 k^2 floats (sym(G) hi, lo; compact k x k) of scratch.
+__global__ void __cluster_dims__(NC_C, 1, 1) __launch_bounds__(NC_THREADS, 1)
+    polar_ns_cl_kernel(int N, int k, int kld, int T, const float* __restrict__ gpart,
+                       const int* __restrict__ gslot_off, float* __restrict__ gscr, double* __restrict__ M64,
+                       float* __restrict__ M32, const double* __restrict__ sqnorm, const int64_t* __restrict__ vox,
+                       const double* __restrict__ SigmaNext, double* __restrict__ Sigma, double* __restrict__ rho2,
+                       double* __restrict__ scal, int* __restrict__ iters_out, int* __restrict__ fallback,
+                       double cert, int comp, int* status) {
+  extern __shared__ __align__(16) float nc_smem[];
+  __shared__ float redf[NC_NW];
+  __shared__ float red2[2][NC_NW];
+  __shared__ float sl_fro[NC_C], sl_inf[NC_C], sl_err[NC_C];
+  __shared__ float sl_e2[NC_C], sl_corr[NC_C], sl_th[NC_C], sl_tl[NC_C];
+  __shared__ double trS_s;
+  const uint32_t r = cluster_ctarank();
+  const int i = blockIdx.y, tid = threadIdx.x;
+  const int KP = (k + 3) & ~3, KK = KP * KP, nt4 = KP / 4;
+  const int nown = (nt4 - (int)r + NC_C - 1) / NC_C;  // own tile rows (>= 1 for k > 32)
+  float* F0 = nc_smem;            // Y (full)          | sym(G) hi (certificate)
+  float* F1 = F0 + KK;            // Z (full)          | M_0 (full)
+  float* F2 = F1 + KK;            // Gram scratch      | sym(G) lo (certificate, comp)
+  float* S0 = F2 + KK;            // T^T: [KP][NC_RMAX] (own rows as columns)
+  float* S1 = S0 + NC_RMAX * KP;  // new Y rows [NC_RMAX][KP] | R^T hi [KP][NC_RMAX]
+  float* S2 = S1 + NC_RMAX * KP;  // new Z rows [NC_RMAX][KP] | R^T lo [KP][NC_RMAX]
+  float* gh_g = gscr + (int64_t)i * 2 * k * k;
+  float* gl_g = gh_g + (int64_t)k * k;
+  auto own_row = [&](int lr) { return 4 * ((int)r + NC_C * (lr >> 2)) + (lr & 3); };
+  cluster_sync_all();  // every CTA of the cluster has started before any remote store
+
+  // ---- G: this CTA's rows a and the transposed entries G(b, a), summed over
+  // the Gram partials in slot order (error-free FP32), then sym(G) = (G + G^T)/2
+  // in float-float.  Scratch in F2: direct hi, lo and transposed hi, lo.
+  float* Dh = F2;
+  float* Dl = Dh + NC_RMAX * KP;
+  float* Th = Dl + NC_RMAX * KP;
+  float* Tl = Th + NC_RMAX * KP;
+  {
+    const int s0 = gslot_off[i], s1 = gslot_off[i + 1];
+    const int64_t sst = (int64_t)kld * kld;
+    const int nq = nt4;
+    const int ndir = nown * 4 * nq, ntr = KP * nown;  // float4 counts (each <= NC_THREADS)
+    // direct: row lr, columns 4j..4j+3; transposed: row b, columns 4 tr..4 tr+3
+    const bool hd = tid < ndir, ht = tid < ntr;
+    const int dlr = hd ? tid / nq : 0, dj = hd ? tid - (tid / nq) * nq : 0;
+    const int ta = own_row(dlr);
+    const int tb = ht ? tid / nown : 0, tl = ht ? tid - (tid / nown) * nown : 0;
+    const int ttr = (int)r + NC_C * tl;
+    const bool dok = hd && ta < k, tok = ht && tb < k;
+    const int64_t doff = (int64_t)ta * kld + 4 * dj, toff = (int64_t)tb * kld + 4 * ttr;
+    float dh[4] = {0.f, 0.f, 0.f, 0.f}, dl[4] = {0.f, 0.f, 0.f, 0.f};
+    float th[4] = {0.f, 0.f, 0.f, 0.f}, tlo[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int q = s0; q < s1; q += 4) {
+      float4 gd[4], gt[4];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const bool in = q + jj < s1;
+        gd[jj] = (dok && in) ? __ldg(reinterpret_cast<const float4*>(gpart + (q + jj) * sst + doff))
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+        gt[jj] = (tok && in) ? __ldg(reinterpret_cast<const float4*>(gpart + (q + jj) * sst + toff))
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const float xd[4] = {gd[jj].x, gd[jj].y, gd[jj].z, gd[jj].w};
+        const float xt[4] = {gt[jj].x, gt[jj].y, gt[jj].z, gt[jj].w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          float sm, se;
+          two_sum(dh[u], xd[u], sm, se);
+          dh[u] = sm;
+          dl[u] += se;
+          two_sum(th[u], xt[u], sm, se);
+          th[u] = sm;
+          tlo[u] += se;
+        }
+      }
+    }
+    if (hd) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool in = dok && 4 * dj + u < k;
+        float sm, se;
+        two_sum(dh[u], dl[u], sm, se);
+        Dh[dlr * KP + 4 * dj + u] = in ? sm : 0.f;
+        Dl[dlr * KP + 4 * dj + u] = in ? se : 0.f;
+      }
+    }
+    if (ht) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {  // G(tb, 4 ttr + u) -> transposed entry of own row (tl, u)
+        const bool in = tok && 4 * ttr + u < k;
+        float sm, se;
+        two_sum(th[u], tlo[u], sm, se);
+        Th[(4 * tl + u) * KP + tb] = in ? sm : 0.f;
+        Tl[(4 * tl + u) * KP + tb] = in ? se : 0.f;
+      }
+    }
+  }
+  if (r == 0 && tid < 32) {  // tr Sigma_s^new: fixed-order FP64 tree over the diagonal
+    double t = 0.0;
+    for (int a = tid; a < k; a += 32) t += SigmaNext[a * k + a];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (tid == 0) trS_s = t;
+  }
+  __syncthreads();
+  // sym(G) own rows -> S1 (hi), S2 (lo) and the global scratch; ||G||_F^2
+  // and the largest absolute row sum over the own rows
+  float fro = 0.f, rowmax = 0.f;
+  for (int e = tid; e < nown * 4 * KP; e += NC_THREADS) {
+    const int lr = e / KP, b = e - (e / KP) * KP;
+    float h = Dh[e], l = Dl[e];
+    ff_add(h, l, Th[e], Tl[e]);
+    h *= 0.5f;  // exact scaling
+    l *= 0.5f;
+    S1[e] = h;
+    S2[e] = l;
+    const int a = own_row(lr);
+    if (a < k && b < k) {
+      gh_g[a * k + b] = h;
+      gl_g[a * k + b] = l;
+    }
+    fro = fmaf(h, h, fro);
+  }
+  __syncthreads();
+  for (int lr = tid >> 5; lr < nown * 4; lr += NC_NW) {  // one warp per own row
+    float s = 0.f;
+    for (int b = tid & 31; b < KP; b += 32) s += fabsf(S1[lr * KP + b]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    rowmax = fmaxf(rowmax, s);
+  }
+  float unused = 0.f;
+  block_sum2_cl(fro, unused, red2);
+  rowmax = block_max_cl(rowmax, redf);
+  if (tid == 0) {
+    cl_publish(sl_fro, r, fro);
+    cl_publish(sl_inf, r, rowmax);
+  }
+  cluster_sync_all();
+  float fro_t = 0.f, ginf = 0.f;
+#pragma unroll
+  for (int d = 0; d < NC_C; ++d) {
+    fro_t += sl_fro[d];
+    ginf = fmaxf(ginf, sl_inf[d]);
+  }
+  // both bound lambda_max from above (the margin covers FP32 rounding of the bounds)
+  const double c = fmin(sqrt((double)fro_t), (double)ginf) * (1.0 + 1e-5);
+  const bool good_c = isfinite(c) && c > 0.0;
+  const float cinv = good_c ? (float)(1.0 / c) : 0.f;
+  // Y_0 = sym(G) / c (own rows, into every CTA's copy); Z_0 = I
+  for (int e = tid; e < nown * 4 * KP; e += NC_THREADS) S1[e] = (S1[e] + S2[e]) * cinv;
+  for (int e = tid; e < KK; e += NC_THREADS) {
+    const int a = e / KP, b = e - (e / KP) * KP;
+    F1[e] = (a == b && a < k) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  cl_broadcast_rows(S1, F0, KP, r, nown);
+  cluster_sync_all();
+
+  float* Y = F0;
+  float* Z = F1;
+  const int ntile = nown * nt4;
+  int it = 0, extra = -1;
+  bool conv = false;
+  for (; good_c && it < NS_MAXIT; ++it) {
+    // P = Z Y (own rows; Z symmetric, so its own rows are read as columns);
+    // T = (3I - P)/2 on the k block, stored transposed in S0; e = max |P - I|
+    float emax = 0.f;
+    {
+      constexpr int KS = 4;
+      const int lt = tid / KS / nt4, tc = tid / KS - (tid / KS / nt4) * nt4, q = tid % KS;
+      const bool valid = tid / KS < ntile;
+      const int tr = (int)r + NC_C * lt;
+      float hi[4][4], lo[4][4];
+      cl_tile<KS, false, false>(Z, nullptr, KP, 4 * tr, Y, nullptr, KP, 4 * tc, q, valid, hi, lo);
+      tile_combine<KS, false>(hi, lo);
+      if (valid && q == 0) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int b = 4 * tc + v;
+          float t[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int a = 4 * tr + u;
+            t[u] = 0.f;
+            if (a < k && b < k) {
+              const float d = (a == b) ? 1.f : 0.f;
+              emax = fmaxf(emax, fabsf(hi[u][v] - d));
+              t[u] = 1.5f * d - 0.5f * hi[u][v];
+            }
+          }
+          *reinterpret_cast<float4*>(S0 + b * NC_RMAX + 4 * lt) = make_float4(t[0], t[1], t[2], t[3]);
+        }
+      }
+    }
+    __syncthreads();
+    // T Y and T Z at once, each by half of the block
+    {
+      constexpr int KS = 2;
+      const int half = tid / (NC_THREADS / 2), lt0 = tid - half * (NC_THREADS / 2);
+      const int lt = lt0 / KS / nt4, tc = lt0 / KS - (lt0 / KS / nt4) * nt4, q = lt0 % KS;
+      const bool valid = lt0 / KS < ntile;
+      float hi[4][4], lo[4][4];
+      cl_tile<KS, false, false>(S0, nullptr, NC_RMAX, 4 * lt, half ? Z : Y, nullptr, KP, 4 * tc, q, valid, hi, lo);
+      tile_combine<KS, false>(hi, lo);
+      if (valid && q == 0) {
+        float* out = half ? S2 : S1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          *reinterpret_cast<float4*>(out + (4 * lt + u) * KP + 4 * tc) =
+              make_float4(hi[u][0], hi[u][1], hi[u][2], hi[u][3]);
+      }
+    }
+    emax = block_max_cl(emax, redf);  // (its barriers also complete S1, S2)
+    if (tid == 0) cl_publish(sl_err, r, emax);
+    cluster_sync_all();  // every CTA has read Y and Z; the errors are published
+    float err = 0.f;
+#pragma unroll
+    for (int d = 0; d < NC_C; ++d) err = fmaxf(err, sl_err[d]);
+    if (!(err == err)) break;  // non-finite
+    if (extra < 0 && err < NS_TOL) extra = 1;
+    if (extra == 0) {
+      conv = true;
+      break;
+    }
+    if (extra > 0) --extra;
+    cl_broadcast_rows(S1, Y, KP, r, nown);
+    cl_broadcast_rows(S2, Z, KP, r, nown);
+    cluster_sync_all();
+  }
+
+  // ---- certificate.  M_0 = Z / sqrt(c) (full, in F1); sym(G) hi / lo from
+  // the global scratch into F0 / F2.  R = M_0 G (own rows, stored transposed
+  // in S1 / S2); E = R M_0 - I (own rows); ||E||_F^2, tr(E R^T) =
+  // sum_ab E_ab R_ab (E symmetric) and tr R = tr(M_0 G).
+  float* Mb = F1;
+  {
+    const float sc = good_c ? (float)sqrt(1.0 / c) : 0.f;
+    for (int e = tid; e < KK; e += NC_THREADS) {
+      const int a = e / KP, b = e - (e / KP) * KP;
+      const bool in = a < k && b < k;
+      Mb[e] *= sc;
+      F0[e] = in ? __ldcg(gh_g + a * k + b) : 0.f;
+      if (comp) F2[e] = in ? __ldcg(gl_g + a * k + b) : 0.f;
+    }
+  }
+  __syncthreads();
+  {
+    constexpr int KS = 4;
+    const int lt = tid / KS / nt4, tc = tid / KS - (tid / KS / nt4) * nt4, q = tid % KS;
+    const bool valid = tid / KS < ntile;
+    const int tr = (int)r + NC_C * lt;
+    float hi[4][4], lo[4][4];
+    if (comp) {
+      cl_tile<KS, false, true>(Mb, nullptr, KP, 4 * tr, F0, F2, KP, 4 * tc, q, valid, hi, lo);
+      tile_combine<KS, true>(hi, lo);
+    } else {
+      cl_tile<KS, false, false>(Mb, nullptr, KP, 4 * tr, F0, nullptr, KP, 4 * tc, q, valid, hi, lo);
+      tile_combine<KS, false>(hi, lo);
+    }
+    if (valid && q == 0) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int b = 4 * tc + v;
+        *reinterpret_cast<float4*>(S1 + b * NC_RMAX + 4 * lt) = make_float4(hi[0][v], hi[1][v], hi[2][v], hi[3][v]);
+        *reinterpret_cast<float4*>(S2 + b * NC_RMAX + 4 * lt) =
+            comp ? make_float4(lo[0][v], lo[1][v], lo[2][v], lo[3][v]) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+  }
+  __syncthreads();
+  float e2 = 0.f, corr = 0.f;
+  {
+    constexpr int KS = 4;
+    const int lt = tid / KS / nt4, tc = tid / KS - (tid / KS / nt4) * nt4, q = tid % KS;
+    const bool valid = tid / KS < ntile;
+    const int tr = (int)r + NC_C * lt;
+    float hi[4][4], lo[4][4];
+    if (comp) {
+      cl_tile<KS, true, false>(S1, S2, NC_RMAX, 4 * lt, Mb, nullptr, KP, 4 * tc, q, valid, hi, lo);
+      tile_combine<KS, true>(hi, lo);
+    } else {
+      cl_tile<KS, false, false>(S1, nullptr, NC_RMAX, 4 * lt, Mb, nullptr, KP, 4 * tc, q, valid, hi, lo);
+      tile_combine<KS, false>(hi, lo);
+    }
+    if (valid && q == 0) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int a = 4 * tr + u, b = 4 * tc + v;
+          if (a >= k || b >= k) continue;
+          const float ev = (hi[u][v] - (a == b ? 1.f : 0.f)) + lo[u][v];
+          e2 = fmaf(ev, ev, e2);
+          corr = fmaf(ev, S1[b * NC_RMAX + 4 * lt + u], corr);
+        }
+    }
+  }
+  // tr R over the own rows in float-float (one warp)
+  if (tid < 32) {
+    float h = 0.f, l = 0.f;
+    for (int lr = tid; lr < nown * 4; lr += 32) {
+      const int a = own_row(lr);
+      if (a < k) ff_add(h, l, S1[a * NC_RMAX + lr], S2[a * NC_RMAX + lr]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+      ff_add(h, l, oh, ol);
+    }
+    if (tid == 0) {
+      cl_publish(sl_th, r, h);
+      cl_publish(sl_tl, r, l);
+    }
+  }
+  block_sum2_cl(e2, corr, red2);
+  if (tid == 0) {
+    cl_publish(sl_e2, r, e2);
+    cl_publish(sl_corr, r, corr);
+  }
+  cluster_sync_all();  // the last exchange: no remote access follows
+  float e2t = 0.f, corrt = 0.f, th = 0.f, tl = 0.f;
+#pragma unroll
+  for (int d = 0; d < NC_C; ++d) {
+    e2t += sl_e2[d];
+    corrt += sl_corr[d];
+    ff_add(th, tl, sl_th[d], sl_tl[d]);
+  }
+  const double enorm = sqrt((double)e2t);
+  const bool ok = conv && good_c && enorm <= cert * sqrt((double)k) && isfinite(enorm);
+  if (r == 0 && tid == 0) {
+    const double trS = trS_s;
+    if (iters_out) iters_out[i] = it;
+    fallback[i] = ok ? 0 : 1;
+    if (ok) {
+      const double nuc = ((double)th + (double)tl) - 0.5 * (double)corrt;
+      const double rr = (sqnorm[i] - 2.0 * nuc + (double)T * trS) / ((double)T * (double)vox[i]);
+      if (!(rr > 0.0) || !isfinite(rr)) flag(status, ST_NONFINITE);
+      rho2[i] = rr;
+    }
+    if (i == 0) scal[SC_TRSIG] = trS;
+  }
+  if (ok) {
+    double* Mi = M64 + (int64_t)i * k * k;
+    float* M32i = M32 + (int64_t)i * kld * kld;
+    for (int e = tid; e < nown * 4 * k; e += NC_THREADS) {
+      const int lr = e / k, b = e - (e / k) * k;
+      const int a = own_row(lr);
+      if (a >= k) continue;
+      const float m = Mb[a * KP + b];
+      Mi[a * k + b] = (double)m;
+      M32i[a * kld + b] = m;
+    }
+  }
+  if (i == 0 && r == 0)
+    for (int e = tid; e < k * k; e += NC_THREADS) Sigma[e] = SigmaNext[e];
+}
+
+size_t ns_cl_smem_bytes(int k) {
+  const int KP = (k + 3) & ~3;
+  return sizeof(float) * (3 * (size_t)KP * KP + 3 * (size_t)NC_RMAX * KP);
+}
+
+// ---------------------------------------------------------------- Phi by Cholesky
+// Phi = B^-1 Sigma_s and ln det B with B = I + rho_0 sym(Sigma_s), in
+// float-float arithmetic: each value is an unevaluated sum h + l of two FP32
+// numbers (about 48 significant bits), with error-free products (the FMA
+// gives a h b exactly as p + fma(a, b, -p)) and error-free sums (two_sum).
+// FP64 runs at a small fraction of the FP32 rate on this part, so the
+// factorisation and the solves, whose steps form long dependent chains, take
+// FP32 operations only; every product that feeds an error-free transformation
+// is rounded on its own (__fmul_rn), never fused with a following add.
+
+// s + e == a + b exactly, for |a| >= |b| or a == 0
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// (h, l) = (ah, al) (bh, bl), renormalised
+__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float& h, float& l) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  fast_two_sum(p, e, h, l);
+}
+
+// (h, l) -= (ah, al) (bh, bl)
+__device__ __forceinline__ void ff_fnms(float& h, float& l, float ah, float al, float bh, float bl) {
+  float ph, pl;
+  ff_mul(ah, al, bh, bl, ph, pl);
+  ff_add(h, l, -ph, -pl);
+}
+
+// 1 / sqrt(d) for d = dh + dl > 0: the FP32 rsqrtf estimate y (about 22
+// correct bits) and one Newton-Raphson step y + y (1 - d y^2) / 2, with the
+// residual 1 - d y^2 formed in float-float (about 44 correct bits)
+__device__ __forceinline__ void ff_rsqrt(float dh, float dl, float& h, float& l) {
+  const float y = rsqrtf(dh);
+  float th, tl;
+  ff_mul(dh, dl, y, 0.f, th, tl);
+  ff_mul(th, tl, y, 0.f, th, tl);
+  const float e = __fsub_rn(__fsub_rn(1.f, th), tl);
+  fast_two_sum(y, __fmul_rn(0.5f * y, e), h, l);
+}
+
+// One CTA.  rho_0 = sum_i rho_i^-2 (eq:srm_wt_psi_w) and the likelihood's sums
+// over subjects (or, for a sharded E-step, sums = {sum rho_i^-2,
+// sum v_i ln rho_i^2, sum ||X^_i||^2 / rho_i^2, sum v_i} over all shards);
+// B in shared memory (column-major, hi and lo planes), factorised
+// right-looking: step j scales column j by 1 / sqrt(d_j) into L (and a
+// shared copy), then the trailing lower triangle takes the rank-1 update
+// B_ic -= L_ij L_cj.  L goes to Lh / Ll (column-major), 1 / L_jj to Dh / Dl,
+// and ln det B = sum_j ln d_j is summed in FP64 after the loop.
+constexpr int PC_THREADS = 1024;
+
+__global__ void __launch_bounds__(PC_THREADS) phi_chol_kernel(int N, int k, const double* __restrict__ rho2,
+                                                              const double* __restrict__ sqnorm,
+                                                              const int64_t* __restrict__ vox,
+                                                              const double* __restrict__ Sigma, float* __restrict__ Lh,
+                                                              float* __restrict__ Ll, float* __restrict__ Dh,
+                                                              float* __restrict__ Dl, double* __restrict__ scal,
+                                                              int* status, double vtot, const double* __restrict__ sums) {
+  extern __shared__ float pc_smem[];
+  float* Bh = pc_smem;       // [k][k] column-major: (i, c) at c * k + i
+  float* Bl = Bh + k * k;
+  float* ch = Bl + k * k;    // [k] column j of L
+  float* cl = ch + k;
+  float* ph = cl + k;        // [k] pivots d_j
+  float* pl = ph + k;
+  __shared__ double red[3][PC_THREADS];
+  const int tid = threadIdx.x;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  if (sums) {
+    s0 = sums[0];
+    s1 = sums[1];
+    s2 = sums[2];
+    vtot = sums[3];
+    if (!(s0 > 0.0) || !isfinite(s0) || !isfinite(s1) || !isfinite(s2) || !(vtot > 0.0)) flag(status, ST_NONFINITE);
+  } else {
+    for (int i = tid; i < N; i += PC_THREADS) {
+      const double r = rho2[i];
+      if (!(r > 0.0) || !isfinite(r)) flag(status, ST_NONFINITE);
+      s0 += 1.0 / r;
+      s1 += (double)vox[i] * log(r);
+      s2 += sqnorm[i] / r;
+    }
+    red[0][tid] = s0;
+    red[1][tid] = s1;
+    red[2][tid] = s2;
+    __syncthreads();
+    for (int st = PC_THREADS / 2; st > 0; st >>= 1) {
+      if (tid < st) {
+        red[0][tid] += red[0][tid + st];
+        red[1][tid] += red[1][tid + st];
+        red[2][tid] += red[2][tid + st];
+      }
+      __syncthreads();
+    }
+    s0 = red[0][0];
+    s1 = red[1][0];
+    s2 = red[2][0];
+    __syncthreads();  // red is reused below
+  }
+  const double rho0 = s0;
+  for (int e = tid; e < k * k; e += PC_THREADS) {
+    const int c = e / k, i = e - c * k;
+    const double x = (i == c ? 1.0 : 0.0) + rho0 * (0.5 * (Sigma[i * k + c] + Sigma[c * k + i]));
+    const float h = (float)x;
+    Bh[e] = h;
+    Bl[e] = (float)(x - (double)h);
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  bool pd = true;
+  int jdone = 0;
+  for (int j = 0; j < k; ++j) {
+    const float dh = Bh[j * k + j], dl = Bl[j * k + j];
+    if (!(dh > 0.f) || !isfinite(dh)) {  // the same value in every thread
+      pd = false;
+      break;
+    }
+    float ih, il;
+    ff_rsqrt(dh, dl, ih, il);
+    for (int i = j + tid; i < k; i += PC_THREADS) {
+      float h, l;
+      ff_mul(Bh[j * k + i], Bl[j * k + i], ih, il, h, l);
+      ch[i] = h;
+      cl[i] = l;
+      Lh[j * k + i] = h;
+      Ll[j * k + i] = l;
+    }
+    if (tid == 0) {
+      ph[j] = dh;
+      pl[j] = dl;
+      Dh[j] = ih;
+      Dl[j] = il;
+    }
+    __syncthreads();
+    for (int cc = j + 1 + warp; cc < k; cc += PC_THREADS / 32) {
+      const float lh = ch[cc], ll = cl[cc];
+      float* bh = Bh + cc * k;
+      float* bl = Bl + cc * k;
+      for (int i = cc + lane; i < k; i += 32) {
+        float h = bh[i], l = bl[i];
+        ff_fnms(h, l, ch[i], cl[i], lh, ll);
+        bh[i] = h;
+        bl[i] = l;
+      }
+    }
+    __syncthreads();
+    jdone = j + 1;
+  }
+  // ln det B = sum_j ln d_j (fixed-order tree over the block)
+  double ld = 0.0;
+  for (int j = tid; j < jdone; j += PC_THREADS) ld += log((double)ph[j] + (double)pl[j]);
+  red[0][tid] = ld;
+  __syncthreads();
+  for (int st = PC_THREADS / 2; st > 0; st >>= 1) {
+    if (tid < st) red[0][tid] += red[0][tid + st];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (!pd) flag(status, ST_NOT_PD);
+    scal[SC_RHO0] = rho0;
+    scal[SC_LOGDET] = red[0][0];
+    scal[SC_VLOGRHO] = s1;
+    scal[SC_SQRHO] = s2;
+    scal[SC_VTOT] = vtot;
+  }
+}
+
+// grid k blocks, PS_THREADS threads.  Block j stages L (hi and lo planes,
+// column-major with an odd leading dimension so that rows and columns are
+// both read without bank conflicts) and one warp solves L L^T x =
+// sym(Sigma_s)[:, j] in float-float by forward and backward substitution,
+// lane l holding entries l + 32 u, by 32-row blocks: the block's triangle
+// step by step (only that block's entries are in the dependent chain), then
+// the other blocks take its contribution.  Phi's row j = x (Phi = B^-1
+// Sigma_s is symmetric), in FP64 and FP32.
+constexpr int PS_THREADS = 128;
+
+template <int R>  // entries per lane: k <= 32 R
+__global__ void __launch_bounds__(PS_THREADS) phi_solve_kernel(int k, const float* __restrict__ Lh,
+                                                               const float* __restrict__ Ll,
+                                                               const float* __restrict__ Dh,
+                                                               const float* __restrict__ Dl,
+                                                               const double* __restrict__ Sigma,
+                                                               double* __restrict__ Phi, float* __restrict__ Phi32,
+                                                               int* status) {
+  extern __shared__ float ps_smem[];
+  const int ld = k | 1;
+  float* Sh = ps_smem;        // [k][ld]: (i, m) at m * ld + i
+  float* Sl = Sh + k * ld;
+  float* dh = Sl + k * ld;    // [k] 1 / L_mm
+  float* dl = dh + k;
+  const int j = blockIdx.x, tid = threadIdx.x;
+  for (int e = tid; e < k * k; e += PS_THREADS) {
+    const int m = e / k, i = e - m * k;
+    const bool low = i >= m;
+    Sh[m * ld + i] = low ? Lh[e] : 0.f;
+    Sl[m * ld + i] = low ? Ll[e] : 0.f;
+  }
+  for (int m = tid; m < k; m += PS_THREADS) {
+    dh[m] = Dh[m];
+    dl[m] = Dl[m];
+  }
+  __syncthreads();
+  if (tid >= 32) return;
+  const int lane = tid;
+  float yh[R], yl[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int i = lane + 32 * u;
+    const double x = i < k ? 0.5 * (Sigma[i * k + j] + Sigma[j * k + i]) : 0.0;
+    yh[u] = (float)x;
+    yl[u] = (float)(x - (double)yh[u]);
+  }
+  // L z = y
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int iu = lane + 32 * u;
+    for (int s = 0; s < 32; ++s) {
+      const int m = 32 * u + s;
+      if (m >= k) break;
+      float zh, zl;
+      ff_mul(__shfl_sync(0xffffffffu, yh[u], s), __shfl_sync(0xffffffffu, yl[u], s), dh[m], dl[m], zh, zl);
+      if (lane == s) {
+        yh[u] = zh;
+        yl[u] = zl;
+      }
+      if (iu > m && iu < k) ff_fnms(yh[u], yl[u], Sh[m * ld + iu], Sl[m * ld + iu], zh, zl);
+    }
+    if (u + 1 < R) {
+      for (int s = 0; s < 32; ++s) {
+        const int m = 32 * u + s;
+        if (m >= k) break;
+        const float zh = __shfl_sync(0xffffffffu, yh[u], s), zl = __shfl_sync(0xffffffffu, yl[u], s);
+#pragma unroll
+        for (int w = u + 1; w < R; ++w) {
+          const int i = lane + 32 * w;
+          if (i < k) ff_fnms(yh[w], yl[w], Sh[m * ld + i], Sl[m * ld + i], zh, zl);
+        }
+      }
+    }
+  }
+  // L^T x = z (column m of L^T is row m of L), blocks from the last
+#pragma unroll
+  for (int u = R - 1; u >= 0; --u) {
+    const int iu = lane + 32 * u;
+    for (int s = 31; s >= 0; --s) {
+      const int m = 32 * u + s;
+      if (m >= k) continue;
+      float xh, xl;
+      ff_mul(__shfl_sync(0xffffffffu, yh[u], s), __shfl_sync(0xffffffffu, yl[u], s), dh[m], dl[m], xh, xl);
+      if (lane == s) {
+        yh[u] = xh;
+        yl[u] = xl;
+      }
+      if (iu < m) ff_fnms(yh[u], yl[u], Sh[iu * ld + m], Sl[iu * ld + m], xh, xl);
+    }
+    if (u > 0) {
+      for (int s = 0; s < 32; ++s) {
+        const int m = 32 * u + s;
+        if (m >= k) break;
+        const float xh = __shfl_sync(0xffffffffu, yh[u], s), xl = __shfl_sync(0xffffffffu, yl[u], s);
+#pragma unroll
+        for (int w = 0; w < u; ++w) {
+          const int i = lane + 32 * w;
+          ff_fnms(yh[w], yl[w], Sh[i * ld + m], Sl[i * ld + m], xh, xl);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int i = lane + 32 * u;
+    if (i < k) {
+      const double x = (double)yh[u] + (double)yl[u];
+      if (!isfinite(x)) flag(status, ST_NONFINITE);
+      Phi[j * k + i] = x;
+      Phi32[j * k + i] = (float)x;
+    }
+  }
+}
+
+size_t phi_chol_smem_bytes(int k) { return sizeof(float) * (2 * (size_t)k * k + 4 * k); }
+size_t phi_solve_smem_bytes(int k) { return sizeof(float) * (2 * (size_t)k * (k | 1) + 2 * k); }
+
+}  // namespace
+
+bool polar_cl_supported(const Ctx* c) { return c->k > 64 && c->k <= NC_KMAX; }
+
+void prepare_tail_kernels() {
+  cudaFuncSetAttribute(polar_ns_cl_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)ns_cl_smem_bytes(NC_KMAX));
+  cudaFuncSetAttribute(polar_ns_cl_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
+  cudaFuncSetAttribute(phi_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)phi_chol_smem_bytes(KMAX));
+  cudaFuncSetAttribute(phi_solve_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)phi_solve_smem_bytes(KMAX));
+}
+
+cudaError_t launch_polar_cl(Ctx* c, double cert, int comp) {
+  // sym(G) hi / lo per subject in the G64 buffer (k^2 doubles = 2 k^2 floats),
+  // which the eigen-decomposition fallback overwrites only afterwards
+  polar_ns_cl_kernel<<<dim3(NC_C, c->N), NC_THREADS, ns_cl_smem_bytes(c->k), c->stream>>>(
+      c->N, c->k, c->kld, c->T, c->Gpart, c->gslot_off, reinterpret_cast<float*>(c->G64), c->M64, c->M32, c->sqnorm,
+      c->d_v, c->SigmaNext, c->Sigma, c->rho2, c->scal, c->jac_sweeps, c->ns_fb, cert, comp, c->status);
+  return cudaGetLastError();
+}
+
+// Phi and ln det(I + rho_0 Sigma_s) from the committed Sigma_s.  The Cholesky
+// factor (hi and lo planes) and its reciprocal diagonal go to the H64 buffer
+// (2 k^2 + 2 k floats of (N + 1) k^2 doubles), which nothing else reads
+// between an M-step tail and the next.
+cudaError_t launch_phi_chol(Ctx* c, const double* sums) {
+  const int k = c->k;
+  if (k > 128) return cudaErrorInvalidValue;
+  float* Lh = reinterpret_cast<float*>(c->H64);
+  float* Ll = Lh + (int64_t)k * k;
+  float* Dh = Ll + (int64_t)k * k;
+  float* Dl = Dh + k;
+  phi_chol_kernel<<<1, PC_THREADS, phi_chol_smem_bytes(k), c->stream>>>(
+      c->N, k, c->rho2, c->sqnorm, c->d_v, c->Sigma, Lh, Ll, Dh, Dl, c->scal, c->status, (double)c->Vtot, sums);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  phi_solve_kernel<4><<<k, PS_THREADS, phi_solve_smem_bytes(k), c->stream>>>(k, Lh, Ll, Dh, Dl, c->Sigma, c->Phi,
+                                                                             c->Phi32, c->status);
+  return cudaGetLastError();
+}
+
+}  // namespace srm

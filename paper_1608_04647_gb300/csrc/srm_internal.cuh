@@ -154,6 +154,7 @@ struct Ctx {
   bool fused = false;
   bool p_from_f = false;      // the current P partials come from the single pass
   bool sig_eig_done = false;  // Sigma_s^new and its eigen-decomposition already ran beside that pass
+  bool force_eig_polar = false;  // every polar factor through the eigen-decomposition path
   float* f_ppart = nullptr;
   ChunkSrc* f_chunk_src = nullptr;
   int* f_chunk_src_off = nullptr;
@@ -259,6 +260,12 @@ cudaError_t launch_eig_sigma(Ctx* c);
 cudaError_t launch_eig_fallback(Ctx* c);
 cudaError_t launch_mtail_fallback(Ctx* c);
 bool ns_supported(const Ctx* c);
+bool sigma_eig_supported(const Ctx* c);
+// k_tail.cu: 64 < k <= 128
+bool polar_cl_supported(const Ctx* c);
+void prepare_tail_kernels();
+cudaError_t launch_polar_cl(Ctx* c, double cert, int comp);
+cudaError_t launch_phi_chol(Ctx* c, const double* sums);
 cudaError_t launch_polar(Ctx* c);
 cudaError_t launch_transform_finish(Ctx* c, int subject, const float* part, int nsplit, int T_new, float* S_out);
 

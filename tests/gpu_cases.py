@@ -35,7 +35,8 @@ def run_oracle(d, n_iter, final_ll=True):
                       final_ll=final_ll)
 
 
-def run_gpu(d, k, n_iter, store="f32", graph=False, final_ll=True, input_bf16=False, single_pass=False):
+def run_gpu(d, k, n_iter, store="f32", graph=False, final_ll=True, input_bf16=False, single_pass=False,
+            eig_polar=False):
     import torch
 
     import paper_1608_04647_gb300 as srm
@@ -44,6 +45,8 @@ def run_gpu(d, k, n_iter, store="f32", graph=False, final_ll=True, input_bf16=Fa
         X = [x.to(torch.bfloat16) for x in X]
     W0 = [torch.from_numpy(w).cuda() for w in d["W0"]]
     m = srm.SRM(X, W0, k, store=store, graph=graph, final_ll=final_ll, single_pass=single_pass)
+    if eig_polar:  # every polar factor through the eigen-decomposition path
+        srm.srm_debug_force_eig_polar(m.ctx, True)
     ll = m.fit(n_iter)
     out = {"ll": ll, "W": [m.get_w(i).cpu().numpy().astype(np.float64) for i in range(len(X))],
            "ES": m.get_s().cpu().numpy().astype(np.float64)}
