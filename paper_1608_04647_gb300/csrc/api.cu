@@ -588,6 +588,7 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
   if (ce != cudaSuccess) return fail(cuda_fail(ce, "cudaMemcpy"));
 
   prepare_small_kernels(prop.sharedMemPerBlockOptin);
+  if (polar_cl_supported(c)) choose_polar_cl(c);
   prepare_center_kernels(prop.sharedMemPerBlockOptin);
   prepare_simt_kernels(prop.sharedMemPerBlockOptin);
   if (batched) {

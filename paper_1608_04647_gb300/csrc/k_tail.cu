@@ -4,8 +4,8 @@
 // polar_ns_cl  the M-step's polar factor W_i = A_i (A_i^T A_i)^-1/2
 //              (eq:srm_mapping_update), ||A_i||_* and rho_i^2 (eq:srm_rho_update)
 //              by the certified coupled Newton-Schulz iteration, on a cluster
-//              of NC_C CTAs per subject (the matrices of one subject do not fit
-//              one CTA's shared memory at k = 128);
+//              of 8 or 4 CTAs per subject (the matrices of one subject do not
+//              fit one CTA's shared memory at k = 128);
 // phi_chol,    the E-step's Phi = (Sigma_s^-1 + rho_0 I)^-1 (eq:srm_inversion_opt)
 // phi_solve    written as B^-1 Sigma_s with B = I + rho_0 Sigma_s, from the
 //              Cholesky factor B = L L^T in float-float arithmetic; ln det B =
@@ -26,7 +26,7 @@
 // the BF16 store, whose threshold is 50 times larger, in plain FP32.
 // ||A_i||_* = tr(M_0 G) - tr(E M_0 G) / 2 + O(|E|^2).
 //
-// Cluster layout: CTA r of the cluster owns the 4-row tiles tr = r + NC_C l of
+// Cluster layout: CTA r of a cluster of C CTAs owns the 4-row tiles tr = r + C l of
 // every matrix (rows a = 4 tr + u).  Each CTA keeps full copies of Y and Z
 // (the right operands) and computes its own rows of each product; after a
 // step the new rows are stored into every CTA's copies (distributed shared
@@ -56,12 +56,16 @@ __device__ __forceinline__ void st_cluster_f32(uint32_t raddr, float v) {
   asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(raddr), "f"(v) : "memory");
 }
 
-constexpr int NC_C = 8;                                   // CTAs per subject
 constexpr int NC_KMAX = 128;
 constexpr int NC_THREADS = 512;
-constexpr int NC_TRMAX = (NC_KMAX / 4 + NC_C - 1) / NC_C;  // own 4-row tiles per CTA
-constexpr int NC_RMAX = 4 * NC_TRMAX;                      // own rows per CTA
 constexpr int NC_NW = NC_THREADS / 32;
+
+// Own rows per CTA for a cluster of C CTAs: the 4-row tiles tr = r + C l.
+template <int C>
+struct NcGeom {
+  static constexpr int TRMAX = (NC_KMAX / 4 + C - 1) / C;
+  static constexpr int RMAX = 4 * TRMAX;
+};
 
 // 4 x 4 tile C[u][v] = sum_m A[m][ac + u] B[m][bc + v] over this lane's share
 // of m (KS adjacent lanes split the inner index in blocks of 4).  A is
@@ -103,7 +107,7 @@ __device__ __forceinline__ void cl_tile(const float* __restrict__ Ah, const floa
       for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          const float p = av[u] * bv[v];
+          const float p = __fmul_rn(av[u], bv[v]);
           const float pe = fmaf(av[u], bv[v], -p);  // exact product error
           float sm, se;
           two_sum(hi[u][v], p, sm, se);
@@ -151,125 +155,150 @@ __device__ __forceinline__ void block_sum2_cl(float& a, float& b, float (*red)[N
   __syncthreads();
 }
 
-// Stores `v` into slot `rank` of the array `slots` in every CTA of the cluster.
-__device__ __forceinline__ void cl_publish(float* slots, uint32_t rank, float v) {
-  const uint32_t a = smem_u32(slots + rank);
+// Stores `v` into slots[idx] in every CTA of the cluster.
+template <int C>
+__device__ __forceinline__ void cl_publish(float* slots, int idx, float v) {
+  const uint32_t a = smem_u32(slots + idx);
 #pragma unroll
-  for (int d = 0; d < NC_C; ++d) st_cluster_f32(mapa_shared(a, (uint32_t)d), v);
+  for (int d = 0; d < C; ++d) st_cluster_f32(mapa_shared(a, (uint32_t)d), v);
 }
 
 // Copies this CTA's rows of S (row-major [own row][KP]) into rows 4 tr + u of
 // the full matrix F in every CTA of the cluster.
+template <int C>
 __device__ __forceinline__ void cl_broadcast_rows(const float* __restrict__ S, float* F, int KP, uint32_t r,
                                                   int nown) {
   const int nq = KP / 4;
   const int n = nown * 4 * nq;
   for (int e = threadIdx.x; e < n; e += NC_THREADS) {
     const int lr = e / nq, j = e - lr * nq;
-    const int a = 4 * ((int)r + NC_C * (lr >> 2)) + (lr & 3);
+    const int a = 4 * ((int)r + C * (lr >> 2)) + (lr & 3);
     const float4 v = *reinterpret_cast<const float4*>(S + lr * KP + 4 * j);
     const uint32_t dst = smem_u32(F + a * KP + 4 * j);
 #pragma unroll
-    for (int d = 0; d < NC_C; ++d) st_cluster_f4(mapa_shared(dst, (uint32_t)d), v);
+    for (int d = 0; d < C; ++d) st_cluster_f4(mapa_shared(dst, (uint32_t)d), v);
   }
 }
 
-// grid (NC_C, N), cluster (NC_C, 1, 1), NC_THREADS threads.
-// gscr: per subject 2 k^2 floats (sym(G) hi, lo; compact k x k) of scratch.
-__global__ void __cluster_dims__(NC_C, 1, 1) __launch_bounds__(NC_THREADS, 1)
+// Products of this CTA's tiles: the KS-lane groups walk the own tiles (lt,
+// tc), lt < nown, tc < nt4, in passes of NTH / KS tiles (NTH threads from
+// thread `base`); f(lt, tc, hi, lo) consumes a finished tile (lane q == 0).
+template <int KS, bool CA, bool CB, typename F>
+__device__ __forceinline__ void cl_product(const float* Ah, const float* Al, int lda, bool a_full, int r, int C,
+                                           const float* Bh, const float* Bl, int KP, int nown, int base, int nth,
+                                           F f) {
+  const int lt0 = (int)threadIdx.x - base;
+  if (lt0 < 0 || lt0 >= nth) return;  // whole warps
+  const int nt4 = KP / 4, ntile = nown * nt4, per = nth / KS, q = lt0 % KS;
+  for (int t0 = 0; t0 < ntile; t0 += per) {
+    const int t = t0 + lt0 / KS;
+    const bool valid = t < ntile;
+    const int lt = valid ? t / nt4 : 0, tc = valid ? t - (t / nt4) * nt4 : 0;
+    const int ac = a_full ? 4 * (r + C * lt) : 4 * lt;
+    float hi[4][4], lo[4][4];
+    cl_tile<KS, CA, CB>(Ah, Al, lda, ac, Bh, Bl, KP, 4 * tc, q, valid, hi, lo);
+    tile_combine<KS, CA || CB>(hi, lo);
+    if (valid && q == 0) f(lt, tc, hi, lo);
+  }
+}
+
+// grid (C, N), cluster (C, 1, 1), NC_THREADS threads.  gscr: per subject
+// 2 k^2 floats (sym(G) hi, lo; compact k x k) of scratch.  Shared memory:
+// full Y and Z, with comp a third full matrix (sym(G) lo in the
+// certificate), and three own-row buffers.
+template <int C>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NC_THREADS, 1)
     polar_ns_cl_kernel(int N, int k, int kld, int T, const float* __restrict__ gpart,
                        const int* __restrict__ gslot_off, float* __restrict__ gscr, double* __restrict__ M64,
                        float* __restrict__ M32, const double* __restrict__ sqnorm, const int64_t* __restrict__ vox,
                        const double* __restrict__ SigmaNext, double* __restrict__ Sigma, double* __restrict__ rho2,
                        double* __restrict__ scal, int* __restrict__ iters_out, int* __restrict__ fallback,
                        double cert, int comp, int* status) {
+  constexpr int RMAX = NcGeom<C>::RMAX;
   extern __shared__ __align__(16) float nc_smem[];
   __shared__ float redf[NC_NW];
   __shared__ float red2[2][NC_NW];
-  __shared__ float sl_fro[NC_C], sl_inf[NC_C], sl_err[NC_C];
-  __shared__ float sl_e2[NC_C], sl_corr[NC_C], sl_th[NC_C], sl_tl[NC_C];
+  __shared__ float sl_fro[C], sl_inf[C], sl_err[C * NC_NW];
+  __shared__ float sl_e2[C], sl_corr[C], sl_th[C], sl_tl[C];
   __shared__ double trS_s;
   const uint32_t r = cluster_ctarank();
-  const int i = blockIdx.y, tid = threadIdx.x;
+  const int i = blockIdx.y, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int KP = (k + 3) & ~3, KK = KP * KP, nt4 = KP / 4;
-  const int nown = (nt4 - (int)r + NC_C - 1) / NC_C;  // own tile rows (>= 1 for k > 32)
-  float* F0 = nc_smem;            // Y (full)          | sym(G) hi (certificate)
-  float* F1 = F0 + KK;            // Z (full)          | M_0 (full)
-  float* F2 = F1 + KK;            // Gram scratch      | sym(G) lo (certificate, comp)
-  float* S0 = F2 + KK;            // T^T: [KP][NC_RMAX] (own rows as columns)
-  float* S1 = S0 + NC_RMAX * KP;  // new Y rows [NC_RMAX][KP] | R^T hi [KP][NC_RMAX]
-  float* S2 = S1 + NC_RMAX * KP;  // new Z rows [NC_RMAX][KP] | R^T lo [KP][NC_RMAX]
+  const int nown = (nt4 - (int)r + C - 1) / C;  // own tile rows (>= 2 for k > 64)
+  float* F0 = nc_smem;                     // Y (full)   | sym(G) hi (certificate)
+  float* F1 = F0 + KK;                     // Z (full)   | M_0 (full)
+  float* F2 = F1 + KK;                     // (comp)       sym(G) lo (certificate)
+  float* S0 = F1 + (comp ? 2 : 1) * KK;    // T^T: [KP][RMAX] (own rows as columns)
+  float* S1 = S0 + RMAX * KP;              // new Y rows [RMAX][KP] | R^T hi [KP][RMAX]
+  float* S2 = S1 + RMAX * KP;              // new Z rows [RMAX][KP] | R^T lo [KP][RMAX]
   float* gh_g = gscr + (int64_t)i * 2 * k * k;
   float* gl_g = gh_g + (int64_t)k * k;
-  auto own_row = [&](int lr) { return 4 * ((int)r + NC_C * (lr >> 2)) + (lr & 3); };
+  auto own_row = [&](int lr) { return 4 * ((int)r + C * (lr >> 2)) + (lr & 3); };
   cluster_sync_all();  // every CTA of the cluster has started before any remote store
 
   // ---- G: this CTA's rows a and the transposed entries G(b, a), summed over
   // the Gram partials in slot order (error-free FP32), then sym(G) = (G + G^T)/2
-  // in float-float.  Scratch in F2: direct hi, lo and transposed hi, lo.
-  float* Dh = F2;
-  float* Dl = Dh + NC_RMAX * KP;
-  float* Th = Dl + NC_RMAX * KP;
-  float* Tl = Th + NC_RMAX * KP;
+  // in float-float.  Scratch (direct hi, lo; transposed hi, lo) in F0 and F1,
+  // which hold nothing yet.
+  float* Dh = F0;
+  float* Dl = Dh + RMAX * KP;
+  float* Th = Dl + RMAX * KP;
+  float* Tl = Th + RMAX * KP;
   {
     const int s0 = gslot_off[i], s1 = gslot_off[i + 1];
     const int64_t sst = (int64_t)kld * kld;
     const int nq = nt4;
-    const int ndir = nown * 4 * nq, ntr = KP * nown;  // float4 counts (each <= NC_THREADS)
-    // direct: row lr, columns 4j..4j+3; transposed: row b, columns 4 tr..4 tr+3
-    const bool hd = tid < ndir, ht = tid < ntr;
-    const int dlr = hd ? tid / nq : 0, dj = hd ? tid - (tid / nq) * nq : 0;
-    const int ta = own_row(dlr);
-    const int tb = ht ? tid / nown : 0, tl = ht ? tid - (tid / nown) * nown : 0;
-    const int ttr = (int)r + NC_C * tl;
-    const bool dok = hd && ta < k, tok = ht && tb < k;
-    const int64_t doff = (int64_t)ta * kld + 4 * dj, toff = (int64_t)tb * kld + 4 * ttr;
-    float dh[4] = {0.f, 0.f, 0.f, 0.f}, dl[4] = {0.f, 0.f, 0.f, 0.f};
-    float th[4] = {0.f, 0.f, 0.f, 0.f}, tlo[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int q = s0; q < s1; q += 4) {
-      float4 gd[4], gt[4];
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
-        const bool in = q + jj < s1;
-        gd[jj] = (dok && in) ? __ldg(reinterpret_cast<const float4*>(gpart + (q + jj) * sst + doff))
-                             : make_float4(0.f, 0.f, 0.f, 0.f);
-        gt[jj] = (tok && in) ? __ldg(reinterpret_cast<const float4*>(gpart + (q + jj) * sst + toff))
-                             : make_float4(0.f, 0.f, 0.f, 0.f);
+    // direct: own row lr, columns 4j..4j+3; transposed: row b, columns 4 tr..4 tr+3
+    for (int e = tid; e < 2 * nown * 4 * nq; e += NC_THREADS) {
+      const bool dir = e < nown * 4 * nq;
+      const int ee = dir ? e : e - nown * 4 * nq;
+      int lr = 0, j = 0, b = 0, tl = 0;
+      int64_t off;
+      bool ok;
+      if (dir) {
+        lr = ee / nq;
+        j = ee - lr * nq;
+        const int a = own_row(lr);
+        ok = a < k;
+        off = (int64_t)a * kld + 4 * j;
+      } else {
+        b = ee / nown;
+        tl = ee - b * nown;
+        ok = b < k;
+        off = (int64_t)b * kld + 4 * ((int)r + C * tl);
       }
+      float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int q = s0; q < s1; q += 4) {
+        float4 g[4];
 #pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
-        const float xd[4] = {gd[jj].x, gd[jj].y, gd[jj].z, gd[jj].w};
-        const float xt[4] = {gt[jj].x, gt[jj].y, gt[jj].z, gt[jj].w};
+        for (int jj = 0; jj < 4; ++jj)
+          g[jj] = (ok && q + jj < s1) ? __ldg(reinterpret_cast<const float4*>(gpart + (q + jj) * sst + off))
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          float sm, se;
-          two_sum(dh[u], xd[u], sm, se);
-          dh[u] = sm;
-          dl[u] += se;
-          two_sum(th[u], xt[u], sm, se);
-          th[u] = sm;
-          tlo[u] += se;
+        for (int jj = 0; jj < 4; ++jj) {
+          const float x[4] = {g[jj].x, g[jj].y, g[jj].z, g[jj].w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            float sm, se;
+            two_sum(h[u], x[u], sm, se);
+            h[u] = sm;
+            l[u] += se;
+          }
         }
       }
-    }
-    if (hd) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const bool in = dok && 4 * dj + u < k;
         float sm, se;
-        two_sum(dh[u], dl[u], sm, se);
-        Dh[dlr * KP + 4 * dj + u] = in ? sm : 0.f;
-        Dl[dlr * KP + 4 * dj + u] = in ? se : 0.f;
-      }
-    }
-    if (ht) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {  // G(tb, 4 ttr + u) -> transposed entry of own row (tl, u)
-        const bool in = tok && 4 * ttr + u < k;
-        float sm, se;
-        two_sum(th[u], tlo[u], sm, se);
-        Th[(4 * tl + u) * KP + tb] = in ? sm : 0.f;
-        Tl[(4 * tl + u) * KP + tb] = in ? se : 0.f;
+        two_sum(h[u], l[u], sm, se);
+        if (dir) {
+          const bool in = ok && 4 * j + u < k;
+          Dh[lr * KP + 4 * j + u] = in ? sm : 0.f;
+          Dl[lr * KP + 4 * j + u] = in ? se : 0.f;
+        } else {  // G(b, 4 tr + u) -> transposed entry of own row (tl, u)
+          const bool in = ok && 4 * ((int)r + C * tl) + u < k;
+          Th[(4 * tl + u) * KP + b] = in ? sm : 0.f;
+          Tl[(4 * tl + u) * KP + b] = in ? se : 0.f;
+        }
       }
     }
   }
@@ -300,24 +329,24 @@ __global__ void __cluster_dims__(NC_C, 1, 1) __launch_bounds__(NC_THREADS, 1)
     fro = fmaf(h, h, fro);
   }
   __syncthreads();
-  for (int lr = tid >> 5; lr < nown * 4; lr += NC_NW) {  // one warp per own row
-    float s = 0.f;
-    for (int b = tid & 31; b < KP; b += 32) s += fabsf(S1[lr * KP + b]);
+  for (int lr = warp; lr < nown * 4; lr += NC_NW) {  // one warp per own row
+    float sum = 0.f;
+    for (int b = lane; b < KP; b += 32) sum += fabsf(S1[lr * KP + b]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    rowmax = fmaxf(rowmax, s);
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    rowmax = fmaxf(rowmax, sum);
   }
   float unused = 0.f;
   block_sum2_cl(fro, unused, red2);
   rowmax = block_max_cl(rowmax, redf);
   if (tid == 0) {
-    cl_publish(sl_fro, r, fro);
-    cl_publish(sl_inf, r, rowmax);
+    cl_publish<C>(sl_fro, (int)r, fro);
+    cl_publish<C>(sl_inf, (int)r, rowmax);
   }
   cluster_sync_all();
   float fro_t = 0.f, ginf = 0.f;
 #pragma unroll
-  for (int d = 0; d < NC_C; ++d) {
+  for (int d = 0; d < C; ++d) {
     fro_t += sl_fro[d];
     ginf = fmaxf(ginf, sl_inf[d]);
   }
@@ -332,78 +361,73 @@ __global__ void __cluster_dims__(NC_C, 1, 1) __launch_bounds__(NC_THREADS, 1)
     F1[e] = (a == b && a < k) ? 1.f : 0.f;
   }
   __syncthreads();
-  cl_broadcast_rows(S1, F0, KP, r, nown);
+  cl_broadcast_rows<C>(S1, F0, KP, r, nown);
   cluster_sync_all();
 
   float* Y = F0;
   float* Z = F1;
-  const int ntile = nown * nt4;
   int it = 0, extra = -1;
   bool conv = false;
   for (; good_c && it < NS_MAXIT; ++it) {
     // P = Z Y (own rows; Z symmetric, so its own rows are read as columns);
     // T = (3I - P)/2 on the k block, stored transposed in S0; e = max |P - I|
     float emax = 0.f;
-    {
-      constexpr int KS = 4;
-      const int lt = tid / KS / nt4, tc = tid / KS - (tid / KS / nt4) * nt4, q = tid % KS;
-      const bool valid = tid / KS < ntile;
-      const int tr = (int)r + NC_C * lt;
-      float hi[4][4], lo[4][4];
-      cl_tile<KS, false, false>(Z, nullptr, KP, 4 * tr, Y, nullptr, KP, 4 * tc, q, valid, hi, lo);
-      tile_combine<KS, false>(hi, lo);
-      if (valid && q == 0) {
+    cl_product<4, false, false>(Z, nullptr, KP, true, (int)r, C, Y, nullptr, KP, nown, 0, NC_THREADS,
+                                [&](int lt, int tc, float (&hi)[4][4], float (&)[4][4]) {
+                                  const int tr = (int)r + C * lt;
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const int b = 4 * tc + v;
-          float t[4];
+                                  for (int v = 0; v < 4; ++v) {
+                                    const int b = 4 * tc + v;
+                                    float t[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int a = 4 * tr + u;
-            t[u] = 0.f;
-            if (a < k && b < k) {
-              const float d = (a == b) ? 1.f : 0.f;
-              emax = fmaxf(emax, fabsf(hi[u][v] - d));
-              t[u] = 1.5f * d - 0.5f * hi[u][v];
-            }
-          }
-          *reinterpret_cast<float4*>(S0 + b * NC_RMAX + 4 * lt) = make_float4(t[0], t[1], t[2], t[3]);
-        }
-      }
-    }
+                                    for (int u = 0; u < 4; ++u) {
+                                      const int a = 4 * tr + u;
+                                      t[u] = 0.f;
+                                      if (a < k && b < k) {
+                                        const float d = (a == b) ? 1.f : 0.f;
+                                        emax = fmaxf(emax, fabsf(hi[u][v] - d));
+                                        t[u] = 1.5f * d - 0.5f * hi[u][v];
+                                      }
+                                    }
+                                    *reinterpret_cast<float4*>(S0 + b * RMAX + 4 * lt) =
+                                        make_float4(t[0], t[1], t[2], t[3]);
+                                  }
+                                });
+    // the warp's largest |P - I| into every CTA's slots (warp-level, no block barrier)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    if (lane == 0) cl_publish<C>(sl_err, (int)r * NC_NW + warp, emax);
     __syncthreads();
     // T Y and T Z at once, each by half of the block
     {
-      constexpr int KS = 2;
-      const int half = tid / (NC_THREADS / 2), lt0 = tid - half * (NC_THREADS / 2);
-      const int lt = lt0 / KS / nt4, tc = lt0 / KS - (lt0 / KS / nt4) * nt4, q = lt0 % KS;
-      const bool valid = lt0 / KS < ntile;
-      float hi[4][4], lo[4][4];
-      cl_tile<KS, false, false>(S0, nullptr, NC_RMAX, 4 * lt, half ? Z : Y, nullptr, KP, 4 * tc, q, valid, hi, lo);
-      tile_combine<KS, false>(hi, lo);
-      if (valid && q == 0) {
-        float* out = half ? S2 : S1;
+      auto store_rows = [&](float* out) {
+        return [&, out](int lt, int tc, float (&hi)[4][4], float (&)[4][4]) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          *reinterpret_cast<float4*>(out + (4 * lt + u) * KP + 4 * tc) =
-              make_float4(hi[u][0], hi[u][1], hi[u][2], hi[u][3]);
-      }
+          for (int u = 0; u < 4; ++u)
+            *reinterpret_cast<float4*>(out + (4 * lt + u) * KP + 4 * tc) =
+                make_float4(hi[u][0], hi[u][1], hi[u][2], hi[u][3]);
+        };
+      };
+      cl_product<2, false, false>(S0, nullptr, RMAX, false, (int)r, C, Y, nullptr, KP, nown, 0, NC_THREADS / 2,
+                                  store_rows(S1));
+      cl_product<2, false, false>(S0, nullptr, RMAX, false, (int)r, C, Z, nullptr, KP, nown, NC_THREADS / 2,
+                                  NC_THREADS / 2, store_rows(S2));
     }
-    emax = block_max_cl(emax, redf);  // (its barriers also complete S1, S2)
-    if (tid == 0) cl_publish(sl_err, r, emax);
+    __syncthreads();
     cluster_sync_all();  // every CTA has read Y and Z; the errors are published
     float err = 0.f;
+    for (int d = lane; d < C * NC_NW; d += 32) err = fmaxf(err, sl_err[d]);
 #pragma unroll
-    for (int d = 0; d < NC_C; ++d) err = fmaxf(err, sl_err[d]);
-    if (!(err == err)) break;  // non-finite
+    for (int o = 16; o > 0; o >>= 1) err = fmaxf(err, __shfl_xor_sync(0xffffffffu, err, o));
+    if (!(err == err)) break;  // non-finite (the same value in every thread of the cluster)
     if (extra < 0 && err < NS_TOL) extra = 1;
     if (extra == 0) {
       conv = true;
       break;
     }
     if (extra > 0) --extra;
-    cl_broadcast_rows(S1, Y, KP, r, nown);
-    cl_broadcast_rows(S2, Z, KP, r, nown);
+    cl_broadcast_rows<C>(S1, Y, KP, r, nown);
+    cl_broadcast_rows<C>(S2, Z, KP, r, nown);
     cluster_sync_all();
   }
 
@@ -424,44 +448,25 @@ __global__ void __cluster_dims__(NC_C, 1, 1) __launch_bounds__(NC_THREADS, 1)
   }
   __syncthreads();
   {
-    constexpr int KS = 4;
-    const int lt = tid / KS / nt4, tc = tid / KS - (tid / KS / nt4) * nt4, q = tid % KS;
-    const bool valid = tid / KS < ntile;
-    const int tr = (int)r + NC_C * lt;
-    float hi[4][4], lo[4][4];
-    if (comp) {
-      cl_tile<KS, false, true>(Mb, nullptr, KP, 4 * tr, F0, F2, KP, 4 * tc, q, valid, hi, lo);
-      tile_combine<KS, true>(hi, lo);
-    } else {
-      cl_tile<KS, false, false>(Mb, nullptr, KP, 4 * tr, F0, nullptr, KP, 4 * tc, q, valid, hi, lo);
-      tile_combine<KS, false>(hi, lo);
-    }
-    if (valid && q == 0) {
+    auto store_rt = [&](int lt, int tc, float (&hi)[4][4], float (&lo)[4][4]) {
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         const int b = 4 * tc + v;
-        *reinterpret_cast<float4*>(S1 + b * NC_RMAX + 4 * lt) = make_float4(hi[0][v], hi[1][v], hi[2][v], hi[3][v]);
-        *reinterpret_cast<float4*>(S2 + b * NC_RMAX + 4 * lt) =
+        *reinterpret_cast<float4*>(S1 + b * RMAX + 4 * lt) = make_float4(hi[0][v], hi[1][v], hi[2][v], hi[3][v]);
+        *reinterpret_cast<float4*>(S2 + b * RMAX + 4 * lt) =
             comp ? make_float4(lo[0][v], lo[1][v], lo[2][v], lo[3][v]) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
-    }
+    };
+    if (comp)
+      cl_product<4, false, true>(Mb, nullptr, KP, true, (int)r, C, F0, F2, KP, nown, 0, NC_THREADS, store_rt);
+    else
+      cl_product<4, false, false>(Mb, nullptr, KP, true, (int)r, C, F0, nullptr, KP, nown, 0, NC_THREADS, store_rt);
   }
   __syncthreads();
   float e2 = 0.f, corr = 0.f;
   {
-    constexpr int KS = 4;
-    const int lt = tid / KS / nt4, tc = tid / KS - (tid / KS / nt4) * nt4, q = tid % KS;
-    const bool valid = tid / KS < ntile;
-    const int tr = (int)r + NC_C * lt;
-    float hi[4][4], lo[4][4];
-    if (comp) {
-      cl_tile<KS, true, false>(S1, S2, NC_RMAX, 4 * lt, Mb, nullptr, KP, 4 * tc, q, valid, hi, lo);
-      tile_combine<KS, true>(hi, lo);
-    } else {
-      cl_tile<KS, false, false>(S1, nullptr, NC_RMAX, 4 * lt, Mb, nullptr, KP, 4 * tc, q, valid, hi, lo);
-      tile_combine<KS, false>(hi, lo);
-    }
-    if (valid && q == 0) {
+    auto acc_e = [&](int lt, int tc, float (&hi)[4][4], float (&lo)[4][4]) {
+      const int tr = (int)r + C * lt;
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -470,16 +475,20 @@ __global__ void __cluster_dims__(NC_C, 1, 1) __launch_bounds__(NC_THREADS, 1)
           if (a >= k || b >= k) continue;
           const float ev = (hi[u][v] - (a == b ? 1.f : 0.f)) + lo[u][v];
           e2 = fmaf(ev, ev, e2);
-          corr = fmaf(ev, S1[b * NC_RMAX + 4 * lt + u], corr);
+          corr = fmaf(ev, S1[b * RMAX + 4 * lt + u], corr);
         }
-    }
+    };
+    if (comp)
+      cl_product<4, true, false>(S1, S2, RMAX, false, (int)r, C, Mb, nullptr, KP, nown, 0, NC_THREADS, acc_e);
+    else
+      cl_product<4, false, false>(S1, nullptr, RMAX, false, (int)r, C, Mb, nullptr, KP, nown, 0, NC_THREADS, acc_e);
   }
   // tr R over the own rows in float-float (one warp)
   if (tid < 32) {
     float h = 0.f, l = 0.f;
     for (int lr = tid; lr < nown * 4; lr += 32) {
       const int a = own_row(lr);
-      if (a < k) ff_add(h, l, S1[a * NC_RMAX + lr], S2[a * NC_RMAX + lr]);
+      if (a < k) ff_add(h, l, S1[a * RMAX + lr], S2[a * RMAX + lr]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -487,19 +496,19 @@ __global__ void __cluster_dims__(NC_C, 1, 1) __launch_bounds__(NC_THREADS, 1)
       ff_add(h, l, oh, ol);
     }
     if (tid == 0) {
-      cl_publish(sl_th, r, h);
-      cl_publish(sl_tl, r, l);
+      cl_publish<C>(sl_th, (int)r, h);
+      cl_publish<C>(sl_tl, (int)r, l);
     }
   }
   block_sum2_cl(e2, corr, red2);
   if (tid == 0) {
-    cl_publish(sl_e2, r, e2);
-    cl_publish(sl_corr, r, corr);
+    cl_publish<C>(sl_e2, (int)r, e2);
+    cl_publish<C>(sl_corr, (int)r, corr);
   }
   cluster_sync_all();  // the last exchange: no remote access follows
   float e2t = 0.f, corrt = 0.f, th = 0.f, tl = 0.f;
 #pragma unroll
-  for (int d = 0; d < NC_C; ++d) {
+  for (int d = 0; d < C; ++d) {
     e2t += sl_e2[d];
     corrt += sl_corr[d];
     ff_add(th, tl, sl_th[d], sl_tl[d]);
@@ -534,9 +543,10 @@ __global__ void __cluster_dims__(NC_C, 1, 1) __launch_bounds__(NC_THREADS, 1)
     for (int e = tid; e < k * k; e += NC_THREADS) Sigma[e] = SigmaNext[e];
 }
 
-size_t ns_cl_smem_bytes(int k) {
+template <int C>
+size_t ns_cl_smem_bytes(int k, int comp) {
   const int KP = (k + 3) & ~3;
-  return sizeof(float) * (3 * (size_t)KP * KP + 3 * (size_t)NC_RMAX * KP);
+  return sizeof(float) * ((size_t)(2 + (comp ? 1 : 0)) * KP * KP + 3 * (size_t)NcGeom<C>::RMAX * KP);
 }
 
 // ---------------------------------------------------------------- Phi by Cholesky
@@ -831,9 +841,14 @@ size_t phi_solve_smem_bytes(int k) { return sizeof(float) * (2 * (size_t)k * (k 
 bool polar_cl_supported(const Ctx* c) { return c->k > 64 && c->k <= NC_KMAX; }
 
 void prepare_tail_kernels() {
-  cudaFuncSetAttribute(polar_ns_cl_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)ns_cl_smem_bytes(NC_KMAX));
-  cudaFuncSetAttribute(polar_ns_cl_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+  cudaFuncSetAttribute(polar_ns_cl_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)ns_cl_smem_bytes<8>(NC_KMAX, 1));
+  cudaFuncSetAttribute(polar_ns_cl_kernel<8>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       cudaSharedmemCarveoutMaxShared);
+  // four-CTA clusters: up to k = 128 without the third full matrix, k <= 112 with it
+  cudaFuncSetAttribute(polar_ns_cl_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)ns_cl_smem_bytes<4>(NC_KMAX, 0));
+  cudaFuncSetAttribute(polar_ns_cl_kernel<4>, cudaFuncAttributePreferredSharedMemoryCarveout,
                        cudaSharedmemCarveoutMaxShared);
   cudaFuncSetAttribute(phi_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)phi_chol_smem_bytes(KMAX));
@@ -841,12 +856,52 @@ void prepare_tail_kernels() {
                        (int)phi_solve_smem_bytes(KMAX));
 }
 
+namespace {
+
+// Clusters of 8 CTAs run as many subjects at once as the GPU holds such
+// clusters (15 on a 152-SM part with one cluster of this size per 8 SMs of a
+// GPC); with more subjects, clusters of 4 (twice the rows per CTA) take fewer
+// waves when their shared memory fits.  The choice is made once per context
+// from the occupancy calculator.
+int polar_cl_waves(const void* fn, int C, int N, size_t smem) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C, N);
+  cfg.blockDim = dim3(NC_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  int active = 0;
+  if (cudaOccupancyMaxActiveClusters(&active, fn, &cfg) != cudaSuccess || active <= 0) {
+    cudaGetLastError();
+    return -1;
+  }
+  return (N + active - 1) / active;
+}
+
+}  // namespace
+
+void choose_polar_cl(Ctx* c) {
+  const int comp = c->store == SRM_BF16 ? 0 : 1;
+  const size_t sm8 = ns_cl_smem_bytes<8>(c->k, comp), sm4 = ns_cl_smem_bytes<4>(c->k, comp);
+  c->ns_cl_c = 8;
+  if (sm4 <= ns_cl_smem_bytes<4>(NC_KMAX, 0)) {
+    const int w8 = polar_cl_waves(reinterpret_cast<const void*>(polar_ns_cl_kernel<8>), 8, c->N, sm8);
+    const int w4 = polar_cl_waves(reinterpret_cast<const void*>(polar_ns_cl_kernel<4>), 4, c->N, sm4);
+    if (w4 > 0 && (w8 < 0 || w4 < w8)) c->ns_cl_c = 4;
+  }
+}
+
 cudaError_t launch_polar_cl(Ctx* c, double cert, int comp) {
+  const size_t sm8 = ns_cl_smem_bytes<8>(c->k, comp), sm4 = ns_cl_smem_bytes<4>(c->k, comp);
   // sym(G) hi / lo per subject in the G64 buffer (k^2 doubles = 2 k^2 floats),
   // which the eigen-decomposition fallback overwrites only afterwards
-  polar_ns_cl_kernel<<<dim3(NC_C, c->N), NC_THREADS, ns_cl_smem_bytes(c->k), c->stream>>>(
-      c->N, c->k, c->kld, c->T, c->Gpart, c->gslot_off, reinterpret_cast<float*>(c->G64), c->M64, c->M32, c->sqnorm,
-      c->d_v, c->SigmaNext, c->Sigma, c->rho2, c->scal, c->jac_sweeps, c->ns_fb, cert, comp, c->status);
+  float* gscr = reinterpret_cast<float*>(c->G64);
+  if (c->ns_cl_c == 4)
+    polar_ns_cl_kernel<4><<<dim3(4, c->N), NC_THREADS, sm4, c->stream>>>(
+        c->N, c->k, c->kld, c->T, c->Gpart, c->gslot_off, gscr, c->M64, c->M32, c->sqnorm, c->d_v, c->SigmaNext,
+        c->Sigma, c->rho2, c->scal, c->jac_sweeps, c->ns_fb, cert, comp, c->status);
+  else
+    polar_ns_cl_kernel<8><<<dim3(8, c->N), NC_THREADS, sm8, c->stream>>>(
+        c->N, c->k, c->kld, c->T, c->Gpart, c->gslot_off, gscr, c->M64, c->M32, c->sqnorm, c->d_v, c->SigmaNext,
+        c->Sigma, c->rho2, c->scal, c->jac_sweeps, c->ns_fb, cert, comp, c->status);
   return cudaGetLastError();
 }
 

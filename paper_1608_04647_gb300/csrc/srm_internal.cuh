@@ -155,6 +155,7 @@ struct Ctx {
   bool p_from_f = false;      // the current P partials come from the single pass
   bool sig_eig_done = false;  // Sigma_s^new and its eigen-decomposition already ran beside that pass
   bool force_eig_polar = false;  // every polar factor through the eigen-decomposition path
+  int ns_cl_c = 0;  // CTAs per subject of the clustered polar factor (0: not chosen yet)
   float* f_ppart = nullptr;
   ChunkSrc* f_chunk_src = nullptr;
   int* f_chunk_src_off = nullptr;
@@ -264,6 +265,7 @@ bool sigma_eig_supported(const Ctx* c);
 // k_tail.cu: 64 < k <= 128
 bool polar_cl_supported(const Ctx* c);
 void prepare_tail_kernels();
+void choose_polar_cl(Ctx* c);
 cudaError_t launch_polar_cl(Ctx* c, double cert, int comp);
 cudaError_t launch_phi_chol(Ctx* c, const double* sums);
 cudaError_t launch_polar(Ctx* c);

@@ -12,7 +12,7 @@ result, and the log-likelihood trace's monotonicity):
 * the same fits with every certificate failed on purpose, so that all polar
   factors and rho_i^2 come from the eigen-decomposition path (Jacobi + FP64
   refinement) that otherwise serves only the subjects whose certificate fails;
-* Phi = B^-1 Sigma_s from the FP64 Cholesky factor of B = I + rho_0 Sigma_s
+* Phi = B^-1 Sigma_s from the float-float Cholesky factor of B = I + rho_0 Sigma_s
   and ln det B in the log-likelihood (every case; the last one has many
   low-noise subjects, so rho_0 Sigma_s spans several decades, and T / k =
   2.3, so A_i is ill-conditioned enough that FP32 rounding of M_i alone
@@ -21,7 +21,10 @@ result, and the log-likelihood trace's monotonicity):
 * a graph-captured fit equal bit for bit to an eager one.
 
 Shapes: k = 65 (the first k of this path), k = 100 padded to 104 with
-ragged v_i, and k = 128 (the largest), v_i not multiples of the tiles."""
+ragged v_i, and k = 128 (the largest), v_i not multiples of the tiles.  With
+up to 15 subjects each subject takes a cluster of eight CTAs; the 20- and
+24-subject cases take clusters of four where those fit in fewer waves (the
+FP32 store's third matrix fits them up to k = 112)."""
 import numpy as np
 import pytest
 
@@ -34,6 +37,9 @@ CASES = [
     Case("k65", [1000, 1211, 877], 131, 65, 4, seed=51),
     Case("k100-ragged", [2500, 3111, 1999], 400, 100, 4, seed=52, rho2_range=(0.3, 3.0)),
     Case("k128", [2222, 2601], 1000, 128, 3, seed=54),
+    # more subjects than clusters of eight CTAs fit at once: clusters of four
+    Case("k100-20-subjects", [int(x) for x in np.random.default_rng(55).integers(1200, 2000, size=20)], 500, 100, 3,
+         seed=55),
     Case("k128-low-noise", [int(x) for x in np.random.default_rng(53).integers(700, 1300, size=24)], 300, 128, 3,
          seed=53, rho2_range=(0.02, 0.1)),
 ]
