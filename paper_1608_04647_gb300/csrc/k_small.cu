@@ -895,7 +895,7 @@ __global__ void __launch_bounds__(128) dk_rho_kernel(int N, int k, int T, const 
 //     P = Z Y,  T = (3 I - P) / 2,  Y <- Y T,  Z <- T Z,   Y_0 = A, Z_0 = I,
 // converges quadratically to Y = A^1/2, Z = A^-1/2 for a symmetric positive
 // definite A (eigenvalues in (0, 1]); it is the stable, coupled form.  It
-// stops two steps after max |P - I| < NS_TOL; M_0 = Z / sqrt(c).
+// stops one update after max |P - I| < NS_TOL; M_0 = Z / sqrt(c).
 //
 // FP32 arithmetic leaves M_0 with an error of about eps cond(G) in the
 // directions of the small eigenvalues, so each result is certified: with
@@ -1227,6 +1227,12 @@ __global__ void __launch_bounds__(NS_THREADS, MINB) polar_ns_kernel(int N, int k
   int it = 0, extra = -1;
   bool conv = false;
   for (; good_c && it < NS_MAXIT; ++it) {
+    // one update after max |P - I| < NS_TOL the iterates have converged (the
+    // error of P squares per step); the certificate checks the result
+    if (extra == 0) {
+      conv = true;
+      break;
+    }
     sym_mm<4>(Z, Y, Tm, KP, ut, nut, 0, NS_THREADS);  // P = Z Y
     __syncthreads();
     // T = (3I - P) / 2 on the k block (zero elsewhere); e = max |P - I|
@@ -1245,10 +1251,6 @@ __global__ void __launch_bounds__(NS_THREADS, MINB) polar_ns_kernel(int N, int k
     const float err = block_max_ns(emax, redf);
     if (!(err == err)) break;  // non-finite
     if (extra < 0 && err < NS_TOL) extra = 1;
-    if (extra == 0) {
-      conv = true;
-      break;
-    }
     if (extra > 0) --extra;
     // Y T and T Z at once, each by half of the block
     sym_mm<2>(Y, Tm, W, KP, ut, nut, 0, NS_THREADS / 2);

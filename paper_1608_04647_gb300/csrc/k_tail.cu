@@ -18,7 +18,7 @@
 // the iteration on A = G / c,
 //     P = Z Y,  T = (3 I - P) / 2,  Y <- T Y,  Z <- T Z,   Y_0 = A, Z_0 = I,
 // converges to Y = A^1/2, Z = A^-1/2 (all iterates are polynomials in G, so
-// T Y = Y T); it stops two steps after max |P - I| < NS_TOL; M_0 = Z / sqrt(c).
+// T Y = Y T); it stops one update after max |P - I| < NS_TOL; M_0 = Z / sqrt(c).
 // The certificate E = M_0 G M_0 - I bounds the polar factor's error
 // (||A_i (M_0 - G^-1/2)||_F <= ||E||_F to first order); a subject with
 // ||E||_F > cert sqrt(k) goes through the eigen-decomposition path.  For the
@@ -369,6 +369,12 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NC_THREADS, 1)
   int it = 0, extra = -1;
   bool conv = false;
   for (; good_c && it < NS_MAXIT; ++it) {
+    // one update after max |P - I| < NS_TOL the iterates have converged (the
+    // error of P squares per step); the certificate checks the result
+    if (extra == 0) {
+      conv = true;
+      break;
+    }
     // P = Z Y (own rows; Z symmetric, so its own rows are read as columns);
     // T = (3I - P)/2 on the k block, stored transposed in S0; e = max |P - I|
     float emax = 0.f;
@@ -421,10 +427,6 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NC_THREADS, 1)
     for (int o = 16; o > 0; o >>= 1) err = fmaxf(err, __shfl_xor_sync(0xffffffffu, err, o));
     if (!(err == err)) break;  // non-finite (the same value in every thread of the cluster)
     if (extra < 0 && err < NS_TOL) extra = 1;
-    if (extra == 0) {
-      conv = true;
-      break;
-    }
     if (extra > 0) --extra;
     cl_broadcast_rows<C>(S1, Y, KP, r, nown);
     cl_broadcast_rows<C>(S2, Z, KP, r, nown);
@@ -601,7 +603,7 @@ __device__ __forceinline__ void ff_rsqrt(float dh, float dl, float& h, float& l)
 // shared copy), then the trailing lower triangle takes the rank-1 update
 // B_ic -= L_ij L_cj.  L goes to Lh / Ll (column-major), 1 / L_jj to Dh / Dl,
 // and ln det B = sum_j ln d_j is summed in FP64 after the loop.
-constexpr int PC_THREADS = 1024;
+constexpr int PC_THREADS = 512;  // each warp repeats a step's prologue: 16 warps balance it against latency
 
 __global__ void __launch_bounds__(PC_THREADS) phi_chol_kernel(int N, int k, const double* __restrict__ rho2,
                                                               const double* __restrict__ sqnorm,
@@ -744,11 +746,36 @@ __global__ void __launch_bounds__(PS_THREADS) phi_solve_kernel(int k, const floa
   float* dh = Sl + k * ld;    // [k] 1 / L_mm
   float* dl = dh + k;
   const int j = blockIdx.x, tid = threadIdx.x;
-  for (int e = tid; e < k * k; e += PS_THREADS) {
-    const int m = e / k, i = e - m * k;
+  // L from L2 with 16-byte loads (both planes start on 16-byte boundaries),
+  // four per plane in flight per thread; the last k^2 mod 4 elements singly
+  const int n4 = (k * k) / 4;
+  for (int e0 = tid; e0 < n4; e0 += 4 * PS_THREADS) {
+    float4 vh[4], vl[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + u * PS_THREADS;
+      vh[u] = e < n4 ? __ldg(reinterpret_cast<const float4*>(Lh) + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+      vl[u] = e < n4 ? __ldg(reinterpret_cast<const float4*>(Ll) + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + u * PS_THREADS;
+      if (e >= n4) continue;
+      const float hv[4] = {vh[u].x, vh[u].y, vh[u].z, vh[u].w}, lv[4] = {vl[u].x, vl[u].y, vl[u].z, vl[u].w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int f = 4 * e + q, m = f / k, i = f - m * k;
+        const bool low = i >= m;
+        Sh[m * ld + i] = low ? hv[q] : 0.f;
+        Sl[m * ld + i] = low ? lv[q] : 0.f;
+      }
+    }
+  }
+  for (int f = 4 * n4 + tid; f < k * k; f += PS_THREADS) {
+    const int m = f / k, i = f - m * k;
     const bool low = i >= m;
-    Sh[m * ld + i] = low ? Lh[e] : 0.f;
-    Sl[m * ld + i] = low ? Ll[e] : 0.f;
+    Sh[m * ld + i] = low ? Lh[f] : 0.f;
+    Sl[m * ld + i] = low ? Ll[f] : 0.f;
   }
   for (int m = tid; m < k; m += PS_THREADS) {
     dh[m] = Dh[m];
@@ -906,15 +933,17 @@ cudaError_t launch_polar_cl(Ctx* c, double cert, int comp) {
 }
 
 // Phi and ln det(I + rho_0 Sigma_s) from the committed Sigma_s.  The Cholesky
-// factor (hi and lo planes) and its reciprocal diagonal go to the H64 buffer
-// (2 k^2 + 2 k floats of (N + 1) k^2 doubles), which nothing else reads
+// factor (hi and lo planes, each padded to a multiple of 4 floats) and its
+// reciprocal diagonal go to the H64 buffer (at most 2 k^2 + 2 k + 6 floats of
+// (N + 1) k^2 doubles), which nothing else reads
 // between an M-step tail and the next.
 cudaError_t launch_phi_chol(Ctx* c, const double* sums) {
   const int k = c->k;
   if (k > 128) return cudaErrorInvalidValue;
+  const int64_t kk4 = ((int64_t)k * k + 3) & ~(int64_t)3;  // planes on 16-byte boundaries
   float* Lh = reinterpret_cast<float*>(c->H64);
-  float* Ll = Lh + (int64_t)k * k;
-  float* Dh = Ll + (int64_t)k * k;
+  float* Ll = Lh + kk4;
+  float* Dh = Ll + kk4;
   float* Dl = Dh + k;
   phi_chol_kernel<<<1, PC_THREADS, phi_chol_smem_bytes(k), c->stream>>>(
       c->N, k, c->rho2, c->sqnorm, c->d_v, c->Sigma, Lh, Ll, Dh, Dl, c->scal, c->status, (double)c->Vtot, sums);
