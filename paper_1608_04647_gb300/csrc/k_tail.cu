@@ -67,26 +67,26 @@ struct NcGeom {
   static constexpr int RMAX = 4 * TRMAX;
 };
 
-// 4 x 4 tile C[u][v] = sum_m A[m][ac + u] B[m][bc + v] over this lane's share
-// of m (KS adjacent lanes split the inner index in blocks of 4).  A is
-// m-major with leading dimension lda, B row-major with leading dimension KP.
+// 4 x 4 tile C[u][v] = sum_m A[m][ac + u] B[m][bc + v], m < KP, over this
+// lane's share of m: the KS adjacent lanes of a tile take m = q, q + KS, ...,
+// so that they read KS consecutive rows at once; with row strides that are
+// odd multiples of 4 floats those rows start in different bank groups.  A is
+// m-major with leading dimension lda, B row-major with leading dimension ldb.
 // With CA (CB) A (B) carries a low part: the products of the high parts are
 // error-free (hi + lo), the low parts' products are added to lo.
 template <int KS, bool CA, bool CB>
 __device__ __forceinline__ void cl_tile(const float* __restrict__ Ah, const float* __restrict__ Al, int lda, int ac,
-                                        const float* __restrict__ Bh, const float* __restrict__ Bl, int KP, int bc,
-                                        int q, bool valid, float (&hi)[4][4], float (&lo)[4][4]) {
+                                        const float* __restrict__ Bh, const float* __restrict__ Bl, int ldb, int bc,
+                                        int KP, int q, bool valid, float (&hi)[4][4], float (&lo)[4][4]) {
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) hi[u][v] = lo[u][v] = 0.f;
   if (!valid) return;
-  const int KQ = ((KP / 4 + KS - 1) / KS) * 4;
-  const int m0 = q * KQ, m1 = min(KP, m0 + KQ);
-#pragma unroll 2
-  for (int m = m0; m < m1; ++m) {
+#pragma unroll 4
+  for (int m = q; m < KP; m += KS) {
     const float4 a = *reinterpret_cast<const float4*>(Ah + m * lda + ac);
-    const float4 b = *reinterpret_cast<const float4*>(Bh + m * KP + bc);
+    const float4 b = *reinterpret_cast<const float4*>(Bh + m * ldb + bc);
     const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
     if (!CA && !CB) {
 #pragma unroll
@@ -100,7 +100,7 @@ __device__ __forceinline__ void cl_tile(const float* __restrict__ Ah, const floa
         alv[0] = t.x, alv[1] = t.y, alv[2] = t.z, alv[3] = t.w;
       }
       if (CB) {
-        const float4 t = *reinterpret_cast<const float4*>(Bl + m * KP + bc);
+        const float4 t = *reinterpret_cast<const float4*>(Bl + m * ldb + bc);
         blv[0] = t.x, blv[1] = t.y, blv[2] = t.z, blv[3] = t.w;
       }
 #pragma unroll
@@ -164,9 +164,9 @@ __device__ __forceinline__ void cl_publish(float* slots, int idx, float v) {
 }
 
 // Copies this CTA's rows of S (row-major [own row][KP]) into rows 4 tr + u of
-// the full matrix F in every CTA of the cluster.
+// the full matrix F (leading dimension ldf) in every CTA of the cluster.
 template <int C>
-__device__ __forceinline__ void cl_broadcast_rows(const float* __restrict__ S, float* F, int KP, uint32_t r,
+__device__ __forceinline__ void cl_broadcast_rows(const float* __restrict__ S, float* F, int KP, int ldf, uint32_t r,
                                                   int nown) {
   const int nq = KP / 4;
   const int n = nown * 4 * nq;
@@ -174,7 +174,7 @@ __device__ __forceinline__ void cl_broadcast_rows(const float* __restrict__ S, f
     const int lr = e / nq, j = e - lr * nq;
     const int a = 4 * ((int)r + C * (lr >> 2)) + (lr & 3);
     const float4 v = *reinterpret_cast<const float4*>(S + lr * KP + 4 * j);
-    const uint32_t dst = smem_u32(F + a * KP + 4 * j);
+    const uint32_t dst = smem_u32(F + a * ldf + 4 * j);
 #pragma unroll
     for (int d = 0; d < C; ++d) st_cluster_f4(mapa_shared(dst, (uint32_t)d), v);
   }
@@ -185,8 +185,8 @@ __device__ __forceinline__ void cl_broadcast_rows(const float* __restrict__ S, f
 // thread `base`); f(lt, tc, hi, lo) consumes a finished tile (lane q == 0).
 template <int KS, bool CA, bool CB, typename F>
 __device__ __forceinline__ void cl_product(const float* Ah, const float* Al, int lda, bool a_full, int r, int C,
-                                           const float* Bh, const float* Bl, int KP, int nown, int base, int nth,
-                                           F f) {
+                                           const float* Bh, const float* Bl, int ldb, int KP, int nown, int base,
+                                           int nth, F f) {
   const int lt0 = (int)threadIdx.x - base;
   if (lt0 < 0 || lt0 >= nth) return;  // whole warps
   const int nt4 = KP / 4, ntile = nown * nt4, per = nth / KS, q = lt0 % KS;
@@ -196,7 +196,7 @@ __device__ __forceinline__ void cl_product(const float* Ah, const float* Al, int
     const int lt = valid ? t / nt4 : 0, tc = valid ? t - (t / nt4) * nt4 : 0;
     const int ac = a_full ? 4 * (r + C * lt) : 4 * lt;
     float hi[4][4], lo[4][4];
-    cl_tile<KS, CA, CB>(Ah, Al, lda, ac, Bh, Bl, KP, 4 * tc, q, valid, hi, lo);
+    cl_tile<KS, CA, CB>(Ah, Al, lda, ac, Bh, Bl, ldb, 4 * tc, KP, q, valid, hi, lo);
     tile_combine<KS, CA || CB>(hi, lo);
     if (valid && q == 0) f(lt, tc, hi, lo);
   }
@@ -215,6 +215,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NC_THREADS, 1)
                        double* __restrict__ scal, int* __restrict__ iters_out, int* __restrict__ fallback,
                        double cert, int comp, int* status) {
   constexpr int RMAX = NcGeom<C>::RMAX;
+  constexpr int LDT = RMAX + 4;  // transposed own rows: an odd multiple of 4 floats
   extern __shared__ __align__(16) float nc_smem[];
   __shared__ float redf[NC_NW];
   __shared__ float red2[2][NC_NW];
@@ -224,13 +225,14 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NC_THREADS, 1)
   const uint32_t r = cluster_ctarank();
   const int i = blockIdx.y, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int KP = (k + 3) & ~3, KK = KP * KP, nt4 = KP / 4;
+  const int LDZ = KP + ((nt4 & 1) ? 0 : 4);  // Z / M_0 are read by columns: an odd multiple of 4 floats
   const int nown = (nt4 - (int)r + C - 1) / C;  // own tile rows (>= 2 for k > 64)
-  float* F0 = nc_smem;                     // Y (full)   | sym(G) hi (certificate)
-  float* F1 = F0 + KK;                     // Z (full)   | M_0 (full)
-  float* F2 = F1 + KK;                     // (comp)       sym(G) lo (certificate)
-  float* S0 = F1 + (comp ? 2 : 1) * KK;    // T^T: [KP][RMAX] (own rows as columns)
-  float* S1 = S0 + RMAX * KP;              // new Y rows [RMAX][KP] | R^T hi [KP][RMAX]
-  float* S2 = S1 + RMAX * KP;              // new Z rows [RMAX][KP] | R^T lo [KP][RMAX]
+  float* F0 = nc_smem;                     // Y (full)   | sym(G) hi (certificate); read by rows
+  float* F1 = F0 + KK;                     // Z (full)   | M_0 (full); leading dimension LDZ
+  float* F2 = F1 + KP * LDZ;               // (comp)       sym(G) lo (certificate)
+  float* S0 = F2 + (comp ? KK : 0);        // T^T: [KP][LDT] (own rows as columns)
+  float* S1 = S0 + LDT * KP;               // new Y rows [RMAX][KP] | R^T hi [KP][LDT]
+  float* S2 = S1 + LDT * KP;               // new Z rows [RMAX][KP] | R^T lo [KP][LDT]
   float* gh_g = gscr + (int64_t)i * 2 * k * k;
   float* gl_g = gh_g + (int64_t)k * k;
   auto own_row = [&](int lr) { return 4 * ((int)r + C * (lr >> 2)) + (lr & 3); };
@@ -358,10 +360,10 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NC_THREADS, 1)
   for (int e = tid; e < nown * 4 * KP; e += NC_THREADS) S1[e] = (S1[e] + S2[e]) * cinv;
   for (int e = tid; e < KK; e += NC_THREADS) {
     const int a = e / KP, b = e - (e / KP) * KP;
-    F1[e] = (a == b && a < k) ? 1.f : 0.f;
+    F1[a * LDZ + b] = (a == b && a < k) ? 1.f : 0.f;
   }
   __syncthreads();
-  cl_broadcast_rows<C>(S1, F0, KP, r, nown);
+  cl_broadcast_rows<C>(S1, F0, KP, KP, r, nown);
   cluster_sync_all();
 
   float* Y = F0;
@@ -378,7 +380,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NC_THREADS, 1)
     // P = Z Y (own rows; Z symmetric, so its own rows are read as columns);
     // T = (3I - P)/2 on the k block, stored transposed in S0; e = max |P - I|
     float emax = 0.f;
-    cl_product<4, false, false>(Z, nullptr, KP, true, (int)r, C, Y, nullptr, KP, nown, 0, NC_THREADS,
+    cl_product<4, false, false>(Z, nullptr, LDZ, true, (int)r, C, Y, nullptr, KP, KP, nown, 0, NC_THREADS,
                                 [&](int lt, int tc, float (&hi)[4][4], float (&)[4][4]) {
                                   const int tr = (int)r + C * lt;
 #pragma unroll
@@ -395,7 +397,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NC_THREADS, 1)
                                         t[u] = 1.5f * d - 0.5f * hi[u][v];
                                       }
                                     }
-                                    *reinterpret_cast<float4*>(S0 + b * RMAX + 4 * lt) =
+                                    *reinterpret_cast<float4*>(S0 + b * LDT + 4 * lt) =
                                         make_float4(t[0], t[1], t[2], t[3]);
                                   }
                                 });
@@ -414,9 +416,9 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NC_THREADS, 1)
                 make_float4(hi[u][0], hi[u][1], hi[u][2], hi[u][3]);
         };
       };
-      cl_product<2, false, false>(S0, nullptr, RMAX, false, (int)r, C, Y, nullptr, KP, nown, 0, NC_THREADS / 2,
+      cl_product<2, false, false>(S0, nullptr, LDT, false, (int)r, C, Y, nullptr, KP, KP, nown, 0, NC_THREADS / 2,
                                   store_rows(S1));
-      cl_product<2, false, false>(S0, nullptr, RMAX, false, (int)r, C, Z, nullptr, KP, nown, NC_THREADS / 2,
+      cl_product<2, false, false>(S0, nullptr, LDT, false, (int)r, C, Z, nullptr, LDZ, KP, nown, NC_THREADS / 2,
                                   NC_THREADS / 2, store_rows(S2));
     }
     __syncthreads();
@@ -428,8 +430,8 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NC_THREADS, 1)
     if (!(err == err)) break;  // non-finite (the same value in every thread of the cluster)
     if (extra < 0 && err < NS_TOL) extra = 1;
     if (extra > 0) --extra;
-    cl_broadcast_rows<C>(S1, Y, KP, r, nown);
-    cl_broadcast_rows<C>(S2, Z, KP, r, nown);
+    cl_broadcast_rows<C>(S1, Y, KP, KP, r, nown);
+    cl_broadcast_rows<C>(S2, Z, KP, LDZ, r, nown);
     cluster_sync_all();
   }
 
@@ -443,7 +445,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NC_THREADS, 1)
     for (int e = tid; e < KK; e += NC_THREADS) {
       const int a = e / KP, b = e - (e / KP) * KP;
       const bool in = a < k && b < k;
-      Mb[e] *= sc;
+      Mb[a * LDZ + b] *= sc;
       F0[e] = in ? __ldcg(gh_g + a * k + b) : 0.f;
       if (comp) F2[e] = in ? __ldcg(gl_g + a * k + b) : 0.f;
     }
@@ -454,15 +456,16 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NC_THREADS, 1)
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         const int b = 4 * tc + v;
-        *reinterpret_cast<float4*>(S1 + b * RMAX + 4 * lt) = make_float4(hi[0][v], hi[1][v], hi[2][v], hi[3][v]);
-        *reinterpret_cast<float4*>(S2 + b * RMAX + 4 * lt) =
+        *reinterpret_cast<float4*>(S1 + b * LDT + 4 * lt) = make_float4(hi[0][v], hi[1][v], hi[2][v], hi[3][v]);
+        *reinterpret_cast<float4*>(S2 + b * LDT + 4 * lt) =
             comp ? make_float4(lo[0][v], lo[1][v], lo[2][v], lo[3][v]) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     };
     if (comp)
-      cl_product<4, false, true>(Mb, nullptr, KP, true, (int)r, C, F0, F2, KP, nown, 0, NC_THREADS, store_rt);
+      cl_product<4, false, true>(Mb, nullptr, LDZ, true, (int)r, C, F0, F2, KP, KP, nown, 0, NC_THREADS, store_rt);
     else
-      cl_product<4, false, false>(Mb, nullptr, KP, true, (int)r, C, F0, nullptr, KP, nown, 0, NC_THREADS, store_rt);
+      cl_product<4, false, false>(Mb, nullptr, LDZ, true, (int)r, C, F0, nullptr, KP, KP, nown, 0, NC_THREADS,
+                                  store_rt);
   }
   __syncthreads();
   float e2 = 0.f, corr = 0.f;
@@ -477,20 +480,21 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NC_THREADS, 1)
           if (a >= k || b >= k) continue;
           const float ev = (hi[u][v] - (a == b ? 1.f : 0.f)) + lo[u][v];
           e2 = fmaf(ev, ev, e2);
-          corr = fmaf(ev, S1[b * RMAX + 4 * lt + u], corr);
+          corr = fmaf(ev, S1[b * LDT + 4 * lt + u], corr);
         }
     };
     if (comp)
-      cl_product<4, true, false>(S1, S2, RMAX, false, (int)r, C, Mb, nullptr, KP, nown, 0, NC_THREADS, acc_e);
+      cl_product<4, true, false>(S1, S2, LDT, false, (int)r, C, Mb, nullptr, LDZ, KP, nown, 0, NC_THREADS, acc_e);
     else
-      cl_product<4, false, false>(S1, nullptr, RMAX, false, (int)r, C, Mb, nullptr, KP, nown, 0, NC_THREADS, acc_e);
+      cl_product<4, false, false>(S1, nullptr, LDT, false, (int)r, C, Mb, nullptr, LDZ, KP, nown, 0, NC_THREADS,
+                                  acc_e);
   }
   // tr R over the own rows in float-float (one warp)
   if (tid < 32) {
     float h = 0.f, l = 0.f;
     for (int lr = tid; lr < nown * 4; lr += 32) {
       const int a = own_row(lr);
-      if (a < k) ff_add(h, l, S1[a * RMAX + lr], S2[a * RMAX + lr]);
+      if (a < k) ff_add(h, l, S1[a * LDT + lr], S2[a * LDT + lr]);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -536,7 +540,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NC_THREADS, 1)
       const int lr = e / k, b = e - (e / k) * k;
       const int a = own_row(lr);
       if (a >= k) continue;
-      const float m = Mb[a * KP + b];
+      const float m = Mb[a * LDZ + b];
       Mi[a * k + b] = (double)m;
       M32i[a * kld + b] = m;
     }
@@ -547,8 +551,10 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NC_THREADS, 1)
 
 template <int C>
 size_t ns_cl_smem_bytes(int k, int comp) {
-  const int KP = (k + 3) & ~3;
-  return sizeof(float) * ((size_t)(2 + (comp ? 1 : 0)) * KP * KP + 3 * (size_t)NcGeom<C>::RMAX * KP);
+  const int KP = (k + 3) & ~3, nt4 = KP / 4;
+  const int LDZ = KP + ((nt4 & 1) ? 0 : 4);
+  return sizeof(float) * ((size_t)(1 + (comp ? 1 : 0)) * KP * KP + (size_t)KP * LDZ +
+                          3 * (size_t)(NcGeom<C>::RMAX + 4) * KP);
 }
 
 // ---------------------------------------------------------------- Phi by Cholesky
