@@ -115,11 +115,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def workload(config: int, rank: int, subjects: int = 0, voxels_cap: int = 0):
+def workload(config: int, rank: int, subjects: int = 0, voxels_cap: int = 0, k: int = 0):
     """The config's planted spec and voxel counts; with subjects > 0 only the
     first `subjects` subjects, and with voxels_cap > 0 each subject cut to at
     most that many voxels (smaller cases of the same T and k, for
-    profiling)."""
+    profiling); with k > 0 the same shapes with that number of features."""
     import dataclasses
 
     import synth
@@ -132,6 +132,8 @@ def workload(config: int, rank: int, subjects: int = 0, voxels_cap: int = 0):
     if voxels_cap and max(vox) > voxels_cap:
         vox = [min(int(v), int(voxels_cap)) for v in vox]
         spec = dataclasses.replace(spec, name=spec.name + " (voxels capped at %d)" % voxels_cap)
+    if k and k != spec.k:
+        spec = dataclasses.replace(spec, k=int(k), name=spec.name + " (k = %d)" % k)
     return spec, vox
 
 
@@ -273,7 +275,7 @@ def bench_workload(args, config, rank, world, stores, dev, peaks, e2e=True, cpu=
     import paper_1608_04647_gb300 as srm
     from synth.planted_torch import planted_dataset_torch
 
-    spec, vox = workload(config, rank, args.subjects, args.voxels_cap)
+    spec, vox = workload(config, rank, args.subjects, args.voxels_cap, args.k)
     T, k = spec.T, spec.k
     d = planted_dataset_torch(spec, vox, device="cuda", seed_offset=rank)
     stream = torch.cuda.Stream()
@@ -341,7 +343,9 @@ def bench_workload(args, config, rank, world, stores, dev, peaks, e2e=True, cpu=
     single = bool(results[head]["layout"]["single_pass"])
     ms_step = results[head]["ms_per_step"]
     value = world * 1000.0 / ms_step
-    roofline = roofline_of(ks, head, e_bytes, m_bytes, f_bytes, len(vox), config, int(sum(vox)), peaks)
+    # the committed captures are of each workload's own k: none applies to another k
+    roofline = roofline_of(ks, head, e_bytes, m_bytes, f_bytes, len(vox), None if args.k else config, int(sum(vox)),
+                           peaks)
     iter_bytes = f_bytes if single else e_bytes + m_bytes
     kernels_per_step = sum(v["launches"] for v in ks.values()) / args.steps
     clocks = results[head]["clocks"]
@@ -438,7 +442,7 @@ def bench_sharded(args, rank, world, dev, peaks):
     from paper_1608_04647_gb300.shard import fit_sharded, imbalance, shard_subjects
     from synth.planted_torch import planted_dataset_torch
 
-    spec, vox = workload(args.config, rank, args.subjects, args.voxels_cap)
+    spec, vox = workload(args.config, rank, args.subjects, args.voxels_cap, args.k)
     T, k = spec.T, spec.k
     plan = shard_subjects(vox, world)
     mine = plan[rank]
@@ -527,7 +531,7 @@ def run_ours(args, rank, world):
     stores = [args.store] if args.store != "both" else ["bf16", "f32"]
     out = bench_workload(args, args.config, rank, world, stores, dev, peaks)
     extras = [int(x) for x in args.extra_configs.split(",") if x.strip() != ""] \
-        if args.subjects == 0 and args.voxels_cap == 0 else []
+        if args.subjects == 0 and args.voxels_cap == 0 and args.k == 0 else []
     for c in extras:
         if c == args.config:
             continue
@@ -692,7 +696,7 @@ def run_reference(args, rank, world):
     being linear in the voxels."""
     import oracle
     import synth
-    spec, vox = workload(args.config, rank, args.subjects, args.voxels_cap)
+    spec, vox = workload(args.config, rank, args.subjects, args.voxels_cap, args.k)
     rows = sample_rows(vox, spec.T, spec.k, args.ref_step_s)
     dd = synth.planted_dataset(spec, voxel_counts=rows, dtype=np.float64)
     Xh = [oracle.center(x)[0] for x in dd["X"]]
@@ -1009,6 +1013,8 @@ def main():
     ap.add_argument("--tune-cache", default=None, help="plan cache file kept across runs (default: a fresh one)")
     ap.add_argument("--plan", default="", help="launch-plan fields set after tuning, e.g. 'single_pass=0' "
                     "(srm_set_plan; for profiling one form)")
+    ap.add_argument("--k", type=int, default=0, help="the headline workload's shapes with this number of features "
+                    "(a smaller or larger case, for profiling; no extra workloads then)")
     ap.add_argument("--voxels-cap", type=int, default=0, help="cut every subject to at most this many voxels (a "
                     "smaller case of the same T and k, for ncu captures)")
     ap.add_argument("--subjects", type=int, default=0, help="only the first K subjects of the workload (a smaller "
