@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(256) p_reduce_kernel(EReduceArgs ar) {
 #pragma unroll
       for (int w = 0; w < FW; ++w) {
         float hs, he;
-        two_sum(acc[u][w], rinv * z[u][w], hs, he);
+        two_sum(acc[u][w], __fmul_rn(rinv, z[u][w]), hs, he);  // the product rounded on its own, never fused
         acc[u][w] = hs;
         accl[u][w] += he;
       }
@@ -991,7 +991,9 @@ __device__ __forceinline__ void tile_part(const float* __restrict__ A, const flo
       for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          const float p = av[u] * bv[v];
+          // rounded on its own (never fused into the sum below), so that
+          // p + pe is the exact product and two_sum stays error-free
+          const float p = __fmul_rn(av[u], bv[v]);
           const float pe = fmaf(av[u], bv[v], -p);  // exact product error
           float sm, se;
           two_sum(hi[u][v], p, sm, se);

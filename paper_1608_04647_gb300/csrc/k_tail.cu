@@ -180,6 +180,30 @@ __device__ __forceinline__ void cl_broadcast_rows(const float* __restrict__ S, f
   }
 }
 
+// One triangle of the k x k block of a full matrix (leading dimension ld)
+// copied onto the other, pair by pair: from_lower sets F_ab = F_ba (a < b),
+// otherwise F_ba = F_ab.  With T and Y symmetric, (T Y)^T = Y T, so after the
+// exchange the lower triangle of T Y is the upper triangle of Y T: mirrored,
+// it gives the update Y <- Y T of the coupled iteration, and the upper
+// triangle of T Z mirrored gives Z <- T Z, both symmetric as the iteration's
+// exact iterates are.  Every CTA holds the same copy and gets the same
+// result.
+__device__ __forceinline__ void cl_mirror(float* F, int k, int ld, bool from_lower) {
+  const int npair = k * (k - 1) / 2;
+  for (int e = threadIdx.x; e < npair; e += NC_THREADS) {
+    // pair e -> (a, b), a < b: row a holds k - 1 - a pairs
+    int a = (int)((2.f * k - 1.f - sqrtf((2.f * k - 1.f) * (2.f * k - 1.f) - 8.f * e)) * 0.5f);
+    a = max(0, min(a, k - 2));
+    while (a > 0 && a * (2 * k - a - 1) / 2 > e) --a;
+    while ((a + 1) * (2 * k - a - 2) / 2 <= e) ++a;
+    const int b = e - a * (2 * k - a - 1) / 2 + a + 1;
+    if (from_lower)
+      F[a * ld + b] = F[b * ld + a];
+    else
+      F[b * ld + a] = F[a * ld + b];
+  }
+}
+
 // Products of this CTA's tiles: the KS-lane groups walk the own tiles (lt,
 // tc), lt < nown, tc < nt4, in passes of NTH / KS tiles (NTH threads from
 // thread `base`); f(lt, tc, hi, lo) consumes a finished tile (lane q == 0).
@@ -377,30 +401,59 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NC_THREADS, 1)
       conv = true;
       break;
     }
-    // P = Z Y (own rows; Z symmetric, so its own rows are read as columns);
+    // P = Z Y with its upper triangle mirrored (own rows, into S1), one tile
+    // product over the whole block: a tile on or above the diagonal (tc >= tr)
+    // is (Z Y)_ab, a tile below it (Y Z)_ab, and a diagonal tile's lower half
+    // is its own upper half transposed (Y and Z symmetric, so rows are read as
+    // columns).  Element (a, b) of Z Y and element (b, a) of Y Z are the same
+    // products summed in the same order, so P and T = (3I - P)/2 are exactly
+    // symmetric across the CTAs: the symmetric form of the one-CTA kernel.  A
+    // T that is not symmetric does not commute with G and breaks the
+    // invariant Y = G Z / c of the coupled iteration, and the mean
+    // (Z Y + Y Z)/2, though symmetric, diverged on Grams of condition 10^3
+    // where this form converges.
+    {
+      constexpr int KS = 4;
+      const int per = NC_THREADS / KS, q = tid % KS, ntile = nown * nt4;
+      for (int t0 = 0; t0 < ntile; t0 += per) {
+        const int t = t0 + tid / KS;
+        const bool valid = t < ntile;
+        const int lt = valid ? t / nt4 : 0, tc = valid ? t - (t / nt4) * nt4 : 0;
+        const int tr = (int)r + C * lt;
+        const bool upper = tc >= tr;
+        float hi[4][4], lo[4][4];
+        cl_tile<KS, false, false>(upper ? Z : Y, nullptr, upper ? LDZ : KP, 4 * tr, upper ? Y : Z, nullptr,
+                                  upper ? KP : LDZ, 4 * tc, KP, q, valid, hi, lo);
+        tile_combine<KS, false>(hi, lo);
+        if (valid && q == 0) {
+          if (tc == tr) {  // the diagonal tile: lower half from the upper half
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < u; ++v) hi[u][v] = hi[v][u];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            *reinterpret_cast<float4*>(S1 + (4 * lt + u) * KP + 4 * tc) =
+                make_float4(hi[u][0], hi[u][1], hi[u][2], hi[u][3]);
+        }
+      }
+    }
+    __syncthreads();
     // T = (3I - P)/2 on the k block, stored transposed in S0; e = max |P - I|
     float emax = 0.f;
-    cl_product<4, false, false>(Z, nullptr, LDZ, true, (int)r, C, Y, nullptr, KP, KP, nown, 0, NC_THREADS,
-                                [&](int lt, int tc, float (&hi)[4][4], float (&)[4][4]) {
-                                  const int tr = (int)r + C * lt;
-#pragma unroll
-                                  for (int v = 0; v < 4; ++v) {
-                                    const int b = 4 * tc + v;
-                                    float t[4];
-#pragma unroll
-                                    for (int u = 0; u < 4; ++u) {
-                                      const int a = 4 * tr + u;
-                                      t[u] = 0.f;
-                                      if (a < k && b < k) {
-                                        const float d = (a == b) ? 1.f : 0.f;
-                                        emax = fmaxf(emax, fabsf(hi[u][v] - d));
-                                        t[u] = 1.5f * d - 0.5f * hi[u][v];
-                                      }
-                                    }
-                                    *reinterpret_cast<float4*>(S0 + b * LDT + 4 * lt) =
-                                        make_float4(t[0], t[1], t[2], t[3]);
-                                  }
-                                });
+    for (int e = tid; e < nown * 4 * KP; e += NC_THREADS) {
+      const int lr = e / KP, b = e - (e / KP) * KP;
+      const int a = own_row(lr);
+      float t = 0.f;
+      if (a < k && b < k) {
+        const float d = (a == b) ? 1.f : 0.f;
+        const float pab = S1[e];
+        emax = fmaxf(emax, fabsf(pab - d));
+        t = 1.5f * d - 0.5f * pab;
+      }
+      S0[b * LDT + lr] = t;
+    }
     // the warp's largest |P - I| into every CTA's slots (warp-level, no block barrier)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
@@ -433,6 +486,9 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NC_THREADS, 1)
     cl_broadcast_rows<C>(S1, Y, KP, KP, r, nown);
     cl_broadcast_rows<C>(S2, Z, KP, LDZ, r, nown);
     cluster_sync_all();
+    cl_mirror(Y, k, KP, true);    // Y <- Y T
+    cl_mirror(Z, k, LDZ, false);  // Z <- T Z
+    __syncthreads();
   }
 
   // ---- certificate.  M_0 = Z / sqrt(c) (full, in F1); sym(G) hi / lo from
