@@ -603,41 +603,73 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
   ce = cudaMemsetAsync(c->A, 0, (size_t)c->Vpad_tot * c->kld * ael, c->stream);
   if (ce != cudaSuccess) return fail(cuda_fail(ce, "cudaMemsetAsync"));
 
-  // centre the data (host input is streamed through a staging buffer)
+  // centre the data.  Host input is streamed through two staging buffers:
+  // the copies of consecutive subjects alternate between the two side
+  // streams (two transfers in flight), and subject i's centring waits for its
+  // copy while the next copy proceeds; a buffer is refilled only after the
+  // centring that read it.
   const size_t iel = cfg->in_dtype == SRM_BF16 ? 2 : 4;
-  void* stage = nullptr;
+  void* stage[2] = {nullptr, nullptr};
+  cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
   if (cfg->flags & SRM_HOST_INPUT) {
     int64_t vmax = 0;
     for (int i = 0; i < N; ++i) vmax = std::max(vmax, c->v[i]);
-    ce = cudaMalloc(&stage, (size_t)vmax * T * iel);
+    const int nstage = N > 1 ? 2 : 1;
+    for (int b = 0; b < nstage && ce == cudaSuccess; ++b) {
+      ce = cudaMalloc(&stage[b], (size_t)vmax * T * iel);
+      if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&copied[b], cudaEventDisableTiming);
+      if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&consumed[b], cudaEventDisableTiming);
+    }
     if (ce != cudaSuccess) {
       cudaGetLastError();
-      set_error("srm_init: cannot allocate the host-input staging buffer");
+      for (int b = 0; b < 2; ++b) {
+        if (stage[b]) cudaFree(stage[b]);
+        if (copied[b]) cudaEventDestroy(copied[b]);
+        if (consumed[b]) cudaEventDestroy(consumed[b]);
+      }
+      set_error("srm_init: cannot allocate the host-input staging buffers");
       return fail(SRM_ERR_NOMEM);
     }
   }
+  auto free_stages = [&]() {
+    for (int b = 0; b < 2; ++b) {
+      if (stage[b]) cudaFree(stage[b]);
+      if (copied[b]) cudaEventDestroy(copied[b]);
+      if (consumed[b]) cudaEventDestroy(consumed[b]);
+    }
+  };
   // Algorithm 1's random orthogonal W^0 drawn here when the caller gives none
   void* haar_work = nullptr;
   if (!W0_dev && ce == cudaSuccess) {
     ce = cudaMalloc(&haar_work, haar_workspace_bytes(c));
     if (ce != cudaSuccess) {
       cudaGetLastError();
-      if (stage) cudaFree(stage);
+      free_stages();
       set_error("srm_init: cannot allocate the workspace of the random initial mappings");
       return fail(SRM_ERR_NOMEM);
     }
   }
   for (int i = 0; i < N; ++i) {
     const void* src = X[i];
-    if (stage) {
-      ce = cudaMemcpyAsync(stage, X[i], (size_t)c->v[i] * T * iel, cudaMemcpyHostToDevice, c->stream);
+    if (stage[0]) {
+      const int b = stage[1] ? (i & 1) : 0;
+      cudaStream_t cs = b ? c->side2 : c->side;
+      if (i >= (stage[1] ? 2 : 1)) ce = cudaStreamWaitEvent(cs, consumed[b], 0);  // the centring that read it
+      if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(stage[b], X[i], (size_t)c->v[i] * T * iel, cudaMemcpyHostToDevice, cs);
+      if (ce == cudaSuccess) ce = cudaEventRecord(copied[b], cs);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(c->stream, copied[b], 0);
       if (ce != cudaSuccess) break;
-      src = stage;
+      src = stage[b];
     }
     int ev0 = -1;
     if (c->profile) prof_begin(c, KK_CENTER, &ev0);
     ce = launch_center(c, i, src, cfg->in_dtype, T);
     if (ce != cudaSuccess) break;
+    if (stage[0]) {
+      ce = cudaEventRecord(consumed[stage[1] ? (i & 1) : 0], c->stream);
+      if (ce != cudaSuccess) break;
+    }
     if (c->profile) prof_end(c, KK_CENTER, ev0);
     ce = W0_dev ? launch_load_w0(c, i, W0_dev[i]) : launch_haar_w0(c, i, cfg->seed, haar_work);
     if (ce != cudaSuccess) break;
@@ -646,7 +678,11 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
   if (ce == cudaSuccess) ce = launch_init_params(c);
   if (ce == cudaSuccess) ce = launch_phi(c);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
-  if (stage) cudaFree(stage);
+  if (stage[0]) {  // the side streams' copies all precede the last centring
+    cudaStreamSynchronize(c->side);
+    cudaStreamSynchronize(c->side2);
+  }
+  free_stages();
   if (haar_work) cudaFree(haar_work);
   if (ce != cudaSuccess) return fail(cuda_fail(ce, "srm_init: centring / initialisation"));
   cudaFree(c->rowsq);
