@@ -302,7 +302,13 @@ def bench_workload(args, config, rank, world, stores, dev, peaks, e2e=True, cpu=
         return m
 
     results = {}
+    e2e_res = None
     for store in stores:
+        if store != stores[0] and e2e and not args.no_e2e and e2e_res is None:
+            # the end-to-end job of the head store runs before the other store's
+            # contexts come and go (their allocations slow a following setup)
+            e2e_res = run_e2e(args, d, spec, vox, stream, world,
+                              None if args.no_autotune or args.single_pass else cache, stores[0])
         m = make(store)
         lay = m.layout()
         if world > 1:
@@ -397,8 +403,8 @@ def bench_workload(args, config, rank, world, stores, dev, peaks, e2e=True, cpu=
                              "kernels_ms_per_step": {n: round(v["ms"] / args.steps, 4) for n, v in
                                                      r["kernels"].items()}}
     if e2e and not args.no_e2e:
-        out["e2e"] = run_e2e(args, d, spec, vox, stream, world,
-                             None if args.no_autotune or args.single_pass else cache, head)
+        out["e2e"] = e2e_res if e2e_res is not None else run_e2e(
+            args, d, spec, vox, stream, world, None if args.no_autotune or args.single_pass else cache, head)
     if cpu and rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(spec, vox, d, budget_s=args.cpu_budget)
     del d

@@ -181,7 +181,7 @@ __device__ __forceinline__ void cl_broadcast_rows(const float* __restrict__ S, f
 }
 
 // One triangle of the k x k block of a full matrix (leading dimension ld)
-// copied onto the other, pair by pair: from_lower sets F_ab = F_ba (a < b),
+// copied onto the other: from_lower sets F_ab = F_ba (a < b),
 // otherwise F_ba = F_ab.  With T and Y symmetric, (T Y)^T = Y T, so after the
 // exchange the lower triangle of T Y is the upper triangle of Y T: mirrored,
 // it gives the update Y <- Y T of the coupled iteration, and the upper
@@ -189,19 +189,14 @@ __device__ __forceinline__ void cl_broadcast_rows(const float* __restrict__ S, f
 // exact iterates are.  Every CTA holds the same copy and gets the same
 // result.
 __device__ __forceinline__ void cl_mirror(float* F, int k, int ld, bool from_lower) {
-  const int npair = k * (k - 1) / 2;
-  for (int e = threadIdx.x; e < npair; e += NC_THREADS) {
-    // pair e -> (a, b), a < b: row a holds k - 1 - a pairs
-    int a = (int)((2.f * k - 1.f - sqrtf((2.f * k - 1.f) * (2.f * k - 1.f) - 8.f * e)) * 0.5f);
-    a = max(0, min(a, k - 2));
-    while (a > 0 && a * (2 * k - a - 1) / 2 > e) --a;
-    while ((a + 1) * (2 * k - a - 2) / 2 <= e) ++a;
-    const int b = e - a * (2 * k - a - 1) / 2 + a + 1;
-    if (from_lower)
-      F[a * ld + b] = F[b * ld + a];
-    else
-      F[b * ld + a] = F[a * ld + b];
-  }
+  // warps over rows a, lanes over the columns b > a
+  for (int a = threadIdx.x >> 5; a < k - 1; a += NC_NW)
+    for (int b = a + 1 + (threadIdx.x & 31); b < k; b += 32) {
+      if (from_lower)
+        F[a * ld + b] = F[b * ld + a];
+      else
+        F[b * ld + a] = F[a * ld + b];
+    }
 }
 
 // Products of this CTA's tiles: the KS-lane groups walk the own tiles (lt,
