@@ -97,11 +97,12 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / np.abs(b).max())
 
 
+@pytest.mark.parametrize("k", [50, 80], ids=["k50", "k80-phi-by-cholesky"])
 @pytest.mark.parametrize("store", ["f32", "bf16"])
-def test_two_shards_match_one_context_and_oracle(store):
+def test_two_shards_match_one_context_and_oracle(store, k):
     import paper_1608_04647_gb300 as srm
     from gpu_cases import run_gpu
-    case = Case("sharded", [2999, 4100, 3333, 2500, 1800], 333, 50, 6, seed=31)
+    case = Case("sharded", [2999, 4100, 3333, 2500, 1800], 333, k, 6, seed=31)
     d = make_inputs(case)
     sh = _fit_two_shards(d, case.k, case.n_iter, store)
     one = run_gpu(d, case.k, case.n_iter, store=store, final_ll=False)

@@ -110,3 +110,32 @@ def test_graph_equals_eager_k100():
         np.testing.assert_array_equal(x, y)
     a["model"].close()
     b["model"].close()
+
+
+@pytest.mark.parametrize("store", ["f32", "bf16"])
+def test_checkpoint_resume_k100(store):
+    """fit(4) equals fit(2), a checkpoint into a fresh context (which rebuilds
+    Phi by Cholesky from the restored Sigma_s and rho^2) and fit(2), bit for
+    bit."""
+    import torch
+
+    import paper_1608_04647_gb300 as srm
+    case = CASES[1]
+    d, _ = _oracle(case)
+    X = [torch.from_numpy(x).cuda() for x in d["X"]]
+    W0 = [torch.from_numpy(w).cuda() for w in d["W0"]]
+    a = srm.SRM(X, W0, case.k, store=store)
+    ll_a = a.fit(4)
+    w_a = [a.get_w(i).cpu().numpy() for i in range(len(X))]
+    b1 = srm.SRM(X, W0, case.k, store=store)
+    b1.fit(2)
+    st = b1.state()
+    b2 = srm.SRM(X, W0, case.k, store=store)
+    b2.set_state(st)
+    b2.fit(2)
+    np.testing.assert_array_equal(b2.ll(), a.ll())
+    for i in range(len(X)):
+        np.testing.assert_array_equal(b2.get_w(i).cpu().numpy(), w_a[i])
+    assert len(ll_a) == 4
+    for m in (a, b1, b2):
+        m.close()
