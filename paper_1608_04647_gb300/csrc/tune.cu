@@ -310,6 +310,10 @@ srm_status search(Ctx* c, int iters, srm_plan* best_out, float* best_ms_out, Rep
 
   // 3. E-pass reserves (split-v depths), as whole iterations of the two-pass form
   std::vector<int> reserves = {0, 4, 8, 12, 16, 20, 24, 32, tc_default_e_reserve(c)};
+  if (polar_cl_supported(c)) {
+    // the clustered polar factors need C SMs per subject beside the pass
+    for (int r : {48, 64, 80}) reserves.push_back(r);
+  }
   std::sort(reserves.begin(), reserves.end());
   reserves.erase(std::unique(reserves.begin(), reserves.end()), reserves.end());
   float best_it = 1e30f;
