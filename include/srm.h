@@ -318,9 +318,10 @@ typedef struct {
     int32_t f_l2_hints;     /* single-pass L2 eviction hints, bits: 1 = a tile's first read
                                evicts last, 2 = its second read (last use) evicts first,
                                4 = A_i stores evict first */
-    int32_t f_first_stages; /* single pass: 32 KB stages (of 4) of the ring that streams each
-                               tile from HBM for A_i; the rest re-read it for A_i^T X^_i, 1..3;
-                               4 = one shared ring serving both reads in turn */
+    int32_t f_first_stages; /* single pass: stages of the ring that streams each tile from HBM
+                               for A_i; the rest re-read it for A_i^T X^_i.  With f_slots = 0,
+                               32 KB stages of 4: 1..3, or 4 = one shared ring serving both
+                               reads in turn.  With f_slots = 8 or 9, 16 KB slots: 2..f_slots - 2 */
     int32_t f_reserve;      /* SMs the single pass leaves to the Sigma_s chain that runs
                                beside it (the pass runs on the rest, in whole clusters) */
     int32_t m_boxes;        /* M-pass: consecutive 64-column boxes of the same 128 rows of X^
@@ -328,6 +329,10 @@ typedef struct {
     int32_t f_lead;         /* single pass with two rings: tiles the first read of X^ may run
                                ahead of the second (which then finds the tile in L2), 1..4;
                                0 = no limit */
+    int32_t f_slots;        /* single pass, T <= 512 only: 0 = four 32 KB stages and two
+                               A_tile buffers; 8 = eight 16 KB slots and two A_tile buffers;
+                               9 = nine 16 KB slots and one A_tile buffer (the phase-1
+                               epilogue of a tile then waits for phase 2 of the one before) */
 } srm_plan;
 
 /* srm_get_plan -- the plan the context runs.  SRM_ERR_UNSUPPORTED for the plain

@@ -77,6 +77,7 @@ class srm_plan(ctypes.Structure):
         ("f_reserve", ctypes.c_int32),
         ("m_boxes", ctypes.c_int32),
         ("f_lead", ctypes.c_int32),
+        ("f_slots", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:

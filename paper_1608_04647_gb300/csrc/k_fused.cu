@@ -30,8 +30,9 @@
 // Warp roles (256 threads): warp 0 TMA loads of the first-read ring, warp 6
 // those of the second-read ring, warp 1 TMEM owner and phase-1 MMA issue,
 // warp 7 phase-2 MMA issue, warps 2-5 epilogue.  The two rings split the four
-// 32 KB stages (s_h and 4 - s_h), so the HBM stream of phase 1 never waits
-// behind the L2 re-reads and MMAs of phase 2.  With s_h = 4 the original
+// 32 KB stages (s_h and 4 - s_h), or for T <= 512 eight or nine 16 KB slots,
+// so the HBM stream of phase 1 never waits behind the L2 re-reads and MMAs
+// of phase 2.  With s_h = 4 the original
 // schedule runs instead: one ring, warp 0 loading and warp 1 issuing the
 // phases of consecutive tiles in turn (warps 6 and 7 idle).  Every wait is bounded; a CTA that gives up
 // raises the status word and stops issuing work.
@@ -85,11 +86,29 @@ template <int C>
 constexpr int f_gops() {
   return 2;
 }
-template <int C>
-constexpr size_t f_smem_bytes() {
-  return 1024 + (size_t)f_stages<C>() * F_STAGE + f_gops<C>() * F_GOP + 8 * F_ECH + 320;
+// The fine-slot form (one CTA per tile, two rings): the 160 KB of stages and
+// A_tile buffers are cut into ten 16 KB units, nine slots and one A_tile
+// buffer or eight and two.  A first-read slot holds one 64-t box of the tile
+// (128 voxel rows); a second-read slot holds 128 t of 64 voxel rows (two
+// 64 x 64 boxes), half the K of one P block.  The rings can then split the
+// stage memory unevenly: the L2 re-reads wait about as long as the HBM
+// reads, and with one A_tile buffer they can hold 80 KB beside the HBM
+// ring's 64 KB.  The MMAs of every accumulator are those of the 32 KB form,
+// in the same order, so both forms give bitwise equal results.
+constexpr uint32_t F_HBOX = 8192;  // 64 t x 64 voxel rows (BF16)
+constexpr int F_UNITS = 10;        // 16 KB units of the fine form
+template <int C, bool FINE>
+constexpr int f_smax() {  // most stages or slots (barrier arrays)
+  return FINE ? F_UNITS - 1 : f_stages<C>();
 }
-static_assert(f_smem_bytes<1>() <= 232448 && f_smem_bytes<2>() <= 232448, "fused pass shared memory");
+template <int C, bool FINE>
+constexpr size_t f_smem_bytes() {
+  return FINE ? 1024 + (size_t)F_UNITS * F_BOX + 8 * F_ECH + 384
+              : 1024 + (size_t)f_stages<C>() * F_STAGE + f_gops<C>() * F_GOP + 8 * F_ECH + 320;
+}
+static_assert(f_smem_bytes<1, false>() <= 232448 && f_smem_bytes<2, false>() <= 232448 &&
+                  f_smem_bytes<1, true>() <= 232448,
+              "fused pass shared memory");
 
 __device__ __forceinline__ bool warp_wait_f(uint64_t* bar, uint32_t parity, volatile int* abort, int* status) {
   bool ok = mbar_wait(bar, parity, abort, status, ST_TIMEOUT);
@@ -113,15 +132,20 @@ __device__ __forceinline__ bool warp_wait_long(uint64_t* bar, uint32_t parity, v
   return ok && mbar_try_wait(bar, parity);
 }
 
-template <int C>
+template <int C, bool FINE>
 __global__ void __launch_bounds__(FT, 1)
     fpass_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapE,
                  const __grid_constant__ CUtensorMap mapAs, const __grid_constant__ CUtensorMap mapXp,
-                 const SegF* __restrict__ segs, const int* __restrict__ seg_off, int T, int s_h, int lead,
-                 int pf_dist, int hints,
+                 const __grid_constant__ CUtensorMap mapX64, const SegF* __restrict__ segs,
+                 const int* __restrict__ seg_off, int T, int s_h, int lead, int pf_dist, int hints, int ng,
                  float* __restrict__ ppart, float* __restrict__ gpart, int* status) {
-  constexpr int S_N = f_stages<C>();
-  constexpr int NG = f_gops<C>();
+  static_assert(!FINE || C == 1, "the fine-slot form runs one CTA per tile");
+  constexpr int SMAX = f_smax<C, FINE>();
+  constexpr uint32_t SLOT = FINE ? F_BOX : F_STAGE;
+  constexpr int NG_C = f_gops<C>(), SN_C = f_stages<C>();
+  // stages (slots) and A_tile buffers; the fine form takes ng buffers of its ten units
+  const int NG = FINE ? ng : NG_C;
+  const int S_N = FINE ? F_UNITS - ng : SN_C;
   constexpr uint32_t IDESC_KM = idesc_bf16(128, 64, false, false);  // phase 1: both K-major
   constexpr uint32_t IDESC_MN = idesc_bf16(128, 64, true, true);    // phase 2 and Gram: both MN-major
   constexpr uint32_t TMEM_COLS = 512;
@@ -133,11 +157,11 @@ __global__ void __launch_bounds__(FT, 1)
   // the A_tile buffers and the 16 KB after them are consecutive: the Gram
   // MMA reads M = 128 "features" from a tile and the 16 KB that follow it;
   // rows 64..127 of its accumulator are never read.
-  uint8_t* gop = smem + S_N * F_STAGE;
+  uint8_t* gop = smem + S_N * SLOT;
   uint8_t* eres = gop + NG * F_GOP;                        // E[S] chunks of this CTA's T-block
   uint64_t* full = reinterpret_cast<uint64_t*>(eres + 8 * F_ECH);
-  uint64_t* empty = full + S_N;
-  uint64_t* acc_full = empty + S_N;    // [2] phase-1 accumulators
+  uint64_t* empty = full + SMAX;
+  uint64_t* acc_full = empty + SMAX;   // [2] phase-1 accumulators
   uint64_t* acc_empty = acc_full + 2;  // [2]
   uint64_t* gop_full = acc_empty + 2;  // [2] A_tile complete in this CTA's copy
   uint64_t* gop_free = gop_full + 2;   // [2] phase 2 of every CTA of the cluster is done with it
@@ -162,8 +186,11 @@ __global__ void __launch_bounds__(FT, 1)
   const int g0 = seg_off[pair], g1 = seg_off[pair + 1];
   const int t0 = F_TB * (int)rank;
   const int nk2 = min(4, (min(T, t0 + F_TB) - t0 + 127) / 128);  // 128-t stages per tile and phase
-  // s_h = S_N: the shared-ring schedule (warps 6 and 7 idle); otherwise two rings
-  const bool shared = s_h >= S_N;
+  // s_h = S_N: the shared-ring schedule (warps 6 and 7 idle); otherwise two
+  // rings (always in the fine form)
+  const bool shared = !FINE && s_h >= S_N;
+  // loads per tile and ring: 128-t stages, or 16 KB slots in the fine form
+  const int nld = FINE ? 2 * nk2 : nk2;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S_N; ++s) {
@@ -213,8 +240,8 @@ __global__ void __launch_bounds__(FT, 1)
     if (lane == 0) {
       int s = 0;
       uint32_t ph = 0;
-      int issued[S_N] = {};
-      uint32_t iss_ph[S_N] = {};
+      int issued[SMAX] = {};
+      uint32_t iss_ph[SMAX] = {};
       bool ok = true;
       if (g0 < g1) {
         mbar_arrive_expect_tx(e_full, (uint32_t)(2 * nk2) * F_ECH);
@@ -382,8 +409,8 @@ __global__ void __launch_bounds__(FT, 1)
       const int sbase = first ? 0 : s_h;
       int s = 0;
       uint32_t ph = 0;
-      int issued[S_N];
-      uint32_t iss_ph[S_N];
+      int issued[SMAX];
+      uint32_t iss_ph[SMAX];
       for (int q = 0; q < S_N; ++q) {
         issued[q] = 0;
         iss_ph[q] = 0;
@@ -421,16 +448,26 @@ __global__ void __launch_bounds__(FT, 1)
               break;
             }
           }
-          for (int j = 0; j < nk2; ++j) {
+          for (int j = 0; j < nld; ++j) {
             const int si = sbase + s;
             if (!mbar_wait(&empty[si], ph ^ 1u, abort_s, status, ST_TIMEOUT)) {
               ok = false;
               break;
             }
-            uint8_t* st = smem + si * F_STAGE;
-            mbar_arrive_expect_tx(&full[si], F_STAGE);
-            tma_load_2d_hint(st, &mapX, t0 + 128 * j, (int)(tile * 128), &full[si], pol);
-            tma_load_2d_hint(st + F_BOX, &mapX, t0 + 128 * j + 64, (int)(tile * 128), &full[si], pol);
+            uint8_t* st = smem + si * SLOT;
+            mbar_arrive_expect_tx(&full[si], SLOT);
+            if (FINE && first) {
+              // 64-t box j of the tile
+              tma_load_2d_hint(st, &mapX, t0 + 64 * j, (int)(tile * 128), &full[si], pol);
+            } else if (FINE) {
+              // P block j / 2 (128 t), voxel rows [64 (j % 2), 64 (j % 2) + 64) of the tile
+              const int tt = t0 + 128 * (j >> 1), rr = (int)(tile * 128) + 64 * (j & 1);
+              tma_load_2d_hint(st, &mapX64, tt, rr, &full[si], pol);
+              tma_load_2d_hint(st + F_HBOX, &mapX64, tt + 64, rr, &full[si], pol);
+            } else {
+              tma_load_2d_hint(st, &mapX, t0 + 128 * j, (int)(tile * 128), &full[si], pol);
+              tma_load_2d_hint(st + F_BOX, &mapX, t0 + 128 * j + 64, (int)(tile * 128), &full[si], pol);
+            }
             issued[si] = 1;
             iss_ph[si] = ph;
             if (++s == nst) {
@@ -467,21 +504,30 @@ __global__ void __launch_bounds__(FT, 1)
           ae_ph[b] ^= 1u;
           tc_fence_after();
           const uint32_t dacc = tmem + (uint32_t)b * 64u;
-          for (int j = 0; j < nk2; ++j) {
+          for (int j = 0; j < nld; ++j) {
             if (!mbar_wait(&full[s], ph, abort_s, status, ST_TIMEOUT)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            const uint32_t xs = smem_u32(smem + s * F_STAGE);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const uint32_t xb = xs + h * F_BOX;
-              const uint32_t eb = smem_u32(eres + (2 * j + h) * F_ECH);
+            const uint32_t xs = smem_u32(smem + s * SLOT);
+            if (FINE) {
+              // one 64-t box against E[S] chunk j
+              const uint32_t eb = smem_u32(eres + j * F_ECH);
 #pragma unroll
               for (int kk = 0; kk < 4; ++kk)
-                mma_bf16(dacc, sdesc_sw128(xb + 32 * kk, 16, 1024), sdesc_sw128(eb + 32 * kk, 16, 1024), IDESC_KM,
-                         (j | h | kk) ? 1u : 0u);
+                mma_bf16(dacc, sdesc_sw128(xs + 32 * kk, 16, 1024), sdesc_sw128(eb + 32 * kk, 16, 1024), IDESC_KM,
+                         (j | kk) ? 1u : 0u);
+            } else {
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const uint32_t xb = xs + h * F_BOX;
+                const uint32_t eb = smem_u32(eres + (2 * j + h) * F_ECH);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                  mma_bf16(dacc, sdesc_sw128(xb + 32 * kk, 16, 1024), sdesc_sw128(eb + 32 * kk, 16, 1024),
+                           IDESC_KM, (j | h | kk) ? 1u : 0u);
+              }
             }
             mma_commit(&empty[s]);
             if (++s == s_h) {
@@ -532,18 +578,29 @@ __global__ void __launch_bounds__(FT, 1)
             const uint64_t d = sdesc_sw128(ga + (uint32_t)(rank * JG + j) * 2048u, F_GOP, 1024);
             mma_bf16(tmem + T_GRAM, d, d, IDESC_MN, (first && j == 0) ? 0u : 1u);
           }
-          for (int m = 0; m < nk2; ++m) {
+          for (int m = 0; m < nld; ++m) {
             const int si = s_h + s;
             if (!mbar_wait(&full[si], ph, abort_s, status, ST_TIMEOUT)) {
               ok = false;
               break;
             }
             tc_fence_after();
-            const uint32_t xs = smem_u32(smem + si * F_STAGE);
+            const uint32_t xs = smem_u32(smem + si * SLOT);
+            if (FINE) {
+              // P block m / 2 over voxel rows [64 h, 64 h + 64): four 16-row K steps
+              const int h = m & 1;
+              const uint32_t dp = tmem + T_P + (uint32_t)(m >> 1) * 64u;
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-              mma_bf16(tmem + T_P + (uint32_t)m * 64u, sdesc_sw128(xs + j * 2048, F_BOX, 1024),
-                       sdesc_sw128(ga + j * 2048, F_GOP, 1024), IDESC_MN, (first && j == 0) ? 0u : 1u);
+              for (int j = 0; j < 4; ++j)
+                mma_bf16(dp, sdesc_sw128(xs + j * 2048, F_HBOX, 1024),
+                         sdesc_sw128(ga + (uint32_t)(4 * h + j) * 2048u, F_GOP, 1024), IDESC_MN,
+                         (first && h == 0 && j == 0) ? 0u : 1u);
+            } else {
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                mma_bf16(tmem + T_P + (uint32_t)m * 64u, sdesc_sw128(xs + j * 2048, F_BOX, 1024),
+                         sdesc_sw128(ga + j * 2048, F_GOP, 1024), IDESC_MN, (first && j == 0) ? 0u : 1u);
+            }
             mma_commit(&empty[si]);
             if (++s == nst) {
               s = 0;
@@ -796,7 +853,7 @@ bool bf16_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, 
 }
 
 struct FState {
-  CUtensorMap mapX, mapE, mapAs, mapXp;
+  CUtensorMap mapX, mapE, mapAs, mapXp, mapX64;
   SegF* d_seg = nullptr;
   int* d_seg_off = nullptr;
   int C = 1, clusters = 0;
@@ -804,6 +861,7 @@ struct FState {
   int hints = F_HINTS;
   int s_h = F_SH;  // stages of the first-read ring (the second-read ring has the rest)
   int lead = 0;    // tiles the first read may run ahead of phase 2 (0: no limit; two rings only)
+  int slots = 0;   // 0: four 32 KB stages; 8 or 9: 16 KB slots (and 2 or 1 A_tile buffers)
   // Gram slots of the two forms; the context points at the active form's
   float* f_gpart = nullptr;
   int* f_gslot_off = nullptr;
@@ -848,11 +906,11 @@ int fused_clusters(Ctx* c, int C, int reserve) {
     at[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(2 * clusters);
     cfg.blockDim = dim3(FT);
-    cfg.dynamicSmemBytes = f_smem_bytes<2>();
+    cfg.dynamicSmemBytes = f_smem_bytes<2, false>();
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int mc = 0;
-    if (cudaOccupancyMaxActiveClusters(&mc, fpass_kernel<2>, &cfg) == cudaSuccess && mc > 0)
+    if (cudaOccupancyMaxActiveClusters(&mc, fpass_kernel<2, false>, &cfg) == cudaSuccess && mc > 0)
       clusters = std::min(clusters, mc);
     cudaGetLastError();
   }
@@ -958,16 +1016,23 @@ srm_status fused_setup(Ctx* c) {
   c->fs = f;
   const int C = c->T > F_TB ? 2 : 1;
   f->C = C;
-  if (C == 2)
-    cudaFuncSetAttribute(fpass_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f_smem_bytes<2>());
-  else
-    cudaFuncSetAttribute(fpass_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f_smem_bytes<1>());
+  if (C == 2) {
+    cudaFuncSetAttribute(fpass_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)f_smem_bytes<2, false>());
+  } else {
+    cudaFuncSetAttribute(fpass_kernel<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)f_smem_bytes<1, false>());
+    cudaFuncSetAttribute(fpass_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)f_smem_bytes<1, true>());
+  }
   f->s_h = F_SH;
   bool ok = bf16_map(&f->mapX, c->Xh, c->T, c->Vpad_tot, (uint64_t)c->ldT * 2, 64, 128) &&
             bf16_map(&f->mapE, c->ESb, c->T, 64, (uint64_t)c->ldT * 2, 64, 64) &&
             bf16_map(&f->mapAs, c->A, 64, c->Vpad_tot, 64 * 2, 64, 128 / C) &&
             // L2 prefetch only (never lands in shared memory): 256 t x 128 rows per box
-            bf16_map(&f->mapXp, c->Xh, c->T, c->Vpad_tot, (uint64_t)c->ldT * 2, 256, 128, false);
+            bf16_map(&f->mapXp, c->Xh, c->T, c->Vpad_tot, (uint64_t)c->ldT * 2, 256, 128, false) &&
+            // second-read slots of the fine form: 64 t x 64 rows per box
+            bf16_map(&f->mapX64, c->Xh, c->T, c->Vpad_tot, (uint64_t)c->ldT * 2, 64, 64);
   if (!ok) {
     set_error("cuTensorMapEncodeTiled failed for the single-pass form");
     return SRM_ERR_CUDA;
@@ -1031,6 +1096,11 @@ int fused_get_pf(const Ctx* c) { return c->fs ? static_cast<const FState*>(c->fs
 int fused_get_hints(const Ctx* c) { return c->fs ? static_cast<const FState*>(c->fs)->hints : F_HINTS; }
 int fused_get_first_stages(const Ctx* c) { return c->fs ? static_cast<const FState*>(c->fs)->s_h : F_SH; }
 int fused_get_lead(const Ctx* c) { return c->fs ? static_cast<const FState*>(c->fs)->lead : 0; }
+int fused_get_slots(const Ctx* c) { return c->fs ? static_cast<const FState*>(c->fs)->slots : 0; }
+bool fused_fine_supported(const Ctx* c) { return fused_supported(c) && c->T <= F_TB; }
+void fused_set_slots(Ctx* c, int slots) {
+  if (c->fs) static_cast<FState*>(c->fs)->slots = slots;
+}
 void fused_set_lead(Ctx* c, int lead) {
   if (c->fs) static_cast<FState*>(c->fs)->lead = lead;
 }
@@ -1061,9 +1131,16 @@ void fused_destroy(Ctx* c) {
 cudaError_t launch_fpass(Ctx* c) {
   auto* f = static_cast<FState*>(c->fs);
   if (!f) return cudaErrorInvalidValue;
+  if (f->C == 1 && f->slots) {
+    fpass_kernel<1, true><<<f->clusters, FT, f_smem_bytes<1, true>(), c->stream>>>(
+        f->mapX, f->mapE, f->mapAs, f->mapXp, f->mapX64, f->d_seg, f->d_seg_off, c->T, f->s_h, f->lead, f->pf,
+        f->hints, F_UNITS - f->slots, c->f_ppart, c->Gpart, c->status);
+    return cudaGetLastError();
+  }
   if (f->C == 1) {
-    fpass_kernel<1><<<f->clusters, FT, f_smem_bytes<1>(), c->stream>>>(
-        f->mapX, f->mapE, f->mapAs, f->mapXp, f->d_seg, f->d_seg_off, c->T, f->s_h, f->lead, f->pf, f->hints, c->f_ppart, c->Gpart, c->status);
+    fpass_kernel<1, false><<<f->clusters, FT, f_smem_bytes<1, false>(), c->stream>>>(
+        f->mapX, f->mapE, f->mapAs, f->mapXp, f->mapX64, f->d_seg, f->d_seg_off, c->T, f->s_h, f->lead, f->pf,
+        f->hints, f_gops<1>(), c->f_ppart, c->Gpart, c->status);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
@@ -1074,12 +1151,13 @@ cudaError_t launch_fpass(Ctx* c) {
   at[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(2 * f->clusters);
   cfg.blockDim = dim3(FT);
-  cfg.dynamicSmemBytes = f_smem_bytes<2>();
+  cfg.dynamicSmemBytes = f_smem_bytes<2, false>();
   cfg.stream = c->stream;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, fpass_kernel<2>, f->mapX, f->mapE, f->mapAs, f->mapXp, (const SegF*)f->d_seg,
-                            (const int*)f->d_seg_off, c->T, f->s_h, f->lead, f->pf, f->hints, c->f_ppart, c->Gpart, c->status);
+  return cudaLaunchKernelEx(&cfg, fpass_kernel<2, false>, f->mapX, f->mapE, f->mapAs, f->mapXp, f->mapX64,
+                            (const SegF*)f->d_seg, (const int*)f->d_seg_off, c->T, f->s_h, f->lead, f->pf, f->hints,
+                            f_gops<2>(), c->f_ppart, c->Gpart, c->status);
 }
 
 }  // namespace srm

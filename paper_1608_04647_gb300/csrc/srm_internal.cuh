@@ -302,6 +302,9 @@ int fused_get_first_stages(const Ctx* c);  // stages of the single pass's first-
 void fused_set_first_stages(Ctx* c, int s_h);
 int fused_get_lead(const Ctx* c);          // tiles the first read may lead phase 2 (0: no limit)
 void fused_set_lead(Ctx* c, int lead);
+int fused_get_slots(const Ctx* c);         // 0: four 32 KB stages; 8 or 9: 16 KB slots
+void fused_set_slots(Ctx* c, int slots);
+bool fused_fine_supported(const Ctx* c);   // the 16 KB-slot form (one CTA per tile: T <= 512)
 int fused_get_reserve(const Ctx* c);       // SMs the single pass leaves to the Sigma_s chain beside it
 srm_status fused_set_reserve(Ctx* c, int reserve);  // rebuilds the pass's schedule
 cudaError_t launch_fpass(Ctx* c);

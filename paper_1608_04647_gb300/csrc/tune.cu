@@ -44,18 +44,25 @@ srm_plan current_plan(const Ctx* c) {
   p.f_first_stages = fused_get_first_stages(c);
   p.f_reserve = fused_get_reserve(c);
   p.f_lead = fused_get_lead(c);
+  p.f_slots = fused_get_slots(c);
   return p;
 }
 
 srm_status apply_plan(Ctx* c, const srm_plan& p) {
+  const bool fine = p.f_slots != 0;
   if ((p.single_pass != 0 && p.single_pass != 1) || p.f_prefetch < 0 || p.f_prefetch > 16 || p.f_l2_hints < 0 ||
-      p.f_l2_hints > 7 || p.f_first_stages < 1 || p.f_first_stages > 4 || p.f_lead < 0 || p.f_lead > 4) {
+      p.f_l2_hints > 7 || (fine && p.f_slots != 8 && p.f_slots != 9) || p.f_first_stages < (fine ? 2 : 1) ||
+      p.f_first_stages > (fine ? p.f_slots - 2 : 4) || p.f_lead < 0 || p.f_lead > 4) {
     set_error("srm_set_plan: field out of range (single_pass 0/1, f_prefetch 0-16, f_l2_hints 0-7, "
-              "f_first_stages 1-4, f_lead 0-4)");
+              "f_slots 0/8/9, f_first_stages 1-4 with f_slots 0 or 2..f_slots-2, f_lead 0-4)");
     return SRM_ERR_ARG;
   }
   if (p.single_pass && !fused_supported(c)) {
     set_error("srm_set_plan: the single-pass form needs k <= 64 and T <= 1024");
+    return SRM_ERR_UNSUPPORTED;
+  }
+  if (fine && !fused_fine_supported(c)) {
+    set_error("srm_set_plan: f_slots 8 or 9 needs the single-pass form's one-CTA tiles (k <= 64, T <= 512)");
     return SRM_ERR_UNSUPPORTED;
   }
   // a pending M-step tail reads the Gram slots of the form that produced them
@@ -83,6 +90,7 @@ srm_status apply_plan(Ctx* c, const srm_plan& p) {
     fused_set_hints(c, p.f_l2_hints);
     fused_set_first_stages(c, p.f_first_stages);
     fused_set_lead(c, p.f_lead);
+    fused_set_slots(c, p.f_slots);
     if (!p.single_pass) c->p_from_f = false;  // the next E-step streams X^ again
     fused_select(c, p.single_pass != 0);
   }
@@ -141,9 +149,10 @@ std::string signature(const Ctx* c) {
 
 std::string plan_line(const std::string& sig, const srm_plan& p, double ms) {
   char buf[320];
-  snprintf(buf, sizeof buf, "%s sp=%d er=%d mst=%d mgb=%d mres=%d mpf=%d mbx=%d fpf=%d fl2=%d fsh=%d fr=%d fld=%d ms=%.6f",
+  snprintf(buf, sizeof buf,
+           "%s sp=%d er=%d mst=%d mgb=%d mres=%d mpf=%d mbx=%d fpf=%d fl2=%d fsh=%d fr=%d fld=%d fsl=%d ms=%.6f",
            sig.c_str(), p.single_pass, p.e_reserve, p.m_stages, p.m_gram_bufs, p.m_resident_es, p.m_prefetch,
-           p.m_boxes, p.f_prefetch, p.f_l2_hints, p.f_first_stages, p.f_reserve, p.f_lead, ms);
+           p.m_boxes, p.f_prefetch, p.f_l2_hints, p.f_first_stages, p.f_reserve, p.f_lead, p.f_slots, ms);
   return buf;
 }
 
@@ -152,9 +161,10 @@ bool parse_line(const std::string& line, const std::string& sig, srm_plan* p, do
   srm_plan q{};
   double t = 0;
   if (sscanf(line.c_str() + sig.size(),
-             " sp=%d er=%d mst=%d mgb=%d mres=%d mpf=%d mbx=%d fpf=%d fl2=%d fsh=%d fr=%d fld=%d ms=%lf",
+             " sp=%d er=%d mst=%d mgb=%d mres=%d mpf=%d mbx=%d fpf=%d fl2=%d fsh=%d fr=%d fld=%d fsl=%d ms=%lf",
              &q.single_pass, &q.e_reserve, &q.m_stages, &q.m_gram_bufs, &q.m_resident_es, &q.m_prefetch,
-             &q.m_boxes, &q.f_prefetch, &q.f_l2_hints, &q.f_first_stages, &q.f_reserve, &q.f_lead, &t) != 13)
+             &q.m_boxes, &q.f_prefetch, &q.f_l2_hints, &q.f_first_stages, &q.f_reserve, &q.f_lead, &q.f_slots,
+             &t) != 14)
     return false;
   *p = q;
   *ms = t;
@@ -234,9 +244,10 @@ struct Report {
   void add(const char* stage, const srm_plan& p, float ms, const char* unit) {
     char buf[200];
     snprintf(buf, sizeof buf,
-             "%-6s sp=%d er=%-3d mst=%d mgb=%d mres=%d mpf=%-2d mbx=%d fpf=%d fl2=%d fsh=%d fr=%-2d fld=%d  %9.4f %s\n",
+             "%-6s sp=%d er=%-3d mst=%d mgb=%d mres=%d mpf=%-2d mbx=%d fpf=%d fl2=%d fsh=%d fr=%-2d fld=%d fsl=%d"
+             "  %9.4f %s\n",
              stage, p.single_pass, p.e_reserve, p.m_stages, p.m_gram_bufs, p.m_resident_es, p.m_prefetch,
-             p.m_boxes, p.f_prefetch, p.f_l2_hints, p.f_first_stages, p.f_reserve, p.f_lead, ms, unit);
+             p.m_boxes, p.f_prefetch, p.f_l2_hints, p.f_first_stages, p.f_reserve, p.f_lead, p.f_slots, ms, unit);
     os << buf;
   }
 };
@@ -283,28 +294,45 @@ srm_status search(Ctx* c, int iters, srm_plan* best_out, float* best_ms_out, Rep
     TTRY(apply_plan(c, bf));
     float best_f = 1e30f;
     srm_plan bfp = bf;
+    // 32 KB stages (every pipeline), then the 16 KB-slot forms (T <= 512),
+    // whose rings split the stage memory more finely (on the forrest-1024-like
+    // workload the L2 re-reads wanted more than half of it); L2 prefetch never
+    // helped the 32 KB form, so the slot forms run without it
+    struct FCand {
+      int slots, sh, lead, hints, pf;
+    };
+    std::vector<FCand> cands;
     for (int sh : {1, 2, 3, 4})
       for (int lead : {0, 3})
         for (int hints : {0, 7})
-          for (int pf : {0, 1}) {
-        if (sh == 4 && lead != 0) continue;  // the shared ring keeps a lead of one tile by construction
-        fused_set_pf(c, pf);
-        fused_set_hints(c, hints);
-        fused_set_first_stages(c, sh);
-        fused_set_lead(c, lead);
-        float ms = 0;
-        TTRY(time_launches(c, launch_fpass, 3, e0, e1, &ms));
-        srm_plan p = bf;
-        p.f_prefetch = pf;
-        p.f_l2_hints = hints;
-        p.f_first_stages = sh;
-        p.f_lead = lead;
-        rep.add("fpass", p, ms, "ms/launch");
-        if (ms < best_f) {
-          best_f = ms;
-          bfp = p;
-        }
+          for (int pf : {0, 1})
+            if (sh != 4 || lead == 0)  // the shared ring keeps a lead of one tile by construction
+              cands.push_back({0, sh, lead, hints, pf});
+    if (fused_fine_supported(c))
+      for (int slots : {8, 9})
+        for (int sh = 3; sh <= 5; ++sh)
+          for (int lead : {0, 3})
+            for (int hints : {0, 7}) cands.push_back({slots, sh, lead, hints, 0});
+    for (const FCand& fc : cands) {
+      fused_set_pf(c, fc.pf);
+      fused_set_hints(c, fc.hints);
+      fused_set_first_stages(c, fc.sh);
+      fused_set_lead(c, fc.lead);
+      fused_set_slots(c, fc.slots);
+      float ms = 0;
+      TTRY(time_launches(c, launch_fpass, 3, e0, e1, &ms));
+      srm_plan p = bf;
+      p.f_prefetch = fc.pf;
+      p.f_l2_hints = fc.hints;
+      p.f_first_stages = fc.sh;
+      p.f_lead = fc.lead;
+      p.f_slots = fc.slots;
+      rep.add("fpass", p, ms, "ms/launch");
+      if (ms < best_f) {
+        best_f = ms;
+        bfp = p;
       }
+    }
     bf = bfp;
   }
 

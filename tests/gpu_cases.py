@@ -36,7 +36,7 @@ def run_oracle(d, n_iter, final_ll=True):
 
 
 def run_gpu(d, k, n_iter, store="f32", graph=False, final_ll=True, input_bf16=False, single_pass=False,
-            eig_polar=False):
+            eig_polar=False, plan=None):
     import torch
 
     import paper_1608_04647_gb300 as srm
@@ -47,6 +47,8 @@ def run_gpu(d, k, n_iter, store="f32", graph=False, final_ll=True, input_bf16=Fa
     m = srm.SRM(X, W0, k, store=store, graph=graph, final_ll=final_ll, single_pass=single_pass)
     if eig_polar:  # every polar factor through the eigen-decomposition path
         srm.srm_debug_force_eig_polar(m.ctx, True)
+    if plan:  # launch-plan fields set before the fit
+        m.set_plan(**plan)
     ll = m.fit(n_iter)
     out = {"ll": ll, "W": [m.get_w(i).cpu().numpy().astype(np.float64) for i in range(len(X))],
            "ES": m.get_s().cpu().numpy().astype(np.float64)}

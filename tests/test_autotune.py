@@ -101,10 +101,15 @@ def test_every_plan_matches_oracle():
     m = _model(d, CASE.k)
     for bad in (dict(m_stages=9), dict(m_gram_bufs=3), dict(e_reserve=-1), dict(f_prefetch=99),
                 dict(f_l2_hints=8), dict(f_first_stages=0), dict(f_first_stages=5), dict(m_boxes=3),
-                dict(single_pass=1, f_reserve=-1), dict(f_lead=5)):
+                dict(single_pass=1, f_reserve=-1), dict(f_lead=5), dict(f_slots=7),
+                dict(f_slots=8, f_first_stages=7), dict(f_slots=9, f_first_stages=1)):
         with pytest.raises(srm.SrmError) as ei:
             m.set_plan(**bad)
         assert ei.value.status == srm.SRM_ERR_ARG, bad
+    # the 16 KB-slot forms need one CTA per tile (T <= 512); this case has T = 1000
+    with pytest.raises(srm.SrmError) as ei:
+        m.set_plan(single_pass=1, f_slots=9, f_first_stages=6)
+    assert ei.value.status == srm.SRM_ERR_UNSUPPORTED
 
 
 def test_pipelining_plans_are_bitwise_identical():
@@ -126,7 +131,9 @@ def test_pipelining_plans_are_bitwise_identical():
                    dict(f_prefetch=2, f_l2_hints=7, f_first_stages=1),
                    dict(f_prefetch=1, f_l2_hints=2, f_first_stages=3),
                    dict(f_prefetch=0, f_l2_hints=7, f_first_stages=4),
-                   dict(f_prefetch=0, f_l2_hints=7, f_first_stages=2, f_lead=2)):
+                   dict(f_prefetch=0, f_l2_hints=7, f_first_stages=2, f_lead=2),
+                   dict(f_prefetch=0, f_l2_hints=7, f_first_stages=5, f_slots=8),
+                   dict(f_prefetch=1, f_l2_hints=7, f_first_stages=6, f_slots=9, f_lead=3)):
         m = _model(d, CASE_T500.k)
         m.set_plan(single_pass=1, **fields)
         fused.append(_results(m, CASE_T500.n_iter))

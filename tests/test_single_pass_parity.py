@@ -52,6 +52,34 @@ def test_single_pass_matches_oracle(case):
     check_ll_trace(g["ll"], o["ll"], "bf16")
 
 
+# 16 KB-slot forms of the one-CTA single pass (f_slots 8: two A_tile
+# buffers; 9: one), with different splits between the two rings
+FINE_PLANS = [dict(f_slots=8, f_first_stages=5), dict(f_slots=9, f_first_stages=7),
+              dict(f_slots=9, f_first_stages=2, f_lead=3), dict(f_slots=8, f_first_stages=4, f_l2_hints=0)]
+
+
+@pytest.mark.parametrize("case", [c for c in SP_CASES if c.T <= 512], ids=lambda c: c.name)
+def test_fine_slot_plans_equal_stage_plan(case):
+    """The 16 KB-slot forms cut the same tile loads finer: phase 1 takes the
+    64-t boxes in the same order and phase 2 the 16-voxel K steps of each P
+    block in the same order, so every accumulator sees the same MMAs in the
+    same order as under 32 KB stages.  Results must be bitwise equal (and so
+    within the oracle bar that the stage plan meets above)."""
+    d = make_inputs(case)
+    ref = run_gpu(d, case.k, case.n_iter, store="bf16", single_pass=True, plan=dict(f_slots=0, f_first_stages=2))
+    ref["model"].close()
+    for plan in FINE_PLANS:
+        g = run_gpu(d, case.k, case.n_iter, store="bf16", single_pass=True, plan=plan)
+        got = g["model"].plan()
+        assert got["single_pass"] == 1 and all(got[key] == v for key, v in plan.items()), got
+        np.testing.assert_array_equal(g["ll"], ref["ll"], err_msg=str(plan))
+        np.testing.assert_array_equal(g["ES"], ref["ES"], err_msg=str(plan))
+        np.testing.assert_array_equal(g["rho2"], ref["rho2"], err_msg=str(plan))
+        for a, b in zip(g["W"], ref["W"]):
+            np.testing.assert_array_equal(a, b, err_msg=str(plan))
+        g["model"].close()
+
+
 def test_single_pass_ignored_where_unsupported():
     # T > 1024 and k > 64: the two-pass form runs and still matches the oracle
     for case in (Case("t1100", [3000, 2500], 1100, 20, 4, seed=4),
