@@ -520,7 +520,7 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
   c->ldT = ((c->T + 7) / 8) * 8;
   c->nchunk = (c->T + TCH - 1) / TCH;
   c->nes_blk = es_blocks(c->T);  // E[S] partials: one per es block
-  c->zgroups = zsum_groups(c->N, c->nchunk, c->num_sms);
+  c->zgroups = zsum_groups(c->N, c->nchunk, c->num_sms, c->kld);
   c->v.resize(c->N);
   c->vpad.resize(c->N);
   c->off.resize(c->N + 1);

@@ -76,19 +76,23 @@ __global__ void __launch_bounds__(256) p_reduce_kernel(EReduceArgs ar) {
   const double* __restrict__ rho2 = ar.rho2;
   float2* __restrict__ ypart = ar.ypart;
   constexpr int KLD = 16 * FW;
-  extern __shared__ float pr_smem[];
+  constexpr int SPT = TCH + 4;  // row stride of Ps (16-byte rows, conflict-free float4 stores)
+  extern __shared__ __align__(16) float pr_smem[];
   float* Ms = pr_smem;               // [KLD][KLD]: Ms[m * KLD + f] = M_i[m][f] = M_i[f][m]
-  float* Ps = pr_smem + KLD * KLD;   // [TCH][KLD + 1]
+  float* Ps = pr_smem + KLD * KLD;   // [KLD][SPT]: Ps[m * SPT + t] = P[t][m]
   const int c = blockIdx.x, g = blockIdx.y;
   const int t0 = c * TCH;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int i0 = (int)(((int64_t)N * g) / G), i1 = (int)(((int64_t)N * (g + 1)) / G);
+  // thread (tx, ty) owns t = 4 tx + u (u < 4) and f = FW ty + w (w < FW):
+  // per m one float4 of P (t) and FW consecutive floats of M (f)
   float acc[4][FW], accl[4][FW];  // hi + lo (error-free FP32 accumulation)
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int w = 0; w < FW; ++w) acc[u][w] = accl[u][w] = 0.f;
-  static_assert(TCH * KLD / 4 == 256 * FW, "a thread owns FW float4 positions of a slot block");
+  static_assert(TCH * KLD % (4 * 256) == 0, "a thread owns whole 4-t columns of a slot block");
+  constexpr int NQ = TCH * KLD / (4 * 256);  // (m, 4-t) columns per thread
   for (int i = i0; i < i1; ++i) {
     __syncthreads();  // the previous subject's tiles have been read
     // M_i (symmetric: row m read as column m): KLD^2 / 4 float4, all of a thread's loads in flight
@@ -119,42 +123,32 @@ __global__ void __launch_bounds__(256) p_reduce_kernel(EReduceArgs ar) {
     const int ns = en - b;
     for (int q = tid; q < ns && q < PR_MAX_SLOTS; q += 256) s_off[q] = src[b + q].off;
     __syncthreads();
-    // a thread's FW float4 positions, two slots at a time: 2 FW loads in flight, summed in slot order
-    float4 a4[FW];
+    // a thread's NQ columns (feature m, 4 consecutive t), summed over the
+    // slots in slot order; lanes take consecutive m (coalesced loads)
+    float4 a4[NQ];
 #pragma unroll
-    for (int j = 0; j < FW; ++j) a4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int q = 0; q < ns; q += 2) {
-      const int64_t o0 = q < PR_MAX_SLOTS ? s_off[q] : src[b + q].off;
-      const bool two = q + 1 < ns;
-      const int64_t o1 = two ? (q + 1 < PR_MAX_SLOTS ? s_off[q + 1] : src[b + q + 1].off) : o0;
-      float4 v0[FW], v1[FW];
+    for (int j = 0; j < NQ; ++j) a4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < ns; ++q) {
+      const float* sl = part + (q < PR_MAX_SLOTS ? s_off[q] : src[b + q].off);
+      float v[NQ][4];
 #pragma unroll
-      for (int j = 0; j < FW; ++j) {
-        v0[j] = __ldg(reinterpret_cast<const float4*>(part + o0) + tid + 256 * j);
-        v1[j] = two ? __ldg(reinterpret_cast<const float4*>(part + o1) + tid + 256 * j) : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int j = 0; j < NQ; ++j) {
+        const int e = tid + 256 * j, m = e % KLD, tq = e / KLD;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v[j][r] = __ldg(sl + (4 * tq + r) * KLD + m);
       }
 #pragma unroll
-      for (int j = 0; j < FW; ++j) {
-        a4[j].x += v0[j].x;
-        a4[j].y += v0[j].y;
-        a4[j].z += v0[j].z;
-        a4[j].w += v0[j].w;
-        if (two) {
-          a4[j].x += v1[j].x;
-          a4[j].y += v1[j].y;
-          a4[j].z += v1[j].z;
-          a4[j].w += v1[j].w;
-        }
+      for (int j = 0; j < NQ; ++j) {
+        a4[j].x += v[j][0];
+        a4[j].y += v[j][1];
+        a4[j].z += v[j][2];
+        a4[j].w += v[j][3];
       }
     }
 #pragma unroll
-    for (int j = 0; j < FW; ++j) {
-      const int e = 4 * (tid + 256 * j), t = e / KLD, f = e - t * KLD;
-      float* d = Ps + t * (KLD + 1) + f;
-      d[0] = a4[j].x;
-      d[1] = a4[j].y;
-      d[2] = a4[j].z;
-      d[3] = a4[j].w;
+    for (int j = 0; j < NQ; ++j) {
+      const int e = tid + 256 * j, m = e % KLD, tq = e / KLD;
+      *reinterpret_cast<float4*>(Ps + m * SPT + 4 * tq) = a4[j];
     }
     __syncthreads();
     float z[4][FW];
@@ -163,11 +157,30 @@ __global__ void __launch_bounds__(256) p_reduce_kernel(EReduceArgs ar) {
 #pragma unroll
       for (int w = 0; w < FW; ++w) z[u][w] = 0.f;
     for (int m = 0; m < k; ++m) {
-      float pv[4], mv[FW];
+      const float4 p4 = *reinterpret_cast<const float4*>(Ps + m * SPT + 4 * tx);
+      const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
+      float mv[FW];
+      const float* mrow = Ms + m * KLD + FW * ty;
+      if constexpr (FW % 4 == 0) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) pv[u] = Ps[(tx + 16 * u) * (KLD + 1) + m];
+        for (int w = 0; w < FW; w += 4) {
+          const float4 q4 = *reinterpret_cast<const float4*>(mrow + w);
+          mv[w] = q4.x;
+          mv[w + 1] = q4.y;
+          mv[w + 2] = q4.z;
+          mv[w + 3] = q4.w;
+        }
+      } else if constexpr (FW % 2 == 0) {
 #pragma unroll
-      for (int w = 0; w < FW; ++w) mv[w] = Ms[m * KLD + ty + 16 * w];
+        for (int w = 0; w < FW; w += 2) {
+          const float2 q2 = *reinterpret_cast<const float2*>(mrow + w);
+          mv[w] = q2.x;
+          mv[w + 1] = q2.y;
+        }
+      } else {
+#pragma unroll
+        for (int w = 0; w < FW; ++w) mv[w] = mrow[w];
+      }
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -188,11 +201,11 @@ __global__ void __launch_bounds__(256) p_reduce_kernel(EReduceArgs ar) {
   float2* out = ypart + (int64_t)g * kT;
 #pragma unroll
   for (int w = 0; w < FW; ++w) {
-    const int f = ty + 16 * w;
+    const int f = FW * ty + w;
     if (f >= k) continue;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int t = t0 + tx + 16 * u;
+      const int t = t0 + 4 * tx + u;
       if (t < T) out[(int64_t)f * T + t] = make_float2(acc[u][w], accl[u][w]);
     }
   }
@@ -1598,8 +1611,29 @@ void prepare_small_kernels(int max_smem) {
   cudaFuncSetAttribute(phi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
 }
 
-int zsum_groups(int N, int nchunk, int num_sms) {
-  const int want = (4 * num_sms + nchunk - 1) / nchunk;
+// Subject groups of the E-step reduction: one wave of its (chunk, group)
+// blocks at the kernel's occupancy (each group's subjects run in series in
+// one block, so a partial second wave would double the time).
+int zsum_groups(int N, int nchunk, int num_sms, int kld) {
+  const size_t sm = sizeof(float) * ((size_t)kld * kld + (size_t)kld * (TCH + 4));
+  int bps = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (kld) {
+#define ZG_CASE(FW)                                                                                   \
+  case 16 * FW:                                                                                       \
+    if (sm > 48 * 1024)                                                                               \
+      cudaFuncSetAttribute(p_reduce_kernel<FW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, p_reduce_kernel<FW>, 256, sm);            \
+    break;
+    ZG_CASE(1) ZG_CASE(2) ZG_CASE(3) ZG_CASE(4) ZG_CASE(5) ZG_CASE(6) ZG_CASE(7) ZG_CASE(8)
+#undef ZG_CASE
+    default: break;
+  }
+  if (e != cudaSuccess || bps < 1) {
+    cudaGetLastError();
+    bps = 2;
+  }
+  const int want = (bps * num_sms + nchunk - 1) / nchunk;
   return std::max(1, std::min(N, std::min(128, want)));
 }
 
@@ -1618,7 +1652,7 @@ cudaError_t launch_p_sum(Ctx* c) {
 cudaError_t launch_p_reduce(Ctx* c) { return launch_p_reduce_from(c, false); }
 
 cudaError_t launch_p_reduce_from(Ctx* c, bool from_sums) {
-  const size_t sm = sizeof(float) * ((size_t)c->kld * c->kld + TCH * (c->kld + 1));
+  const size_t sm = sizeof(float) * ((size_t)c->kld * c->kld + (size_t)c->kld * (TCH + 4));
   const dim3 grid(c->nchunk, c->zgroups);
   EReduceArgs ar;
   ar.N = c->N;

@@ -239,7 +239,7 @@ cudaError_t launch_p_simt_generic(const void* A, bool a_bf16, int kld, int kq, c
 cudaError_t launch_a_simt(Ctx* c, int subject);
 
 // k_small.cu
-int zsum_groups(int N, int nchunk, int num_sms);
+int zsum_groups(int N, int nchunk, int num_sms, int kld);
 int es_blocks(int T);
 cudaError_t launch_p_reduce(Ctx* c);
 // the single pass's slot sums (beside the polar factors), then the reduction from them
