@@ -67,7 +67,7 @@ struct EReduceArgs {
 };
 
 template <int FW>  // kld = 16 FW
-__global__ void __launch_bounds__(256) p_reduce_kernel(EReduceArgs ar) {
+__global__ void __launch_bounds__(256, FW <= 4 ? 3 : 2) p_reduce_kernel(EReduceArgs ar) {
   const int N = ar.N, G = ar.G, T = ar.T, k = ar.k, nchunk = ar.nchunk;
   const float* __restrict__ part = ar.part;
   const ChunkSrc* __restrict__ src = ar.src;
@@ -78,8 +78,13 @@ __global__ void __launch_bounds__(256) p_reduce_kernel(EReduceArgs ar) {
   constexpr int KLD = 16 * FW;
   constexpr int SPT = TCH + 4;  // row stride of Ps (16-byte rows, conflict-free float4 stores)
   extern __shared__ __align__(16) float pr_smem[];
-  float* Ms = pr_smem;               // [KLD][KLD]: Ms[m * KLD + f] = M_i[m][f] = M_i[f][m]
-  float* Ps = pr_smem + KLD * KLD;   // [KLD][SPT]: Ps[m * SPT + t] = P[t][m]
+  float* Ms = pr_smem;                 // [KLD][KLD]: Ms[m * KLD + f] = M_i[m][f] = M_i[f][m]
+  float* Ps = pr_smem + KLD * KLD;     // [KLD][SPT]: Ps[m * SPT + t] = P[t][m]
+  // the slot sum as loaded, P0[t * (KLD + 1) + m] ([TCH][KLD + 1]); for
+  // kld = 128 it shares M_i's space (M_i is then loaded after the transpose)
+  constexpr bool P0_IN_MS = FW > 4;
+  float* P0 = P0_IN_MS ? Ms : Ps + KLD * SPT;
+  static_assert(!P0_IN_MS || TCH * (KLD + 1) <= KLD * KLD, "P0 fits in M_i's space");
   const int c = blockIdx.x, g = blockIdx.y;
   const int t0 = c * TCH;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -91,11 +96,9 @@ __global__ void __launch_bounds__(256) p_reduce_kernel(EReduceArgs ar) {
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int w = 0; w < FW; ++w) acc[u][w] = accl[u][w] = 0.f;
-  static_assert(TCH * KLD % (4 * 256) == 0, "a thread owns whole 4-t columns of a slot block");
-  constexpr int NQ = TCH * KLD / (4 * 256);  // (m, 4-t) columns per thread
-  for (int i = i0; i < i1; ++i) {
-    __syncthreads();  // the previous subject's tiles have been read
-    // M_i (symmetric: row m read as column m): KLD^2 / 4 float4, all of a thread's loads in flight
+  static_assert(TCH * KLD / 4 == 256 * FW, "a thread owns FW float4 positions of a slot block");
+  // M_i (symmetric: row m read as column m): KLD^2 / 4 float4, all of a thread's loads in flight
+  auto load_m = [&](int i) {
     {
       constexpr int NM4 = KLD * KLD / 4;          // 64 FW^2
       constexpr int MJ = (NM4 + 255) / 256;
@@ -117,38 +120,69 @@ __global__ void __launch_bounds__(256) p_reduce_kernel(EReduceArgs ar) {
         *reinterpret_cast<float4*>(Ms + e) = v;
       }
     }
+  };
+  for (int i = i0; i < i1; ++i) {
+    __syncthreads();  // the previous subject's tiles have been read
+    if (!P0_IN_MS) load_m(i);
     const int b = src_off[i * nchunk + c], en = src_off[i * nchunk + c + 1];
     // slot offsets of this (subject, chunk) staged in shared memory
     __shared__ int64_t s_off[PR_MAX_SLOTS];
     const int ns = en - b;
     for (int q = tid; q < ns && q < PR_MAX_SLOTS; q += 256) s_off[q] = src[b + q].off;
     __syncthreads();
-    // a thread's NQ columns (feature m, 4 consecutive t), summed over the
-    // slots in slot order; lanes take consecutive m (coalesced loads)
-    float4 a4[NQ];
+    // a thread's FW float4 positions (4 consecutive m of one t; lanes take
+    // consecutive positions, so the loads are coalesced), two slots at a
+    // time: 2 FW loads in flight, summed in slot order
+    float4 a4[FW];
 #pragma unroll
-    for (int j = 0; j < NQ; ++j) a4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int q = 0; q < ns; ++q) {
-      const float* sl = part + (q < PR_MAX_SLOTS ? s_off[q] : src[b + q].off);
-      float v[NQ][4];
+    for (int j = 0; j < FW; ++j) a4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int q = 0; q < ns; q += 2) {
+      const int64_t o0 = q < PR_MAX_SLOTS ? s_off[q] : src[b + q].off;
+      const bool two = q + 1 < ns;
+      const int64_t o1 = two ? (q + 1 < PR_MAX_SLOTS ? s_off[q + 1] : src[b + q + 1].off) : o0;
+      float4 v0[FW], v1[FW];
 #pragma unroll
-      for (int j = 0; j < NQ; ++j) {
-        const int e = tid + 256 * j, m = e % KLD, tq = e / KLD;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) v[j][r] = __ldg(sl + (4 * tq + r) * KLD + m);
+      for (int j = 0; j < FW; ++j) {
+        v0[j] = __ldg(reinterpret_cast<const float4*>(part + o0) + tid + 256 * j);
+        v1[j] = two ? __ldg(reinterpret_cast<const float4*>(part + o1) + tid + 256 * j) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
 #pragma unroll
-      for (int j = 0; j < NQ; ++j) {
-        a4[j].x += v[j][0];
-        a4[j].y += v[j][1];
-        a4[j].z += v[j][2];
-        a4[j].w += v[j][3];
+      for (int j = 0; j < FW; ++j) {
+        a4[j].x += v0[j].x;
+        a4[j].y += v0[j].y;
+        a4[j].z += v0[j].z;
+        a4[j].w += v0[j].w;
+        if (two) {
+          a4[j].x += v1[j].x;
+          a4[j].y += v1[j].y;
+          a4[j].z += v1[j].z;
+          a4[j].w += v1[j].w;
+        }
       }
     }
+    // as loaded (t-major, odd row stride: conflict-free scalar stores) ...
 #pragma unroll
-    for (int j = 0; j < NQ; ++j) {
+    for (int j = 0; j < FW; ++j) {
+      const int e = 4 * (tid + 256 * j), t = e / KLD, m = e - t * KLD;
+      float* d = P0 + t * (KLD + 1) + m;
+      d[0] = a4[j].x;
+      d[1] = a4[j].y;
+      d[2] = a4[j].z;
+      d[3] = a4[j].w;
+    }
+    __syncthreads();
+    // ... then feature-major: thread (m, 4-t group) reads down a column of P0
+    // (lanes take consecutive m: distinct banks) and stores one float4
+#pragma unroll
+    for (int j = 0; j < FW; ++j) {
       const int e = tid + 256 * j, m = e % KLD, tq = e / KLD;
-      *reinterpret_cast<float4*>(Ps + m * SPT + 4 * tq) = a4[j];
+      const float* sp = P0 + 4 * tq * (KLD + 1) + m;
+      *reinterpret_cast<float4*>(Ps + m * SPT + 4 * tq) =
+          make_float4(sp[0], sp[KLD + 1], sp[2 * (KLD + 1)], sp[3 * (KLD + 1)]);
+    }
+    if (P0_IN_MS) {
+      __syncthreads();  // P0 has been read
+      load_m(i);
     }
     __syncthreads();
     float z[4][FW];
@@ -1587,6 +1621,7 @@ void prepare_small_kernels(int max_smem) {
   prepare_tail_kernels();
   cudaFuncSetAttribute(es_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float) * KMAX * KMAX));
   // (these kernels also hold a few KB of static shared memory)
+  cudaFuncSetAttribute(p_reduce_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
   cudaFuncSetAttribute(p_reduce_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
   cudaFuncSetAttribute(p_reduce_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
   cudaFuncSetAttribute(p_reduce_kernel<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
@@ -1611,11 +1646,17 @@ void prepare_small_kernels(int max_smem) {
   cudaFuncSetAttribute(phi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem - 8 * 1024);
 }
 
+// p_reduce's shared memory: M_i, the feature-major P and (kld <= 64) the
+// slot sum as loaded.
+size_t p_reduce_smem_bytes(int kld) {
+  return sizeof(float) * ((size_t)kld * kld + (size_t)kld * (TCH + 4) + (kld <= 64 ? (size_t)TCH * (kld + 1) : 0));
+}
+
 // Subject groups of the E-step reduction: one wave of its (chunk, group)
 // blocks at the kernel's occupancy (each group's subjects run in series in
 // one block, so a partial second wave would double the time).
 int zsum_groups(int N, int nchunk, int num_sms, int kld) {
-  const size_t sm = sizeof(float) * ((size_t)kld * kld + (size_t)kld * (TCH + 4));
+  const size_t sm = p_reduce_smem_bytes(kld);
   int bps = 0;
   cudaError_t e = cudaErrorInvalidValue;
   switch (kld) {
@@ -1652,7 +1693,7 @@ cudaError_t launch_p_sum(Ctx* c) {
 cudaError_t launch_p_reduce(Ctx* c) { return launch_p_reduce_from(c, false); }
 
 cudaError_t launch_p_reduce_from(Ctx* c, bool from_sums) {
-  const size_t sm = sizeof(float) * ((size_t)c->kld * c->kld + (size_t)c->kld * (TCH + 4));
+  const size_t sm = p_reduce_smem_bytes(c->kld);
   const dim3 grid(c->nchunk, c->zgroups);
   EReduceArgs ar;
   ar.N = c->N;
