@@ -56,6 +56,9 @@ def test_autotuned_fit_matches_oracle_and_cache_replays(case, tmp_path):
     assert plan == m.plan()
     if case.k > 64:
         assert plan["single_pass"] == 0
+    # the single pass's 16 KB-slot forms are candidates where one CTA takes a tile (T <= 512)
+    fine_tried = any(" fsl=9 " in ln or " fsl=8 " in ln for ln in rep.splitlines() if ln.startswith("fpass"))
+    assert fine_tried == (case.k <= 64 and case.T <= 512), rep
     g = _results(m, case.n_iter)
     err = rel_errors(g, o)
     print(case.name, plan, {k: f"{v:.2e}" for k, v in err.items()})
