@@ -113,6 +113,7 @@ void free_all(Ctx* c) {
   if (c->ev_sig) cudaEventDestroy(c->ev_sig);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_polar) cudaEventDestroy(c->ev_polar);
 }
 
 // Plain path: per-subject launch geometry and the partial-slot tables.
@@ -257,21 +258,25 @@ namespace {
 srm_status do_estep_fused(Ctx* c) {
   if (c->p_from_f && c->side_pending && c->sig_eig_done && !c->sigma_pending && c->psum) {
     // after a single pass: its slot sums (which need no M_i) on the context
-    // stream beside the polar factors and Phi on the second, then the
-    // reduction from the sums
+    // stream beside the polar factors and Phi on the second; the reduction
+    // from the sums once the polar factors are done (beside Phi), E[S] = Phi y
+    // once Phi is
     CK(cudaEventRecord(c->ev_fork, c->stream));
     CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     {
       OnStream on(c, c->side);
       TRY(do_polar(c));
+      CK(cudaEventRecord(c->ev_polar, c->side));
       LAUNCH(c, KK_PHI, launch_phi(c));
     }
     CK(cudaEventRecord(c->ev_join, c->side));
     LAUNCH(c, KK_P_SUM, launch_p_sum(c));
-    CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    CK(cudaStreamWaitEvent(c->stream, c->ev_polar, 0));
     c->side_pending = false;
     c->sig_eig_done = false;
-    LAUNCH(c, KK_P_REDUCE, launch_p_reduce_from(c, true));
+    LAUNCH(c, KK_P_REDUCE, launch_p_reduce_part(c, true));
+    CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    LAUNCH(c, KK_P_REDUCE, launch_p_reduce_finish(c));
     c->sigma_pending = true;
     return SRM_OK;
   }
@@ -515,6 +520,7 @@ srm_status srm_init(const srm_config* cfg, const void* const* X, const float* co
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&c->ev_sig, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&c->ev_polar, cudaEventDisableTiming);
   if (ce != cudaSuccess) return fail(cuda_fail(ce, "side stream / events"));
   c->kld = batched ? (c->k <= 64 ? 64 : 128) : ((c->k + 15) / 16) * 16;
   c->ldT = ((c->T + 7) / 8) * 8;

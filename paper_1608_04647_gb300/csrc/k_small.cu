@@ -1693,6 +1693,11 @@ cudaError_t launch_p_sum(Ctx* c) {
 cudaError_t launch_p_reduce(Ctx* c) { return launch_p_reduce_from(c, false); }
 
 cudaError_t launch_p_reduce_from(Ctx* c, bool from_sums) {
+  const cudaError_t e = launch_p_reduce_part(c, from_sums);
+  return e != cudaSuccess ? e : launch_p_reduce_finish(c);
+}
+
+cudaError_t launch_p_reduce_part(Ctx* c, bool from_sums) {
   const size_t sm = p_reduce_smem_bytes(c->kld);
   const dim3 grid(c->nchunk, c->zgroups);
   EReduceArgs ar;
@@ -1715,7 +1720,11 @@ cudaError_t launch_p_reduce_from(Ctx* c, bool from_sums) {
 #undef PR_CASE
     default: return cudaErrorInvalidValue;
   }
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_p_reduce_finish(Ctx* c) {
+  cudaError_t e;
   if (c->shard_y) {
     // a sharded E-step stops at this context's share of y and of the sums
     ysum_kernel<<<nblocks((int64_t)c->k * c->T, 256), 256, 0, c->stream>>>(c->zgroups, c->k, c->T, c->Ypart,

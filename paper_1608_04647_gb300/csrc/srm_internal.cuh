@@ -89,6 +89,7 @@ struct Ctx {
   cudaStream_t side2 = nullptr;         // third stream (Sigma_s eigen-decomposition)
   cudaEvent_t ev_join2 = nullptr, ev_sig = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_polar = nullptr;  // the polar factors are done (M_i, rho_i^2), Phi may still run
   bool side_pending = false;            // an M-step's tail has not run yet
   bool sigma_pending = false;           // an E-step's Sigma_s^new / log-likelihood have not been formed yet
 
@@ -245,6 +246,10 @@ cudaError_t launch_p_reduce(Ctx* c);
 // the single pass's slot sums (beside the polar factors), then the reduction from them
 cudaError_t launch_p_sum(Ctx* c);
 cudaError_t launch_p_reduce_from(Ctx* c, bool from_sums);
+// its two halves: the subject-group reduction (needs M_i and rho_i^2), then
+// E[S] = Phi y (needs Phi) or, for a sharded E-step, this context's share
+cudaError_t launch_p_reduce_part(Ctx* c, bool from_sums);
+cudaError_t launch_p_reduce_finish(Ctx* c);
 cudaError_t launch_sigma(Ctx* c);
 cudaError_t launch_phi(Ctx* c);
 // Phi and the likelihood's scalars from sums over all shards (sums != nullptr)
